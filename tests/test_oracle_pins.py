@@ -1,0 +1,363 @@
+"""Pins of the FP64 oracle against facts fixed by the paper or by mathematics.
+
+Each test checks the oracle through a route other than its own code: a closed
+form, a library routine applied differently, a textbook identity, a value the
+paper prints, or brute force on tiny inputs. They are chosen so that a dropped
+term, a transposed operand, a wrong index order or a wrong sign in the oracle
+fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special
+
+import oracle.pttk_oracle as o
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --- Section 2.4: nodes, transform, basis -----------------------------------
+
+@pytest.mark.parametrize("n", [2, 5, 12, 16, 20])
+def test_nodes_are_roots_of_T_n(n):
+    e = np.zeros(n + 1)
+    e[n] = 1.0
+    roots = np.sort(np.polynomial.chebyshev.chebroots(e).real)
+    assert np.allclose(np.sort(o.cheb_nodes(n)), roots, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [3, 12, 16, 20])
+def test_transform_inverts_node_values(n):
+    # discrete orthogonality of T_k at the roots of T_n: T A = A T = I, T[i, k] = T_k(zeta_i)
+    zeta = o.cheb_nodes(n)
+    T = np.stack([np.polynomial.chebyshev.chebval(zeta, np.eye(n)[k]) for k in range(n)], axis=1)
+    A = o.cheb_transform_matrix(n)
+    assert np.allclose(T @ A, np.eye(n), atol=1e-13)
+    assert np.allclose(A @ T, np.eye(n), atol=1e-13)
+
+
+@pytest.mark.parametrize("a,b", [(0.0, 1.0), (2.0, 3.0), (0.2, 2.0), (-1.0, 1.0)])
+def test_basis_is_nodal_and_matches_coefficient_form(a, b):
+    n = 9
+    eta = o.interval_map(o.cheb_nodes(n), a, b)
+    # phi(eta_i, eta_j) = delta_ij (Section 2.4, proof of Lemma cheb_bound)
+    assert np.allclose(o.basis_q(eta, a, b, n), np.eye(n), atol=1e-13)
+    x = np.linspace(a, b, 37)
+    q = o.basis_q(x, a, b, n)
+    # q(x) = T(xhat)^T A with T evaluated by numpy's Chebyshev series (reading R3)
+    xh = o.interval_map_inv(x, a, b)
+    T = np.stack([np.polynomial.chebyshev.chebval(xh, np.eye(n)[k]) for k in range(n)], axis=1)
+    assert np.allclose(q, T @ o.cheb_transform_matrix(n), atol=1e-13)
+    assert np.allclose(q.sum(axis=1), 1.0, atol=1e-13)       # constants are reproduced
+
+
+@pytest.mark.parametrize("n", [4, 12, 16, 20, 32])
+def test_lebesgue_bound(n):
+    # Lemma cheb_bound: max_x sum_k |phi(zeta_k, x)| <= (2/pi) log n + 1
+    x = np.linspace(-1.0, 1.0, 4001)
+    lam = np.abs(o.basis_q(x, -1.0, 1.0, n)).sum(axis=1).max()
+    assert lam <= 2.0 / math.pi * math.log(n) + 1.0
+
+
+def test_interval_map_is_the_printed_one():
+    # Section 2.4 prints phi_[a,b](x) = ((a-b)/2) x + (a+b)/2: +1 -> a, -1 -> b
+    assert o.interval_map(1.0, 2.0, 3.0) == 2.0
+    assert o.interval_map(-1.0, 2.0, 3.0) == 3.0
+    assert o.interval_map_inv(o.interval_map(0.3, 2.0, 5.0), 2.0, 5.0) == pytest.approx(0.3)
+
+
+@pytest.mark.parametrize("n", [12, 16])
+def test_coefficients_of_separable_exponential(n):
+    # exp(s t) = I_0(s) + 2 sum_k I_k(s) T_k(t) (textbook Chebyshev expansion; modified Bessel I).
+    # A product over modes with a different s per mode pins the mode order of C = M x_k A.
+    s = [0.7, -1.3, 0.4]
+    boxes = [(0.0, 1.0), (0.5, 2.0), (2.0, 3.0)]
+    eta = o.node_vectors(boxes, n)
+    grids = np.meshgrid(*[o.interval_map_inv(e, a, b) for e, (a, b) in zip(eta, boxes)], indexing="ij")
+    M = np.exp(sum(sj * g for sj, g in zip(s, grids)))
+    C = o.coefficient_tensor(M, n)
+    # interpolation at the n roots of T_n aliases T_{2n-k} onto -T_k and T_{2n+k} onto -T_k
+    # (T_{2n +- k}(zeta_i) = -T_k(zeta_i)), so the discrete coefficient is
+    # a_k - a_{2n-k} - a_{2n+k} + ...; two alias terms suffice at these s and n.
+    def discrete(sj):
+        a = lambda k: (1.0 if k == 0 else 2.0) * special.iv(k, sj)
+        return np.array([a(k) - a(2 * n - k) - a(2 * n + k) for k in range(n)])
+    expected = np.einsum("i,j,k->ijk", *[discrete(sj) for sj in s])
+    assert np.allclose(C, expected, atol=2e-16 * n ** 3)
+
+
+# --- Table kern-table: kernels -----------------------------------------------
+
+@pytest.mark.parametrize("l", [0.5, 1.0, 2.0])
+def test_matern_general_nu_reduces_to_closed_forms(l):
+    r = np.linspace(0.05, 6.0, 200)
+    a = r / l
+    exp_ = np.exp(-a)                                                     # nu = 1/2
+    m32 = (1 + math.sqrt(3) * a) * np.exp(-math.sqrt(3) * a)              # nu = 3/2
+    m52 = (1 + math.sqrt(5) * a + 5 * a ** 2 / 3) * np.exp(-math.sqrt(5) * a)  # nu = 5/2
+    assert np.allclose(o.kernel_of_r(o.MATERN_NU, r, (l, 0.5)), exp_, rtol=1e-13, atol=0)
+    assert np.allclose(o.kernel_of_r(o.MATERN_NU, r, (l, 1.5)), m32, rtol=1e-13, atol=0)
+    assert np.allclose(o.kernel_of_r(o.MATERN_NU, r, (l, 2.5)), m52, rtol=1e-13, atol=0)
+    assert np.allclose(o.kernel_of_r(o.MATERN32, r, (l,)), m32, rtol=1e-14, atol=0)
+    # normalisation 2^(1-nu)/Gamma(nu): kappa -> 1 as r -> 0 for every nu
+    for nu in (0.7, 1.9, 2.5):
+        assert o.kernel_of_r(o.MATERN_NU, np.array([1e-9]), (l, nu))[0] == pytest.approx(1.0, abs=1e-6)
+
+
+def test_gaussian_has_no_half():
+    # Table kern-table: exp(-(r/l)^2); at r = l the value is exp(-1)
+    assert o.kernel_of_r(o.GAUSS, np.array([1.3]), (1.3,))[0] == pytest.approx(math.exp(-1.0), rel=1e-15)
+
+
+def test_grid_entries_are_kernel_values_at_nodes():
+    # Eq. mdc: m_{i} = f_kappa(eta) with xi = (x, theta, y); checked against the dense kernel
+    d, dth, n = 2, 2, 4
+    boxes = [(0, 1), (0, 1), (0.5, 2.0), (0.5, 2.5), (3, 4), (0, 1)]
+    M = o.grid_tensor(o.kernel_f(o.MATERN_NU), d, dth, boxes, n)
+    eta = o.node_vectors(boxes, n)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        i = rng.integers(0, n, size=6)
+        x = np.array([eta[0][i[0]], eta[1][i[1]]])
+        th = (eta[2][i[2]], eta[3][i[3]])
+        y = np.array([eta[4][i[4]], eta[5][i[5]]])
+        assert M[tuple(i)] == pytest.approx(o.kernel_matrix(o.MATERN_NU, x, y, th)[0, 0], rel=1e-14)
+
+
+def test_grid_sizes_printed_in_appendix_c():
+    rows = [l.split("#")[0].split() for l in open(os.path.join(GOLDEN, "appendix_c_grid_sizes.txt"))]
+    rows = [list(map(int, r)) for r in rows if r]
+    assert len(rows) == 4
+    for d, dth, n, count in rows:
+        boxes = [(0.0, 1.0)] * (2 * d + dth)
+        M = o.grid_tensor(lambda x, th, y: 0.0 * sum(x) + 1.0, d, dth, boxes, 2) if d + dth < 0 else None
+        assert n ** (2 * d + dth) == count
+
+
+# --- Section 2.3: TT-SVD -----------------------------------------------------
+
+def _random_tt(dims, ranks, rng):
+    return [rng.standard_normal((ranks[k], dims[k], ranks[k + 1])) for k in range(len(dims))]
+
+
+def test_tt_svd_recovers_known_ranks():
+    rng = np.random.default_rng(1)
+    dims, ranks = (5, 6, 4, 5, 3), [1, 3, 4, 5, 2, 1]
+    X = o.tt_full(_random_tt(dims, ranks, rng))
+    cores, r = o.tt_svd(X, 1e-12)
+    assert r == ranks
+    assert o.rel_fro(X, o.tt_full(cores)) < 1e-13
+    for G in cores[:-1]:                                  # left-orthonormal cores
+        G2 = o.unfold2(G)
+        assert np.allclose(G2.T @ G2, np.eye(G2.shape[1]), atol=1e-12)
+
+
+def _odeco(dims, sigma, rng):
+    """sum_i sigma_i u_i (x) v_i (x) ... with orthonormal factor columns: every
+    unfolding has singular values exactly sigma."""
+    Qs = [np.linalg.qr(rng.standard_normal((n, len(sigma))))[0] for n in dims]
+    X = 0
+    for i, s in enumerate(sigma):
+        t = np.array(s)
+        for Q in Qs:
+            t = np.multiply.outer(t, Q[:, i])
+        X = X + t
+    return X
+
+
+def test_tt_svd_threshold_uses_sqrt_D_minus_1():
+    # delta = eps / sqrt(D-1) ||X||_F (Algorithm 1). Put delta at 0.8 x the tail after rank 3:
+    # the correct rule keeps rank 4 at every bond; dropping sqrt(D-1) (= sqrt 3) would keep 3.
+    rng = np.random.default_rng(2)
+    sigma = np.array([1.0, 1e-2, 1e-4, 1e-6, 1e-8])
+    X = _odeco((6, 6, 6, 6), sigma, rng)
+    tail3 = math.sqrt(float(np.sum(sigma[3:] ** 2)))
+    eps = 0.8 * tail3 * math.sqrt(3) / np.linalg.norm(X)
+    cores, r = o.tt_svd(X, eps)
+    assert r == [1, 4, 4, 4, 1]
+    assert o.rel_fro(X, o.tt_full(cores)) <= eps
+    eps_loose = 1.2 * tail3 * math.sqrt(3) / np.linalg.norm(X)
+    assert o.tt_svd(X, eps_loose)[1] == [1, 3, 3, 3, 1]
+
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-2, 1e-4])
+def test_tt_svd_error_bound_and_rank_caps(eps):
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((4, 5, 3, 4, 5))
+    cores, r = o.tt_svd(X, eps)
+    assert o.rel_fro(X, o.tt_full(cores)) <= eps * (1 + 1e-12)
+    dims = X.shape
+    for k in range(1, len(dims)):
+        assert r[k] <= min(np.prod(dims[:k]), np.prod(dims[k:]))
+
+
+def test_tt_svd_order_two_is_eckart_young():
+    # for D = 2 the TT-SVD is a truncated SVD; its error must equal the optimal tail
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((30, 20)) @ np.diag(0.5 ** np.arange(20)) @ rng.standard_normal((20, 20))
+    cores, r = o.tt_svd(X, 1e-3)
+    s = __import__("scipy").linalg.svdvals(X, lapack_driver="gesvd") if False else np.linalg.svd(X, compute_uv=False)
+    tail = math.sqrt(float(np.sum(s[r[1]:] ** 2)))
+    assert np.linalg.norm(X - o.tt_full(cores)) == pytest.approx(tail, rel=1e-8)
+    assert math.sqrt(float(np.sum(s[r[1] - 1:] ** 2))) > 1e-3 * np.linalg.norm(X)
+
+
+def test_separable_function_has_unit_ranks():
+    f = lambda x, th, y: np.exp(x[0]) * np.cos(th[0]) * (1 + y[0] ** 2)
+    boxes = [(0, 1), (0.5, 2), (2, 3)]
+    cores, r, C = o.build_offline(o.GAUSS, 1, 1, boxes, 10, 1e-12, f=f)
+    assert r == [1, 1, 1, 1]
+
+
+# --- Algorithms 2-3: online stage and factor chain ---------------------------
+
+def test_polynomial_kernel_is_reproduced_exactly():
+    # Proposition compress (p = n): a kernel of degree < n in every variable is interpolated exactly
+    f = lambda x, th, y: (1.0 + x[0] * y[0] + x[1] * y[1] + th[0]) ** 3
+    d, dth = 2, 1
+    boxes = [(0, 1), (0, 1), (0.2, 2.0), (2, 3), (0, 1)]
+    rng = np.random.default_rng(5)
+    X = rng.random((40, 2))
+    Y = np.column_stack([2 + rng.random(40), rng.random(40)])
+    theta = (1.37,)
+    exact = (1.0 + X @ Y.T + theta[0]) ** 3
+    cores, r, C = o.build_offline(None, d, dth, boxes, 5, 1e-13, f=f)
+    assert max(r) <= 10
+    U, M, V = o.instantiate(cores, d, dth, boxes, theta, X, Y)
+    assert o.rel_fro(exact, U @ M @ V.T) < 1e-13
+    # with too few nodes (n = 3, degree 3 needs 4) the same pipeline is not exact
+    cores3, _, _ = o.build_offline(None, d, dth, boxes, 3, 1e-13, f=f)
+    U, M, V = o.instantiate(cores3, d, dth, boxes, theta, X, Y)
+    assert o.rel_fro(exact, U @ M @ V.T) > 1e-6
+
+
+def test_factor_chain_equals_full_interpolant():
+    # mixed-product identities (Eq. mixedprod) behind Phase 3: S H T^T = F_s C_F^{d}(theta) F_t^T
+    rng = np.random.default_rng(6)
+    d, dth, n = 2, 2, 5
+    ranks = [1, 3, 7, 4, 6, 5, 2, 1][: 2 * d + dth + 1]
+    ranks[-1] = 1
+    cores = _random_tt((n,) * (2 * d + dth), ranks, rng)
+    boxes = [(0, 1), (0, 1), (0.5, 2), (0.5, 2.5), (3, 4), (0, 1)]
+    X = rng.random((17, 2))
+    Y = np.column_stack([3 + rng.random(13), rng.random(13)])
+    theta = (1.1, 0.9)
+    U, M, V = o.instantiate(cores, d, dth, boxes, theta, X, Y)
+    full = o.full_interpolant(o.tt_full(cores), d, dth, boxes, theta, X, Y)
+    assert np.allclose(U @ M @ V.T, full, rtol=1e-12, atol=1e-12 * np.abs(full).max())
+    assert U.shape == (17, ranks[d]) and V.shape == (13, ranks[d + dth]) and M.shape == (ranks[d], ranks[d + dth])
+
+
+def test_dense_kernel_brute_force_c1():
+    # end to end on tiny inputs: K~ vs dense K; the error is the interpolation floor
+    # (Proposition error: E(n) plus an amplified TT term that is negligible at tol 1e-10)
+    from paper_2406_06344_gb300 import workloads as W
+    w = W.C1
+    cores, r, C = o.build_offline(w.kernel, w.d, w.dtheta, w.mode_boxes(), w.n, w.tol)
+    X, Y = W.sources(w, 300), W.targets(w, 300)
+    for th, bound in (((1.9,), 1e-6), ((1.2,), 1e-5), ((0.5,), 1e-3)):
+        K = o.kernel_matrix(w.kernel, X, Y, th)
+        U, M, V = o.instantiate(cores, w.d, w.dtheta, w.mode_boxes(), th, X, Y)
+        Kf = o.full_interpolant(C, w.d, w.dtheta, w.mode_boxes(), th, X, Y)
+        assert o.rel_fro(K, U @ M @ V.T) < bound
+        # the TT truncation error is absolute (delta ~ 1e-10 ||C||_F), far below the floor
+        assert np.abs(Kf - U @ M @ V.T).max() < 1e-9
+    # exponential convergence in n at fixed theta
+    errs = []
+    for n in (8, 12, 16, 24):
+        cores, _, _ = o.build_offline(w.kernel, w.d, w.dtheta, w.mode_boxes(), n, 1e-12)
+        U, M, V = o.instantiate(cores, w.d, w.dtheta, w.mode_boxes(), (1.2,), X, Y)
+        errs.append(o.rel_fro(o.kernel_matrix(w.kernel, X, Y, (1.2,)), U @ M @ V.T))
+    assert errs[0] > errs[1] > errs[2] > errs[3] and errs[3] < 1e-9
+
+
+def test_error_bound_of_proposition_error():
+    # ||K~_full - K~_TT||_C <= lambda^D ||M - M^||_C  (proof of Proposition error, Eq. inter2)
+    from paper_2406_06344_gb300 import workloads as W
+    w = W.C1
+    n = w.n
+    cores, r, C = o.build_offline(w.kernel, w.d, w.dtheta, w.mode_boxes(), n, 1e-4)
+    Ainv = np.linalg.inv(o.cheb_transform_matrix(n))
+    M = C
+    Mhat = o.tt_full(cores)
+    for k in range(3):
+        M = o.mode_product(M, Ainv, k)
+        Mhat = o.mode_product(Mhat, Ainv, k)
+    lam = 2.0 / math.pi * math.log(n) + 1.0
+    X, Y = W.sources(w, 100), W.targets(w, 100)
+    for th in ((0.7,), (1.6,)):
+        U, Mh, V = o.instantiate(cores, w.d, w.dtheta, w.mode_boxes(), th, X, Y)
+        Kf = o.full_interpolant(C, w.d, w.dtheta, w.mode_boxes(), th, X, Y)
+        assert np.abs(Kf - U @ Mh @ V.T).max() <= lam ** 3 * np.abs(M - Mhat).max()
+
+
+def test_orientation_of_interval_map_does_not_change_the_interpolant():
+    # reading R1: reversing every box (b, a) turns the printed map into the usual one
+    from paper_2406_06344_gb300 import workloads as W
+    w = W.C2
+    boxes = w.mode_boxes()
+    n = 8
+    X, Y = W.sources(w, 50), W.targets(w, 50)
+    th = (0.9,)
+    c1, _, _ = o.build_offline(w.kernel, w.d, w.dtheta, boxes, n, 1e-12)
+    c2, _, _ = o.build_offline(w.kernel, w.d, w.dtheta, boxes[:, ::-1], n, 1e-12)
+    K1 = np.linalg.multi_dot(o.instantiate(c1, w.d, w.dtheta, boxes, th, X, Y)[:2] + (o.instantiate(c1, w.d, w.dtheta, boxes, th, X, Y)[2].T,))
+    U2, M2, V2 = o.instantiate(c2, w.d, w.dtheta, boxes[:, ::-1], th, X, Y)
+    assert o.rel_fro(K1, U2 @ M2 @ V2.T) < 1e-12
+
+
+def test_apply_matches_dense_product():
+    rng = np.random.default_rng(7)
+    U, M, V, w = rng.random((30, 5)), rng.random((5, 4)), rng.random((20, 4)), rng.random(20)
+    assert np.allclose(o.apply(U, M, V, w), (U @ M @ V.T) @ w, rtol=1e-14)
+
+
+# --- gradients of L = w^T K~ z -----------------------------------------------
+
+def _small_tt(kind, d, dth, boxes, n):
+    return o.build_offline(kind, d, dth, boxes, n, 1e-12)[0]
+
+
+def test_gradients_match_central_differences():
+    d, dth, n = 2, 2, 7
+    boxes = [(0, 1), (0, 1), (0.5, 2.0), (0.5, 2.5), (3, 4), (0, 1)]
+    cores = _small_tt(o.MATERN_NU, d, dth, boxes, n)
+    rng = np.random.default_rng(8)
+    X = rng.random((25, 2))
+    Y = np.column_stack([3 + rng.random(30), rng.random(30)])
+    w, z = rng.standard_normal(25), rng.standard_normal(30)
+    theta = np.array([1.3, 1.7])
+    gth, gX = o.loss_grad(cores, d, dth, boxes, theta, X, Y, w, z)
+    L = lambda th, XX: o.loss(*o.instantiate(cores, d, dth, boxes, th, XX, Y), w, z)
+    h = 1e-6
+    for j in range(dth):
+        e = np.zeros(dth)
+        e[j] = h
+        fd = (L(theta + e, X) - L(theta - e, X)) / (2 * h)
+        assert gth[j] == pytest.approx(fd, rel=1e-7, abs=1e-9)
+    for _ in range(4):
+        v = rng.standard_normal(X.shape)
+        fd = (L(theta, X + h * v) - L(theta, X - h * v)) / (2 * h)
+        assert float(np.sum(gX * v)) == pytest.approx(fd, rel=1e-7, abs=1e-9)
+
+
+def test_gradients_match_dense_matern32_closed_form():
+    # at nu = 3/2: dkappa/dl = a^2 e^{-a} / l, grad_x kappa = -3 e^{-a} (x - y) / l^2, a = sqrt(3) r / l
+    d, dth, n = 1, 1, 24          # n = 24: the interpolation floor is ~1e-13 here
+    boxes = [(0, 1), (0.5, 2.0), (2, 3)]
+    cores = _small_tt(o.MATERN32, d, dth, boxes, n)
+    rng = np.random.default_rng(9)
+    X, Y = rng.random((40, 1)), 2 + rng.random((50, 1))
+    w, z = rng.standard_normal(40), rng.standard_normal(50)
+    l = 1.4
+    gth, gX = o.loss_grad(cores, d, dth, boxes, np.array([l]), X, Y, w, z)
+    diff = X[:, None, 0] - Y[None, :, 0]
+    r = np.abs(diff)
+    a = math.sqrt(3) * r / l
+    dK_dl = a ** 2 * np.exp(-a) / l
+    dK_dx = -3 * np.exp(-a) * diff / l ** 2
+    assert gth[0] == pytest.approx(w @ dK_dl @ z, rel=1e-9)
+    gx = w * (dK_dx @ z)
+    assert np.linalg.norm(gX[:, 0] - gx) <= 1e-10 * np.linalg.norm(gx)
