@@ -1,0 +1,190 @@
+/*
+ * pttk.h: C ABI of libpttk, a GB300 (sm_103a) implementation of the parametric
+ * tensor-train kernel (PTTK) low-rank method of Khan & Saibaba, "Parametric kernel
+ * low-rank approximations using tensor train decomposition" (arXiv 2406.06344).
+ *
+ * The method approximates a parametric kernel matrix
+ *     K(X, Y; theta)_ij = kappa(x_i, y_j; theta)                     (Eq. matparamkernel)
+ * by K ~= U(X) M(theta) V(Y)^T                                          (Eq. paramlowrank)
+ * in two stages:
+ *   offline  evaluate f_kappa(x, theta, y) on the tensor grid of Chebyshev nodes over
+ *            B_s x B_theta x B_t (Eq. mdc), map the values to Chebyshev coefficients
+ *            per mode, and compress the coefficient tensor by TT-SVD (Section 2.3);
+ *   online   contract the theta cores with the Chebyshev vector of theta (Eq. hmat,
+ *            Algorithm 3) and build the factors U, V by the chained Khatri-Rao/core
+ *            contractions of Algorithm 2, Phase 3.
+ *
+ * Conventions shared by every entry point
+ *   - Variable order is xi = (x, theta, y); D = 2 d + d_theta (Eq. fkappa).
+ *   - Boxes are arrays of (lo, hi) pairs: box[2 j] = alpha_j, box[2 j + 1] = beta_j, and
+ *     lo < hi is required. The interval map is the one printed in Section 2.4,
+ *     phi_[a,b](t) = ((a-b)/2) t + (a+b)/2; Chebyshev nodes are the roots of T_n.
+ *   - The coefficient tensor C (n^D entries) is stored column-major: i_1 varies fastest
+ *     (the little-endian flattening of Section 2.2).
+ *   - A TT core G_k has shape r_{k-1} x n x r_k, stored column-major (index
+ *     a + r_{k-1} (j + n b)); r_0 = r_D = 1.
+ *   - Point sets X (N_s x d), Y (N_t x d) and the factors U (N_s x r_d),
+ *     M (r_d x r_{d+d_theta}) and V (N_t x r_{d+d_theta}) are row-major.
+ *   - Precision: PTTK_FP64 takes and returns double; every other precision takes float
+ *     points and returns float factors. TF32/BF16 forms run on the tensor cores with
+ *     FP32 accumulation; the X3 forms split each operand into a high and a low part
+ *     and issue three products (high*high + high*low + low*high).
+ *   - Memory: "dev" pointers are device (or managed) memory owned by the caller; "host"
+ *     pointers are host memory owned by the caller. The library owns pttk_tt handles.
+ *   - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream). Calls
+ *     enqueue work on it and return; results are ready when the stream is synchronised,
+ *     except where a call says it synchronises.
+ *   - Errors: every call returns a pttk_status; on failure pttk_last_error() returns a
+ *     message for the calling thread. No C++ exception crosses this boundary. A call that
+ *     fails leaves its outputs unspecified and the handle unchanged.
+ */
+#ifndef PTTK_H
+#define PTTK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pttk_status {
+  PTTK_OK = 0,
+  PTTK_EINVAL = 1,   /* bad argument: size, box, pointer, precision, rank mismatch */
+  PTTK_EDOMAIN = 2,  /* theta outside its box */
+  PTTK_ENOMEM = 3,   /* a device or host allocation failed */
+  PTTK_ECUDA = 4,    /* a CUDA runtime error; pttk_last_error() has its text */
+  PTTK_ETIMEOUT = 5, /* a bounded device-side wait ran out */
+  PTTK_ENOTSUP = 6   /* combination not implemented (e.g. a precision for this shape) */
+} pttk_status;
+
+/* Kernels of Table kern-table (r = ||x - y||_2):
+ *   PTTK_GAUSS      theta = (l):      exp(-(r/l)^2)
+ *   PTTK_MATERN32   theta = (l):      (1 + sqrt(3) r/l) exp(-sqrt(3) r/l)
+ *   PTTK_MATERN_NU  theta = (l, nu):  2^(1-nu)/Gamma(nu) (sqrt(2 nu) r/l)^nu K_nu(sqrt(2 nu) r/l)
+ * (the table prints Gamma(l) in the Matern normalisation; Gamma(nu) is used). */
+typedef enum pttk_kernel { PTTK_GAUSS = 0, PTTK_MATERN32 = 1, PTTK_MATERN_NU = 2 } pttk_kernel;
+
+typedef enum pttk_prec {
+  PTTK_FP64 = 0,
+  PTTK_FP32 = 1,
+  PTTK_TF32 = 2,
+  PTTK_TF32X3 = 3,
+  PTTK_BF16 = 4,
+  PTTK_BF16X3 = 5
+} pttk_prec;
+
+typedef struct pttk_tt pttk_tt; /* opaque: TT cores on the device plus their metadata */
+
+/* Message for the last failing call on this thread ("" if none). Never NULL. */
+const char* pttk_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int pttk_version(void);
+
+/* ---- offline stage ----------------------------------------------------------------- */
+
+/* Grid evaluation and Chebyshev transform (Eq. mdc; Eq. cheb_trans rewritten as
+ * coefficients). Writes C = M x_1 A x_2 A ... x_D A to `C` (dev, n^D elements, column-major),
+ * where m_{i_1..i_D} = f_kappa(eta^(1)_{i_1}, ..., eta^(D)_{i_D}) and
+ * A[k, i] = (c_k / n) T_k(zeta_i), c_0 = 1, c_k = 2.
+ *   src_box, tgt_box: host [2 d]; theta_box: host [2 d_theta].
+ *   grid_prec: PTTK_FP64 (C is double) or PTTK_FP32 (C is float; evaluation and transform
+ *   in FP32).
+ *   1 <= d <= 3, 2 <= n <= 32, n^D <= 4e9; d_theta = 1 (theta = (l)) for PTTK_GAUSS and
+ *   PTTK_MATERN32, d_theta = 2 (theta = (l, nu)) for PTTK_MATERN_NU; l > 0 and nu > 0 over
+ *   their boxes. Otherwise PTTK_EINVAL. */
+pttk_status pttk_grid_coeffs(pttk_kernel kernel, int d, const double* src_box,
+                             const double* tgt_box, int d_theta, const double* theta_box, int n,
+                             pttk_prec grid_prec, void* C, void* stream);
+
+/* TT-SVD of a coefficient tensor (Section 2.3; Oseledets 2011, Algorithm 1) with the
+ * truncation threshold delta = tol / sqrt(D-1) * ||C||_F of Algorithm 1 (TT-Round):
+ * r_k is the smallest r >= 1 whose discarded singular values satisfy
+ * sqrt(sum_{i>r} sigma_i^2) <= delta. All QR/SVD steps run in FP64 on the device.
+ *   C: dev, n^D elements (double if c_prec = PTTK_FP64, float if PTTK_FP32), column-major,
+ *   not modified. The kernel, boxes and n describe the grid C came from and are stored in
+ *   the handle for the online stage. On success *out owns a new handle; free it with
+ *   pttk_tt_free. Synchronises `stream` (the ranks are decided on the host). */
+pttk_status pttk_tt_from_coeffs(pttk_kernel kernel, int d, const double* src_box,
+                                const double* tgt_box, int d_theta, const double* theta_box,
+                                int n, double tol, const void* C, pttk_prec c_prec,
+                                void* stream, pttk_tt** out);
+
+/* Offline stage (Algorithm 2, Phases 1-2, with the full grid and TT-SVD in place of
+ * TT greedy-cross): pttk_grid_coeffs into a library-owned buffer, then
+ * pttk_tt_from_coeffs. Synchronises `stream`. */
+pttk_status pttk_build_offline(pttk_kernel kernel, int d, const double* src_box,
+                               const double* tgt_box, int d_theta, const double* theta_box,
+                               int n, double tol, pttk_prec grid_prec, void* stream,
+                               pttk_tt** out);
+
+/* ---- handle queries, checkpoint ---------------------------------------------------- */
+
+/* d, d_theta, n and the kernel of a handle (any pointer may be NULL). */
+pttk_status pttk_tt_dims(const pttk_tt* tt, int* d, int* d_theta, int* n, int* kernel);
+
+/* TT ranks r_0..r_D (host array of D + 1 ints; r_0 = r_D = 1). */
+pttk_status pttk_tt_ranks(const pttk_tt* tt, int* ranks);
+
+/* Copy core k (0-based, 0 <= k < D) to host memory: r_{k-1} * n * r_k doubles,
+ * column-major. Synchronous. */
+pttk_status pttk_tt_get_core(const pttk_tt* tt, int k, double* host_out);
+
+/* Write / read a handle (kernel, d, d_theta, n, boxes, ranks, FP64 cores) to / from a
+ * little-endian binary file. pttk_tt_load allocates device memory on the current device. */
+pttk_status pttk_tt_save(const pttk_tt* tt, const char* path);
+pttk_status pttk_tt_load(const char* path, pttk_tt** out);
+
+/* Release a handle and its device memory (NULL is a no-op). */
+void pttk_tt_free(pttk_tt* tt);
+
+/* ---- online stage ------------------------------------------------------------------ */
+
+/* Core matrix H(theta) = H_1(theta_1) ... H_{d_theta}(theta_{d_theta}),
+ * H_j = sum_k G_{d+j}[:, k, :] T_k(phi^{-1}(theta_j)) (Eq. hmat, Algorithm 3, coefficient
+ * form). theta: host [d_theta], inside the theta box (else PTTK_EDOMAIN).
+ * M: dev, r_d x r_{d+d_theta} row-major, double for PTTK_FP64 and float otherwise.
+ */
+pttk_status pttk_theta_core(const pttk_tt* tt, const double* theta, pttk_prec prec, void* M,
+                            void* stream);
+
+/* Online instantiation: M = H(theta) as above, and the factor matrices of Algorithm 2,
+ * Phase 3 for the given points: U = S(X) (N_s x r_d) by S <- B_1 G_1^{2},
+ * S <- (B_i face-split S) G_i^{2}; V = T(Y) (N_t x r_{d+d_theta}) by the mirrored
+ * Khatri-Rao chain; B_i[p, k] = T_k(phi^{-1}(x_{p,i})). K(X, Y; theta) ~= U M V^T.
+ *   X: dev N_s x d, Y: dev N_t x d (double for PTTK_FP64, float otherwise); points are
+ *   expected inside their boxes (a point outside is extrapolated, not rejected).
+ *   N_s, N_t >= 0 (0 is allowed and writes nothing for that side).
+ *   U, M, V: dev outputs (double for PTTK_FP64, float otherwise). */
+pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void* X,
+                             int64_t N_s, const void* Y, int64_t N_t, pttk_prec prec, void* U,
+                             void* M, void* V, void* stream);
+
+/* Low-rank product out = U (M (V^T w)) (Eq. paramlowrank applied to a vector).
+ *   U: dev N_s x rs, M: dev rs x rt, V: dev N_t x rt, row-major; w: dev [N_t];
+ *   out: dev [N_s]. prec: PTTK_FP64 (all double) or PTTK_FP32 (all float; reductions
+ *   accumulate in FP32). The library allocates a small temporary for V^T w and M (V^T w). */
+pttk_status pttk_apply(const void* U, const void* M, const void* V, int64_t N_s, int64_t N_t,
+                       int rs, int rt, pttk_prec prec, const void* w, void* out, void* stream);
+
+/* ---- kernel timing ------------------------------------------------------------------ */
+
+/* When enabled, every launch of the library's timed kernels is bracketed by two CUDA
+ * events recorded on the launching stream. Kernel names: "grid_tile", "mode_transform",
+ * "householder", "jacobi_round", "dgemm", "chain", "apply". Off by default; enabling adds
+ * two event records per launch. */
+pttk_status pttk_profile_enable(int on);
+/* Forget all accumulated timings (waits for pending events). */
+pttk_status pttk_profile_reset(void);
+/* Total milliseconds and launch count accumulated for one kernel name (synchronises on the
+ * pending events of that kernel). Unknown names give 0 and 0. */
+pttk_status pttk_profile_get(const char* kernel_name, double* ms_total, int64_t* launches);
+/* Names of the kernels timed so far, newline-separated, NUL-terminated, truncated to len. */
+pttk_status pttk_profile_names(char* buf, int64_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTTK_H */

@@ -1,0 +1,411 @@
+// Online stage: H(theta) (Eq. hmat, Algorithm 3), the factor chains of Algorithm 2,
+// Phase 3 (SIMT FP64 / FP32 form), and the low-rank product U (M (V^T w)).
+//
+// Factor chain. Per point p the source chain is
+//   S_1 = B_1 G_1^{2},   S_i = (B_i face-split S_{i-1}) G_i^{2},   U[p, :] = S_d,
+// with B_i[p, k] = T_k(xhat_{p,i}) and the Kronecker column index a + r_{i-1} j matching
+// the row index of G_i^{2}. The target chain T <- G_D^{1} V_d^T,
+// T <- G_{D-i}^{1} (T Khatri-Rao V_{d-i}^T) has the same per-point form once each core is
+// read as (input rank, j, output rank) = (right rank, j, left rank); the handle keeps those
+// transposed copies of the target-side cores ("oriented" cores). Each chain step is then a
+// GEMM  S_out (P x R_out) = A (P x n R_in) * Gs^{2} (n R_in x R_out)  whose A operand
+// A[p, a + R_in j] = B[p, j] S_in[p, a] is generated in shared memory, never stored.
+#include <math.h>
+
+#include <algorithm>
+
+#include "pttk_internal.cuh"
+
+namespace pttk {
+
+int oriented_core_dims(const pttk_tt* tt, bool source, int step, int* R_in, int* R_out,
+                       int* coord);
+
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v);
+template <>
+__device__ __forceinline__ double warp_sum<double>(double v) { return warp_sum_d(v); }
+template <>
+__device__ __forceinline__ float warp_sum<float>(float v) { return warp_sum_f(v); }
+
+// ---------------- H(theta) -------------------------------------------------------------
+// out[a + ra b] = sum_k G[a + ra (k + n b)] T_k(th)   (G: ra x n x rb, column-major)
+__global__ void contract_theta_kernel(const double* __restrict__ G, int ra, int n, int rb,
+                                      double th, double* __restrict__ out) {
+  double T[PTTK_MAX_N];
+  T[0] = 1.0;
+  if (n > 1) T[1] = th;
+  for (int k = 2; k < n; ++k) T[k] = 2.0 * th * T[k - 1] - T[k - 2];
+  const int64_t total = (int64_t)ra * rb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e % ra, b = e / ra;
+    const double* g = G + a + (int64_t)ra * n * b;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc = fma(g[(int64_t)ra * k], T[k], acc);
+    out[e] = acc;
+  }
+}
+
+// M row-major (rs x rt) from H column-major (rs x rt)
+template <typename T>
+__global__ void store_rowmajor_kernel(const double* __restrict__ H, int rs, int rt,
+                                      T* __restrict__ M) {
+  const int64_t total = (int64_t)rs * rt;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / rt, b = e % rt;
+    M[e] = (T)H[a + (int64_t)rs * b];
+  }
+}
+
+__global__ void identity_rowmajor_kernel(void* M, int r, bool fp64) {
+  const int64_t total = (int64_t)r * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (e / r == e % r) ? 1.0 : 0.0;
+    if (fp64) static_cast<double*>(M)[e] = v;
+    else static_cast<float*>(M)[e] = (float)v;
+  }
+}
+
+// ---------------- factor chain (SIMT) -----------------------------------------------
+struct ChainStep {
+  const void* G;  // oriented core, column-major (R_in x n x R_out)
+  int R_in, R_out, coord;
+  double lo, hi;
+};
+struct ChainArgs {
+  ChainStep st[3];
+  int nsteps, n, d, Rmax;  // Rmax: largest R (padded to 64) held in shared memory
+  int64_t N;
+};
+
+constexpr int CT = 64;  // output columns per tile
+constexpr int BK = 16;  // K chunk
+
+// One CTA builds the factor rows of P points. Threads: (P/4) x 16, each owning a 4 x 4
+// register tile of (points, output columns).
+template <typename T, int P>
+__global__ void __launch_bounds__((P / 4) * 16) chain_kernel(ChainArgs a, const T* __restrict__ pts,
+                                                             T* __restrict__ out) {
+  constexpr int NT = (P / 4) * 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Sa = reinterpret_cast<T*>(smem_raw);  // P x Rmax (point-major: Sa[p * Rmax + r])
+  T* Sb = Sa + (size_t)P * a.Rmax;
+  T* Bv = Sb + (size_t)P * a.Rmax;         // P x n basis values
+  T* As = Bv + (size_t)P * PTTK_MAX_N;     // BK x P
+  T* Gs = As + BK * P;                     // BK x CT
+
+  const int64_t p0 = (int64_t)blockIdx.x * P;
+  const int tp = threadIdx.x / 16, to = threadIdx.x % 16;
+  const int n = a.n;
+  T* Sin = Sa;
+  T* Sout = Sb;
+  // S_0 = 1 (r_0 = 1)
+  for (int p = threadIdx.x; p < P; p += NT) Sin[p * a.Rmax] = T(1);
+
+  for (int si = 0; si < a.nsteps; ++si) {
+    const ChainStep st = a.st[si];
+    const T* G = static_cast<const T*>(st.G);
+    // Chebyshev basis of this coordinate by the three-term recurrence
+    for (int p = threadIdx.x; p < P; p += NT) {
+      const int64_t gp = p0 + p;
+      const T x = gp < a.N ? pts[gp * a.d + st.coord] : T(st.lo);
+      const T xh = (T(2) * x - T(st.lo) - T(st.hi)) / (T(st.lo) - T(st.hi));
+      T t0 = T(1), t1 = xh;
+      Bv[p * PTTK_MAX_N + 0] = t0;
+      if (n > 1) Bv[p * PTTK_MAX_N + 1] = t1;
+      for (int k = 2; k < n; ++k) {
+        const T t2 = T(2) * xh * t1 - t0;
+        Bv[p * PTTK_MAX_N + k] = t2;
+        t0 = t1;
+        t1 = t2;
+      }
+    }
+    __syncthreads();
+    const int K = n * st.R_in;
+    for (int o0 = 0; o0 < st.R_out; o0 += CT) {
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+      for (int k0 = 0; k0 < K; k0 += BK) {
+        // A chunk: As[kk][p] = B[p, j] * S_in[p, a], k = a + R_in j
+        for (int e = threadIdx.x; e < BK * P; e += NT) {
+          const int kk = e / P, p = e % P;
+          const int k = k0 + kk;
+          T v = T(0);
+          if (k < K) {
+            const int j = k / st.R_in, ar = k % st.R_in;
+            v = Bv[p * PTTK_MAX_N + j] * Sin[p * a.Rmax + ar];
+          }
+          As[kk * P + p] = v;
+        }
+        // core chunk: Gs[kk][o] = Gs2[k, o0 + o]
+        for (int e = threadIdx.x; e < BK * CT; e += NT) {
+          const int kk = e / CT, o = e % CT;
+          const int k = k0 + kk, oc = o0 + o;
+          Gs[kk * CT + o] = (k < K && oc < st.R_out) ? G[k + (int64_t)K * oc] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+          T av[4], bv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) av[i] = As[kk * P + tp * 4 + i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) bv[j] = Gs[kk * CT + to * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+      const bool last = si == a.nsteps - 1;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int p = tp * 4 + i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int oc = o0 + to * 4 + j;
+          if (oc >= st.R_out) continue;
+          if (last) {
+            const int64_t gp = p0 + p;
+            if (gp < a.N) out[gp * st.R_out + oc] = acc[i][j];
+          } else {
+            Sout[p * a.Rmax + oc] = acc[i][j];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    T* tmp = Sin;
+    Sin = Sout;
+    Sout = tmp;
+  }
+}
+
+// ---------------- apply: out = U (M (V^T w)) ----------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) vtw_partial_kernel(const T* __restrict__ V, int64_t N,
+                                                          int rt, const T* __restrict__ w,
+                                                          T* __restrict__ partial) {
+  const int64_t rows_per = (N + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = std::min<int64_t>(N, r0 + rows_per);
+  for (int c = threadIdx.x; c < rt; c += blockDim.x) {
+    T acc = T(0);
+    for (int64_t r = r0; r < r1; ++r) acc = fma(V[r * rt + c], w[r], acc);
+    partial[(int64_t)blockIdx.x * rt + c] = acc;
+  }
+}
+
+// t = sum over partial rows; s = M t (one CTA)
+template <typename T>
+__global__ void __launch_bounds__(256) reduce_mt_kernel(const T* __restrict__ partial, int nparts,
+                                                        int rs, int rt, const T* __restrict__ M,
+                                                        T* __restrict__ s_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* t = reinterpret_cast<T*>(smem_raw);
+  for (int c = threadIdx.x; c < rt; c += blockDim.x) {
+    T acc = T(0);
+    for (int b = 0; b < nparts; ++b) acc += partial[(int64_t)b * rt + c];
+    t[c] = acc;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < rs; r += blockDim.x) {
+    T acc = T(0);
+    for (int c = 0; c < rt; ++c) acc = fma(M[(int64_t)r * rt + c], t[c], acc);
+    s_out[r] = acc;
+  }
+}
+
+// out[p] = U[p, :] . s, one warp per row
+template <typename T>
+__global__ void __launch_bounds__(256) us_kernel(const T* __restrict__ U, int64_t N, int rs,
+                                                 const T* __restrict__ s, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sv = reinterpret_cast<T*>(smem_raw);
+  for (int c = threadIdx.x; c < rs; c += blockDim.x) sv[c] = s[c];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N;
+       row += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const T* u = U + row * rs;
+    T acc = T(0);
+    for (int c = lane; c < rs; c += 32) acc = fma(u[c], sv[c], acc);
+    acc = warp_sum<T>(acc);
+    if (lane == 0) out[row] = acc;
+  }
+}
+
+template <typename T>
+pttk_status apply_typed(const T* U, const T* M, const T* V, int64_t N_s, int64_t N_t, int rs,
+                        int rt, const T* w, T* out, T* scratch, int nparts, cudaStream_t s) {
+  T* partial = scratch;
+  T* sv = scratch + (size_t)nparts * rt;
+  PTTK_PROF("apply", s);
+  if (N_t > 0) {
+    vtw_partial_kernel<T><<<nparts, 256, 0, s>>>(V, N_t, rt, w, partial);
+  } else {
+    PTTK_CUDA(cudaMemsetAsync(partial, 0, sizeof(T) * (size_t)nparts * rt, s));
+  }
+  reduce_mt_kernel<T><<<1, 256, sizeof(T) * rt, s>>>(partial, nparts, rs, rt, M, sv);
+  if (N_s > 0) {
+    const int64_t blocks = std::min<int64_t>((N_s * 32 + 255) / 256, (int64_t)sm_count() * 16);
+    us_kernel<T><<<(unsigned)blocks, 256, sizeof(T) * rs, s>>>(U, N_s, rs, sv, out);
+  }
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
+int apply_parts(int64_t N_t) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((N_t + 255) / 256, (int64_t)sm_count() * 4));
+}
+
+}  // namespace
+
+// Step `step` of a side's chain: dimensions of its oriented core and the point coordinate.
+int oriented_core_dims(const pttk_tt* tt, bool source, int step, int* R_in, int* R_out,
+                       int* coord) {
+  if (source) {
+    const int k = step;  // core G_{k+1}
+    *R_in = tt->ranks[k];
+    *R_out = tt->ranks[k + 1];
+    *coord = step;
+    return k;
+  }
+  const int k = tt->D - 1 - step;  // core G_{D-step}, read transposed
+  *R_in = tt->ranks[k + 1];
+  *R_out = tt->ranks[k];
+  *coord = tt->d - 1 - step;
+  return k;
+}
+
+pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64, void* M,
+                           cudaStream_t s) {
+  const int d = tt->d, dth = tt->dtheta, n = tt->n;
+  const int rs = tt->ranks[d], rt = tt->ranks[d + dth];
+  if (dth == 0) {
+    identity_rowmajor_kernel<<<64, 256, 0, s>>>(M, rs, fp64);
+    PTTK_CUDA(cudaGetLastError());
+    return PTTK_OK;
+  }
+  size_t need = 0;
+  for (int j = 0; j < dth; ++j) need += (size_t)tt->ranks[d + j] * tt->ranks[d + j + 1];
+  need += (size_t)rs * rt * (dth > 1 ? 2 : 0);
+  double* work = nullptr;
+  PTTK_CUDA(cudaMallocAsync(&work, sizeof(double) * std::max<size_t>(need, 1), s));
+  double* Hj[2] = {work, work + (size_t)tt->ranks[d] * tt->ranks[d + 1]};
+  for (int j = 0; j < dth; ++j) {
+    const int ra = tt->ranks[d + j], rb = tt->ranks[d + j + 1];
+    const int64_t total = (int64_t)ra * rb;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, sm_count() * 8);
+    contract_theta_kernel<<<blocks, 256, 0, s>>>(tt->cores64 + tt->core_off[d + j], ra, n, rb,
+                                                 theta_hat[j], Hj[j]);
+  }
+  const double* H = Hj[0];
+  if (dth == 2) {
+    double* Hp = Hj[1] + (size_t)tt->ranks[d + 1] * tt->ranks[d + 2];
+    dgemm(false, false, rs, rt, tt->ranks[d + 1], 1.0, Hj[0], rs, Hj[1], tt->ranks[d + 1], 0.0,
+          Hp, rs, s);
+    H = Hp;
+  }
+  const unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)rs * rt + 255) / 256, sm_count() * 8);
+  if (fp64) store_rowmajor_kernel<double><<<blocks, 256, 0, s>>>(H, rs, rt, static_cast<double*>(M));
+  else store_rowmajor_kernel<float><<<blocks, 256, 0, s>>>(H, rs, rt, static_cast<float*>(M));
+  PTTK_CUDA(cudaGetLastError());
+  PTTK_CUDA(cudaFreeAsync(work, s));
+  return PTTK_OK;
+}
+
+template <typename T, int P>
+static pttk_status launch_chain(const ChainArgs& a, const T* pts, T* out, cudaStream_t s) {
+  const size_t smem = sizeof(T) * ((size_t)2 * P * a.Rmax + (size_t)P * PTTK_MAX_N + BK * P + BK * CT);
+  auto kfn = chain_kernel<T, P>;
+  PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t blocks = (a.N + P - 1) / P;
+  PTTK_PROF("chain", s);
+  kfn<<<(unsigned)blocks, (P / 4) * 16, smem, s>>>(a, pts, out);
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
+// Oriented core pointer for a chain step (see pttk_tt::oriented).
+const void* oriented_core_ptr(const pttk_tt* tt, bool source, int k, bool fp64);
+
+pttk_status factor_build_run(const pttk_tt* tt, bool source, const void* P, int64_t N,
+                             pttk_prec prec, void* out, cudaStream_t s) {
+  if (N == 0) return PTTK_OK;
+  const bool fp64 = prec == PTTK_FP64;
+  ChainArgs a{};
+  a.nsteps = tt->d;
+  a.n = tt->n;
+  a.d = tt->d;
+  a.N = N;
+  int rmax = 1;
+  for (int i = 0; i < tt->d; ++i) {
+    int rin, rout, coord;
+    const int k = oriented_core_dims(tt, source, i, &rin, &rout, &coord);
+    a.st[i].G = oriented_core_ptr(tt, source, k, fp64);
+    a.st[i].R_in = rin;
+    a.st[i].R_out = rout;
+    a.st[i].coord = coord;
+    const int bj = source ? coord : tt->d + tt->dtheta + coord;
+    a.st[i].lo = tt->box[bj][0];
+    a.st[i].hi = tt->box[bj][1];
+    rmax = std::max(rmax, std::max(rin, rout));
+  }
+  a.Rmax = ((rmax + CT - 1) / CT) * CT;
+  const size_t elem = fp64 ? 8 : 4;
+  const size_t budget = 200000;
+  auto fits = [&](int P) {
+    return elem * ((size_t)2 * P * a.Rmax + (size_t)P * PTTK_MAX_N + BK * P + BK * CT) <= budget;
+  };
+  if (fp64) {
+    if (fits(64)) return launch_chain<double, 64>(a, static_cast<const double*>(P), static_cast<double*>(out), s);
+    if (fits(32)) return launch_chain<double, 32>(a, static_cast<const double*>(P), static_cast<double*>(out), s);
+    if (fits(16)) return launch_chain<double, 16>(a, static_cast<const double*>(P), static_cast<double*>(out), s);
+  } else {
+    if (fits(64)) return launch_chain<float, 64>(a, static_cast<const float*>(P), static_cast<float*>(out), s);
+    if (fits(32)) return launch_chain<float, 32>(a, static_cast<const float*>(P), static_cast<float*>(out), s);
+    if (fits(16)) return launch_chain<float, 16>(a, static_cast<const float*>(P), static_cast<float*>(out), s);
+  }
+  return set_error(PTTK_ENOTSUP, "TT ranks too large for the SIMT factor chain");
+}
+
+size_t apply_scratch_bytes(int64_t N_t, int rs, int rt, bool fp64) {
+  const int nparts = apply_parts(N_t);
+  return (fp64 ? 8 : 4) * ((size_t)nparts * rt + (size_t)rs);
+}
+
+pttk_status apply_run(const void* U, const void* M, const void* V, int64_t N_s, int64_t N_t,
+                      int rs, int rt, bool fp64, const void* w, void* out, void* scratch,
+                      cudaStream_t s) {
+  const int nparts = apply_parts(N_t);
+  if (fp64)
+    return apply_typed<double>(static_cast<const double*>(U), static_cast<const double*>(M),
+                               static_cast<const double*>(V), N_s, N_t, rs, rt,
+                               static_cast<const double*>(w), static_cast<double*>(out),
+                               static_cast<double*>(scratch), nparts, s);
+  return apply_typed<float>(static_cast<const float*>(U), static_cast<const float*>(M),
+                            static_cast<const float*>(V), N_s, N_t, rs, rt,
+                            static_cast<const float*>(w), static_cast<float*>(out),
+                            static_cast<float*>(scratch), nparts, s);
+}
+
+}  // namespace pttk

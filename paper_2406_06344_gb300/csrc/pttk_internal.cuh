@@ -1,0 +1,91 @@
+// Internal declarations shared by the libpttk translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/pttk.h"
+
+#define PTTK_MAX_D 8
+#define PTTK_MAX_N 32
+
+struct pttk_tt {
+  int kernel = 0, d = 0, dtheta = 0, D = 0, n = 0;
+  double box[PTTK_MAX_D][2] = {};   // (alpha_j, beta_j) in the variable order (x, theta, y)
+  int ranks[PTTK_MAX_D + 1] = {};   // r_0..r_D
+  size_t core_off[PTTK_MAX_D] = {}; // element offset of core k in the core buffers
+  size_t core_total = 0;            // total core elements
+  double* cores64 = nullptr;        // device, FP64 cores, column-major r_{k-1} x n x r_k
+  float* cores32 = nullptr;         // device, FP32 copy (online FP32 / tensor-core forms)
+  int device = 0;
+  size_t core_elems(int k) const { return (size_t)ranks[k] * n * ranks[k + 1]; }
+};
+
+namespace pttk {
+
+// Thread-local message for pttk_last_error(); set_error returns its status for chaining.
+pttk_status set_error(pttk_status s, const std::string& msg);
+pttk_status cuda_error(cudaError_t e, const char* what);
+void clear_error();
+
+#define PTTK_CUDA(call)                                     \
+  do {                                                      \
+    cudaError_t e__ = (call);                               \
+    if (e__ != cudaSuccess) return pttk::cuda_error(e__, #call); \
+  } while (0)
+
+#define PTTK_TRY(call)                                      \
+  do {                                                      \
+    pttk_status s__ = (call);                               \
+    if (s__ != PTTK_OK) return s__;                         \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int sm_count();
+
+// Kernel timing (profile.cu): when enabled, PTTK_PROF brackets a launch with CUDA events
+// recorded on its stream; results are read through pttk_profile_get.
+bool prof_on();
+void* prof_begin(const char* name, cudaStream_t s);
+void prof_end(const char* name, cudaStream_t s);
+struct ProfScope {
+  const char* name;
+  cudaStream_t s;
+  ProfScope(const char* n, cudaStream_t st) : name(n), s(st) { prof_begin(n, st); }
+  ~ProfScope() { prof_end(name, s); }
+};
+#define PTTK_PROF(name, stream) pttk::ProfScope pttk_prof_scope__(name, stream)
+
+// --- grid.cu ---------------------------------------------------------------------------
+pttk_status grid_coeffs_launch(int kernel, int d, int dtheta, int n, const double (*box)[2],
+                               bool fp64, void* C, cudaStream_t s);
+
+// --- ttsvd.cu --------------------------------------------------------------------------
+// TT-SVD of the FP64 tensor in `X` (n^D elements, modified). Fills tt->ranks and
+// allocates tt->cores64 / cores32. Synchronises `s`.
+pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s);
+pttk_status widen_to_f64(const float* in, int64_t n, double* out, cudaStream_t s);
+
+// FP64 column-major GEMM: C[M x N] = alpha * op(A) * op(B) + beta * C.
+void dgemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
+           const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+           int64_t ldc, cudaStream_t s);
+
+// --- online.cu -------------------------------------------------------------------------
+pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64, void* M,
+                           cudaStream_t s);
+pttk_status factor_build_run(const pttk_tt* tt, bool source, const void* P, int64_t N,
+                             pttk_prec prec, void* out, cudaStream_t s);
+pttk_status apply_run(const void* U, const void* M, const void* V, int64_t N_s, int64_t N_t,
+                      int rs, int rt, bool fp64, const void* w, void* out, void* scratch,
+                      cudaStream_t s);
+size_t apply_scratch_bytes(int64_t N_t, int rs, int rt, bool fp64);
+
+}  // namespace pttk

@@ -1,0 +1,614 @@
+// Offline stage, Phase 2 with TT-SVD (Section 2.3; Oseledets 2011, Algorithm 1) in place
+// of TT greedy-cross, entirely in FP64 on the device.
+//
+// Step k (k = 1..D-1) works on the unfolding X (m x c, column-major, m = r_{k-1} n):
+//   wide  (c >= m): W = X^T; R = qr_r(W) (Householder); one-sided Jacobi on R gives
+//                   R V = U_R Sigma, so the left singular vectors of X are V. The core is
+//                   G_k = V[:, top r] and the remainder X <- G_k^T X.
+//   tall  (c <  m): R = qr_r(X); Jacobi on R gives Sigma and the right singular vectors V;
+//                   Y = X V[:, top r] spans the top-r left singular subspace; a second
+//                   Jacobi pass orthogonalises Y's columns (they are nearly orthogonal
+//                   already) and G_k is Y with unit columns; X <- G_k^T X.
+// In both cases G_k has orthonormal columns to working precision, so G_k G_k^T X is the
+// orthogonal projection of X and the discarded part has norm sqrt(sum_{i>r} sigma_i^2).
+// r_k is the smallest r >= 1 with that tail <= delta = tol / sqrt(D-1) ||C||_F (the
+// threshold of Algorithm 1, TT-Round). QR first keeps singular values down to
+// ~1e-16 ||X|| meaningful (a Gram-matrix route would lose everything below ~1e-8 ||X||).
+//
+// Every kernel is launched as a sequence of independent grids; no kernel waits on another
+// CTA, so nothing here can spin.
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "pttk_internal.cuh"
+
+namespace pttk {
+namespace {
+
+constexpr int RC = 1024;  // Householder rows per chunk
+constexpr int CG = 32;    // Householder columns per group
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < THREADS / 32) ? red[l] : 0.0;
+    v = warp_sum(v);
+  }
+  __syncthreads();
+  return v;  // valid in warp 0
+}
+
+// partial[b] = sum of squares of x over the block's grid-stride share
+__global__ void __launch_bounds__(256) sumsq_kernel(const double* __restrict__ x, int64_t n,
+                                                    double* __restrict__ partial) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(x[i], x[i], acc);
+  acc = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void sum_kernel(const double* __restrict__ partial, int np, double* __restrict__ out) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partial[i];
+  acc = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+// W (c x m, column-major) = X^T, X m x c column-major
+__global__ void transpose_kernel(const double* __restrict__ X, int64_t m, int64_t c,
+                                 double* __restrict__ W) {
+  __shared__ double t[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, m0 = (int64_t)blockIdx.y * 32;
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t row = m0 + threadIdx.x, col = c0 + yy;
+    if (row < m && col < c) t[yy][threadIdx.x] = X[row + col * m];
+  }
+  __syncthreads();
+  for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+    const int64_t row = c0 + threadIdx.x, col = m0 + yy;  // W[row, col] = X[col, row]
+    if (row < c && col < m) W[row + col * c] = t[threadIdx.x][yy];
+  }
+}
+
+// ---------------- Householder QR, R factor only (A: M x N column-major, M >= N) --------
+// Reflector j: x = A[j:M, j], beta = -sign(x_0) ||x||, v = [1; x_{1:}/(x_0 - beta)],
+// tau = (beta - x_0) / beta, H_j = I - tau v v^T, H_j x = beta e_1 (LAPACK convention).
+struct HHScal {
+  double beta, scale, tau;
+};
+
+__global__ void hh_colnorm_kernel(const double* __restrict__ A, int64_t M, int64_t col,
+                                  int64_t row0, double* __restrict__ norm_part) {
+  __shared__ double red[8];
+  const int64_t c = blockIdx.x + row0 / RC;
+  const int64_t r_begin = std::max<int64_t>(c * RC, row0), r_end = std::min<int64_t>((c + 1) * RC, M);
+  double acc = 0.0;
+  for (int64_t i = r_begin + threadIdx.x; i < r_end; i += blockDim.x) {
+    const double a = A[i + col * M];
+    acc = fma(a, a, acc);
+  }
+  acc = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) norm_part[c] = acc;
+}
+
+__global__ void hh_scalar_kernel(const double* __restrict__ A, int64_t M, int64_t N, int64_t j,
+                                 const double* __restrict__ norm_part, int64_t nchunks,
+                                 HHScal* __restrict__ hs, double* __restrict__ R) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int64_t c = j / RC + threadIdx.x; c < nchunks; c += blockDim.x) acc += norm_part[c];
+  acc = block_sum<256>(acc, red);  // sum of squares strictly below the diagonal
+  if (threadIdx.x == 0) {
+    const double x0 = A[j + j * M];
+    HHScal h;
+    if (!(acc > 0.0)) {  // nothing below the diagonal: no reflection
+      h.beta = x0;
+      h.scale = 0.0;
+      h.tau = 0.0;
+    } else {
+      const double nrm = hypot(x0, sqrt(acc));
+      h.beta = (x0 >= 0.0) ? -nrm : nrm;
+      h.scale = 1.0 / (x0 - h.beta);
+      h.tau = (h.beta - x0) / h.beta;
+    }
+    *hs = h;
+    R[j + j * N] = h.beta;
+  }
+}
+
+// w_part[c, l] = sum_{i in chunk c, i >= j} v_i A[i, l], l in (j, N)
+__global__ void __launch_bounds__(256) hh_w_kernel(const double* __restrict__ A, int64_t M,
+                                                   int64_t N, int64_t j,
+                                                   const HHScal* __restrict__ hs,
+                                                   double* __restrict__ w_part) {
+  __shared__ double v[RC];
+  const int64_t c = blockIdx.x + j / RC;
+  const int64_t r_begin = std::max<int64_t>(c * RC, j), r_end = std::min<int64_t>((c + 1) * RC, M);
+  const double scale = hs->scale;
+  for (int64_t i = r_begin + threadIdx.x; i < r_end; i += blockDim.x)
+    v[i - c * RC] = (i == j) ? 1.0 : A[i + j * M] * scale;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t l0 = j + 1 + (int64_t)blockIdx.y * CG;
+  for (int q = warp; q < CG; q += 8) {
+    const int64_t l = l0 + q;
+    if (l >= N) break;
+    const double* col = A + l * M;
+    double acc = 0.0;
+    for (int64_t i = r_begin + lane; i < r_end; i += 32) acc = fma(v[i - c * RC], col[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) w_part[c * N + l] = acc;
+  }
+}
+
+// w[l] = tau * sum_c w_part[c, l]
+__global__ void hh_wsum_kernel(const double* __restrict__ w_part, int64_t N, int64_t j,
+                               int64_t nchunks, const HHScal* __restrict__ hs,
+                               double* __restrict__ w) {
+  __shared__ double red[8];
+  const int64_t l = j + 1 + blockIdx.x;
+  double acc = 0.0;
+  for (int64_t c = j / RC + threadIdx.x; c < nchunks; c += blockDim.x) acc += w_part[c * N + l];
+  acc = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) w[l] = hs->tau * acc;
+}
+
+// A[i, l] -= v_i w[l]; row j of the result is row j of R; partial norm of column j+1.
+__global__ void __launch_bounds__(256) hh_update_kernel(double* __restrict__ A, int64_t M,
+                                                        int64_t N, int64_t j,
+                                                        const HHScal* __restrict__ hs,
+                                                        const double* __restrict__ w,
+                                                        double* __restrict__ R,
+                                                        double* __restrict__ norm_part) {
+  __shared__ double v[RC];
+  __shared__ double red[8];
+  const int64_t c = blockIdx.x + j / RC;
+  const int64_t r_begin = std::max<int64_t>(c * RC, j), r_end = std::min<int64_t>((c + 1) * RC, M);
+  const double scale = hs->scale;
+  for (int64_t i = r_begin + threadIdx.x; i < r_end; i += blockDim.x)
+    v[i - c * RC] = (i == j) ? 1.0 : A[i + j * M] * scale;
+  __syncthreads();
+  const int64_t l0 = j + 1 + (int64_t)blockIdx.y * CG;
+  const int64_t l1 = std::min<int64_t>(l0 + CG, N);
+  double nacc = 0.0;
+  for (int64_t l = l0; l < l1; ++l) {
+    const double wl = w[l];
+    double* col = A + l * M;
+    for (int64_t i = r_begin + threadIdx.x; i < r_end; i += blockDim.x) {
+      const double a = fma(-v[i - c * RC], wl, col[i]);
+      col[i] = a;
+      if (i == j) R[j + l * N] = a;
+      if (l == j + 1 && i >= j + 2) nacc = fma(a, a, nacc);
+    }
+  }
+  if (l0 == j + 1) {  // this column group holds column j+1
+    nacc = block_sum<256>(nacc, red);
+    if (threadIdx.x == 0) norm_part[c] = nacc;
+  }
+}
+
+// ---------------- one-sided Jacobi (Hestenes) with round-robin pairing -----------------
+// One launch per round; each warp rotates one column pair (a, b) of A (rows x ncols,
+// column-major) and the same pair of V (nv x ncols) so that the pair becomes orthogonal.
+// Rotation (Rutishauser): zeta = (beta - alpha) / (2 gamma),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t,
+// [a, b] <- [c a - s b, s a + c b].
+__global__ void __launch_bounds__(256) jacobi_round_kernel(double* __restrict__ A, int64_t rows,
+                                                           int ncols, double* __restrict__ V,
+                                                           int64_t nv, int p, int round,
+                                                           double tol,
+                                                           unsigned* __restrict__ counter) {
+  const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= p / 2) return;
+  int a, b;
+  if (gw == 0) {
+    a = p - 1;
+    b = round;
+  } else {
+    a = (round + gw) % (p - 1);
+    b = (round - gw + (p - 1)) % (p - 1);
+  }
+  if (a > b) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  if (b >= ncols) return;  // dummy player when ncols is odd
+  double* ca = A + (int64_t)a * rows;
+  double* cb = A + (int64_t)b * rows;
+  double al = 0.0, be = 0.0, ga = 0.0;
+  for (int64_t i = lane; i < rows; i += 32) {
+    const double x = ca[i], y = cb[i];
+    al = fma(x, x, al);
+    be = fma(y, y, be);
+    ga = fma(x, y, ga);
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if (!(al > 0.0) || !(be > 0.0) || !(fabs(ga) > tol * sqrt(al) * sqrt(be))) return;
+  const double zeta = (be - al) / (2.0 * ga);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+  for (int64_t i = lane; i < rows; i += 32) {
+    const double x = ca[i], y = cb[i];
+    ca[i] = cs * x - sn * y;
+    cb[i] = sn * x + cs * y;
+  }
+  double* va = V + (int64_t)a * nv;
+  double* vb = V + (int64_t)b * nv;
+  for (int64_t i = lane; i < nv; i += 32) {
+    const double x = va[i], y = vb[i];
+    va[i] = cs * x - sn * y;
+    vb[i] = sn * x + cs * y;
+  }
+  if (lane == 0) atomicAdd(counter, 1u);
+}
+
+__global__ void set_identity_kernel(double* __restrict__ V, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    V[e] = (e % n == e / n) ? 1.0 : 0.0;
+}
+
+// norms[c] = ||A[:, c]||_2, one warp per column
+__global__ void colnorm_kernel(const double* __restrict__ A, int64_t rows, int ncols,
+                               double* __restrict__ norms) {
+  const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= ncols) return;
+  const double* col = A + (int64_t)gw * rows;
+  double acc = 0.0;
+  for (int64_t i = lane; i < rows; i += 32) acc = fma(col[i], col[i], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) norms[gw] = sqrt(acc);
+}
+
+// out[:, q] = in[:, perm[q]] * (scale ? 1/norms[perm[q]] : 1), q < r
+__global__ void gather_cols_kernel(const double* __restrict__ in, int64_t rows,
+                                   const int* __restrict__ perm, int r,
+                                   const double* __restrict__ norms, double* __restrict__ out) {
+  const int64_t total = rows * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows;
+    const int q = (int)(e / rows);
+    const int src = perm[q];
+    double val = in[i + (int64_t)src * rows];
+    if (norms) {
+      const double nr = norms[src];
+      val = nr > 0.0 ? val / nr : 0.0;
+    }
+    out[e] = val;
+  }
+}
+
+__global__ void cast_f32_kernel(const double* __restrict__ in, int64_t n, float* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
+}
+
+__global__ void widen_f32_kernel(const float* __restrict__ in, int64_t n, double* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (double)in[e];
+}
+
+// ---------------- FP64 SIMT GEMM (column-major) -------------------------------------
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    dgemm_kernel(bool tA, bool tB, int64_t M, int64_t N, int64_t K, double alpha,
+                 const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
+                 int64_t ldb, double beta, double* __restrict__ C, int64_t ldc) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tx = threadIdx.x % (BN / TN), ty = threadIdx.x / (BN / TN);
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += NT) {
+      int mm, kk;
+      if (tA) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      double val = 0.0;
+      if (gm < M && gk < K) val = tA ? A[gk + gm * lda] : A[gm + gk * lda];
+      As[kk][mm] = val;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += NT) {
+      int nn, kk;
+      if (tB) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+      const int64_t gn = n0 + nn, gk = k0 + kk;
+      double val = 0.0;
+      if (gn < N && gk < K) val = tB ? B[gn + gk * ldb] : B[gk + gn * ldb];
+      Bs[kk][nn] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t gm = m0 + ty * TM + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gn = n0 + tx * TN + j;
+      if (gn >= N) continue;
+      double* cp = C + gm + gn * ldc;
+      *cp = alpha * acc[i][j] + (beta == 0.0 ? 0.0 : beta * *cp);
+    }
+  }
+}
+
+struct Buf {
+  double* p = nullptr;
+  ~Buf() {
+    if (p) cudaFree(p);
+  }
+  pttk_status alloc(size_t elems) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    if (elems == 0) elems = 1;
+    const cudaError_t e = cudaMalloc(&p, elems * sizeof(double));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return set_error(PTTK_ENOMEM, "device allocation failed in TT-SVD");
+    }
+    return PTTK_OK;
+  }
+};
+
+unsigned grid1d(int64_t work, int threads, int cap_per_sm = 8) {
+  const int64_t b = (work + threads - 1) / threads;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * cap_per_sm));
+}
+
+// R (N x N) of A (M x N, M >= N), A overwritten.
+pttk_status householder_r(double* A, int64_t M, int64_t N, double* R, double* norm_part,
+                          double* w_part, double* w, HHScal* hs, cudaStream_t s) {
+  const int64_t nchunks = (M + RC - 1) / RC;
+  PTTK_PROF("householder", s);
+  PTTK_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * N * N, s));
+  hh_colnorm_kernel<<<(unsigned)nchunks, 256, 0, s>>>(A, M, 0, 1, norm_part);
+  for (int64_t j = 0; j < N; ++j) {
+    hh_scalar_kernel<<<1, 256, 0, s>>>(A, M, N, j, norm_part, nchunks, hs, R);
+    const int64_t trailing = N - j - 1;
+    if (trailing <= 0) break;
+    const unsigned gx = (unsigned)(nchunks - j / RC);
+    const unsigned gy = (unsigned)((trailing + CG - 1) / CG);
+    hh_w_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, hs, w_part);
+    hh_wsum_kernel<<<(unsigned)trailing, 256, 0, s>>>(w_part, N, j, nchunks, hs, w);
+    hh_update_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, hs, w, R, norm_part);
+  }
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
+// One-sided Jacobi on A (rows x ncols) accumulating V (nv x ncols). Synchronises `s` once
+// per sweep to read the rotation count.
+pttk_status jacobi(double* A, int64_t rows, int ncols, double* V, int64_t nv, unsigned* d_counter,
+                   cudaStream_t s) {
+  if (ncols < 2) return PTTK_OK;
+  const int p = ncols + (ncols & 1);
+  const double tol = sqrt((double)rows) * 2.220446049250313e-16;
+  const unsigned blocks = (unsigned)((p / 2 * 32 + 255) / 256);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    PTTK_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s));
+    for (int r = 0; r < p - 1; ++r)
+    {
+      PTTK_PROF("jacobi_round", s);
+      jacobi_round_kernel<<<blocks, 256, 0, s>>>(A, rows, ncols, V, nv, p, r, tol, d_counter);
+    }
+    PTTK_CUDA(cudaGetLastError());
+    unsigned h = 0;
+    PTTK_CUDA(cudaMemcpyAsync(&h, d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PTTK_CUDA(cudaStreamSynchronize(s));
+    if (h == 0) return PTTK_OK;
+  }
+  return set_error(PTTK_ECUDA, "one-sided Jacobi SVD did not converge in 60 sweeps");
+}
+
+// Sorted order of sigma (descending) and the truncation rank for threshold delta.
+int truncation(const std::vector<double>& sigma, double delta, std::vector<int>& perm) {
+  perm.resize(sigma.size());
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return sigma[x] > sigma[y]; });
+  const int m = (int)sigma.size();
+  std::vector<double> tail(m + 1, 0.0);  // tail[r] = sum_{i >= r} sigma_(i)^2
+  for (int i = m - 1; i >= 0; --i) tail[i] = tail[i + 1] + sigma[perm[i]] * sigma[perm[i]];
+  for (int r = 1; r <= m; ++r)
+    if (sqrt(tail[r]) <= delta) return r;
+  return m;
+}
+
+}  // namespace
+
+void dgemm(bool tA, bool tB, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+           int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+           cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  PTTK_PROF("dgemm", s);
+  if (M <= 16) {
+    dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 15) / 16));
+    dgemm_kernel<16, 128, 16, 2, 4><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, B, ldb,
+                                                         beta, C, ldc);
+  } else {
+    dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+    dgemm_kernel<64, 64, 16, 4, 4><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, B, ldb,
+                                                        beta, C, ldc);
+  }
+}
+
+pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
+  const int D = tt->D, n = tt->n;
+  int64_t total = 1;
+  for (int k = 0; k < D; ++k) total *= n;
+
+  // ||C||_F
+  Buf part, scal;
+  const unsigned nb = grid1d(total, 256, 4);
+  PTTK_TRY(part.alloc(nb));
+  PTTK_TRY(scal.alloc(64));
+  sumsq_kernel<<<nb, 256, 0, s>>>(X, total, part.p);
+  sum_kernel<<<1, 256, 0, s>>>(part.p, (int)nb, scal.p);
+  PTTK_CUDA(cudaGetLastError());
+  double sumsq = 0.0;
+  PTTK_CUDA(cudaMemcpyAsync(&sumsq, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  const double delta = tol / sqrt((double)(D - 1)) * sqrt(sumsq);
+
+  Buf W, Xn, R, V, Y, norms, wpart, wv, core_tmp;
+  PTTK_TRY(W.alloc(total));
+  PTTK_TRY(Xn.alloc(total));
+  int* d_perm = nullptr;
+  unsigned* d_counter = nullptr;
+  HHScal* d_hs = nullptr;
+  PTTK_CUDA(cudaMalloc(&d_counter, sizeof(unsigned)));
+  PTTK_CUDA(cudaMalloc(&d_hs, sizeof(HHScal)));
+  struct Guard {
+    int*& a; unsigned*& b; HHScal*& c;
+    ~Guard() { if (a) cudaFree(a); if (b) cudaFree(b); if (c) cudaFree(c); }
+  } guard{d_perm, d_counter, d_hs};
+
+  std::vector<Buf> cores(D);
+  tt->ranks[0] = 1;
+  int64_t r_prev = 1;
+  double* cur = X;
+  double* nxt = Xn.p;
+  int64_t cur_elems = total;
+  for (int k = 0; k < D - 1; ++k) {
+    PTTK_CUDA(cudaStreamSynchronize(s));  // buffers below are reallocated per step
+    const int64_t m = r_prev * n;
+    const int64_t c = cur_elems / m;
+    const bool wide = c >= m;
+    const int64_t q = wide ? m : c;  // size of the square R
+    PTTK_TRY(R.alloc(q * q));
+    PTTK_TRY(V.alloc(q * q));
+    PTTK_TRY(norms.alloc(q));
+    const int64_t Mqr = wide ? c : m;
+    const int64_t nchunks = (Mqr + RC - 1) / RC;
+    PTTK_TRY(part.alloc(nchunks));
+    PTTK_TRY(wpart.alloc(nchunks * q));
+    PTTK_TRY(wv.alloc(q));
+    if (wide) {
+      dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
+      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, W.p);
+    } else {
+      PTTK_CUDA(cudaMemcpyAsync(W.p, cur, sizeof(double) * m * c, cudaMemcpyDeviceToDevice, s));
+    }
+    PTTK_TRY(householder_r(W.p, Mqr, q, R.p, part.p, wpart.p, wv.p, d_hs, s));
+    set_identity_kernel<<<grid1d(q * q, 256), 256, 0, s>>>(V.p, q);
+    PTTK_TRY(jacobi(R.p, q, (int)q, V.p, q, d_counter, s));
+    colnorm_kernel<<<(unsigned)((q * 32 + 255) / 256), 256, 0, s>>>(R.p, q, (int)q, norms.p);
+    std::vector<double> sigma(q);
+    PTTK_CUDA(cudaMemcpyAsync(sigma.data(), norms.p, sizeof(double) * q, cudaMemcpyDeviceToHost, s));
+    PTTK_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> perm;
+    const int r = truncation(sigma, delta, perm);
+    if (d_perm) cudaFree(d_perm);
+    d_perm = nullptr;
+    PTTK_CUDA(cudaMalloc(&d_perm, sizeof(int) * perm.size()));
+    PTTK_CUDA(cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * perm.size(),
+                              cudaMemcpyHostToDevice, s));
+    PTTK_TRY(cores[k].alloc(m * r));
+    if (wide) {
+      // G_k = V[:, top r]
+      gather_cols_kernel<<<grid1d(m * r, 256), 256, 0, s>>>(V.p, m, d_perm, r, nullptr, cores[k].p);
+    } else {
+      // Y = X V[:, top r]; orthogonalise Y's columns; G_k = Y with unit columns
+      PTTK_TRY(core_tmp.alloc(c * r));
+      gather_cols_kernel<<<grid1d(c * r, 256), 256, 0, s>>>(V.p, c, d_perm, r, nullptr, core_tmp.p);
+      PTTK_TRY(Y.alloc(m * r));
+      dgemm(false, false, m, r, c, 1.0, cur, m, core_tmp.p, c, 0.0, Y.p, m, s);
+      Buf V2;
+      PTTK_TRY(V2.alloc((int64_t)r * r));
+      set_identity_kernel<<<grid1d((int64_t)r * r, 256), 256, 0, s>>>(V2.p, r);
+      PTTK_TRY(jacobi(Y.p, m, r, V2.p, r, d_counter, s));
+      Buf ynorm;
+      PTTK_TRY(ynorm.alloc(r));
+      colnorm_kernel<<<(unsigned)(((int64_t)r * 32 + 255) / 256), 256, 0, s>>>(Y.p, m, r, ynorm.p);
+      std::vector<double> yn(r);
+      PTTK_CUDA(cudaMemcpyAsync(yn.data(), ynorm.p, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
+      PTTK_CUDA(cudaStreamSynchronize(s));
+      std::vector<int> yperm;
+      truncation(yn, 0.0, yperm);
+      PTTK_CUDA(cudaMemcpyAsync(d_perm, yperm.data(), sizeof(int) * r, cudaMemcpyHostToDevice, s));
+      gather_cols_kernel<<<grid1d(m * r, 256), 256, 0, s>>>(Y.p, m, d_perm, r, ynorm.p, cores[k].p);
+      PTTK_CUDA(cudaStreamSynchronize(s));
+    }
+    // X <- G_k^T X  (r x c)
+    dgemm(true, false, r, c, m, 1.0, cores[k].p, m, cur, m, 0.0, nxt, r, s);
+    PTTK_CUDA(cudaGetLastError());
+    tt->ranks[k + 1] = r;
+    std::swap(cur, nxt);
+    cur_elems = (int64_t)r * c;
+    r_prev = r;
+  }
+  tt->ranks[D] = 1;
+  // last core: the remainder (r_{D-1} x n)
+  PTTK_TRY(cores[D - 1].alloc(r_prev * n));
+  PTTK_CUDA(cudaMemcpyAsync(cores[D - 1].p, cur, sizeof(double) * r_prev * n,
+                            cudaMemcpyDeviceToDevice, s));
+
+  // pack into the handle
+  size_t off = 0;
+  for (int k = 0; k < D; ++k) {
+    tt->core_off[k] = off;
+    off += tt->core_elems(k);
+  }
+  tt->core_total = off;
+  PTTK_CUDA(cudaMalloc(&tt->cores64, sizeof(double) * off));
+  PTTK_CUDA(cudaMalloc(&tt->cores32, sizeof(float) * off));
+  for (int k = 0; k < D; ++k)
+    PTTK_CUDA(cudaMemcpyAsync(tt->cores64 + tt->core_off[k], cores[k].p,
+                              sizeof(double) * tt->core_elems(k), cudaMemcpyDeviceToDevice, s));
+  cast_f32_kernel<<<grid1d((int64_t)off, 256), 256, 0, s>>>(tt->cores64, (int64_t)off, tt->cores32);
+  PTTK_CUDA(cudaGetLastError());
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  return PTTK_OK;
+}
+
+// FP32 tensor -> FP64 work buffer
+pttk_status widen_to_f64(const float* in, int64_t n, double* out, cudaStream_t s) {
+  widen_f32_kernel<<<grid1d(n, 256), 256, 0, s>>>(in, n, out);
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
+}  // namespace pttk

@@ -1,0 +1,279 @@
+"""Python binding of libpttk (include/pttk.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch tensors to
+device pointers, checks shapes and dtypes, and turns status codes into exceptions.
+It raises if libpttk.so has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpttk.so")
+
+OK, EINVAL, EDOMAIN, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP = range(7)
+STATUS_NAMES = {0: "PTTK_OK", 1: "PTTK_EINVAL", 2: "PTTK_EDOMAIN", 3: "PTTK_ENOMEM",
+                4: "PTTK_ECUDA", 5: "PTTK_ETIMEOUT", 6: "PTTK_ENOTSUP"}
+GAUSS, MATERN32, MATERN_NU = 0, 1, 2
+FP64, FP32, TF32, TF32X3, BF16, BF16X3 = range(6)
+PREC_NAMES = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "tf32x3": TF32X3, "bf16": BF16, "bf16x3": BF16X3}
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+# (name, restype, argtypes) for every entry point of include/pttk.h
+SIGNATURES = [
+    ("pttk_last_error", ctypes.c_char_p, []),
+    ("pttk_version", _int, []),
+    ("pttk_grid_coeffs", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int, _int, _vp, _vp]),
+    ("pttk_tt_from_coeffs", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int,
+                                   ctypes.c_double, _vp, _int, _vp, ctypes.POINTER(_vp)]),
+    ("pttk_build_offline", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int,
+                                  ctypes.c_double, _int, _vp, ctypes.POINTER(_vp)]),
+    ("pttk_tt_dims", _int, [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p]),
+    ("pttk_tt_ranks", _int, [_vp, _c_int_p]),
+    ("pttk_tt_get_core", _int, [_vp, _int, _c_double_p]),
+    ("pttk_tt_save", _int, [_vp, ctypes.c_char_p]),
+    ("pttk_tt_load", _int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
+    ("pttk_tt_free", None, [_vp]),
+    ("pttk_theta_core", _int, [_vp, _c_double_p, _int, _vp, _vp]),
+    ("pttk_instantiate", _int, [_vp, _c_double_p, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp, _vp]),
+    ("pttk_apply", _int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, _vp, _vp, _vp]),
+    ("pttk_profile_enable", _int, [_int]),
+    ("pttk_profile_reset", _int, []),
+    ("pttk_profile_get", _int, [ctypes.c_char_p, _c_double_p, ctypes.POINTER(_i64)]),
+    ("pttk_profile_names", _int, [ctypes.c_char_p, _i64]),
+]
+
+_lib = None
+
+
+class PttkError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libpttk.so (built by paper_2406_06344_gb300._build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2406_06344_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise PttkError(status, load().pttk_last_error().decode())
+
+
+def _dbl(values: Sequence[float]):
+    arr = (ctypes.c_double * max(1, len(values)))(*[float(v) for v in values])
+    return arr
+
+
+def _boxflat(box) -> list:
+    return [float(v) for pair in box for v in pair]
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _prec(p) -> int:
+    return PREC_NAMES[p] if isinstance(p, str) else int(p)
+
+
+def _dtype(prec: int):
+    import torch
+    return torch.float64 if prec == FP64 else torch.float32
+
+
+def grid_coeffs(kernel: int, d: int, src_box, tgt_box, dtheta: int, theta_box, n: int,
+                prec="fp64", out=None, stream=None):
+    """pttk_grid_coeffs: coefficient tensor C (n^D, column-major) on the current device.
+    Returned as a 1-D tensor of n^D entries."""
+    import torch
+    prec = _prec(prec)
+    D = 2 * d + dtheta
+    if out is None:
+        out = torch.empty(n ** D, dtype=_dtype(prec), device="cuda")
+    _check(load().pttk_grid_coeffs(kernel, d, _dbl(_boxflat(src_box)), _dbl(_boxflat(tgt_box)), dtheta,
+                                   _dbl(_boxflat(theta_box)), n, prec, _ptr(out), _stream(stream)))
+    return out
+
+
+class TT:
+    """Owns a pttk_tt handle (TT cores on the device)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("TT handle already freed")
+        return self._h
+
+    @classmethod
+    def build_offline(cls, kernel: int, d: int, src_box, tgt_box, dtheta: int, theta_box, n: int,
+                      tol: float, grid_prec="fp64", stream=None) -> "TT":
+        h = ctypes.c_void_p()
+        _check(load().pttk_build_offline(kernel, d, _dbl(_boxflat(src_box)), _dbl(_boxflat(tgt_box)),
+                                         dtheta, _dbl(_boxflat(theta_box)), n, tol, _prec(grid_prec),
+                                         _stream(stream), ctypes.byref(h)))
+        return cls(h.value)
+
+    @classmethod
+    def from_coeffs(cls, kernel: int, d: int, src_box, tgt_box, dtheta: int, theta_box, n: int,
+                    tol: float, C, stream=None) -> "TT":
+        import torch
+        prec = FP64 if C.dtype == torch.float64 else FP32
+        h = ctypes.c_void_p()
+        _check(load().pttk_tt_from_coeffs(kernel, d, _dbl(_boxflat(src_box)), _dbl(_boxflat(tgt_box)),
+                                          dtheta, _dbl(_boxflat(theta_box)), n, tol, _ptr(C), prec,
+                                          _stream(stream), ctypes.byref(h)))
+        return cls(h.value)
+
+    @classmethod
+    def load(cls, path: str) -> "TT":
+        h = ctypes.c_void_p()
+        _check(load().pttk_tt_load(path.encode(), ctypes.byref(h)))
+        return cls(h.value)
+
+    def save(self, path: str):
+        _check(load().pttk_tt_save(self.handle, path.encode()))
+
+    @property
+    def dims(self):
+        d, dth, n, k = _int(), _int(), _int(), _int()
+        _check(load().pttk_tt_dims(self.handle, ctypes.byref(d), ctypes.byref(dth), ctypes.byref(n),
+                                   ctypes.byref(k)))
+        return d.value, dth.value, n.value, k.value
+
+    @property
+    def ranks(self) -> list:
+        d, dth, _, _ = self.dims
+        arr = (_int * (2 * d + dth + 1))()
+        _check(load().pttk_tt_ranks(self.handle, arr))
+        return list(arr)
+
+    def core(self, k: int) -> np.ndarray:
+        """Core k as a (r_{k-1}, n, r_k) FP64 numpy array (copied from the device)."""
+        r = self.ranks
+        n = self.dims[2]
+        buf = np.empty(r[k] * n * r[k + 1], dtype=np.float64)
+        _check(load().pttk_tt_get_core(self.handle, k, buf.ctypes.data_as(_c_double_p)))
+        return buf.reshape(r[k], n, r[k + 1], order="F")
+
+    def cores(self) -> list:
+        d, dth, _, _ = self.dims
+        return [self.core(k) for k in range(2 * d + dth)]
+
+    def free(self):
+        if self._h:
+            load().pttk_tt_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def theta_core(tt: TT, theta, prec="fp64", M=None, stream=None):
+    import torch
+    prec = _prec(prec)
+    r = tt.ranks
+    d, dth, _, _ = tt.dims
+    if M is None:
+        M = torch.empty(r[d], r[d + dth], dtype=_dtype(prec), device="cuda")
+    _check(load().pttk_theta_core(tt.handle, _dbl(theta), prec, _ptr(M), _stream(stream)))
+    return M
+
+
+def instantiate(tt: TT, theta, X, Y, prec="fp64", U=None, M=None, V=None, stream=None):
+    """pttk_instantiate: returns (U, M, V) with K(X, Y; theta) ~= U M V^T."""
+    import torch
+    prec = _prec(prec)
+    dt = _dtype(prec)
+    r = tt.ranks
+    d, dth, _, _ = tt.dims
+    for P in (X, Y):
+        if P.dtype != dt or P.dim() != 2 or P.shape[1] != d:
+            raise ValueError(f"points must be (N, {d}) {dt}")
+    if U is None:
+        U = torch.empty(X.shape[0], r[d], dtype=dt, device="cuda")
+    if M is None:
+        M = torch.empty(r[d], r[d + dth], dtype=dt, device="cuda")
+    if V is None:
+        V = torch.empty(Y.shape[0], r[d + dth], dtype=dt, device="cuda")
+    _check(load().pttk_instantiate(tt.handle, _dbl(theta), _ptr(X), X.shape[0], _ptr(Y), Y.shape[0],
+                                   prec, _ptr(U), _ptr(M), _ptr(V), _stream(stream)))
+    return U, M, V
+
+
+def apply(U, M, V, w, out=None, stream=None):
+    """pttk_apply: out = U (M (V^T w))."""
+    import torch
+    prec = FP64 if U.dtype == torch.float64 else FP32
+    if out is None:
+        out = torch.empty(U.shape[0], dtype=U.dtype, device="cuda")
+    _check(load().pttk_apply(_ptr(U), _ptr(M), _ptr(V), U.shape[0], V.shape[0], U.shape[1], V.shape[1],
+                             prec, _ptr(w), _ptr(out), _stream(stream)))
+    return out
+
+
+def profile_enable(on: bool = True):
+    _check(load().pttk_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(load().pttk_profile_reset())
+
+
+def profile_get(name: str):
+    """(total ms, launches) accumulated for a library kernel since the last reset."""
+    ms, n = ctypes.c_double(), _i64()
+    _check(load().pttk_profile_get(name.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def profile_names() -> list:
+    buf = ctypes.create_string_buffer(4096)
+    _check(load().pttk_profile_names(buf, 4096))
+    return [s for s in buf.value.decode().split("\n") if s]

@@ -1,0 +1,107 @@
+"""The C-ABI library: loads, exports every declared entry point, and rejects bad
+arguments on the host (no GPU work is issued by these calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pttk.h")
+
+
+@pytest.fixture(scope="module")
+def so():
+    from paper_2406_06344_gb300 import _build, pttk
+    if not os.path.exists(pttk.LIB_PATH):
+        _build.build()
+    return pttk.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pttk_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("pttk_grid_coeffs", "pttk_tt_from_coeffs", "pttk_build_offline", "pttk_tt_ranks",
+                 "pttk_tt_save", "pttk_tt_load", "pttk_tt_free", "pttk_theta_core", "pttk_instantiate",
+                 "pttk_apply", "pttk_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(so):
+    for name in declared_symbols():
+        assert hasattr(so, name), name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2406_06344_gb300 import pttk
+    bound = {name for name, _, _ in pttk.SIGNATURES}
+    assert set(declared_symbols()) <= bound
+
+
+def test_version(so):
+    assert so.pttk_version() >= 100
+
+
+def _boxes():
+    from paper_2406_06344_gb300 import pttk
+    dbl = pttk._dbl
+    return dbl([0, 1]), dbl([2, 3]), dbl([0.5, 2.0])
+
+
+@pytest.mark.parametrize("kernel,d,dth,n,expect", [
+    (7, 1, 1, 16, "unknown kernel"),
+    (0, 0, 1, 16, "d must be"),
+    (0, 4, 1, 16, "d must be"),
+    (0, 1, 2, 16, "d_theta = 1"),
+    (2, 1, 1, 16, "d_theta = 2"),
+    (0, 1, 1, 1, "n must be"),
+    (0, 1, 1, 33, "n must be"),
+])
+def test_invalid_problem_is_rejected(so, kernel, d, dth, n, expect):
+    from paper_2406_06344_gb300 import pttk
+    s, t, p = _boxes()
+    if dth == 2:
+        p = pttk._dbl([0.5, 2.0, 0.5, 2.5])
+    h = ctypes.c_void_p()
+    st = so.pttk_build_offline(kernel, d, s, t, dth, p, n, 1e-10, 0, None, ctypes.byref(h))
+    assert st == pttk.EINVAL
+    assert expect in so.pttk_last_error().decode()
+    assert not h.value
+
+
+def test_bad_box_and_tol_are_rejected(so):
+    from paper_2406_06344_gb300 import pttk
+    h = ctypes.c_void_p()
+    st = so.pttk_build_offline(0, 1, pttk._dbl([1, 0]), pttk._dbl([2, 3]), 1, pttk._dbl([0.5, 2]), 8,
+                               1e-10, 0, None, ctypes.byref(h))
+    assert st == pttk.EINVAL and "lo >= hi" in so.pttk_last_error().decode()
+    s, t, p = _boxes()
+    st = so.pttk_build_offline(0, 1, s, t, 1, p, 8, 0.0, 0, None, ctypes.byref(h))
+    assert st == pttk.EINVAL and "tol" in so.pttk_last_error().decode()
+    st = so.pttk_build_offline(0, 1, s, t, 1, p, 8, 1e-10, 4, None, ctypes.byref(h))
+    assert st == pttk.EINVAL and "precision" in so.pttk_last_error().decode()
+    st = so.pttk_grid_coeffs(0, 1, s, t, 1, p, 8, 0, None, None)
+    assert st == pttk.EINVAL and "NULL" in so.pttk_last_error().decode()
+
+
+def test_null_handles_are_rejected(so):
+    from paper_2406_06344_gb300 import pttk
+    ranks = (ctypes.c_int * 4)()
+    assert so.pttk_tt_ranks(None, ranks) == pttk.EINVAL
+    assert so.pttk_instantiate(None, None, None, 0, None, 0, 0, None, None, None, None) == pttk.EINVAL
+    assert so.pttk_apply(None, None, None, 1, 1, 1, 1, 0, None, None, None) == pttk.EINVAL
+    so.pttk_tt_free(None)  # no-op
+
+
+def test_load_rejects_garbage(so, tmp_path):
+    from paper_2406_06344_gb300 import pttk
+    p = tmp_path / "bad.tt"
+    p.write_bytes(b"not a tensor train")
+    h = ctypes.c_void_p()
+    assert so.pttk_tt_load(str(p).encode(), ctypes.byref(h)) == pttk.EINVAL
+    assert so.pttk_tt_load(str(tmp_path / "missing.tt").encode(), ctypes.byref(h)) == pttk.EINVAL
