@@ -168,6 +168,24 @@ pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void*
 pttk_status pttk_apply(const void* U, const void* M, const void* V, int64_t N_s, int64_t N_t,
                        int rs, int rt, pttk_prec prec, const void* w, void* out, void* stream);
 
+/* The same product as pttk_apply, for callers that cannot allocate device memory once
+ * they are running, e.g. a process whose device memory is entirely reserved by another
+ * allocator (a framework's caching pool), or a latency-bound loop in which cudaMalloc or
+ * cudaFree could stall or fail under memory pressure. This call allocates nothing: its
+ * scratch (the per-block partial sums of V^T w and the vector M (V^T w)) is a 1 MiB
+ * file-scope device array inside libpttk, held by every device that loads the library until
+ * the process exits. The paper has no counterpart; arguments and results are those of
+ * pttk_apply, and it uses fewer partial-sum blocks when they would not fit.
+ *   Limit: rs + rt <= 131072 (FP64) or 262144 (FP32); larger ranks give PTTK_EINVAL.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ *   All calls share the one array, which keeps the last call's contents: calls whose work
+ *   overlaps on the GPU (on different streams, or from different threads) race, so
+ *   serialise them. */
+pttk_status pttk_apply_noalloc(const void* U, const void* M, const void* V, int64_t N_s,
+                               int64_t N_t, int rs, int rt, pttk_prec prec, const void* w,
+                               void* out, void* stream);
+
 /* ---- kernel timing ------------------------------------------------------------------ */
 
 /* When enabled, every launch of the library's timed kernels is bracketed by two CUDA

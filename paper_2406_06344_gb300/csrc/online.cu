@@ -12,7 +12,10 @@
 // A[p, a + R_in j] = B[p, j] S_in[p, a] is generated in shared memory, never stored.
 #include <math.h>
 
+#include <stdio.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "pttk_internal.cuh"
 
@@ -409,3 +412,71 @@ pttk_status apply_run(const void* U, const void* M, const void* V, int64_t N_s, 
 }
 
 }  // namespace pttk
+
+// ---------------- apply without device allocation ---------------------------------------
+// pttk_apply_noalloc runs the same kernels as pttk_apply, with its scratch (the per-block
+// partial sums of V^T w and the vector M (V^T w)) in this file-scope device array instead of
+// a stream-ordered allocation. Every device that loads the library holds the array until the
+// process exits. All calls share it, so calls whose work overlaps on the GPU race.
+namespace pttk {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 1u << 20;  // 1 MiB
+static __device__ __align__(256) unsigned char g_apply_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mu;
+void* g_scratch_dev[64] = {nullptr};
+
+// Device address of g_apply_scratch on the current device, looked up once per device.
+// In host code the symbol name is only a host-side stand-in, never a device address.
+pttk_status scratch_address(void** out) {
+  int dev = 0;
+  PTTK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(PTTK_EINVAL, "device ordinal above 63");
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_dev[dev]) {
+    void* p = nullptr;
+    PTTK_CUDA(cudaGetSymbolAddress(&p, g_apply_scratch));
+    g_scratch_dev[dev] = p;
+  }
+  *out = g_scratch_dev[dev];
+  return PTTK_OK;
+}
+
+}  // namespace
+}  // namespace pttk
+
+extern "C" pttk_status pttk_apply_noalloc(const void* U, const void* M, const void* V, int64_t N_s,
+                                          int64_t N_t, int rs, int rt, pttk_prec prec, const void* w,
+                                          void* out, void* stream) {
+  using namespace pttk;
+  clear_error();
+  if (!M || (N_s > 0 && (!U || !out)) || (N_t > 0 && (!V || !w))) return set_error(PTTK_EINVAL, "NULL argument");
+  if (N_s < 0 || N_t < 0 || rs < 1 || rt < 1) return set_error(PTTK_EINVAL, "bad size");
+  if (prec != PTTK_FP64 && prec != PTTK_FP32) return set_error(PTTK_EINVAL, "apply precision must be FP64 or FP32");
+  const bool fp64 = prec == PTTK_FP64;
+  const size_t elem = fp64 ? 8 : 4;
+  const size_t cap = kNoAllocScratchBytes / elem;
+  if ((size_t)rs + (size_t)rt > cap) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "pttk_apply_noalloc: rs + rt = %lld exceeds its fixed scratch of %zu %s elements",
+             (long long)rs + rt, cap, fp64 ? "FP64" : "FP32");
+    return set_error(PTTK_EINVAL, buf);
+  }
+  void* scratch = nullptr;
+  PTTK_TRY(scratch_address(&scratch));
+  // as many partial-sum blocks as pttk_apply uses, fewer if they would not fit
+  const int nparts = (int)std::max<int64_t>(
+      1, std::min<int64_t>(apply_parts(N_t), (int64_t)((cap - (size_t)rs) / (size_t)rt)));
+  cudaStream_t s = as_stream(stream);
+  if (fp64)
+    return apply_typed<double>(static_cast<const double*>(U), static_cast<const double*>(M),
+                               static_cast<const double*>(V), N_s, N_t, rs, rt,
+                               static_cast<const double*>(w), static_cast<double*>(out),
+                               static_cast<double*>(scratch), nparts, s);
+  return apply_typed<float>(static_cast<const float*>(U), static_cast<const float*>(M),
+                            static_cast<const float*>(V), N_s, N_t, rs, rt,
+                            static_cast<const float*>(w), static_cast<float*>(out),
+                            static_cast<float*>(scratch), nparts, s);
+}

@@ -46,6 +46,7 @@ SIGNATURES = [
     ("pttk_theta_core", _int, [_vp, _c_double_p, _int, _vp, _vp]),
     ("pttk_instantiate", _int, [_vp, _c_double_p, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp, _vp]),
     ("pttk_apply", _int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, _vp, _vp, _vp]),
+    ("pttk_apply_noalloc", _int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, _vp, _vp, _vp]),
     ("pttk_profile_enable", _int, [_int]),
     ("pttk_profile_reset", _int, []),
     ("pttk_profile_get", _int, [ctypes.c_char_p, _c_double_p, ctypes.POINTER(_i64)]),
@@ -255,6 +256,15 @@ def apply(U, M, V, w, out=None, stream=None):
         out = torch.empty(U.shape[0], dtype=U.dtype, device="cuda")
     _check(load().pttk_apply(_ptr(U), _ptr(M), _ptr(V), U.shape[0], V.shape[0], U.shape[1], V.shape[1],
                              prec, _ptr(w), _ptr(out), _stream(stream)))
+    return out
+
+
+def apply_noalloc(U, M, V, w, out, stream=None):
+    """pttk_apply_noalloc: out = U (M (V^T w)) with no device allocation (fixed library scratch)."""
+    import torch
+    prec = FP64 if U.dtype == torch.float64 else FP32
+    _check(load().pttk_apply_noalloc(_ptr(U), _ptr(M), _ptr(V), U.shape[0], V.shape[0], U.shape[1],
+                                     V.shape[1], prec, _ptr(w), _ptr(out), _stream(stream)))
     return out
 
 
