@@ -37,7 +37,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "online factor builds/s (N=1M) & grid entries/s vs FP64 plain at stated rel err"
 UNIT = "builds/s"
-FAST_FORM = "fp32"
+FAST_FORM = "tf32x3"
+OTHER_FORMS = ("fp64", "fp32", "tf32", "bf16", "bf16x3")
 N_THETA = 256
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12   # FFMA lanes/SM x 2 flops x SMs x max clock
 FP64_PEAK_TFLOPS = 1.25                             # nominal FP64 rate of the part
@@ -243,17 +244,26 @@ def main():
         e5 = ev()
         out = P.apply(U, M, V, wv)
         e6 = ev()
-        flush.zero_()
+        form_ms = {}
         e7 = ev()
-        P.instantiate(tt, thetas[0], X64, Y64, "fp64", U=state["U64"], M=state["M64"], V=state["V64"])
+        for form in OTHER_FORMS:
+            flush.zero_()
+            fa = ev()
+            if form == "fp64":
+                P.instantiate(tt, thetas[0], X64, Y64, "fp64", U=state["U64"], M=state["M64"], V=state["V64"])
+            else:
+                P.instantiate(tt, thetas[0], X32, Y32, form, U=U, M=M, V=V)
+            form_ms[form] = (fa, ev())
         e8 = ev()
+        tt.check()
         torch.cuda.synchronize()
+        r["form_ms"] = {k: a.elapsed_time(b) for k, (a, b) in form_ms.items()}
         r["grid64_ms"] = e0.elapsed_time(e1)
         r["grid32_ms"] = e1.elapsed_time(e2)
         r["ttsvd_ms"] = e2.elapsed_time(e3)
         r["inst_ms"] = e4.elapsed_time(e5)
         r["apply_ms"] = e5.elapsed_time(e6)
-        r["inst64_ms"] = e7.elapsed_time(e8)
+        r["inst64_ms"] = r["form_ms"]["fp64"]
         r["step_ms"] = e0.elapsed_time(e8)
         r["ranks"] = ranks
         state["tt"] = tt
@@ -293,7 +303,7 @@ def main():
     # roofline of the dominant kernel of the step (largest share of device time)
     hbm, bf16, src = peaks()
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
-    chain_ms, chain_launches = prof.get("chain", (0.0, 0))
+    chain_ms, chain_launches = prof.get("chain_tc", (0.0, 0))
     flops_build = chain_flops(ranks, w.d, w.dtheta, w.n, N)
     # one chain launch builds one side; average flops per launch over the fast and fp64 builds
     launches_fast = 2 * args.n_theta * args.steps
@@ -367,6 +377,8 @@ def main():
             "grid_entries_per_s": {"fp64": total * args.steps * world / (g64_max / 1000.0),
                                    "fp32": total * args.steps * world / (g32_max / 1000.0)},
             "fp64_plain_builds_per_s": args.steps * world / (tot("inst64_ms") / 1000.0),
+            "builds_per_s_by_form": dict({FAST_FORM: value}, **{
+                f: args.steps * world / (sum(r["form_ms"][f] for r in results) / 1000.0) for f in OTHER_FORMS}),
             "stage_ms_per_step": {k: tot(k) / args.steps for k in
                                   ("grid64_ms", "grid32_ms", "ttsvd_ms", "inst_ms", "apply_ms", "inst64_ms")},
             "roofline": roof if roof else chain_roof,

@@ -149,6 +149,12 @@ void pttk_tt_free(pttk_tt* tt);
 pttk_status pttk_theta_core(const pttk_tt* tt, const double* theta, pttk_prec prec, void* M,
                             void* stream);
 
+/* Synchronise `stream` and report the handle's device status word: PTTK_ETIMEOUT if a kernel
+ * working with this handle gave up a bounded wait since the last check (the word is then
+ * cleared), else PTTK_OK. The tensor-core factor chain records such timeouts instead of
+ * spinning; its outputs are unspecified when it does. */
+pttk_status pttk_tt_check(const pttk_tt* tt, void* stream);
+
 /* Online instantiation: M = H(theta) as above, and the factor matrices of Algorithm 2,
  * Phase 3 for the given points: U = S(X) (N_s x r_d) by S <- B_1 G_1^{2},
  * S <- (B_i face-split S) G_i^{2}; V = T(Y) (N_t x r_{d+d_theta}) by the mirrored
@@ -156,7 +162,12 @@ pttk_status pttk_theta_core(const pttk_tt* tt, const double* theta, pttk_prec pr
  *   X: dev N_s x d, Y: dev N_t x d (double for PTTK_FP64, float otherwise); points are
  *   expected inside their boxes (a point outside is extrapolated, not rejected).
  *   N_s, N_t >= 0 (0 is allowed and writes nothing for that side).
- *   U, M, V: dev outputs (double for PTTK_FP64, float otherwise). */
+ *   U, M, V: dev outputs (double for PTTK_FP64, float otherwise).
+ *   prec: PTTK_FP64 / PTTK_FP32 run the SIMT chain; PTTK_TF32, PTTK_TF32X3, PTTK_BF16 and
+ *   PTTK_BF16X3 run the tensor-core chain (tcgen05, FP32 accumulation; TMEM accumulator of
+ *   128 points x N_pad columns), which needs every TT rank it touches <= 256 and, on first
+ *   use of a form with a handle, lays out that form's core images on the device
+ *   (synchronising `stream` once). Check pttk_tt_check after tensor-core calls. */
 pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void* X,
                              int64_t N_s, const void* Y, int64_t N_t, pttk_prec prec, void* U,
                              void* M, void* V, void* stream);

@@ -59,6 +59,8 @@ __global__ void orient_kernel(const double* __restrict__ G, int ra, int n, int r
 struct pttk_tt_ext : pttk_tt {
   double* tgt64 = nullptr;
   float* tgt32 = nullptr;
+  pttk::TcImageCache* tc = nullptr;  // tensor-core core images, built on first use per form
+  int* dstatus = nullptr;            // device status word (bounded waits that ran out)
 };
 
 namespace pttk {
@@ -70,6 +72,9 @@ const void* oriented_core_ptr(const pttk_tt* tt, bool source, int k, bool fp64) 
 }
 
 static pttk_status prepare_oriented(pttk_tt_ext* t, cudaStream_t s) {
+  t->tc = tc_cache_new();
+  PTTK_CUDA(cudaMalloc(&t->dstatus, sizeof(int)));
+  PTTK_CUDA(cudaMemsetAsync(t->dstatus, 0, sizeof(int), s));
   PTTK_CUDA(cudaMalloc(&t->tgt64, sizeof(double) * std::max<size_t>(t->core_total, 1)));
   PTTK_CUDA(cudaMalloc(&t->tgt32, sizeof(float) * std::max<size_t>(t->core_total, 1)));
   for (int k = t->d + t->dtheta; k < t->D; ++k) {
@@ -89,6 +94,8 @@ static void free_handle(pttk_tt_ext* t) {
   if (t->cores32) cudaFree(t->cores32);
   if (t->tgt64) cudaFree(t->tgt64);
   if (t->tgt32) cudaFree(t->tgt32);
+  if (t->dstatus) cudaFree(t->dstatus);
+  tc_cache_free(t->tc);
   delete t;
 }
 
@@ -401,14 +408,36 @@ pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void*
   if (!tt || !M) return set_error(PTTK_EINVAL, "NULL argument");
   if (N_s < 0 || N_t < 0) return set_error(PTTK_EINVAL, "negative point count");
   if ((N_s > 0 && (!X || !U)) || (N_t > 0 && (!Y || !V))) return set_error(PTTK_EINVAL, "NULL point or factor buffer");
-  if (prec != PTTK_FP64 && prec != PTTK_FP32)
-    return set_error(PTTK_ENOTSUP, "precision not available for pttk_instantiate");
+  if (prec < PTTK_FP64 || prec > PTTK_BF16X3) return set_error(PTTK_EINVAL, "unknown precision");
   double th[PTTK_MAX_D];
   PTTK_TRY(theta_hat(tt, theta, th));
   cudaStream_t s = as_stream(stream);
   PTTK_TRY(theta_core_run(tt, th, prec == PTTK_FP64, M, s));
-  PTTK_TRY(factor_build_run(tt, true, X, N_s, prec, U, s));
-  PTTK_TRY(factor_build_run(tt, false, Y, N_t, prec, V, s));
+  if (prec == PTTK_FP64 || prec == PTTK_FP32) {
+    PTTK_TRY(factor_build_run(tt, true, X, N_s, prec, U, s));
+    PTTK_TRY(factor_build_run(tt, false, Y, N_t, prec, V, s));
+    return PTTK_OK;
+  }
+  const pttk_tt_ext* t = static_cast<const pttk_tt_ext*>(tt);
+  PTTK_TRY(factor_build_tc(tt, t->tc, true, static_cast<const float*>(X), N_s, prec, static_cast<float*>(U),
+                           t->dstatus, s));
+  PTTK_TRY(factor_build_tc(tt, t->tc, false, static_cast<const float*>(Y), N_t, prec, static_cast<float*>(V),
+                           t->dstatus, s));
+  return PTTK_OK;
+}
+
+pttk_status pttk_tt_check(const pttk_tt* tt, void* stream) {
+  clear_error();
+  if (!tt) return set_error(PTTK_EINVAL, "NULL handle");
+  const pttk_tt_ext* t = static_cast<const pttk_tt_ext*>(tt);
+  cudaStream_t s = as_stream(stream);
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  int h = 0;
+  PTTK_CUDA(cudaMemcpy(&h, t->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    PTTK_CUDA(cudaMemset(t->dstatus, 0, sizeof(int)));
+    return set_error((pttk_status)h, "a bounded device-side wait ran out in a kernel using this handle");
+  }
   return PTTK_OK;
 }
 

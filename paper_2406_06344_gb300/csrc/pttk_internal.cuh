@@ -78,6 +78,13 @@ void dgemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alp
            const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
            int64_t ldc, cudaStream_t s);
 
+// --- chain_tc.cu (tensor-core factor chain) ------------------------------------------
+struct TcImageCache;
+TcImageCache* tc_cache_new();
+void tc_cache_free(TcImageCache* c);
+pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, bool source, const float* P,
+                            int64_t N, pttk_prec prec, float* out, int* d_status, cudaStream_t s);
+
 // --- online.cu -------------------------------------------------------------------------
 pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64, void* M,
                            cudaStream_t s);

@@ -44,6 +44,7 @@ SIGNATURES = [
     ("pttk_tt_load", _int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
     ("pttk_tt_free", None, [_vp]),
     ("pttk_theta_core", _int, [_vp, _c_double_p, _int, _vp, _vp]),
+    ("pttk_tt_check", _int, [_vp, _vp]),
     ("pttk_instantiate", _int, [_vp, _c_double_p, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp, _vp]),
     ("pttk_apply", _int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, _vp, _vp, _vp]),
     ("pttk_apply_noalloc", _int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, _vp, _vp, _vp]),
@@ -203,6 +204,10 @@ class TT:
     def cores(self) -> list:
         d, dth, _, _ = self.dims
         return [self.core(k) for k in range(2 * d + dth)]
+
+    def check(self, stream=None):
+        """pttk_tt_check: synchronise and raise if a bounded device wait ran out."""
+        _check(load().pttk_tt_check(self.handle, _stream(stream)))
 
     def free(self):
         if self._h:
