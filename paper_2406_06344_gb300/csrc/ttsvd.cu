@@ -18,6 +18,8 @@
 // Every kernel is launched as a sequence of independent grids; no kernel waits on another
 // CTA, so nothing here can spin.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <numeric>
@@ -71,14 +73,15 @@ __global__ void sum_kernel(const double* __restrict__ partial, int np, double* _
   if (threadIdx.x == 0) *out = acc;
 }
 
-// W (c x m, column-major) = X^T, X m x c column-major
+// W (c x m, column-major) = (P X)^T for X m x c column-major, where row i of P X is row
+// rowperm[i] of X (rowperm may be null: identity)
 __global__ void transpose_kernel(const double* __restrict__ X, int64_t m, int64_t c,
-                                 double* __restrict__ W) {
+                                 const int* __restrict__ rowperm, double* __restrict__ W) {
   __shared__ double t[32][33];
   const int64_t c0 = (int64_t)blockIdx.x * 32, m0 = (int64_t)blockIdx.y * 32;
   for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
     const int64_t row = m0 + threadIdx.x, col = c0 + yy;
-    if (row < m && col < c) t[yy][threadIdx.x] = X[row + col * m];
+    if (row < m && col < c) t[yy][threadIdx.x] = X[(rowperm ? rowperm[row] : row) + col * m];
   }
   __syncthreads();
   for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
@@ -206,14 +209,24 @@ __global__ void __launch_bounds__(256) hh_update_kernel(double* __restrict__ A, 
 
 // ---------------- one-sided Jacobi (Hestenes) with round-robin pairing -----------------
 // One launch per round; each warp rotates one column pair (a, b) of A (rows x ncols,
-// column-major) and the same pair of V (nv x ncols) so that the pair becomes orthogonal.
-// Rotation (Rutishauser): zeta = (beta - alpha) / (2 gamma),
+// column-major) and, if V is given, the same pair of V (nv x ncols) so that the pair becomes
+// orthogonal. Rotation (Rutishauser): zeta = (beta - alpha) / (2 gamma),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t,
 // [a, b] <- [c a - s b, s a + c b].
+// colsq[] holds every column's squared norm (refreshed for the two columns of each
+// rotation). A pair whose squared norms are both below `small2` is skipped without being
+// read, and a rotation counts toward convergence only if it moves a column of squared norm
+// >= `count2` by more than rounding (a rotation of a large column with a far smaller one
+// changes only the smaller). The sweeps end when no such rotation is left. With
+// small2 = (1e-3 delta)^2 / q and count2 = (1e-2 delta)^2 / q the columns left unsettled carry
+// < 1e-4 delta^2 in total, so they change neither the kept subspace nor, except within that
+// margin of the threshold, the truncation rank.
 __global__ void __launch_bounds__(256) jacobi_round_kernel(double* __restrict__ A, int64_t rows,
                                                            int ncols, double* __restrict__ V,
                                                            int64_t nv, int p, int round,
-                                                           double tol,
+                                                           double tol, double small2,
+                                                           double count2,
+                                                           double* __restrict__ colsq,
                                                            unsigned* __restrict__ counter) {
   const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -232,6 +245,7 @@ __global__ void __launch_bounds__(256) jacobi_round_kernel(double* __restrict__ 
     b = t;
   }
   if (b >= ncols) return;  // dummy player when ncols is odd
+  if (colsq[a] < small2 && colsq[b] < small2) return;
   double* ca = A + (int64_t)a * rows;
   double* cb = A + (int64_t)b * rows;
   double al = 0.0, be = 0.0, ga = 0.0;
@@ -248,19 +262,47 @@ __global__ void __launch_bounds__(256) jacobi_round_kernel(double* __restrict__ 
   const double zeta = (be - al) / (2.0 * ga);
   const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
   const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+  double na = 0.0, nb = 0.0;
   for (int64_t i = lane; i < rows; i += 32) {
     const double x = ca[i], y = cb[i];
-    ca[i] = cs * x - sn * y;
-    cb[i] = sn * x + cs * y;
+    const double xa = cs * x - sn * y, yb = sn * x + cs * y;
+    ca[i] = xa;
+    cb[i] = yb;
+    na = fma(xa, xa, na);
+    nb = fma(yb, yb, nb);
   }
-  double* va = V + (int64_t)a * nv;
-  double* vb = V + (int64_t)b * nv;
-  for (int64_t i = lane; i < nv; i += 32) {
-    const double x = va[i], y = vb[i];
-    va[i] = cs * x - sn * y;
-    vb[i] = sn * x + cs * y;
+  na = warp_sum(na);
+  nb = warp_sum(nb);
+  if (V) {
+    double* va = V + (int64_t)a * nv;
+    double* vb = V + (int64_t)b * nv;
+    for (int64_t i = lane; i < nv; i += 32) {
+      const double x = va[i], y = vb[i];
+      va[i] = cs * x - sn * y;
+      vb[i] = sn * x + cs * y;
+    }
   }
-  if (lane == 0) atomicAdd(counter, 1u);
+  if (lane == 0) {
+    colsq[a] = na;
+    colsq[b] = nb;
+    // the rotation counts toward convergence if it moved a column of squared norm >= count2
+    // by more than rounding: column a changes by ~|t| ||b||, column b by ~|t| ||a||
+    const double move_a = al >= count2 ? fabs(t) * sqrt(be / al) : 0.0;
+    const double move_b = be >= count2 ? fabs(t) * sqrt(al / be) : 0.0;
+    if (fmax(move_a, move_b) > 4.0 * 2.220446049250313e-16) atomicAdd(counter, 1u);
+  }
+}
+
+__global__ void colsq_init_kernel(const double* __restrict__ A, int64_t rows, int ncols,
+                                  double* __restrict__ colsq) {
+  const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= ncols) return;
+  const double* col = A + (int64_t)gw * rows;
+  double acc = 0.0;
+  for (int64_t i = lane; i < rows; i += 32) acc = fma(col[i], col[i], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) colsq[gw] = acc;
 }
 
 __global__ void set_identity_kernel(double* __restrict__ V, int64_t n) {
@@ -298,6 +340,41 @@ __global__ void gather_cols_kernel(const double* __restrict__ in, int64_t rows,
       val = nr > 0.0 ? val / nr : 0.0;
     }
     out[e] = val;
+  }
+}
+
+// Column sums of squares of A (rows x ncols, column-major) in two deterministic levels:
+// partial[col * nsplit + split] over a contiguous slice of the column, then a fixed-order sum.
+__global__ void __launch_bounds__(256) colsq_partial_kernel(const double* __restrict__ A, int64_t rows,
+                                                            int nsplit, double* __restrict__ partial) {
+  __shared__ double red[8];
+  const int64_t col = blockIdx.y;
+  const int64_t per = (rows + nsplit - 1) / nsplit;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = std::min<int64_t>(rows, r0 + per);
+  const double* a = A + col * rows;
+  double acc = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) acc = fma(a[i], a[i], acc);
+  acc = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) partial[col * nsplit + blockIdx.x] = acc;
+}
+
+__global__ void colsq_final_kernel(const double* __restrict__ partial, int nsplit, int ncols,
+                                   double* __restrict__ norms) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncols) return;
+  double acc = 0.0;
+  for (int k = 0; k < nsplit; ++k) acc += partial[(int64_t)col * nsplit + k];
+  norms[col] = sqrt(acc);
+}
+
+// out[perm[i] + rows q] = in[i + rows q] (rows x ncols, column-major)
+__global__ void scatter_rows_kernel(const double* __restrict__ in, int64_t rows, int ncols,
+                                    const int* __restrict__ perm, double* __restrict__ out) {
+  const int64_t total = rows * ncols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, q = e / rows;
+    out[perm[i] + q * rows] = in[e];
   }
 }
 
@@ -423,22 +500,33 @@ pttk_status householder_r(double* A, int64_t M, int64_t N, double* R, double* no
 // One-sided Jacobi on A (rows x ncols) accumulating V (nv x ncols). Synchronises `s` once
 // per sweep to read the rotation count.
 pttk_status jacobi(double* A, int64_t rows, int ncols, double* V, int64_t nv, unsigned* d_counter,
-                   cudaStream_t s) {
+                   cudaStream_t s, double small = 0.0) {
   if (ncols < 2) return PTTK_OK;
+  Buf colsq;
+  PTTK_TRY(colsq.alloc(ncols));
+  colsq_init_kernel<<<(unsigned)(((int64_t)ncols * 32 + 255) / 256), 256, 0, s>>>(A, rows, ncols, colsq.p);
+  const double small2 = small * small;
+  const double count2 = 100.0 * small2;
   const int p = ncols + (ncols & 1);
-  const double tol = sqrt((double)rows) * 2.220446049250313e-16;
+  // A pair counts as orthogonal once |a.b| <= sqrt(rows) eps ||a|| ||b||: the typical rounding
+  // level of a computed dot product. The singular subspaces are then accurate to that level,
+  // which the 1e-12 parity of K~ needs (a looser rows * eps stops ~20x earlier in accuracy).
+  const double tol = sqrt((double)std::max<int64_t>(rows, 16)) * 2.220446049250313e-16;
   const unsigned blocks = (unsigned)((p / 2 * 32 + 255) / 256);
+  static const bool verbose = getenv("PTTK_VERBOSE") != nullptr;
   for (int sweep = 0; sweep < 60; ++sweep) {
     PTTK_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s));
     for (int r = 0; r < p - 1; ++r)
     {
       PTTK_PROF("jacobi_round", s);
-      jacobi_round_kernel<<<blocks, 256, 0, s>>>(A, rows, ncols, V, nv, p, r, tol, d_counter);
+      jacobi_round_kernel<<<blocks, 256, 0, s>>>(A, rows, ncols, V, nv, p, r, tol, small2, count2,
+                                                 colsq.p, d_counter);
     }
     PTTK_CUDA(cudaGetLastError());
     unsigned h = 0;
     PTTK_CUDA(cudaMemcpyAsync(&h, d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     PTTK_CUDA(cudaStreamSynchronize(s));
+    if (verbose) fprintf(stderr, "pttk: jacobi %lld x %d sweep %d rotations %u\n", (long long)rows, ncols, sweep, h);
     if (h == 0) return PTTK_OK;
   }
   return set_error(PTTK_ECUDA, "one-sided Jacobi SVD did not converge in 60 sweeps");
@@ -493,7 +581,7 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   PTTK_CUDA(cudaStreamSynchronize(s));
   const double delta = tol / sqrt((double)(D - 1)) * sqrt(sumsq);
 
-  Buf W, Xn, R, V, Y, norms, wpart, wv, core_tmp;
+  Buf W, Xn, R, wpart, wv;
   PTTK_TRY(W.alloc(total));
   PTTK_TRY(Xn.alloc(total));
   int* d_perm = nullptr;
@@ -512,64 +600,104 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   double* cur = X;
   double* nxt = Xn.p;
   int64_t cur_elems = total;
+  Buf qrin, A, U, Y, Yt, norms, colpart;
   for (int k = 0; k < D - 1; ++k) {
     PTTK_CUDA(cudaStreamSynchronize(s));  // buffers below are reallocated per step
     const int64_t m = r_prev * n;
     const int64_t c = cur_elems / m;
     const bool wide = c >= m;
-    const int64_t q = wide ? m : c;  // size of the square R
-    PTTK_TRY(R.alloc(q * q));
-    PTTK_TRY(V.alloc(q * q));
-    PTTK_TRY(norms.alloc(q));
-    const int64_t Mqr = wide ? c : m;
+    // QR input: wide -> W = (P X)^T (c x m), tall -> W = X P (m x c); P orders the rows
+    // (wide) or columns (tall) of X by decreasing norm, which makes the triangular factor
+    // graded so that one-sided Jacobi on R^T converges in a few sweeps.
+    const int64_t q = wide ? m : c;        // size of the square R
+    const int64_t Mqr = wide ? c : m;      // rows of the QR input
+    PTTK_TRY(norms.alloc(std::max<int64_t>(q, 1)));
+    {
+      // norms of the q vectors to be ordered: rows of X (wide, via W = X^T) or columns (tall)
+      const double* src = cur;
+      int64_t len = m;
+      if (wide) {
+        dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
+        transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, nullptr, W.p);
+        src = W.p;
+        len = c;
+      }
+      const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (len * q) / (256 * 1024 * 8) + 1));
+      PTTK_TRY(colpart.alloc((int64_t)nsplit * q));
+      colsq_partial_kernel<<<dim3((unsigned)nsplit, (unsigned)q), 256, 0, s>>>(src, len, nsplit, colpart.p);
+      colsq_final_kernel<<<(unsigned)((q + 255) / 256), 256, 0, s>>>(colpart.p, nsplit, (int)q, norms.p);
+    }
+    std::vector<double> nv(q);
+    PTTK_CUDA(cudaMemcpyAsync(nv.data(), norms.p, sizeof(double) * q, cudaMemcpyDeviceToHost, s));
+    PTTK_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> order;
+    truncation(nv, 0.0, order);  // descending order
+    if (d_perm) cudaFree(d_perm);
+    d_perm = nullptr;
+    PTTK_CUDA(cudaMalloc(&d_perm, sizeof(int) * q));
+    PTTK_CUDA(cudaMemcpyAsync(d_perm, order.data(), sizeof(int) * q, cudaMemcpyHostToDevice, s));
+    PTTK_TRY(qrin.alloc(Mqr * q));
+    if (wide) {
+      dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
+      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, d_perm, qrin.p);
+    } else {
+      gather_cols_kernel<<<grid1d(m * c, 256), 256, 0, s>>>(cur, m, d_perm, (int)c, nullptr, qrin.p);
+    }
+    // R (q x q) of the ordered matrix, then A = R^T
     const int64_t nchunks = (Mqr + RC - 1) / RC;
     PTTK_TRY(part.alloc(nchunks));
     PTTK_TRY(wpart.alloc(nchunks * q));
     PTTK_TRY(wv.alloc(q));
-    if (wide) {
-      dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
-      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, W.p);
-    } else {
-      PTTK_CUDA(cudaMemcpyAsync(W.p, cur, sizeof(double) * m * c, cudaMemcpyDeviceToDevice, s));
+    PTTK_TRY(R.alloc(q * q));
+    PTTK_TRY(A.alloc(q * q));
+    PTTK_TRY(householder_r(qrin.p, Mqr, q, R.p, part.p, wpart.p, wv.p, d_hs, s));
+    {
+      dim3 tg((unsigned)((q + 31) / 32), (unsigned)((q + 31) / 32));
+      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(R.p, q, q, nullptr, A.p);
     }
-    PTTK_TRY(householder_r(W.p, Mqr, q, R.p, part.p, wpart.p, wv.p, d_hs, s));
-    set_identity_kernel<<<grid1d(q * q, 256), 256, 0, s>>>(V.p, q);
-    PTTK_TRY(jacobi(R.p, q, (int)q, V.p, q, d_counter, s));
-    colnorm_kernel<<<(unsigned)((q * 32 + 255) / 256), 256, 0, s>>>(R.p, q, (int)q, norms.p);
+    // one-sided Jacobi on R^T: R^T V = U' Sigma, so R = V Sigma U'^T and the right singular
+    // vectors of R (= of the ordered QR input) are the normalised columns of the rotated R^T
+    // columns below 1e-3 delta / sqrt(q) together carry < 1e-6 delta^2: pairs of them are skipped
+    PTTK_TRY(jacobi(A.p, q, (int)q, nullptr, 0, d_counter, s, 1e-3 * delta / sqrt((double)q)));
+    colnorm_kernel<<<(unsigned)((q * 32 + 255) / 256), 256, 0, s>>>(A.p, q, (int)q, norms.p);
     std::vector<double> sigma(q);
     PTTK_CUDA(cudaMemcpyAsync(sigma.data(), norms.p, sizeof(double) * q, cudaMemcpyDeviceToHost, s));
     PTTK_CUDA(cudaStreamSynchronize(s));
     std::vector<int> perm;
     const int r = truncation(sigma, delta, perm);
-    if (d_perm) cudaFree(d_perm);
-    d_perm = nullptr;
-    PTTK_CUDA(cudaMalloc(&d_perm, sizeof(int) * perm.size()));
-    PTTK_CUDA(cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * perm.size(),
-                              cudaMemcpyHostToDevice, s));
-    PTTK_TRY(cores[k].alloc(m * r));
-    if (wide) {
-      // G_k = V[:, top r]
-      gather_cols_kernel<<<grid1d(m * r, 256), 256, 0, s>>>(V.p, m, d_perm, r, nullptr, cores[k].p);
-    } else {
-      // Y = X V[:, top r]; orthogonalise Y's columns; G_k = Y with unit columns
-      PTTK_TRY(core_tmp.alloc(c * r));
-      gather_cols_kernel<<<grid1d(c * r, 256), 256, 0, s>>>(V.p, c, d_perm, r, nullptr, core_tmp.p);
-      PTTK_TRY(Y.alloc(m * r));
-      dgemm(false, false, m, r, c, 1.0, cur, m, core_tmp.p, c, 0.0, Y.p, m, s);
-      Buf V2;
-      PTTK_TRY(V2.alloc((int64_t)r * r));
-      set_identity_kernel<<<grid1d((int64_t)r * r, 256), 256, 0, s>>>(V2.p, r);
-      PTTK_TRY(jacobi(Y.p, m, r, V2.p, r, d_counter, s));
-      Buf ynorm;
-      PTTK_TRY(ynorm.alloc(r));
-      colnorm_kernel<<<(unsigned)(((int64_t)r * 32 + 255) / 256), 256, 0, s>>>(Y.p, m, r, ynorm.p);
-      std::vector<double> yn(r);
-      PTTK_CUDA(cudaMemcpyAsync(yn.data(), ynorm.p, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
+    int* d_top = nullptr;
+    PTTK_CUDA(cudaMalloc(&d_top, sizeof(int) * std::max<int64_t>(q, 1)));
+    struct TopGuard { int* p; ~TopGuard() { if (p) cudaFree(p); } } top_guard{d_top};
+    PTTK_CUDA(cudaMemcpyAsync(d_top, perm.data(), sizeof(int) * q, cudaMemcpyHostToDevice, s));
+    // top-r right singular vectors (unit columns), in the ordered basis
+    PTTK_TRY(U.alloc(q * r));
+    PTTK_TRY(Y.alloc(q * r));
+    gather_cols_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(A.p, q, d_top, r, norms.p, Y.p);
+    // back to the original order: row order[i] of the result is row i of Y
+    scatter_rows_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(Y.p, q, r, d_perm, U.p);
+    double* basis = U.p;  // m x r (wide): left singular vectors of X
+    if (!wide) {
+      // tall: U holds the top right singular vectors of X (c x r); Y = X U spans the top-r
+      // left singular subspace
+      PTTK_TRY(Yt.alloc(m * r));
+      dgemm(false, false, m, r, c, 1.0, cur, m, U.p, c, 0.0, Yt.p, m, s);
+      basis = Yt.p;
+    }
+    // make the m x r basis orthonormal to working precision: its columns are orthogonal up
+    // to ~eps ||X|| / sigma_i, so one-sided Jacobi needs one or two sweeps
+    PTTK_TRY(jacobi(basis, m, r, nullptr, 0, d_counter, s));
+    {
+      Buf bn;
+      PTTK_TRY(bn.alloc(r));
+      colnorm_kernel<<<(unsigned)(((int64_t)r * 32 + 255) / 256), 256, 0, s>>>(basis, m, r, bn.p);
+      std::vector<double> bnh(r);
+      PTTK_CUDA(cudaMemcpyAsync(bnh.data(), bn.p, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
       PTTK_CUDA(cudaStreamSynchronize(s));
-      std::vector<int> yperm;
-      truncation(yn, 0.0, yperm);
-      PTTK_CUDA(cudaMemcpyAsync(d_perm, yperm.data(), sizeof(int) * r, cudaMemcpyHostToDevice, s));
-      gather_cols_kernel<<<grid1d(m * r, 256), 256, 0, s>>>(Y.p, m, d_perm, r, ynorm.p, cores[k].p);
+      std::vector<int> bperm;
+      truncation(bnh, 0.0, bperm);
+      PTTK_CUDA(cudaMemcpyAsync(d_top, bperm.data(), sizeof(int) * r, cudaMemcpyHostToDevice, s));
+      PTTK_TRY(cores[k].alloc(m * r));
+      gather_cols_kernel<<<grid1d(m * r, 256), 256, 0, s>>>(basis, m, d_top, r, bn.p, cores[k].p);
       PTTK_CUDA(cudaStreamSynchronize(s));
     }
     // X <- G_k^T X  (r x c)
