@@ -45,10 +45,8 @@ const void* oriented_core_ptr(const pttk_tt* tt, bool source, int k, bool fp64);
 namespace {
 
 constexpr int TILE_M = 128;
-constexpr int NTHREADS = 128;
 constexpr int KC_BYTES = 128;            // bytes of K per row per chunk
 constexpr int CHUNK_ROW_GROUP = 1024;    // bytes per 8-row group in a chunk
-constexpr int BV_LD = PTTK_MAX_N + 1;    // basis row stride (odd: conflict-free)
 
 // ---------------- PTX wrappers ------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -75,11 +73,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the completion of the phase with the given parity; gives up after ~2 s or
+// as soon as another thread of the CTA has raised the abort flag.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
   for (uint32_t i = 0; i < (1u << 24); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (i >= 32) __nanosleep(128);
+    if (i >= 32) {
+      if (*abort_flag) return false;
+      __nanosleep(128);
+    }
   }
   return false;
 }
@@ -152,14 +154,18 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-// UMMA shared-memory descriptor: no swizzle, K-major, LBO = 128 B, SBO = 1024 B.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+// UMMA shared-memory descriptor: no swizzle, K-major; K-adjacent core matrices 128 B apart
+// (leading byte offset), 8-row groups `sbo` bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t smem_desc2(uint32_t saddr, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((KC_BYTES >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((CHUNK_ROW_GROUP >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of tcgen05
-  return d;                // base offset 0, absolute LBO mode, layout type 0 (no swizzle)
+  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;  // K-adjacent core matrices: 128 B apart
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;   // 8-row groups: sbo bytes apart
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // Instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1), K-major A and B.
@@ -169,9 +175,9 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, int M, int
 }
 
 struct TcStep {
-  const uint8_t* img_hi;  // nchunks x (Npad x 128 B)
+  const uint8_t* img_hi;  // nchunks x (Npad x KC_BYTES)
   const uint8_t* img_lo;  // same, or null for single-product forms
-  int K, nchunks, R_in, R_out, Npad, coord;
+  int nchunks, R_in, R_in_pad, R_out, Npad, coord;
   float lo, hi;           // box of the coordinate
 };
 struct TcArgs {
@@ -181,38 +187,46 @@ struct TcArgs {
   const float* pts;
   float* out;
   int* status;
-  int ld_s;        // row stride of S_in (floats, odd)
+  int ld_s;               // row stride of S (floats, multiple of 4)
   int tmem_cols;
   uint32_t b_slot_bytes;  // bytes reserved per B part per slot
-  int out_aligned;        // output base is 16-byte aligned
 };
 
-// One unit (16 bytes) of the generated A operand: 4 TF32 or 8 BF16 elements of row p.
+constexpr int NSLOT = 4;                   // operand ring depth
+constexpr int NGEN_WARPS = 8;              // A generators (2 threads per point row)
+constexpr int TC_THREADS = 64 + 32 * NGEN_WARPS;  // warp 0: TMA, warp 1: MMA, warps 2..9: A
+constexpr int STAGE_LD = 33;               // epilogue staging row stride (floats)
+
 template <bool BF16, bool SPLIT>
-__device__ __forceinline__ void gen_unit(const float* bv, const float* srow, int R_in, int K, int k,
-                                         uint8_t* dst_hi, uint8_t* dst_lo) {
-  constexpr int E = BF16 ? 8 : 4;
-  float v[E];
-  int j = k / R_in;
-  int a = k - j * R_in;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    v[e] = (k + e < K) ? bv[j] * srow[a] : 0.f;
-    if (++a == R_in) {
-      a = 0;
-      ++j;
-    }
-  }
+struct Cfg {
+  static constexpr int KCB = SPLIT ? 64 : 128;            // bytes of K per row per chunk
+  static constexpr int PARTS = SPLIT ? 2 : 1;             // hi (and lo) operand parts
+  static constexpr int E = BF16 ? 8 : 4;                  // elements per 16-byte unit
+  static constexpr int UNITS = KCB / 16;                  // units per row per chunk
+  static constexpr int KC = KCB / (BF16 ? 2 : 4);         // K elements per chunk
+  static constexpr uint32_t SBO = 8 * KCB;                // 8-row group stride
+  static constexpr uint32_t A_PART = TILE_M * KCB;
+  static constexpr int KSTEPS = KCB / 32;                 // MMAs (per product) per chunk
+};
+
+// 16-byte unit of the generated A operand from E consecutive S values times one basis value.
+template <bool BF16, bool SPLIT>
+__device__ __forceinline__ void write_unit(float b, const float* sv, uint8_t* hi, uint8_t* lo) {
   if constexpr (!BF16) {
+    const float4 x = *reinterpret_cast<const float4*>(sv);
+    const float v[4] = {b * x.x, b * x.y, b * x.z, b * x.w};
     float h[4], l[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       h[e] = to_tf32(v[e]);
-      l[e] = SPLIT ? to_tf32(v[e] - h[e]) : 0.f;
+      if (SPLIT) l[e] = to_tf32(v[e] - h[e]);
     }
-    *reinterpret_cast<float4*>(dst_hi) = make_float4(h[0], h[1], h[2], h[3]);
-    if (SPLIT) *reinterpret_cast<float4*>(dst_lo) = make_float4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<float4*>(hi) = make_float4(h[0], h[1], h[2], h[3]);
+    if (SPLIT) *reinterpret_cast<float4*>(lo) = make_float4(l[0], l[1], l[2], l[3]);
   } else {
+    const float4 x0 = *reinterpret_cast<const float4*>(sv);
+    const float4 x1 = *reinterpret_cast<const float4*>(sv + 4);
+    const float v[8] = {b * x0.x, b * x0.y, b * x0.z, b * x0.w, b * x1.x, b * x1.y, b * x1.z, b * x1.w};
     __nv_bfloat162 h[4], l[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -222,38 +236,78 @@ __device__ __forceinline__ void gen_unit(const float* bv, const float* srow, int
         l[e] = __halves2bfloat162(__float2bfloat16_rn(v[2 * e] - __bfloat162float(h0)),
                                   __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1)));
     }
-    *reinterpret_cast<uint4*>(dst_hi) = *reinterpret_cast<uint4*>(h);
-    if (SPLIT) *reinterpret_cast<uint4*>(dst_lo) = *reinterpret_cast<uint4*>(l);
+    *reinterpret_cast<uint4*>(hi) = *reinterpret_cast<uint4*>(h);
+    if (SPLIT) *reinterpret_cast<uint4*>(lo) = *reinterpret_cast<uint4*>(l);
   }
 }
 
-template <bool BF16, bool SPLIT>
-__global__ void __launch_bounds__(NTHREADS, 1) chain_tc_kernel(TcArgs a) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  // layout: [A slots: 2 x (hi, lo) x 16 KB][B slots: 2 x (hi, lo) x b_slot_bytes]
-  //         [S_in: 128 x ld_s floats][Bv: 128 x BV_LD floats][mbarriers][tmem addr][flags]
-  constexpr uint32_t A_PART = TILE_M * KC_BYTES;  // 16 KB
-  uint8_t* a_base = smem;
-  uint8_t* b_base = a_base + 2 * 2 * A_PART;
-  float* S = reinterpret_cast<float*>(b_base + 2 * 2 * (size_t)a.b_slot_bytes);
-  float* Bv = S + (size_t)TILE_M * a.ld_s;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Bv + (size_t)TILE_M * BV_LD + 1);  // 8-byte aligned below
-  bars = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(bars) + 7) & ~uintptr_t(7));
-  uint64_t* bar_b = bars;        // [2] B chunk arrived
-  uint64_t* bar_mma = bars + 2;  // [2] MMAs of the chunk done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+__device__ __forceinline__ void gen_barrier() {  // the 256 generator threads only
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * NGEN_WARPS) : "memory");
+}
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+// Per-step constants, staged once in shared memory.
+struct StepS {
+  const uint8_t* hi;
+  const uint8_t* lo;
+  uint32_t bytes;   // bytes of one chunk part (Npad x KCB)
+  uint32_t idesc;
+  int nchunks, R_in_pad, R_out, Npad, coord;
+  float lo_box, hi_box;
+};
+
+// Warp-specialised factor chain. Warp 0 (one lane) loads the core chunks with TMA into a
+// NSLOT-deep ring; warp 1 (one lane) issues the MMAs; warps 2..9 generate the A chunks (two
+// threads per point row, each writing half of the row's units) and run the epilogues.
+// Barriers per slot: full_a (8 generator warps arrive), full_b (TMA transaction bytes), empty
+// (tcgen05.commit of the slot's MMAs); acc_ready is committed after each step's last chunk.
+template <bool BF16, bool SPLIT>
+__global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
+  using C = Cfg<BF16, SPLIT>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int bv_ld = (a.n + 1) | 1;                                 // odd row stride > n
+  uint8_t* a_base = smem;                                            // NSLOT x PARTS x A_PART
+  uint8_t* b_base = a_base + (size_t)NSLOT * C::PARTS * C::A_PART;    // NSLOT x PARTS x b_slot_bytes
+  float* S = reinterpret_cast<float*>(b_base + (size_t)NSLOT * C::PARTS * a.b_slot_bytes);  // 128 x ld_s
+  float* Bv = S + (size_t)TILE_M * a.ld_s;                           // 2 x 128 x bv_ld
+  StepS* steps = reinterpret_cast<StepS*>(
+      (reinterpret_cast<uintptr_t>(Bv + (size_t)2 * TILE_M * bv_ld) + 15) & ~uintptr_t(15));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(steps + 3);
+  uint64_t* full_a = bars;
+  uint64_t* full_b = bars + NSLOT;
+  uint64_t* empty = bars + 2 * NSLOT;
+  uint64_t* acc_ready = bars + 3 * NSLOT;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * NSLOT + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* stage = S;  // epilogue staging of the last step aliases S (8 x 32 x STAGE_LD floats)
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(&bar_b[0], 1);
-    mbar_init(&bar_b[1], 1);
-    mbar_init(&bar_mma[0], 1);
-    mbar_init(&bar_mma[1], 1);
+    for (int i = 0; i < NSLOT; ++i) {
+      mbar_init(&full_a[i], NGEN_WARPS);
+      mbar_init(&full_b[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(acc_ready, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0) {
+  if (tid < a.nsteps) {
+    const TcStep& st = a.st[tid];
+    StepS v;
+    v.hi = st.img_hi;
+    v.lo = st.img_lo;
+    v.bytes = (uint32_t)st.Npad * C::KCB;
+    v.idesc = instr_desc(BF16 ? 1u : 2u, TILE_M, st.Npad);
+    v.nchunks = st.nchunks;
+    v.R_in_pad = st.R_in_pad;
+    v.R_out = st.R_out;
+    v.Npad = st.Npad;
+    v.coord = st.coord;
+    v.lo_box = st.lo;
+    v.hi_box = st.hi;
+    steps[tid] = v;
+  }
+  if (warp == 1) {
     tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
     tmem_relinquish();
   }
@@ -261,174 +315,247 @@ __global__ void __launch_bounds__(NTHREADS, 1) chain_tc_kernel(TcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
   const int64_t ntiles = (a.N + TILE_M - 1) / TILE_M;
-  uint32_t g = 0;          // chunks issued so far by this CTA (slot = g & 1)
-  uint32_t b_issued[2] = {0, 0}, b_waited[2] = {0, 0};  // TMA uses per slot (thread 0)
-  bool failed = false;
+  const int nsteps = a.nsteps;
 
-  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const int64_t row0 = tile * TILE_M;
-    const int rows = (int)std::min<int64_t>(TILE_M, a.N - row0);
-    S[tid * a.ld_s] = 1.f;  // S_0 = 1 (r_0 = 1)
-    for (int si = 0; si < a.nsteps && !failed; ++si) {
-      const TcStep st = a.st[si];
-      // Chebyshev basis T_0..T_{n-1} of this point's coordinate (three-term recurrence)
-      {
-        const int64_t gp = row0 + tid;
-        const float x = tid < rows ? a.pts[gp * a.d + st.coord] : st.lo;
-        const float xh = (2.f * x - st.lo - st.hi) / (st.lo - st.hi);
-        float t0 = 1.f, t1 = xh;
-        Bv[tid * BV_LD] = t0;
-        if (a.n > 1) Bv[tid * BV_LD + 1] = t1;
-        for (int k = 2; k < a.n; ++k) {
-          const float t2 = 2.f * xh * t1 - t0;
-          Bv[tid * BV_LD + k] = t2;
-          t0 = t1;
-          t1 = t2;
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t h = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+        for (int si = 0; si < nsteps && ok; ++si) {
+          const StepS st = steps[si];
+          for (int c = 0; c < st.nchunks; ++c, ++h) {
+            const uint32_t slot = h % NSLOT;
+            if (h >= NSLOT && !mbar_wait(&empty[slot], ((h / NSLOT) - 1) & 1, abort_flag)) { ok = false; break; }
+            uint8_t* bh = b_base + (size_t)slot * C::PARTS * a.b_slot_bytes;
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&full_b[slot], SPLIT ? 2 * st.bytes : st.bytes);
+            tma_load_1d(bh, st.hi + (size_t)c * st.bytes, st.bytes, &full_b[slot]);
+            if (SPLIT) tma_load_1d(bh + a.b_slot_bytes, st.lo + (size_t)c * st.bytes, st.bytes, &full_b[slot]);
+          }
         }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(a.status, (int)PTTK_ETIMEOUT);
       }
-      __syncthreads();
-      const uint32_t idesc = instr_desc(BF16 ? 1u : 2u, TILE_M, st.Npad);
-      const uint32_t b_bytes = (uint32_t)st.Npad * KC_BYTES;
-      constexpr int E = BF16 ? 8 : 4;  // elements per 16-byte unit
-      const float* bv = Bv + tid * BV_LD;
-      const float* srow = S + (size_t)tid * a.ld_s;
-      for (int c = 0; c < st.nchunks; ++c, ++g) {
-        const int slot = g & 1;
-        if (g >= 2 && !mbar_wait(&bar_mma[slot], ((g >> 1) - 1) & 1)) *abort_flag = 1;
-        uint8_t* a_hi = a_base + (size_t)slot * 2 * A_PART;
-        uint8_t* a_lo = a_hi + A_PART;
-        uint8_t* b_hi = b_base + (size_t)slot * 2 * a.b_slot_bytes;
-        uint8_t* b_lo = b_hi + a.b_slot_bytes;
-        if (tid == 0 && !*abort_flag) {
-          fence_proxy_async();  // earlier generic accesses of this slot precede the TMA write
-          mbar_arrive_expect_tx(&bar_b[slot], SPLIT ? 2 * b_bytes : b_bytes);
-          tma_load_1d(b_hi, st.img_hi + (size_t)c * b_bytes, b_bytes, &bar_b[slot]);
-          if (SPLIT) tma_load_1d(b_lo, st.img_lo + (size_t)c * b_bytes, b_bytes, &bar_b[slot]);
-          ++b_issued[slot];
-        }
-        // generate this chunk of A for row tid: 8 units of 16 bytes
-        const int kbase = c * (KC_BYTES / (BF16 ? 2 : 4));
-        const uint32_t row_off = (uint32_t)(tid >> 3) * CHUNK_ROW_GROUP + (uint32_t)(tid & 7) * 16;
-#pragma unroll 2
-        for (int u = 0; u < 8; ++u)
-          gen_unit<BF16, SPLIT>(bv, srow, st.R_in, st.K, kbase + u * E, a_hi + row_off + u * 128,
-                                a_lo + row_off + u * 128);
-        fence_proxy_async();
-        __syncthreads();
-        if (*abort_flag) {
-          failed = true;
-          break;
-        }
-        if (tid == 0) {
-          if (!mbar_wait(&bar_b[slot], (b_waited[slot]++) & 1)) {
-            *abort_flag = 1;
-          } else {
+      // drain: every issued load has landed before the CTA may exit (the MMA side consumes them)
+      const int zero = 0;
+      for (uint32_t k = (h > NSLOT ? h - NSLOT : 0); k < h; ++k)
+        mbar_wait(&full_b[k % NSLOT], (k / NSLOT) & 1, &zero);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+        for (int si = 0; si < nsteps && ok; ++si) {
+          const StepS st = steps[si];
+          for (int c = 0; c < st.nchunks; ++c, ++g) {
+            const uint32_t slot = g % NSLOT, par = (g / NSLOT) & 1;
+            if (!mbar_wait(&full_a[slot], par, abort_flag) || !mbar_wait(&full_b[slot], par, abort_flag)) {
+              ok = false;
+              break;
+            }
             tc_fence_after();
-            const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo);
-            const uint32_t sb_hi = smem_u32(b_hi), sb_lo = smem_u32(b_lo);
+            const uint32_t sa = smem_u32(a_base + (size_t)slot * C::PARTS * C::A_PART);
+            const uint32_t sb = smem_u32(b_base + (size_t)slot * C::PARTS * a.b_slot_bytes);
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-              const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-              const uint64_t ah = smem_desc(sa_hi + s * 256), bh = smem_desc(sb_hi + s * 256);
+            for (int k = 0; k < C::KSTEPS; ++k) {
+              const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+              const uint64_t ah = smem_desc2(sa + k * 256, C::SBO), bh = smem_desc2(sb + k * 256, C::SBO);
               if constexpr (BF16) {
-                umma_f16(tmem, ah, bh, idesc, acc);
+                umma_f16(tmem, ah, bh, st.idesc, acc);
                 if (SPLIT) {
-                  umma_f16(tmem, ah, smem_desc(sb_lo + s * 256), idesc, 1u);
-                  umma_f16(tmem, smem_desc(sa_lo + s * 256), bh, idesc, 1u);
+                  umma_f16(tmem, ah, smem_desc2(sb + a.b_slot_bytes + k * 256, C::SBO), st.idesc, 1u);
+                  umma_f16(tmem, smem_desc2(sa + C::A_PART + k * 256, C::SBO), bh, st.idesc, 1u);
                 }
               } else {
-                umma_tf32(tmem, ah, bh, idesc, acc);
+                umma_tf32(tmem, ah, bh, st.idesc, acc);
                 if (SPLIT) {
-                  umma_tf32(tmem, ah, smem_desc(sb_lo + s * 256), idesc, 1u);
-                  umma_tf32(tmem, smem_desc(sa_lo + s * 256), bh, idesc, 1u);
+                  umma_tf32(tmem, ah, smem_desc2(sb + a.b_slot_bytes + k * 256, C::SBO), st.idesc, 1u);
+                  umma_tf32(tmem, smem_desc2(sa + C::A_PART + k * 256, C::SBO), bh, st.idesc, 1u);
                 }
               }
             }
-            umma_commit(&bar_mma[slot]);
+            umma_commit(&empty[slot]);
+            if (c == st.nchunks - 1) umma_commit(acc_ready);
           }
         }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(a.status, (int)PTTK_ETIMEOUT);
       }
-      if (failed) break;
-      // all MMAs of this step are complete once the last chunk's commit has landed
-      const uint32_t glast = g - 1;
-      if (!mbar_wait(&bar_mma[glast & 1], (glast >> 1) & 1)) *abort_flag = 1;
-      __syncthreads();
-      if (*abort_flag) {
-        failed = true;
-        break;
+      const int zero = 0;
+      if (g > 0) mbar_wait(&empty[(g - 1) % NSLOT], ((g - 1) / NSLOT) & 1, &zero);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- generator warps: A chunks and epilogues ----------------
+    // Every generator thread runs the same sequence of named barriers whatever happens: a wait
+    // that gives up only marks the warp dead (warp-uniform), after which its work is skipped.
+    const int gw = warp - 2;                   // 0..7
+    const int row = 32 * (warp & 3) + lane;    // TMEM lane quarter of this warp
+    const int half = gw >> 2;                  // which half of the row's units
+    uint32_t g = 0, steps_done = 0;
+    bool dead = false;
+    // basis of step (tile, si) into Bv buffer `buf` (threads of half 0; zero from index n on)
+    auto basis = [&](int64_t tile, int si, int buf, float x) {
+      const StepS& st = steps[si];
+      const float xh = (2.f * x - st.lo_box - st.hi_box) / (st.lo_box - st.hi_box);
+      float* bv = Bv + ((size_t)buf * TILE_M + row) * bv_ld;
+      float t0 = 1.f, t1 = xh;
+      bv[0] = 1.f;
+      for (int k = 1; k < a.n; ++k) {
+        bv[k] = t1;
+        const float t2 = 2.f * xh * t1 - t0;
+        t0 = t1;
+        t1 = t2;
       }
-      tc_fence_after();
-      const bool last = si == a.nsteps - 1;
-      float* otile = reinterpret_cast<float*>(a_base);  // output tile (reuses operand space)
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-      for (int cb = 0; cb < st.Npad; cb += 32) {
-        float v[32];
-        tmem_ld32(lane_addr + (uint32_t)cb, v);
+      for (int k = a.n; k < bv_ld; ++k) bv[k] = 0.f;
+    };
+    auto coord_of = [&](int64_t tile, int si) -> float {
+      const int64_t gp = tile * TILE_M + row;
+      return gp < a.N ? a.pts[gp * a.d + steps[si].coord] : steps[si].lo_box;
+    };
+    float xn[3] = {0.f, 0.f, 0.f};  // coordinates of this row for the tile being built
+    if (half == 0 && blockIdx.x < ntiles)
+      for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
+    uint32_t bufsel = 0;
+    if (half == 0 && blockIdx.x < ntiles) basis(blockIdx.x, 0, 0, xn[0]);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int64_t row0 = tile * TILE_M;
+      const int rows = (int)std::min<int64_t>(TILE_M, a.N - row0);
+      float xcur[3] = {xn[0], xn[1], xn[2]};
+      // prefetch the next tile's coordinates (latency hidden behind this tile)
+      const int64_t tnext = tile + gridDim.x;
+      if (half == 0 && tnext < ntiles)
+        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(tnext, si);
+      if (half == 0) {
+        float4* s4 = reinterpret_cast<float4*>(S + (size_t)row * a.ld_s);
+        s4[0] = make_float4(1.f, 0.f, 0.f, 0.f);  // S_0 = 1 (r_0 = 1), zero padding
+        s4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      gen_barrier();
+      for (int si = 0; si < nsteps; ++si) {
+        const StepS st = steps[si];
+        const float* bvrow = Bv + ((size_t)bufsel * TILE_M + row) * bv_ld;
+        const float* srow = S + (size_t)row * a.ld_s;
+        for (int c = 0; c < st.nchunks; ++c, ++g) {
+          const uint32_t slot = g % NSLOT, use = g / NSLOT;
+          dead = dead || *abort_flag;
+          if (!dead && g >= NSLOT) dead = !mbar_wait(&empty[slot], (use - 1) & 1, abort_flag);
+          dead = __any_sync(0xffffffffu, dead);
+          if (dead && lane == 0) *abort_flag = 1;
+          if (!dead) {
+            uint8_t* ah = a_base + (size_t)slot * C::PARTS * C::A_PART;
+            const uint32_t row_off = (uint32_t)(row >> 3) * C::SBO + (uint32_t)(row & 7) * 16;
+            constexpr int UH = C::UNITS / 2;  // units of this thread
+            const int k = c * C::KC + half * UH * C::E;
+            int j = k / st.R_in_pad;
+            int ai = k - j * st.R_in_pad;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = cb + i;
-          if (col < st.R_out) {
-            if (last) otile[(size_t)tid * st.R_out + col] = v[i];
-            else S[(size_t)tid * a.ld_s + col] = v[i];
+            for (int u = 0; u < UH; ++u) {
+              const uint32_t off = row_off + (uint32_t)(half * UH + u) * 128;
+              write_unit<BF16, SPLIT>(bvrow[j < a.n ? j : a.n], srow + ai, ah + off, ah + C::A_PART + off);
+              ai += C::E;
+              if (ai == st.R_in_pad) {
+                ai = 0;
+                ++j;
+              }
+            }
+            fence_proxy_async();
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full_a[slot]);
+        }
+        // the next basis (next step, or step 0 of the next tile) goes to the other buffer
+        // while this step's MMAs drain
+        const bool last = si == nsteps - 1;
+        if (half == 0) {
+          if (!last) basis(tile, si + 1, bufsel ^ 1, xcur[si + 1]);
+          else if (tnext < ntiles) basis(tnext, 0, bufsel ^ 1, xn[0]);
+        }
+        // accumulator of this step is complete (all A chunks of the step, hence all reads of
+        // S for it, are done once it is)
+        if (!dead && !*abort_flag) dead = !mbar_wait(acc_ready, steps_done & 1, abort_flag);
+        ++steps_done;
+        dead = __any_sync(0xffffffffu, dead || *abort_flag);
+        if (dead && lane == 0) *abort_flag = 1;
+        tc_fence_after();
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        if (!last) {
+          // S for the next step: columns [0, Npad) (zero beyond R_out); this thread's half of
+          // the 32-column blocks
+          if (!dead)
+            for (int cb = 32 * half; cb < st.Npad; cb += 64) {
+              float v[32];
+              tmem_ld32(lane_addr + (uint32_t)cb, v);
+              float* dst = S + (size_t)row * a.ld_s + cb;
+#pragma unroll
+              for (int i = 0; i < 32; i += 4)
+                if (cb + i < a.ld_s)
+                  *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
+        } else if (!dead) {
+          // output rows: each warp stages 32 rows x 32 columns, then writes row segments
+          float* stg = stage + (size_t)gw * 32 * STAGE_LD;
+          const int R = st.R_out;
+          float* outbase = a.out + (row0 + 32 * (warp & 3)) * R;
+          const int wrows = std::max(0, std::min(32, rows - 32 * (warp & 3)));
+          for (int cb = 32 * half; cb < st.Npad; cb += 64) {
+            float v[32];
+            tmem_ld32(lane_addr + (uint32_t)cb, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) stg[lane * STAGE_LD + i] = v[i];
+            __syncwarp();
+            const int col = cb + lane;
+            if (col < R)
+              for (int rr = 0; rr < wrows; ++rr) outbase[(int64_t)rr * R + col] = stg[rr * STAGE_LD + lane];
+            __syncwarp();
           }
         }
-      }
-      tc_fence_before();
-      __syncthreads();
-      if (last) {
-        // rows row0 .. row0 + rows - 1 of the row-major output are one contiguous block
-        float* dst = a.out + row0 * st.R_out;
-        const int64_t nflt = (int64_t)rows * st.R_out;
-        if (rows == TILE_M && a.out_aligned) {  // 128 * R_out * 4 bytes: a multiple of 16
-          const float4* s4 = reinterpret_cast<const float4*>(otile);
-          float4* d4 = reinterpret_cast<float4*>(dst);
-          for (int64_t e = tid; e < nflt / 4; e += NTHREADS) d4[e] = s4[e];
-        } else {
-          for (int64_t e = tid; e < nflt; e += NTHREADS) dst[e] = otile[e];
-        }
-        __syncthreads();
+        bufsel ^= 1;
+        tc_fence_before();
+        gen_barrier();
       }
     }
-  }
-
-  // drain: outstanding TMA copies and MMA commits (bounded), then release TMEM
-  if (tid == 0) {
-    for (int s = 0; s < 2; ++s)
-      while (b_waited[s] < b_issued[s]) {
-        if (!mbar_wait(&bar_b[s], (b_waited[s]++) & 1)) break;
-      }
-  }
-  if (failed && tid == 0) atomicExch(a.status, (int)PTTK_ETIMEOUT);
-  if (g > 0) {
-    const uint32_t glast = g - 1;
-    mbar_wait(&bar_mma[glast & 1], (glast >> 1) & 1);
+    if (dead && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(a.status, (int)PTTK_ETIMEOUT);
+    }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+  if (warp == 1) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
 }
 
 // ---------------- core images -------------------------------------------------------------
-// Image of the oriented core (K x R_out, column-major, FP64) for one chain step: chunk c holds
-// rows o < Npad and K-elements [c*KC, (c+1)*KC) in the K-major no-swizzle layout above.
+// Image of the oriented core (K x R_out, column-major, FP64; K = n R_in) for one chain step in
+// the padded K order k' = a + R_in_pad j (zero rows for a >= R_in): chunk c holds rows o < Npad
+// and K'-elements [c KC, (c+1) KC) in the K-major no-swizzle layout (row group stride 8 KCB).
 template <bool BF16>
-__global__ void core_image_kernel(const double* __restrict__ G, int K, int R_out, int Npad, int nchunks,
-                                  bool split, uint8_t* __restrict__ hi, uint8_t* __restrict__ lo) {
-  constexpr int KC = BF16 ? 64 : 32;
+__global__ void core_image_kernel(const double* __restrict__ G, int n, int R_in, int R_in_pad, int R_out,
+                                  int Npad, int nchunks, int KCB, bool split, uint8_t* __restrict__ hi,
+                                  uint8_t* __restrict__ lo) {
   constexpr int E = BF16 ? 8 : 4;
+  const int KC = KCB / (BF16 ? 2 : 4);
+  const int K = n * R_in;
   const int64_t total = (int64_t)nchunks * Npad * KC;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int kk = (int)(e % KC);
     const int o = (int)((e / KC) % Npad);
     const int c = (int)(e / ((int64_t)KC * Npad));
-    const int k = c * KC + kk;
-    const double v = (k < K && o < R_out) ? G[k + (int64_t)K * o] : 0.0;
-    const size_t off = (size_t)c * Npad * KC_BYTES + (size_t)(o >> 3) * CHUNK_ROW_GROUP +
-                       (size_t)(kk / E) * 128 + (size_t)(o & 7) * 16;
+    const int kp = c * KC + kk;
+    const int j = kp / R_in_pad, ai = kp - j * R_in_pad;
+    const double v = (ai < R_in && j < n && o < R_out) ? G[(ai + R_in * j) + (int64_t)K * o] : 0.0;
+    const size_t off = (size_t)c * Npad * KCB + (size_t)(o >> 3) * (8 * KCB) + (size_t)(kk / E) * 128 +
+                       (size_t)(o & 7) * 16;
     if constexpr (BF16) {
       const __nv_bfloat16 h = __double2bfloat16(v);
       reinterpret_cast<__nv_bfloat16*>(hi + off)[kk % E] = h;
@@ -444,7 +571,7 @@ __global__ void core_image_kernel(const double* __restrict__ G, int K, int R_out
 struct Images {
   uint8_t* buf = nullptr;
   size_t hi_off[2][3] = {}, lo_off[2][3] = {};
-  int Npad[2][3] = {}, nchunks[2][3] = {};
+  int Npad[2][3] = {}, nchunks[2][3] = {}, R_in_pad[2][3] = {};
 };
 
 std::mutex g_img_mu;
@@ -466,6 +593,8 @@ static int form_index(pttk_prec p) {
   }
 }
 
+static int form_kcb(pttk_prec p) { return (p == PTTK_TF32X3 || p == PTTK_BF16X3) ? 64 : 128; }
+
 TcImageCache* tc_cache_new() { return new TcImageCache(); }
 void tc_cache_free(TcImageCache* c) {
   if (!c) return;
@@ -477,16 +606,18 @@ void tc_cache_free(TcImageCache* c) {
 static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, Images& im, cudaStream_t s) {
   const bool bf16 = prec == PTTK_BF16 || prec == PTTK_BF16X3;
   const bool split = prec == PTTK_TF32X3 || prec == PTTK_BF16X3;
-  const int KC = bf16 ? 64 : 32;
+  const int KCB = form_kcb(prec);
+  const int KC = KCB / (bf16 ? 2 : 4);
+  const int E = bf16 ? 8 : 4;
   size_t total = 0;
   for (int side = 0; side < 2; ++side)
     for (int i = 0; i < tt->d; ++i) {
       int rin, rout, coord;
       oriented_core_dims(tt, side == 0, i, &rin, &rout, &coord);
-      const int K = tt->n * rin;
+      im.R_in_pad[side][i] = ((rin + E - 1) / E) * E;
       im.Npad[side][i] = ((rout + 15) / 16) * 16;
-      im.nchunks[side][i] = (K + KC - 1) / KC;
-      const size_t bytes = (size_t)im.nchunks[side][i] * im.Npad[side][i] * KC_BYTES;
+      im.nchunks[side][i] = (tt->n * im.R_in_pad[side][i] + KC - 1) / KC;
+      const size_t bytes = (size_t)im.nchunks[side][i] * im.Npad[side][i] * KCB;
       im.hi_off[side][i] = total;
       total += bytes;
       im.lo_off[side][i] = total;
@@ -499,25 +630,15 @@ static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, Images& im, c
       int rin, rout, coord;
       const int k = oriented_core_dims(tt, side == 0, i, &rin, &rout, &coord);
       const double* G = static_cast<const double*>(oriented_core_ptr(tt, side == 0, k, true));
-      const int K = tt->n * rin;
       const int64_t work = (int64_t)im.nchunks[side][i] * im.Npad[side][i] * KC;
       const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count() * 8);
-      if (bf16)
-        core_image_kernel<true><<<blocks, 256, 0, s>>>(G, K, rout, im.Npad[side][i], im.nchunks[side][i], split,
-                                                       im.buf + im.hi_off[side][i], im.buf + im.lo_off[side][i]);
-      else
-        core_image_kernel<false><<<blocks, 256, 0, s>>>(G, K, rout, im.Npad[side][i], im.nchunks[side][i], split,
-                                                        im.buf + im.hi_off[side][i], im.buf + im.lo_off[side][i]);
+      auto* kfn = bf16 ? core_image_kernel<true> : core_image_kernel<false>;
+      kfn<<<blocks, 256, 0, s>>>(G, tt->n, rin, im.R_in_pad[side][i], rout, im.Npad[side][i], im.nchunks[side][i],
+                                 KCB, split, im.buf + im.hi_off[side][i], im.buf + im.lo_off[side][i]);
     }
   PTTK_CUDA(cudaGetLastError());
   PTTK_CUDA(cudaStreamSynchronize(s));
   return PTTK_OK;
-}
-
-// Shared memory needed by chain_tc_kernel for this handle and form.
-static size_t tc_smem_bytes(int ld_s, uint32_t b_slot_bytes) {
-  return 2 * 2 * (size_t)TILE_M * KC_BYTES + 2 * 2 * (size_t)b_slot_bytes +
-         sizeof(float) * ((size_t)TILE_M * ld_s + (size_t)TILE_M * BV_LD + 1) + 8 + 6 * 8 + 16;
 }
 
 pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, bool source, const float* P, int64_t N,
@@ -533,6 +654,7 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, bool source,
   const int side = source ? 0 : 1;
   const bool bf16 = prec == PTTK_BF16 || prec == PTTK_BF16X3;
   const bool split = prec == PTTK_TF32X3 || prec == PTTK_BF16X3;
+  const int KCB = form_kcb(prec);
   TcArgs a{};
   a.nsteps = tt->d;
   a.n = tt->n;
@@ -541,46 +663,50 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, bool source,
   a.pts = P;
   a.out = out;
   a.status = d_status;
-  int rin_max = 1, npad_max = 16;
+  int npad_max = 16, spad_max = 8;
   for (int i = 0; i < tt->d; ++i) {
     int rin, rout, coord;
     oriented_core_dims(tt, source, i, &rin, &rout, &coord);
     TcStep& st = a.st[i];
     st.img_hi = im.buf + im.hi_off[side][i];
     st.img_lo = split ? im.buf + im.lo_off[side][i] : nullptr;
-    st.K = tt->n * rin;
     st.nchunks = im.nchunks[side][i];
     st.R_in = rin;
+    st.R_in_pad = im.R_in_pad[side][i];
     st.R_out = rout;
     st.Npad = im.Npad[side][i];
     st.coord = coord;
     const int bj = source ? coord : tt->d + tt->dtheta + coord;
     st.lo = (float)tt->box[bj][0];
     st.hi = (float)tt->box[bj][1];
-    rin_max = std::max(rin_max, rin);
     npad_max = std::max(npad_max, st.Npad);
+    // S must hold every R_in_pad (read) and, for non-last steps, Npad columns (written)
+    spad_max = std::max(spad_max, st.R_in_pad);
+    if (i < tt->d - 1) spad_max = std::max(spad_max, st.Npad);
   }
   if (npad_max > 256) return set_error(PTTK_ENOTSUP, "tensor-core chain: a rank above 256");
-  a.ld_s = (rin_max | 1);
-  if (a.ld_s < rin_max) a.ld_s += 2;
+  // row stride of S: a multiple of 4 floats, = 4 (mod 32) so float4 rows fall in distinct banks;
+  // it also holds the last step's 8 x 32 x 33 staging floats
+  int ld_s = ((spad_max + 31) / 32) * 32 + 4;
+  while ((size_t)TILE_M * ld_s < (size_t)NGEN_WARPS * 32 * STAGE_LD) ld_s += 32;
+  a.ld_s = ld_s;
   int cols = 32;
   while (cols < npad_max) cols <<= 1;
   a.tmem_cols = cols;
-  a.b_slot_bytes = (uint32_t)npad_max * KC_BYTES;
-  // the final output tile (128 x R_out floats) reuses the operand slots
-  const int rout_last = a.st[tt->d - 1].R_out;
-  const size_t operand_bytes = 2 * 2 * (size_t)TILE_M * KC_BYTES + 2 * 2 * (size_t)a.b_slot_bytes;
-  if ((size_t)TILE_M * rout_last * 4 > operand_bytes) return set_error(PTTK_ENOTSUP, "tensor-core chain: output tile");
-  a.out_aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
-  // at least 116 KB so that one CTA (and one TMEM allocation) fits per SM
-  const size_t smem = std::max<size_t>(tc_smem_bytes(a.ld_s, a.b_slot_bytes), 116 * 1024);
+  a.b_slot_bytes = (uint32_t)npad_max * KCB;
+  const size_t parts = split ? 2 : 1;
+  const int bv_ld = (tt->n + 1) | 1;
+  const size_t smem = (size_t)NSLOT * parts * TILE_M * KCB + (size_t)NSLOT * parts * a.b_slot_bytes +
+                      sizeof(float) * ((size_t)TILE_M * a.ld_s + (size_t)2 * TILE_M * bv_ld) + 16 +
+                      sizeof(StepS) * 3 + 8 * (3 * NSLOT + 1) + 16;
   if (smem > 227 * 1024) return set_error(PTTK_ENOTSUP, "tensor-core chain: ranks too large for shared memory");
+  const size_t smem_req = std::max<size_t>(smem, 116 * 1024);  // one CTA (one TMEM allocation) per SM
   const int64_t ntiles = (N + TILE_M - 1) / TILE_M;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sm_count());
   PTTK_PROF("chain_tc", s);
   auto launch = [&](auto kfn) -> pttk_status {
-    PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kfn<<<grid, NTHREADS, smem, s>>>(a);
+    PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req));
+    kfn<<<grid, TC_THREADS, smem_req, s>>>(a);
     PTTK_CUDA(cudaGetLastError());
     return PTTK_OK;
   };
