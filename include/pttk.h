@@ -149,10 +149,10 @@ void pttk_tt_free(pttk_tt* tt);
 pttk_status pttk_theta_core(const pttk_tt* tt, const double* theta, pttk_prec prec, void* M,
                             void* stream);
 
-/* Synchronise `stream` and report the handle's device status word: PTTK_ETIMEOUT if a kernel
- * working with this handle gave up a bounded wait since the last check (the word is then
- * cleared), else PTTK_OK. The tensor-core factor chain records such timeouts instead of
- * spinning; its outputs are unspecified when it does. */
+/* Synchronise `stream` and report the handle's device status word, then clear it:
+ * PTTK_ETIMEOUT if a kernel working with this handle gave up a bounded wait, PTTK_EDOMAIN if a
+ * batched call met a theta outside its box, else PTTK_OK. The tensor-core factor chain records
+ * such timeouts instead of spinning; its outputs are unspecified when it does. */
 pttk_status pttk_tt_check(const pttk_tt* tt, void* stream);
 
 /* Online instantiation: M = H(theta) as above, and the factor matrices of Algorithm 2,
@@ -171,6 +171,41 @@ pttk_status pttk_tt_check(const pttk_tt* tt, void* stream);
 pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void* X,
                              int64_t N_s, const void* Y, int64_t N_t, pttk_prec prec, void* U,
                              void* M, void* V, void* stream);
+
+/* ---- batched online stage --------------------------------------------------------- */
+
+/* A plan for B instances (theta_b, X_b, Y_b) of one TT: the points of all instances are
+ * concatenated, instance b owning rows [xoff[b], xoff[b+1]) of X (and of U) and rows
+ * [yoff[b], yoff[b+1]) of Y (and of V). xoff, yoff: host arrays of B + 1 nondecreasing
+ * int64 with xoff[0] = yoff[0] = 0, copied. prec as for pttk_instantiate. The plan allocates
+ * its scratch and, for tensor-core forms, lays out the core images (synchronising `stream`),
+ * so that pttk_instantiate_batched itself allocates nothing and never synchronises (it can
+ * be captured in a CUDA graph). The plan refers to `tt`, which must outlive it. */
+typedef struct pttk_batch pttk_batch;
+pttk_status pttk_batch_create(const pttk_tt* tt, int B, const int64_t* xoff, const int64_t* yoff,
+                              pttk_prec prec, void* stream, pttk_batch** out);
+void pttk_batch_free(pttk_batch* b);
+
+/* Launch configuration of the plan's tensor-core factor build (chunk width and operand-ring
+ * depth): 0 is the default; pttk_batch_get_config reports the current one and how many exist. */
+pttk_status pttk_batch_set_config(pttk_batch* b, int cfg);
+pttk_status pttk_batch_get_config(const pttk_batch* b, int* cfg, int* n_configs);
+
+/* Autotuner: times every launch configuration of the plan's factor build on the given inputs
+ * (one warm-up and three timed runs each, CUDA events on `stream`), keeps the fastest, and
+ * writes the mean milliseconds per configuration to ms_out (host, n_configs floats; may be
+ * NULL). Overwrites U and V. Synchronises. */
+pttk_status pttk_batch_autotune(pttk_batch* b, const void* X, const void* Y, void* U, void* V,
+                                float* ms_out, void* stream);
+
+/* Batched instantiation (Algorithm 3 per instance plus the Phase-3 factors of all points):
+ * M[b] = H(theta_b) for b < B (M: dev B x r_d x r_{d+d_theta}, each row-major), U = the
+ * source factors of all rows of X, V = the target factors of all rows of Y (factor rows depend
+ * only on their point). thetas: dev B x d_theta doubles (read on the device; a theta outside
+ * its box records PTTK_EDOMAIN in the handle's status word, see pttk_tt_check). X, Y, U, V as
+ * in pttk_instantiate for the concatenated point sets. Allocates nothing; no host sync. */
+pttk_status pttk_instantiate_batched(const pttk_batch* b, const double* thetas, const void* X,
+                                     const void* Y, void* U, void* M, void* V, void* stream);
 
 /* Low-rank product out = U (M (V^T w)) (Eq. paramlowrank applied to a vector).
  *   U: dev N_s x rs, M: dev rs x rt, V: dev N_t x rt, row-major; w: dev [N_t];

@@ -65,6 +65,9 @@ struct pttk_tt_ext : pttk_tt {
 
 namespace pttk {
 
+int* tt_status_word(const pttk_tt* tt) { return static_cast<const pttk_tt_ext*>(tt)->dstatus; }
+TcImageCache* tt_tc_cache(const pttk_tt* tt) { return static_cast<const pttk_tt_ext*>(tt)->tc; }
+
 const void* oriented_core_ptr(const pttk_tt* tt, bool source, int k, bool fp64) {
   const pttk_tt_ext* t = static_cast<const pttk_tt_ext*>(tt);
   if (source) return fp64 ? (const void*)(t->cores64 + t->core_off[k]) : (const void*)(t->cores32 + t->core_off[k]);
@@ -419,11 +422,8 @@ pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void*
     return PTTK_OK;
   }
   const pttk_tt_ext* t = static_cast<const pttk_tt_ext*>(tt);
-  PTTK_TRY(factor_build_tc(tt, t->tc, true, static_cast<const float*>(X), N_s, prec, static_cast<float*>(U),
-                           t->dstatus, s));
-  PTTK_TRY(factor_build_tc(tt, t->tc, false, static_cast<const float*>(Y), N_t, prec, static_cast<float*>(V),
-                           t->dstatus, s));
-  return PTTK_OK;
+  return factor_build_tc(tt, t->tc, static_cast<const float*>(X), N_s, static_cast<const float*>(Y), N_t, prec,
+                         static_cast<float*>(U), static_cast<float*>(V), t->dstatus, 0, s);
 }
 
 pttk_status pttk_tt_check(const pttk_tt* tt, void* stream) {

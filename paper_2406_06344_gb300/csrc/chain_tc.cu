@@ -175,31 +175,36 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, int M, int
 }
 
 struct TcStep {
-  const uint8_t* img_hi;  // nchunks x (Npad x KC_BYTES)
+  const uint8_t* img_hi;  // nchunks x (Npad x KCB)
   const uint8_t* img_lo;  // same, or null for single-product forms
   int nchunks, R_in, R_in_pad, R_out, Npad, coord;
   float lo, hi;           // box of the coordinate
 };
+// One launch builds both factors: work item i < T0 is tile i of the source points (side 0),
+// item i >= T0 is tile i - T0 of the target points (side 1). Factor rows depend only on their
+// own point, so a tile may span several instances of a batch.
 struct TcArgs {
-  TcStep st[3];
+  TcStep st[2][3];
   int nsteps, n, d;
-  int64_t N;
-  const float* pts;
-  float* out;
+  int64_t N[2];
+  int64_t T0, ntiles;
+  const float* pts[2];
+  float* out[2];
   int* status;
   int ld_s;               // row stride of S (floats, multiple of 4)
   int tmem_cols;
   uint32_t b_slot_bytes;  // bytes reserved per B part per slot
 };
 
-constexpr int NSLOT = 4;                   // operand ring depth
 constexpr int NGEN_WARPS = 8;              // A generators (2 threads per point row)
 constexpr int TC_THREADS = 64 + 32 * NGEN_WARPS;  // warp 0: TMA, warp 1: MMA, warps 2..9: A
 constexpr int STAGE_LD = 33;               // epilogue staging row stride (floats)
 
-template <bool BF16, bool SPLIT>
+// Launch configurations: bytes of K per row per chunk (KCB) and operand ring depth (NS).
+template <bool BF16, bool SPLIT, int KCB_, int NS>
 struct Cfg {
-  static constexpr int KCB = SPLIT ? 64 : 128;            // bytes of K per row per chunk
+  static constexpr int KCB = KCB_;
+  static constexpr int NSLOT = NS;
   static constexpr int PARTS = SPLIT ? 2 : 1;             // hi (and lo) operand parts
   static constexpr int E = BF16 ? 8 : 4;                  // elements per 16-byte unit
   static constexpr int UNITS = KCB / 16;                  // units per row per chunk
@@ -255,23 +260,25 @@ struct StepS {
   float lo_box, hi_box;
 };
 
-// Warp-specialised factor chain. Warp 0 (one lane) loads the core chunks with TMA into a
-// NSLOT-deep ring; warp 1 (one lane) issues the MMAs; warps 2..9 generate the A chunks (two
-// threads per point row, each writing half of the row's units) and run the epilogues.
-// Barriers per slot: full_a (8 generator warps arrive), full_b (TMA transaction bytes), empty
-// (tcgen05.commit of the slot's MMAs); acc_ready is committed after each step's last chunk.
-template <bool BF16, bool SPLIT>
+// Warp-specialised factor chain over both sides. Warp 0 (one lane) loads the core chunks with
+// TMA into an NSLOT-deep ring; warp 1 (one lane) issues the MMAs; warps 2..9 generate the A
+// chunks (two threads per point row, each writing half of the row's units) and run the
+// epilogues. Barriers per slot: full_a (8 generator warps arrive), full_b (TMA transaction
+// bytes), empty (tcgen05.commit of the slot's MMAs); acc_ready is committed after each step's
+// last chunk.
+template <bool BF16, bool SPLIT, int KCB_, int NS>
 __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
-  using C = Cfg<BF16, SPLIT>;
+  using C = Cfg<BF16, SPLIT, KCB_, NS>;
+  constexpr int NSLOT = C::NSLOT;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const int bv_ld = (a.n + 1) | 1;                                 // odd row stride > n
+  const int bv_ld = (a.n + 1) | 1;                                   // odd row stride > n
   uint8_t* a_base = smem;                                            // NSLOT x PARTS x A_PART
   uint8_t* b_base = a_base + (size_t)NSLOT * C::PARTS * C::A_PART;    // NSLOT x PARTS x b_slot_bytes
   float* S = reinterpret_cast<float*>(b_base + (size_t)NSLOT * C::PARTS * a.b_slot_bytes);  // 128 x ld_s
   float* Bv = S + (size_t)TILE_M * a.ld_s;                           // 2 x 128 x bv_ld
   StepS* steps = reinterpret_cast<StepS*>(
-      (reinterpret_cast<uintptr_t>(Bv + (size_t)2 * TILE_M * bv_ld) + 15) & ~uintptr_t(15));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(steps + 3);
+      (reinterpret_cast<uintptr_t>(Bv + (size_t)2 * TILE_M * bv_ld) + 15) & ~uintptr_t(15));  // [2][3]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(steps + 6);
   uint64_t* full_a = bars;
   uint64_t* full_b = bars + NSLOT;
   uint64_t* empty = bars + 2 * NSLOT;
@@ -291,8 +298,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (tid < a.nsteps) {
-    const TcStep& st = a.st[tid];
+  if (tid < 2 * a.nsteps) {
+    const int sd = tid / a.nsteps, si = tid % a.nsteps;
+    const TcStep& st = a.st[sd][si];
     StepS v;
     v.hi = st.img_hi;
     v.lo = st.img_lo;
@@ -305,7 +313,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     v.coord = st.coord;
     v.lo_box = st.lo;
     v.hi_box = st.hi;
-    steps[tid] = v;
+    steps[sd * 3 + si] = v;
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
@@ -315,7 +323,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int64_t ntiles = (a.N + TILE_M - 1) / TILE_M;
+  const int64_t ntiles = a.ntiles;
   const int nsteps = a.nsteps;
 
   if (warp == 0) {
@@ -323,9 +331,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     if (lane == 0) {
       uint32_t h = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+      for (int64_t it = blockIdx.x; it < ntiles && ok; it += gridDim.x) {
+        const int sd = it >= a.T0 ? 1 : 0;
         for (int si = 0; si < nsteps && ok; ++si) {
-          const StepS st = steps[si];
+          const StepS st = steps[sd * 3 + si];
           for (int c = 0; c < st.nchunks; ++c, ++h) {
             const uint32_t slot = h % NSLOT;
             if (h >= NSLOT && !mbar_wait(&empty[slot], ((h / NSLOT) - 1) & 1, abort_flag)) { ok = false; break; }
@@ -336,13 +345,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
             if (SPLIT) tma_load_1d(bh + a.b_slot_bytes, st.lo + (size_t)c * st.bytes, st.bytes, &full_b[slot]);
           }
         }
+      }
       if (!ok) {
         *abort_flag = 1;
         atomicExch(a.status, (int)PTTK_ETIMEOUT);
       }
-      // drain: every issued load has landed before the CTA may exit (the MMA side consumes them)
+      // drain: every issued load has landed before the CTA may exit
       const int zero = 0;
-      for (uint32_t k = (h > NSLOT ? h - NSLOT : 0); k < h; ++k)
+      for (uint32_t k = (h > (uint32_t)NSLOT ? h - NSLOT : 0); k < h; ++k)
         mbar_wait(&full_b[k % NSLOT], (k / NSLOT) & 1, &zero);
     }
     __syncwarp();
@@ -351,9 +361,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+      for (int64_t it = blockIdx.x; it < ntiles && ok; it += gridDim.x) {
+        const int sd = it >= a.T0 ? 1 : 0;
         for (int si = 0; si < nsteps && ok; ++si) {
-          const StepS st = steps[si];
+          const StepS st = steps[sd * 3 + si];
           for (int c = 0; c < st.nchunks; ++c, ++g) {
             const uint32_t slot = g % NSLOT, par = (g / NSLOT) & 1;
             if (!mbar_wait(&full_a[slot], par, abort_flag) || !mbar_wait(&full_b[slot], par, abort_flag)) {
@@ -385,6 +396,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
             if (c == st.nchunks - 1) umma_commit(acc_ready);
           }
         }
+      }
       if (!ok) {
         *abort_flag = 1;
         atomicExch(a.status, (int)PTTK_ETIMEOUT);
@@ -402,9 +414,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     const int half = gw >> 2;                  // which half of the row's units
     uint32_t g = 0, steps_done = 0;
     bool dead = false;
-    // basis of step (tile, si) into Bv buffer `buf` (threads of half 0; zero from index n on)
-    auto basis = [&](int64_t tile, int si, int buf, float x) {
-      const StepS& st = steps[si];
+    // basis of step si of side sd into Bv buffer `buf` (threads of half 0; zero from index n on)
+    auto basis = [&](int sd, int si, int buf, float x) {
+      const StepS& st = steps[sd * 3 + si];
       const float xh = (2.f * x - st.lo_box - st.hi_box) / (st.lo_box - st.hi_box);
       float* bv = Bv + ((size_t)buf * TILE_M + row) * bv_ld;
       float t0 = 1.f, t1 = xh;
@@ -417,23 +429,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
       }
       for (int k = a.n; k < bv_ld; ++k) bv[k] = 0.f;
     };
-    auto coord_of = [&](int64_t tile, int si) -> float {
-      const int64_t gp = tile * TILE_M + row;
-      return gp < a.N ? a.pts[gp * a.d + steps[si].coord] : steps[si].lo_box;
+    auto coord_of = [&](int64_t it, int si) -> float {
+      const int sd = it >= a.T0 ? 1 : 0;
+      const int64_t gp = (sd ? it - a.T0 : it) * TILE_M + row;
+      const StepS& st = steps[sd * 3 + si];
+      return gp < a.N[sd] ? a.pts[sd][gp * a.d + st.coord] : st.lo_box;
     };
-    float xn[3] = {0.f, 0.f, 0.f};  // coordinates of this row for the tile being built
-    if (half == 0 && blockIdx.x < ntiles)
+    float xn[3] = {0.f, 0.f, 0.f};  // coordinates of this row for the next tile to build
+    if (half == 0 && blockIdx.x < ntiles) {
       for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
+      basis(blockIdx.x >= a.T0 ? 1 : 0, 0, 0, xn[0]);
+    }
     uint32_t bufsel = 0;
-    if (half == 0 && blockIdx.x < ntiles) basis(blockIdx.x, 0, 0, xn[0]);
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      const int64_t row0 = tile * TILE_M;
-      const int rows = (int)std::min<int64_t>(TILE_M, a.N - row0);
+    for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
+      const int sd = it >= a.T0 ? 1 : 0;
+      const int64_t row0 = (sd ? it - a.T0 : it) * TILE_M;
+      const int rows = (int)std::min<int64_t>(TILE_M, a.N[sd] - row0);
       float xcur[3] = {xn[0], xn[1], xn[2]};
-      // prefetch the next tile's coordinates (latency hidden behind this tile)
-      const int64_t tnext = tile + gridDim.x;
-      if (half == 0 && tnext < ntiles)
-        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(tnext, si);
+      const int64_t itn = it + gridDim.x;  // next item: prefetch its coordinates
+      if (half == 0 && itn < ntiles)
+        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
       if (half == 0) {
         float4* s4 = reinterpret_cast<float4*>(S + (size_t)row * a.ld_s);
         s4[0] = make_float4(1.f, 0.f, 0.f, 0.f);  // S_0 = 1 (r_0 = 1), zero padding
@@ -441,13 +456,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
       }
       gen_barrier();
       for (int si = 0; si < nsteps; ++si) {
-        const StepS st = steps[si];
+        const StepS st = steps[sd * 3 + si];
         const float* bvrow = Bv + ((size_t)bufsel * TILE_M + row) * bv_ld;
         const float* srow = S + (size_t)row * a.ld_s;
         for (int c = 0; c < st.nchunks; ++c, ++g) {
           const uint32_t slot = g % NSLOT, use = g / NSLOT;
           dead = dead || *abort_flag;
-          if (!dead && g >= NSLOT) dead = !mbar_wait(&empty[slot], (use - 1) & 1, abort_flag);
+          if (!dead && g >= (uint32_t)NSLOT) dead = !mbar_wait(&empty[slot], (use - 1) & 1, abort_flag);
           dead = __any_sync(0xffffffffu, dead);
           if (dead && lane == 0) *abort_flag = 1;
           if (!dead) {
@@ -472,12 +487,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
           __syncwarp();
           if (lane == 0) mbar_arrive(&full_a[slot]);
         }
-        // the next basis (next step, or step 0 of the next tile) goes to the other buffer
+        // the next basis (next step, or step 0 of the next item) goes to the other buffer
         // while this step's MMAs drain
         const bool last = si == nsteps - 1;
         if (half == 0) {
-          if (!last) basis(tile, si + 1, bufsel ^ 1, xcur[si + 1]);
-          else if (tnext < ntiles) basis(tnext, 0, bufsel ^ 1, xn[0]);
+          if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
+          else if (itn < ntiles) basis(itn >= a.T0 ? 1 : 0, 0, bufsel ^ 1, xn[0]);
         }
         // accumulator of this step is complete (all A chunks of the step, hence all reads of
         // S for it, are done once it is)
@@ -504,7 +519,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
           // output rows: each warp stages 32 rows x 32 columns, then writes row segments
           float* stg = stage + (size_t)gw * 32 * STAGE_LD;
           const int R = st.R_out;
-          float* outbase = a.out + (row0 + 32 * (warp & 3)) * R;
+          float* outbase = a.out[sd] + (row0 + 32 * (warp & 3)) * R;
           const int wrows = std::max(0, std::min(32, rows - 32 * (warp & 3)));
           for (int cb = 32 * half; cb < st.Npad; cb += 64) {
             float v[32];
@@ -578,9 +593,9 @@ std::mutex g_img_mu;
 
 }  // namespace
 
-// Per-handle image cache (indexed by form), allocated on first use and freed with the handle.
+// Per-handle image cache, indexed by form and chunk width (64 or 128 bytes of K per row).
 struct TcImageCache {
-  Images img[4];
+  Images img[4][2];
 };
 
 static int form_index(pttk_prec p) {
@@ -593,20 +608,18 @@ static int form_index(pttk_prec p) {
   }
 }
 
-static int form_kcb(pttk_prec p) { return (p == PTTK_TF32X3 || p == PTTK_BF16X3) ? 64 : 128; }
-
 TcImageCache* tc_cache_new() { return new TcImageCache(); }
 void tc_cache_free(TcImageCache* c) {
   if (!c) return;
-  for (auto& im : c->img)
-    if (im.buf) cudaFree(im.buf);
+  for (auto& f : c->img)
+    for (auto& im : f)
+      if (im.buf) cudaFree(im.buf);
   delete c;
 }
 
-static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, Images& im, cudaStream_t s) {
+static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, int KCB, Images& im, cudaStream_t s) {
   const bool bf16 = prec == PTTK_BF16 || prec == PTTK_BF16X3;
   const bool split = prec == PTTK_TF32X3 || prec == PTTK_BF16X3;
-  const int KCB = form_kcb(prec);
   const int KC = KCB / (bf16 ? 2 : 4);
   const int E = bf16 ? 8 : 4;
   size_t total = 0;
@@ -641,49 +654,89 @@ static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, Images& im, c
   return PTTK_OK;
 }
 
-pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, bool source, const float* P, int64_t N,
-                            pttk_prec prec, float* out, int* d_status, cudaStream_t s) {
-  if (N == 0) return PTTK_OK;
+// Launch configurations per form: {KCB, NSLOT}. Configuration 0 is the default.
+static const int kTcConfigs[2][2] = {{128, 4}, {64, 4}};
+static const int kTcConfigsSplit[2][2] = {{64, 4}, {128, 2}};
+
+int tc_config_count() { return 2; }
+
+static void tc_config(pttk_prec prec, int cfg, int* KCB, int* NS) {
+  const bool split = prec == PTTK_TF32X3 || prec == PTTK_BF16X3;
+  const int (*t)[2] = split ? kTcConfigsSplit : kTcConfigs;
+  cfg = (cfg < 0 || cfg > 1) ? 0 : cfg;
+  *KCB = t[cfg][0];
+  *NS = t[cfg][1];
+}
+
+// Images for (prec, config) exist after this returns (first use lays them out; synchronises).
+pttk_status tc_prepare(const pttk_tt* tt, TcImageCache* cache, pttk_prec prec, int cfg, cudaStream_t s) {
   const int fi = form_index(prec);
   if (fi < 0) return set_error(PTTK_EINVAL, "not a tensor-core form");
-  Images& im = cache->img[fi];
-  {
-    std::lock_guard<std::mutex> lk(g_img_mu);
-    if (!im.buf) PTTK_TRY(build_images(tt, prec, im, s));
-  }
-  const int side = source ? 0 : 1;
+  int KCB, NS;
+  tc_config(prec, cfg, &KCB, &NS);
+  Images& im = cache->img[fi][KCB == 64 ? 0 : 1];
+  std::lock_guard<std::mutex> lk(g_img_mu);
+  if (!im.buf) PTTK_TRY(build_images(tt, prec, KCB, im, s));
+  return PTTK_OK;
+}
+
+template <bool BF16, bool SPLIT, int KCB, int NS>
+static pttk_status launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
+  auto kfn = chain_tc_kernel<BF16, SPLIT, KCB, NS>;
+  PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned grid = (unsigned)std::min<int64_t>(a.ntiles, sm_count());
+  kfn<<<grid, TC_THREADS, smem, s>>>(a);
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
+// Both factors in one persistent launch: U (N_s rows from X) and V (N_t rows from Y).
+pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float* X, int64_t N_s,
+                            const float* Y, int64_t N_t, pttk_prec prec, float* U, float* V, int* d_status,
+                            int cfg, cudaStream_t s) {
+  if (N_s == 0 && N_t == 0) return PTTK_OK;
+  PTTK_TRY(tc_prepare(tt, cache, prec, cfg, s));
+  const int fi = form_index(prec);
+  int KCB, NS;
+  tc_config(prec, cfg, &KCB, &NS);
+  const Images& im = cache->img[fi][KCB == 64 ? 0 : 1];
   const bool bf16 = prec == PTTK_BF16 || prec == PTTK_BF16X3;
   const bool split = prec == PTTK_TF32X3 || prec == PTTK_BF16X3;
-  const int KCB = form_kcb(prec);
   TcArgs a{};
   a.nsteps = tt->d;
   a.n = tt->n;
   a.d = tt->d;
-  a.N = N;
-  a.pts = P;
-  a.out = out;
+  a.N[0] = N_s;
+  a.N[1] = N_t;
+  a.T0 = (N_s + TILE_M - 1) / TILE_M;
+  a.ntiles = a.T0 + (N_t + TILE_M - 1) / TILE_M;
+  a.pts[0] = X;
+  a.pts[1] = Y;
+  a.out[0] = U;
+  a.out[1] = V;
   a.status = d_status;
   int npad_max = 16, spad_max = 8;
-  for (int i = 0; i < tt->d; ++i) {
-    int rin, rout, coord;
-    oriented_core_dims(tt, source, i, &rin, &rout, &coord);
-    TcStep& st = a.st[i];
-    st.img_hi = im.buf + im.hi_off[side][i];
-    st.img_lo = split ? im.buf + im.lo_off[side][i] : nullptr;
-    st.nchunks = im.nchunks[side][i];
-    st.R_in = rin;
-    st.R_in_pad = im.R_in_pad[side][i];
-    st.R_out = rout;
-    st.Npad = im.Npad[side][i];
-    st.coord = coord;
-    const int bj = source ? coord : tt->d + tt->dtheta + coord;
-    st.lo = (float)tt->box[bj][0];
-    st.hi = (float)tt->box[bj][1];
-    npad_max = std::max(npad_max, st.Npad);
-    // S must hold every R_in_pad (read) and, for non-last steps, Npad columns (written)
-    spad_max = std::max(spad_max, st.R_in_pad);
-    if (i < tt->d - 1) spad_max = std::max(spad_max, st.Npad);
-  }
+  for (int side = 0; side < 2; ++side)
+    for (int i = 0; i < tt->d; ++i) {
+      int rin, rout, coord;
+      oriented_core_dims(tt, side == 0, i, &rin, &rout, &coord);
+      TcStep& st = a.st[side][i];
+      st.img_hi = im.buf + im.hi_off[side][i];
+      st.img_lo = split ? im.buf + im.lo_off[side][i] : nullptr;
+      st.nchunks = im.nchunks[side][i];
+      st.R_in = rin;
+      st.R_in_pad = im.R_in_pad[side][i];
+      st.R_out = rout;
+      st.Npad = im.Npad[side][i];
+      st.coord = coord;
+      const int bj = side == 0 ? coord : tt->d + tt->dtheta + coord;
+      st.lo = (float)tt->box[bj][0];
+      st.hi = (float)tt->box[bj][1];
+      npad_max = std::max(npad_max, st.Npad);
+      // S must hold every R_in_pad (read) and, for non-last steps, Npad columns (written)
+      spad_max = std::max(spad_max, st.R_in_pad);
+      if (i < tt->d - 1) spad_max = std::max(spad_max, st.Npad);
+    }
   if (npad_max > 256) return set_error(PTTK_ENOTSUP, "tensor-core chain: a rank above 256");
   // row stride of S: a multiple of 4 floats, = 4 (mod 32) so float4 rows fall in distinct banks;
   // it also holds the last step's 8 x 32 x 33 staging floats
@@ -694,24 +747,20 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, bool source,
   while (cols < npad_max) cols <<= 1;
   a.tmem_cols = cols;
   a.b_slot_bytes = (uint32_t)npad_max * KCB;
-  const size_t parts = split ? 2 : 1;
   const int bv_ld = (tt->n + 1) | 1;
-  const size_t smem = (size_t)NSLOT * parts * TILE_M * KCB + (size_t)NSLOT * parts * a.b_slot_bytes +
+  const size_t parts = split ? 2 : 1;
+  const size_t smem = (size_t)NS * parts * TILE_M * KCB + (size_t)NS * parts * a.b_slot_bytes +
                       sizeof(float) * ((size_t)TILE_M * a.ld_s + (size_t)2 * TILE_M * bv_ld) + 16 +
-                      sizeof(StepS) * 3 + 8 * (3 * NSLOT + 1) + 16;
+                      sizeof(StepS) * 6 + 8 * (3 * NS + 1) + 16;
   if (smem > 227 * 1024) return set_error(PTTK_ENOTSUP, "tensor-core chain: ranks too large for shared memory");
   const size_t smem_req = std::max<size_t>(smem, 116 * 1024);  // one CTA (one TMEM allocation) per SM
-  const int64_t ntiles = (N + TILE_M - 1) / TILE_M;
-  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sm_count());
   PTTK_PROF("chain_tc", s);
-  auto launch = [&](auto kfn) -> pttk_status {
-    PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req));
-    kfn<<<grid, TC_THREADS, smem_req, s>>>(a);
-    PTTK_CUDA(cudaGetLastError());
-    return PTTK_OK;
-  };
-  if (bf16) return split ? launch(chain_tc_kernel<true, true>) : launch(chain_tc_kernel<true, false>);
-  return split ? launch(chain_tc_kernel<false, true>) : launch(chain_tc_kernel<false, false>);
+  if (bf16) {
+    if (split) return KCB == 64 ? launch_tc<true, true, 64, 4>(a, smem_req, s) : launch_tc<true, true, 128, 2>(a, smem_req, s);
+    return KCB == 128 ? launch_tc<true, false, 128, 4>(a, smem_req, s) : launch_tc<true, false, 64, 4>(a, smem_req, s);
+  }
+  if (split) return KCB == 64 ? launch_tc<false, true, 64, 4>(a, smem_req, s) : launch_tc<false, true, 128, 2>(a, smem_req, s);
+  return KCB == 128 ? launch_tc<false, false, 128, 4>(a, smem_req, s) : launch_tc<false, false, 64, 4>(a, smem_req, s);
 }
 
 }  // namespace pttk

@@ -82,8 +82,13 @@ void dgemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alp
 struct TcImageCache;
 TcImageCache* tc_cache_new();
 void tc_cache_free(TcImageCache* c);
-pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, bool source, const float* P,
-                            int64_t N, pttk_prec prec, float* out, int* d_status, cudaStream_t s);
+// Both factors in one persistent launch; cfg selects a launch configuration (0 = default,
+// tc_config_count() of them). Lays out the core images on first use (synchronises once).
+pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float* X, int64_t N_s,
+                            const float* Y, int64_t N_t, pttk_prec prec, float* U, float* V,
+                            int* d_status, int cfg, cudaStream_t s);
+pttk_status tc_prepare(const pttk_tt* tt, TcImageCache* cache, pttk_prec prec, int cfg, cudaStream_t s);
+int tc_config_count();
 
 // --- online.cu -------------------------------------------------------------------------
 pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64, void* M,

@@ -47,6 +47,13 @@ SIGNATURES = [
     ("pttk_tt_check", _int, [_vp, _vp]),
     ("pttk_instantiate", _int, [_vp, _c_double_p, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp, _vp]),
     ("pttk_apply", _int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, _vp, _vp, _vp]),
+    ("pttk_batch_create", _int, [_vp, _int, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _int, _vp,
+                                 ctypes.POINTER(_vp)]),
+    ("pttk_batch_free", None, [_vp]),
+    ("pttk_batch_set_config", _int, [_vp, _int]),
+    ("pttk_batch_get_config", _int, [_vp, _c_int_p, _c_int_p]),
+    ("pttk_batch_autotune", _int, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_float), _vp]),
+    ("pttk_instantiate_batched", _int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("pttk_apply_noalloc", _int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, _vp, _vp, _vp]),
     ("pttk_profile_enable", _int, [_int]),
     ("pttk_profile_reset", _int, []),
@@ -262,6 +269,66 @@ def apply(U, M, V, w, out=None, stream=None):
     _check(load().pttk_apply(_ptr(U), _ptr(M), _ptr(V), U.shape[0], V.shape[0], U.shape[1], V.shape[1],
                              prec, _ptr(w), _ptr(out), _stream(stream)))
     return out
+
+
+class Batch:
+    """pttk_batch plan: B instances with concatenated point sets (offsets on the host)."""
+
+    def __init__(self, tt: TT, xoff, yoff, prec="fp32", stream=None):
+        self.tt = tt
+        self.prec = _prec(prec)
+        xo = np.ascontiguousarray(xoff, dtype=np.int64)
+        yo = np.ascontiguousarray(yoff, dtype=np.int64)
+        self.B = len(xo) - 1
+        self.Ns, self.Nt = int(xo[-1]), int(yo[-1])
+        h = ctypes.c_void_p()
+        _check(load().pttk_batch_create(tt.handle, self.B, xo.ctypes.data_as(ctypes.POINTER(_i64)),
+                                        yo.ctypes.data_as(ctypes.POINTER(_i64)), self.prec, _stream(stream),
+                                        ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def config(self):
+        c, n = _int(), _int()
+        _check(load().pttk_batch_get_config(self._h, ctypes.byref(c), ctypes.byref(n)))
+        return c.value, n.value
+
+    def set_config(self, cfg: int):
+        _check(load().pttk_batch_set_config(self._h, cfg))
+
+    def autotune(self, X, Y, U, V, stream=None):
+        """Times every launch configuration (pttk_batch_autotune); returns ms per configuration."""
+        n = self.config[1]
+        ms = (ctypes.c_float * n)()
+        _check(load().pttk_batch_autotune(self._h, _ptr(X), _ptr(Y), _ptr(U), _ptr(V), ms, _stream(stream)))
+        return list(ms)
+
+    def instantiate(self, thetas, X, Y, U=None, M=None, V=None, stream=None):
+        """pttk_instantiate_batched: thetas is a (B, d_theta) float64 CUDA tensor."""
+        import torch
+        dt = _dtype(self.prec)
+        r = self.tt.ranks
+        d, dth, _, _ = self.tt.dims
+        if U is None:
+            U = torch.empty(self.Ns, r[d], dtype=dt, device="cuda")
+        if V is None:
+            V = torch.empty(self.Nt, r[d + dth], dtype=dt, device="cuda")
+        if M is None:
+            M = torch.empty(self.B, r[d], r[d + dth], dtype=dt, device="cuda")
+        _check(load().pttk_instantiate_batched(self._h, _ptr(thetas), _ptr(X), _ptr(Y), _ptr(U), _ptr(M),
+                                               _ptr(V), _stream(stream)))
+        return U, M, V
+
+    def free(self):
+        if getattr(self, "_h", None):
+            load().pttk_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def apply_noalloc(U, M, V, w, out, stream=None):
