@@ -207,6 +207,24 @@ pttk_status pttk_batch_autotune(pttk_batch* b, const void* X, const void* Y, voi
 pttk_status pttk_instantiate_batched(const pttk_batch* b, const double* thetas, const void* X,
                                      const void* Y, void* U, void* M, void* V, void* stream);
 
+/* ---- adjoint ------------------------------------------------------------------------ */
+
+/* Loss L = w^T K~(X, Y; theta) z = w^T U M V^T z and its gradients (the paper motivates
+ * derivatives in the hyperparameters for Gaussian-process use but gives no adjoint; these
+ * follow from Eq. hmat and Algorithm 2, Phase 3 by the chain rule):
+ *   dL/dtheta_j = (U^T w)^T H_1 .. H_j' .. H_dtheta (V^T z), H_j' with T_k' in place of T_k;
+ *   dL/dX by a reverse pass through the factor chain that recomputes the Chebyshev bases
+ *   and their derivatives per point.
+ *   theta: host [d_theta] (inside its box, else PTTK_EDOMAIN). X, Y, w (N_s), z (N_t): dev,
+ *   double for PTTK_FP64, float otherwise. prec selects the form of the forward factors (as in
+ *   pttk_instantiate); the reverse pass runs in FP64 (PTTK_FP64) or FP32 SIMT, sums over the
+ *   points accumulate in FP64. Outputs (each may be NULL): loss (host double), dtheta (host
+ *   [d_theta] doubles), dX (dev N_s x d, row-major, type of X). Allocates stream-ordered
+ *   scratch; synchronises `stream`. */
+pttk_status pttk_grad(const pttk_tt* tt, const double* theta, const void* X, int64_t N_s,
+                      const void* Y, int64_t N_t, const void* w, const void* z, pttk_prec prec,
+                      double* loss, double* dtheta, void* dX, void* stream);
+
 /* Low-rank product out = U (M (V^T w)) (Eq. paramlowrank applied to a vector).
  *   U: dev N_s x rs, M: dev rs x rt, V: dev N_t x rt, row-major; w: dev [N_t];
  *   out: dev [N_s]. prec: PTTK_FP64 (all double) or PTTK_FP32 (all float; reductions

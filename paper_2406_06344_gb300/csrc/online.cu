@@ -352,16 +352,16 @@ static pttk_status launch_chain(const ChainArgs& a, const T* pts, T* out, cudaSt
 const void* oriented_core_ptr(const pttk_tt* tt, bool source, int k, bool fp64);
 
 pttk_status factor_build_run(const pttk_tt* tt, bool source, const void* P, int64_t N,
-                             pttk_prec prec, void* out, cudaStream_t s) {
+                             pttk_prec prec, void* out, cudaStream_t s, int nsteps) {
   if (N == 0) return PTTK_OK;
   const bool fp64 = prec == PTTK_FP64;
   ChainArgs a{};
-  a.nsteps = tt->d;
+  a.nsteps = (nsteps > 0 && nsteps < tt->d) ? nsteps : tt->d;
   a.n = tt->n;
   a.d = tt->d;
   a.N = N;
   int rmax = 1;
-  for (int i = 0; i < tt->d; ++i) {
+  for (int i = 0; i < a.nsteps; ++i) {
     int rin, rout, coord;
     const int k = oriented_core_dims(tt, source, i, &rin, &rout, &coord);
     a.st[i].G = oriented_core_ptr(tt, source, k, fp64);

@@ -93,8 +93,14 @@ int tc_config_count();
 // --- online.cu -------------------------------------------------------------------------
 pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64, void* M,
                            cudaStream_t s);
+// SIMT chain (FP64 / FP32); nsteps < d stops after that many steps (out: N x r_nsteps).
 pttk_status factor_build_run(const pttk_tt* tt, bool source, const void* P, int64_t N,
-                             pttk_prec prec, void* out, cudaStream_t s);
+                             pttk_prec prec, void* out, cudaStream_t s, int nsteps = 0);
+int oriented_core_dims(const pttk_tt* tt, bool source, int step, int* R_in, int* R_out, int* coord);
+const void* oriented_core_ptr(const pttk_tt* tt, bool source, int k, bool fp64);
+int* tt_status_word(const pttk_tt* tt);
+struct TcImageCache;
+TcImageCache* tt_tc_cache(const pttk_tt* tt);
 pttk_status apply_run(const void* U, const void* M, const void* V, int64_t N_s, int64_t N_t,
                       int rs, int rt, bool fp64, const void* w, void* out, void* scratch,
                       cudaStream_t s);

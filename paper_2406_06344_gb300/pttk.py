@@ -54,6 +54,8 @@ SIGNATURES = [
     ("pttk_batch_get_config", _int, [_vp, _c_int_p, _c_int_p]),
     ("pttk_batch_autotune", _int, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_float), _vp]),
     ("pttk_instantiate_batched", _int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("pttk_grad", _int, [_vp, _c_double_p, _vp, _i64, _vp, _i64, _vp, _vp, _int, _c_double_p, _c_double_p,
+                         _vp, _vp]),
     ("pttk_apply_noalloc", _int, [_vp, _vp, _vp, _i64, _i64, _int, _int, _int, _vp, _vp, _vp]),
     ("pttk_profile_enable", _int, [_int]),
     ("pttk_profile_reset", _int, []),
@@ -269,6 +271,61 @@ def apply(U, M, V, w, out=None, stream=None):
     _check(load().pttk_apply(_ptr(U), _ptr(M), _ptr(V), U.shape[0], V.shape[0], U.shape[1], V.shape[1],
                              prec, _ptr(w), _ptr(out), _stream(stream)))
     return out
+
+
+def grad(tt: TT, theta, X, Y, w, z, prec="fp32", want_dX=True, stream=None):
+    """pttk_grad: returns (loss, dL/dtheta as a numpy array, dL/dX as a CUDA tensor or None)."""
+    import torch
+    prec = _prec(prec)
+    d, dth, _, _ = tt.dims
+    loss = ctypes.c_double()
+    dtheta = (ctypes.c_double * max(1, dth))()
+    dX = torch.empty_like(X) if want_dX else None
+    _check(load().pttk_grad(tt.handle, _dbl(theta), _ptr(X), X.shape[0], _ptr(Y), Y.shape[0], _ptr(w), _ptr(z),
+                            prec, ctypes.byref(loss), dtheta, _ptr(dX) if want_dX else None, _stream(stream)))
+    return loss.value, np.array(dtheta[:dth]), dX
+
+
+def _make_loss_function():
+    import torch
+
+    class PTTKLoss(torch.autograd.Function):
+        """L = w^T K~(X, Y; theta) z with gradients in theta and X from pttk_grad.
+
+        forward(theta (d_theta tensor), X (N_s x d CUDA tensor), Y, w, z, tt, prec) -> scalar.
+        The gradients are computed by the library in the same call as the loss and handed
+        back by backward (scaled by the incoming gradient)."""
+
+        @staticmethod
+        def forward(ctx, theta, X, Y, w, z, tt, prec):
+            th = [float(v) for v in theta.detach().cpu().reshape(-1)]
+            loss, dth, dX = grad(tt, th, X.detach().contiguous(), Y.detach().contiguous(),
+                                 w.detach().contiguous(), z.detach().contiguous(), prec,
+                                 want_dX=X.requires_grad)
+            ctx.save_for_backward(torch.tensor(dth, dtype=theta.dtype, device=theta.device),
+                                  dX if dX is not None else torch.empty(0))
+            ctx.has_dX = dX is not None
+            return torch.tensor(loss, dtype=X.dtype, device=X.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            dth, dX = ctx.saved_tensors
+            g = grad_out.to(dth.dtype)
+            return (g.to(dth.device) * dth, (grad_out * dX) if ctx.has_dX else None,
+                    None, None, None, None, None)
+
+    return PTTKLoss
+
+
+_loss_fn = None
+
+
+def pttk_loss(theta, X, Y, w, z, tt: TT, prec="fp32"):
+    """Differentiable L = w^T K~ z (theta: tensor of d_theta values; X: CUDA tensor)."""
+    global _loss_fn
+    if _loss_fn is None:
+        _loss_fn = _make_loss_function()
+    return _loss_fn.apply(theta, X, Y, w, z, tt, prec)
 
 
 class Batch:
