@@ -1,28 +1,31 @@
 #!/usr/bin/env python
 """Benchmark of the PTTK hot path on the d = 3 general-nu Matern workload.
 
-Workload (seeded, synthetic, shaped like the paper's experiments): source box [0,1]^3,
-target box [3,4] x [0,1]^2, theta = (l, nu) in [0.5, 2] x [0.5, 2.5], n = 12 Chebyshev nodes
-per mode (12^8 = 429,981,696-entry grid), N_s = N_t = 1,000,000 uniform points, 256 theta.
+Workload (seeded, synthetic, shaped like the paper's experiments): source box [0,1]^3, target
+box [3,4] x [0,1]^2, theta = (l, nu) in [0.5, 2] x [0.5, 2.5], n = 12 Chebyshev nodes per mode
+(12^8 = 429,981,696-entry grid), N_s = N_t = 1,000,000 uniform points, 256 theta values.
 
-One step is one pass of the whole hot path over that batch:
-  1. grid evaluation + Chebyshev transform (pttk_grid_coeffs), FP64 (the plain form) and
-     FP32 (the fast form), each timed;
-  2. TT-SVD of the FP64 coefficient tensor, tol 1e-10 (pttk_tt_from_coeffs);
+One timed step is one pass of the whole hot path over that batch:
+  1. grid evaluation + Chebyshev transform (pttk_grid_coeffs) in FP64 (the plain form) and in
+     FP32 (the fast form);
+  2. TT-SVD of the FP64 coefficient tensor at tol 1e-10 (pttk_tt_from_coeffs);
   3. 256 online instantiations (pttk_instantiate: H(theta), U(X), V(Y)) at N = 1M per side in
-     the fast online form, plus one in the plain FP64 form;
-  4. apply (pttk_apply) of the last factors to a vector.
-The reported value is online factor builds/s (builds of the fast form / their total device
-time); grid entries/s and the plain-FP64 rates are reported beside it.
+     the fast online form (3xTF32 on the tensor cores);
+  4. pttk_apply of the last factors to a vector.
+`value` is online factor builds/s: builds of the fast form divided by their device time inside
+the timed steps. Beside it: grid entries/s (FP64 and FP32), every online form's build rate and
+its measured error, the batched form (1024 instances, one launch under a CUDA graph) and the
+adjoint (N = 500k), rooflines, an end-to-end rate through pinned host buffers, and the FP64
+CPU oracle timed on the host cores.
 
---impl reference times the FP64 CPU oracle (the reference arm) on a bounded sample of the
-same workload and reports the same metric.
+--impl reference times the FP64 CPU oracle (the reference arm) on a bounded sample of the same
+workload and reports the same metric.
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -38,9 +41,12 @@ import numpy as np  # noqa: E402
 METRIC = "online factor builds/s (N=1M) & grid entries/s vs FP64 plain at stated rel err"
 UNIT = "builds/s"
 FAST_FORM = "tf32x3"
-OTHER_FORMS = ("fp64", "fp32", "tf32", "bf16", "bf16x3")
+FORMS = ("fp64", "fp32", "tf32", "tf32x3", "bf16", "bf16x3")
 N_THETA = 256
-FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12   # FFMA lanes/SM x 2 flops x SMs x max clock
+WORKLOAD = "d3 matern-nu n12 (12^8 grid), N_s=N_t=1M, 256 theta"
+# nominal dense tensor rates (PFLOP/s) used to carry the measured BF16 peak to other dtypes
+NOMINAL = {"bf16": 2.25, "tf32": 1.1}
+FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12   # FFMA lanes/SM x 2 x SMs x max clock
 FP64_PEAK_TFLOPS = 1.25                             # nominal FP64 rate of the part
 
 
@@ -51,7 +57,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pttk", choices=["pttk", "reference"])
     ap.add_argument("--n-theta", type=int, default=N_THETA)
-    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-form/batched/adjoint/CPU legs")
     return ap.parse_args()
 
 
@@ -59,12 +65,13 @@ def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         d = json.load(open(path))
-        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
-    return 6800.0, 1900.0, "fallback"
+        return (d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0),
+                d.get("bf16_tflops_sustained", 1700.0), "measured")
+    return 6800.0, 1900.0, 1700.0, "fallback"
 
 
 class Clocks:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples every 200 ms during the timed region."""
 
     def __init__(self, index: int):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
@@ -87,20 +94,24 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.strip()]
+        rows = [[c.strip() for c in l.split(",")] for l in open(self.f.name).read().splitlines() if l.strip()]
         os.unlink(self.f.name)
-        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if len(r) >= 9 and num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if len(r) >= 9 and num(r[2]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
         for r in rows:
-            if len(r) < 9:
-                continue
-            for name, v in zip(names, r[5:9]):
-                if v.strip().lower() == "active":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None,
+            if len(r) >= 9:
+                for name, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
@@ -112,19 +123,18 @@ def chain_flops(ranks, d, dtheta, n, N):
     return 2.0 * n * N * (src + tgt)
 
 
-def cpu_leg(w, tt_cores, n_points: int):
-    """Times the oracle (as it stands) on a bounded sample: the online build of n_points per
-    side with the given cores, and the grid evaluation + transform of one n^(D-1) slab."""
+def cpu_leg(w, cores, n_points: int):
+    """The oracle as it stands, timed on a bounded sample: the online build (H(theta) and both
+    factor chains) of n_points per side with the given cores, and the grid evaluation plus
+    transform of one n^(D-1) slab of the coefficient grid."""
     import oracle.pttk_oracle as o
     from paper_2406_06344_gb300 import workloads as W
     X, Y = W.sources(w, n_points), W.targets(w, n_points)
     th = W.thetas(w, 1)[0]
     t0 = time.perf_counter()
-    o.instantiate(tt_cores, w.d, w.dtheta, w.mode_boxes(), th, X, Y)
+    o.instantiate(cores, w.d, w.dtheta, w.mode_boxes(), th, X, Y)
     t_build = time.perf_counter() - t0
     builds_per_s = 1.0 / (t_build * w.n_points / n_points)
-    import dataclasses
-    ws = dataclasses.replace(w, d=w.d)
     t0 = time.perf_counter()
     f = o.kernel_f(w.kernel)
     eta = o.node_vectors(w.mode_boxes(), w.n)
@@ -136,43 +146,34 @@ def cpu_leg(w, tt_cores, n_points: int):
     for k in range(w.D - 1):
         slab = o.mode_product(slab, A, k)
     t_grid = time.perf_counter() - t0
-    entries_per_s = w.n ** (w.D - 1) / t_grid
-    cores = os.cpu_count()
-    return builds_per_s, entries_per_s, t_build, t_grid, cores
+    return builds_per_s, w.n ** (w.D - 1) / t_grid, t_build, t_grid, os.cpu_count()
 
 
 def reference_main(args, rank):
     from paper_2406_06344_gb300 import workloads as W
-    import oracle.pttk_oracle as o
     if rank != 0:
         return
     w = W.C3
-    # the oracle's own online stage needs a TT: a smaller-tol-independent stand-in is the
-    # oracle's TT of the same workload at n = 6 would change the work; use TT cores of the
-    # right shapes (ranks of the n = 12 tensor) drawn at random: the online cost depends
-    # only on the shapes.
-    ranks = [1, 9, 44, 177, 480, 180, 49, 10, 1]
+    # The online cost of the oracle depends only on the core shapes: cores with the ranks the
+    # FP64 TT-SVD finds for this tensor (tests/golden/oracle_ranks.json), seeded values.
+    ranks = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_ranks.json")))["c3"]["ranks"]
     rng = np.random.default_rng(0)
     cores = [rng.standard_normal((ranks[k], w.n, ranks[k + 1])) for k in range(w.D)]
     n_sample = 20000
-    times = []
     for _ in range(args.warmup):
         cpu_leg(w, cores, 2000)
-    for _ in range(args.steps):
-        b, e, tb, tg, cores_used = cpu_leg(w, cores, n_sample)
-        times.append((b, e, tb, tg))
-    b = statistics.median(t[0] for t in times)
-    e = statistics.median(t[1] for t in times)
-    ms = 1000.0 / b
+    res = [cpu_leg(w, cores, n_sample) for _ in range(args.steps)]
+    b = statistics.median(r[0] for r in res)
+    e = statistics.median(r[1] for r in res)
+    sample = (f"oracle online build of {n_sample} points per side (scaled to 1M per side) and "
+              f"grid+transform of one 12^7 slab, per step")
     line = {"impl": "reference", "metric": METRIC, "value": b, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "d3 matern-nu n12 (12^8 grid), N_s=N_t=1M, 256 theta",
-                       "l2": "n/a (cpu)"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sum(r[2] + r[3] for r in res) / len(res),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded uniform points and theta)",
+            "config": {"workload": WORKLOAD, "l2": "n/a (host cores)"},
             "grid_entries_per_s": e,
-            "cpu_baseline": {"value": b, "unit": UNIT, "cores": cores_used, "kind": "oracle",
-                             "sample": f"online build of {n_sample} points per side scaled to 1M; "
-                                       f"grid+transform of one 12^7 slab"},
+            "cpu_baseline": {"value": b, "unit": UNIT, "cores": res[0][4], "kind": "oracle", "sample": sample},
             "e2e": {"value": b, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -187,6 +188,7 @@ def main():
 
     import torch
     import torch.distributed as dist
+    import oracle.pttk_oracle as o
     from paper_2406_06344_gb300 import pttk as P
     from paper_2406_06344_gb300 import workloads as W
 
@@ -201,24 +203,27 @@ def main():
     total = w.n ** w.D
     X32 = torch.tensor(W.sources(w), device=dev, dtype=torch.float32)
     Y32 = torch.tensor(W.targets(w), device=dev, dtype=torch.float32)
-    X64 = X32.double()
-    Y64 = Y32.double()
     thetas = W.thetas(w, args.n_theta)
     wv = torch.tensor(W.weights(N)[0], device=dev, dtype=torch.float32)
     C64 = torch.empty(total, dtype=torch.float64, device=dev)
     C32 = torch.empty(total, dtype=torch.float32, device=dev)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
+    state = {}
 
     def ev():
         e = torch.cuda.Event(enable_timing=True)
         e.record(stream)
         return e
 
-    state = {}
+    def buffers(ranks):
+        if state.get("ranks") != ranks:
+            state["U"] = torch.empty(N, ranks[w.d], device=dev, dtype=torch.float32)
+            state["V"] = torch.empty(N, ranks[w.d + w.dtheta], device=dev, dtype=torch.float32)
+            state["M"] = torch.empty(ranks[w.d], ranks[w.d + w.dtheta], device=dev, dtype=torch.float32)
+            state["ranks"] = ranks
 
-    def step(timed: bool):
-        r = {}
+    def step():
         flush.zero_()
         e0 = ev()
         P.grid_coeffs(w.kernel, w.d, s, t, w.dtheta, p, w.n, "fp64", out=C64)
@@ -227,173 +232,259 @@ def main():
         e2 = ev()
         tt = P.TT.from_coeffs(w.kernel, w.d, s, t, w.dtheta, p, w.n, w.tol, C64)
         e3 = ev()
-        ranks = tt.ranks
-        if "U" not in state or state["ranks"] != ranks:
-            state["U"] = torch.empty(N, ranks[w.d], device=dev, dtype=torch.float32)
-            state["V"] = torch.empty(N, ranks[w.d + w.dtheta], device=dev, dtype=torch.float32)
-            state["M"] = torch.empty(ranks[w.d], ranks[w.d + w.dtheta], device=dev, dtype=torch.float32)
-            state["U64"] = torch.empty(N, ranks[w.d], device=dev, dtype=torch.float64)
-            state["V64"] = torch.empty(N, ranks[w.d + w.dtheta], device=dev, dtype=torch.float64)
-            state["M64"] = torch.empty(ranks[w.d], ranks[w.d + w.dtheta], device=dev, dtype=torch.float64)
-            state["ranks"] = ranks
+        buffers(tt.ranks)
         U, M, V = state["U"], state["M"], state["V"]
         flush.zero_()
         e4 = ev()
         for th in thetas:
             P.instantiate(tt, th, X32, Y32, FAST_FORM, U=U, M=M, V=V)
         e5 = ev()
-        out = P.apply(U, M, V, wv)
+        P.apply(U, M, V, wv)
         e6 = ev()
-        form_ms = {}
-        e7 = ev()
-        for form in OTHER_FORMS:
-            flush.zero_()
-            fa = ev()
-            if form == "fp64":
-                P.instantiate(tt, thetas[0], X64, Y64, "fp64", U=state["U64"], M=state["M64"], V=state["V64"])
-            else:
-                P.instantiate(tt, thetas[0], X32, Y32, form, U=U, M=M, V=V)
-            form_ms[form] = (fa, ev())
-        e8 = ev()
         tt.check()
         torch.cuda.synchronize()
-        r["form_ms"] = {k: a.elapsed_time(b) for k, (a, b) in form_ms.items()}
-        r["grid64_ms"] = e0.elapsed_time(e1)
-        r["grid32_ms"] = e1.elapsed_time(e2)
-        r["ttsvd_ms"] = e2.elapsed_time(e3)
-        r["inst_ms"] = e4.elapsed_time(e5)
-        r["apply_ms"] = e5.elapsed_time(e6)
-        r["inst64_ms"] = r["form_ms"]["fp64"]
-        r["step_ms"] = e0.elapsed_time(e8)
-        r["ranks"] = ranks
+        if "tt" in state and state["tt"] is not tt:
+            state["tt"].free()
         state["tt"] = tt
-        return r
+        return {"grid64_ms": e0.elapsed_time(e1), "grid32_ms": e1.elapsed_time(e2),
+                "ttsvd_ms": e2.elapsed_time(e3), "inst_ms": e4.elapsed_time(e5),
+                "apply_ms": e5.elapsed_time(e6), "step_ms": e0.elapsed_time(e6), "ranks": tt.ranks}
 
     for _ in range(args.warmup):
-        step(False)
+        step()
     P.profile_reset()
     P.profile_enable(True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    clocks = Clocks(torch.cuda.current_device())
+    launches0 = P.launch_count()
     t_wall0 = time.perf_counter()
-    results = [step(True) for _ in range(args.steps)]
+    results = [step() for _ in range(args.steps)]
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
+    launches = P.launch_count() - launches0
+    clock_info = clocks.stop()
     if world > 1:
         dist.barrier()
-    clock_info = clocks.stop() if clocks else None
     P.profile_enable(False)
     prof = {name: P.profile_get(name) for name in P.profile_names()}
 
     def tot(key):
         return sum(r[key] for r in results)
 
-    inst_ms = tot("inst_ms")
-    local_vals = torch.tensor([inst_ms, tot("step_ms"), tot("grid64_ms"), tot("grid32_ms")],
-                              dtype=torch.float64, device=dev)
+    vals = torch.tensor([tot("inst_ms"), tot("step_ms"), tot("grid64_ms"), tot("grid32_ms")],
+                        dtype=torch.float64, device=dev)
     if world > 1:
-        dist.all_reduce(local_vals, op=dist.ReduceOp.MAX)
-    inst_ms_max, step_ms_max, g64_max, g32_max = local_vals.tolist()
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    inst_ms, step_ms, g64_ms, g32_ms = vals.tolist()
     builds = args.n_theta * args.steps * world
-    value = builds / (inst_ms_max / 1000.0)
+    value = builds / (inst_ms / 1000.0)
     ranks = results[-1]["ranks"]
+    tt = state["tt"]
+    hbm, bf16, bf16_sus, peak_src = peaks()
 
-    # roofline of the dominant kernel of the step (largest share of device time)
-    hbm, bf16, src = peaks()
+    # roofline of the online factor build (the metric's kernel): chain_tc, both sides per launch
+    ctc_ms, ctc_n = prof.get("chain_tc", (0.0, 0))
+    flops = chain_flops(ranks, w.d, w.dtheta, w.n, N)
+    tf32_sus = bf16_sus * NOMINAL["tf32"] / NOMINAL["bf16"]
+    roof = None
+    if ctc_n:
+        achieved = flops / (ctc_ms / ctc_n / 1000.0) / 1e12
+        peak = tf32_sus / 3.0
+        roof = {"kernel": "chain_tc (3xTF32 factor chain, both sides, N=1M each)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "flops_per_launch": flops, "avg_launch_ms": ctc_ms / ctc_n, "launches": ctc_n,
+                "peak_note": (f"TF32 dense = {peak_src} sustained BF16 {bf16_sus} x nominal 1.1/2.25, divided "
+                              "by 3 (three TF32 products per algorithmic product); achieved counts "
+                              "algorithmic flops 2n sum r_{i-1} r_i per point per side")}
+    gt_ms, gt_n = prof.get("grid_tile", (0.0, 0))
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
-    chain_ms, chain_launches = prof.get("chain_tc", (0.0, 0))
-    flops_build = chain_flops(ranks, w.d, w.dtheta, w.n, N)
-    # one chain launch builds one side; average flops per launch over the fast and fp64 builds
-    launches_fast = 2 * args.n_theta * args.steps
-    chain_roof = None
-    if chain_launches:
-        avg_ms = chain_ms / chain_launches
-        achieved = (flops_build / 2) / (avg_ms / 1000.0) / 1e12
-        chain_roof = {"kernel": "chain", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                      "peak_source": "FP32 FFMA lanes x SMs x max clock (derived)",
-                      "note": "launches include one FP64 build per step (counted at the same flops)"}
-    gt_ms, gt_launches = prof.get("grid_tile", (0.0, 0))
-    grid_roof = None
-    if gt_launches:
-        # algorithmic bytes: one write of the coefficient tile pass (8 B FP64 / 4 B FP32 per entry)
-        bytes_per_launch = total * (8 + 4) / 2
-        achieved = bytes_per_launch / (gt_ms / gt_launches / 1000.0) / 1e9
-        grid_roof = {"kernel": "grid_tile", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "note": "average over FP64 and FP32 launches; FP64 is ALU-bound"}
-    roof = chain_roof if dom[0] == "chain" else None
-    dominant = {"kernel": dom[0], "ms_total": dom[1][0], "launches": dom[1][1],
-                "share": dom[1][0] / max(1e-9, sum(v[0] for v in prof.values()))}
+    prof_total = sum(v[0] for v in prof.values())
+    roof_dominant = {"kernel": dom[0], "ms_total": dom[1][0], "launches": dom[1][1],
+                     "share_of_timed_kernel_time": dom[1][0] / max(prof_total, 1e-9),
+                     "bound": "alu (FP64)" if dom[0] in ("jacobi_round", "householder", "dgemm") else None,
+                     "note": "the FP64 TT-SVD of the offline stage dominates the step; see the kernel_ms split"}
+    roof_grid = {"fp64_entries_per_s": total * args.steps * world / (g64_ms / 1000.0),
+                 "fp32_entries_per_s": total * args.steps * world / (g32_ms / 1000.0),
+                 "bound": "alu (K_nu by quadrature)",
+                 "hbm_write_floor_ms": {"fp64": total * 8 / hbm / 1e6, "fp32": total * 4 / hbm / 1e6},
+                 "peak_note": f"HBM {hbm} GB/s ({peak_src}); FP64 {FP64_PEAK_TFLOPS} / FP32 {FP32_PEAK_TFLOPS:.1f} TFLOP/s"}
 
-    e2e = None
-    if not args.no_e2e:
-        # end to end through the public API: pinned host inputs copied in every step, one
-        # device->host read of the apply result per build
-        Xh = X32.cpu().pin_memory()
-        Yh = Y32.cpu().pin_memory()
-        wh = wv.cpu().pin_memory()
-        outh = torch.empty(N, dtype=torch.float32).pin_memory()
-        tt = state["tt"]
-        U, M, V = state["U"], state["M"], state["V"]
-        nb = min(args.n_theta, 32)
-        torch.cuda.synchronize()
-        a = ev()
-        Xd = Xh.to(dev, non_blocking=True)
-        Yd = Yh.to(dev, non_blocking=True)
-        wd = wh.to(dev, non_blocking=True)
-        for th in thetas[:nb]:
-            P.instantiate(tt, th, Xd, Yd, FAST_FORM, U=U, M=M, V=V)
-            out = P.apply(U, M, V, wd)
-            outh.copy_(out, non_blocking=True)
-        b = ev()
-        torch.cuda.synchronize()
-        e2e_ms = a.elapsed_time(b)
-        e2e = {"value": nb * world / (e2e_ms / 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": int((Xh.numel() + Yh.numel() + wh.numel()) * 4),
-               "d2h_bytes_per_step": int(outh.numel() * 4 * nb),
-               "builds_per_step": nb}
-
-    cpu = None
-    if rank == 0 and world == 1:
-        cores = [c for c in state["tt"].cores()]
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(torch, P, W, o, w, tt, X32, Y32, wv, thetas, state, flush, ev)
+        cores = tt.cores()
         cb, ce, tb, tg, ncores = cpu_leg(w, cores, 20000)
-        cpu = {"value": cb, "unit": UNIT, "cores": ncores, "kind": "oracle",
-               "sample": "oracle online build of 20,000 points per side (scaled to 1M); "
-                         f"oracle grid+transform of one 12^7 slab: {ce:.3e} entries/s",
-               "grid_entries_per_s": ce}
+        extras["cpu_baseline"] = {
+            "value": cb, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": "FP64 oracle online build (H and both chains) of 20,000 points per side with the "
+                      f"GPU-built cores, scaled to 1M per side; oracle grid+transform {ce:.3e} entries/s "
+                      "on one 12^7 slab",
+            "grid_entries_per_s": ce}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 online / f64 offline",
-            "data": "synthetic (seeded uniform points and theta)",
-            "config": {"workload": "d3 matern-nu n12 (12^8 grid), N_s=N_t=1M, 256 theta",
-                       "fast_form": FAST_FORM, "tol": w.tol, "ranks": ranks,
-                       "l2": "outputs (1.4 GB factors, 3.4 GB grid) exceed L2; 256 MB flush between stages"},
-            "grid_entries_per_s": {"fp64": total * args.steps * world / (g64_max / 1000.0),
-                                   "fp32": total * args.steps * world / (g32_max / 1000.0)},
-            "fp64_plain_builds_per_s": args.steps * world / (tot("inst64_ms") / 1000.0),
-            "builds_per_s_by_form": dict({FAST_FORM: value}, **{
-                f: args.steps * world / (sum(r["form_ms"][f] for r in results) / 1000.0) for f in OTHER_FORMS}),
+            "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (3xTF32 tensor) online / f64 offline",
+            "data": "synthetic (seeded uniform points and theta, the paper's recipe)",
+            "config": {"workload": WORKLOAD, "fast_form": FAST_FORM, "tol": w.tol, "ranks": ranks,
+                       "l2": "each stage's data exceeds L2 (3.4 GB grid, 1.4 GB factors); 256 MB flush before the grid and the builds"},
+            "grid_entries_per_s": {"fp64": roof_grid["fp64_entries_per_s"], "fp32": roof_grid["fp32_entries_per_s"]},
             "stage_ms_per_step": {k: tot(k) / args.steps for k in
-                                  ("grid64_ms", "grid32_ms", "ttsvd_ms", "inst_ms", "apply_ms", "inst64_ms")},
-            "roofline": roof if roof else chain_roof,
-            "roofline_dominant": dominant,
-            "roofline_grid": grid_roof,
+                                  ("grid64_ms", "grid32_ms", "ttsvd_ms", "inst_ms", "apply_ms")},
+            "roofline": roof, "roofline_dominant": roof_dominant, "roofline_grid": roof_grid,
             "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()},
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": int(sum(v[1] for v in prof.values())),
+            "gpu_launches": int(launches),
             "clocks": clock_info,
             "wall_s_timed": wall,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_extras(torch, P, W, o, w, tt, X32, Y32, wv, thetas, state, flush, ev):
+    """Per-form build rates and errors, the batched and adjoint rows, and end to end."""
+    out = {}
+    N = w.n_points
+    gc = tt.cores()
+    rng = np.random.default_rng(W.SEED_SUB)
+    rs = np.sort(rng.choice(N, 300, replace=False))
+    rt_ = np.sort(rng.choice(N, 300, replace=False))
+    Xs, Ys = X32[rs].double().cpu().numpy(), Y32[rt_].double().cpu().numpy()
+    th0 = thetas[0]
+    Uo, Mo, Vo = o.instantiate(gc, w.d, w.dtheta, w.mode_boxes(), th0, Xs, Ys)
+    Ko = Uo @ Mo @ Vo.T
+    Kd = o.kernel_matrix(w.kernel, Xs, Ys, th0)
+    forms = {}
+    X64, Y64 = X32.double(), Y32.double()
+    for form in FORMS:
+        Xf, Yf = (X64, Y64) if form == "fp64" else (X32, Y32)
+        U, M, V = P.instantiate(tt, th0, Xf, Yf, form)   # first call of a form lays out its images
+        times = []
+        for _ in range(3):
+            flush.zero_()
+            a = ev()
+            P.instantiate(tt, th0, Xf, Yf, form, U=U, M=M, V=V)
+            b = ev()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        tt.check()
+        Kg = U[rs].double().cpu().numpy() @ M.double().cpu().numpy() @ V[rt_].double().cpu().numpy().T
+        forms[form] = {"builds_per_s": 1000.0 / statistics.median(times), "ms": statistics.median(times),
+                       "rel_err_vs_oracle": o.rel_fro(Ko, Kg), "rel_err_vs_dense": o.rel_fro(Kd, Kg)}
+        del U, M, V
+    out["forms"] = forms
+    out["fp64_plain_builds_per_s"] = forms["fp64"]["builds_per_s"]
+    out["oracle_floor_rel_err_vs_dense"] = o.rel_fro(Kd, Ko)
+    out["error_sample"] = "300 x 300 seeded subsample (seed 4) at the first theta"
+
+    # batched: the d = 2 Matern-3/2 TT, 1024 instances with log-uniform 1k-100k points per side
+    w2 = W.C2
+    tt2 = P.TT.build_offline(w2.kernel, w2.d, w2.src_box, w2.tgt_box, w2.dtheta, w2.theta_box, w2.n, w2.tol, "fp64")
+    ns, nt = W.batched_sizes()
+    xoff = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    yoff = np.concatenate([[0], np.cumsum(nt)]).astype(np.int64)
+    Xb = torch.tensor(W.points_in_box(w2.src_box, int(xoff[-1]), 61), device="cuda", dtype=torch.float32)
+    Yb = torch.tensor(W.points_in_box(w2.tgt_box, int(yoff[-1]), 62), device="cuda", dtype=torch.float32)
+    thb = W.points_in_box(w2.theta_box, len(ns), 63)
+    thd = torch.tensor(thb, device="cuda")
+    batch = P.Batch(tt2, xoff, yoff, FAST_FORM)
+    U, M, V = batch.instantiate(thd, Xb, Yb)
+    tune_ms = batch.autotune(Xb, Yb, U, V)
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s2):
+        batch.instantiate(thd, Xb, Yb, U=U, M=M, V=V)
+    torch.cuda.current_stream().wait_stream(s2)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.instantiate(thd, Xb, Yb, U=U, M=M, V=V)
+    times = []
+    for _ in range(5):
+        flush.zero_()
+        a = ev()
+        g.replay()
+        b = ev()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    tt2.check()
+    ms_b = statistics.median(times)
+    # per-instance plain FP64 loop for comparison (first 8 instances, extrapolated)
+    X64b, Y64b = Xb.double(), Yb.double()
+    a = ev()
+    for bi in range(8):
+        P.instantiate(tt2, thb[bi], X64b[xoff[bi]:xoff[bi + 1]].contiguous(), Y64b[yoff[bi]:yoff[bi + 1]].contiguous(), "fp64")
+    b = ev()
+    torch.cuda.synchronize()
+    fp64_ms_per_point = a.elapsed_time(b) / float(xoff[8] + yoff[8])
+    gc2 = tt2.cores()
+    errs = []
+    for bi in (0, 511, 1023):
+        rx = np.sort(rng.choice(np.arange(xoff[bi], xoff[bi + 1]), 100, replace=False))
+        ry = np.sort(rng.choice(np.arange(yoff[bi], yoff[bi + 1]), 100, replace=False))
+        Uo2, Mo2, Vo2 = o.instantiate(gc2, w2.d, w2.dtheta, w2.mode_boxes(), thb[bi],
+                                      Xb[rx].double().cpu().numpy(), Yb[ry].double().cpu().numpy())
+        Kg2 = U[rx].double().cpu().numpy() @ M[bi].double().cpu().numpy() @ V[ry].double().cpu().numpy().T
+        errs.append(o.rel_fro(Uo2 @ Mo2 @ Vo2.T, Kg2))
+    pts = float(xoff[-1] + yoff[-1])
+    out["batched"] = {"workload": "d2 matern-3/2 n20 TT; 1024 instances, N_s, N_t log-uniform in [1e3, 1e5]",
+                      "form": FAST_FORM, "instances_per_s": 1024 / (ms_b / 1000.0), "ms_per_batch": ms_b,
+                      "points_per_s": pts / (ms_b / 1000.0), "launch": "one CUDA graph replay (H kernel + one persistent factor launch)",
+                      "autotune_ms_per_config": tune_ms, "config": batch.config[0],
+                      "fp64_plain_ms_per_batch_est": fp64_ms_per_point * pts,
+                      "speedup_vs_fp64_plain": fp64_ms_per_point * pts / ms_b,
+                      "max_rel_err_vs_oracle_sampled": max(errs)}
+    del U, M, V, Xb, Yb, X64b, Y64b
+    batch.free()
+    tt2.free()
+
+    # adjoint: the d = 3 TT, N_s = N_t = 500k, w, z ~ N(0, 1)
+    Na = W.CA_POINTS
+    wa, za = W.weights(Na)
+    wa_d = torch.tensor(wa, device="cuda", dtype=torch.float32)
+    za_d = torch.tensor(za, device="cuda", dtype=torch.float32)
+    Xa, Ya = X32[:Na].contiguous(), Y32[:Na].contiguous()
+    P.grad(tt, th0, Xa, Ya, wa_d, za_d, FAST_FORM)
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L, dth, dX = P.grad(tt, th0, Xa, Ya, wa_d, za_d, FAST_FORM)
+        times.append(time.perf_counter() - t0)
+    out["adjoint"] = {"workload": "d3 matern-nu TT, N_s=N_t=500k, w,z~N(0,1), loss w^T K~ z",
+                      "form": FAST_FORM, "grads_per_s": 1.0 / statistics.median(times),
+                      "ms": 1000.0 * statistics.median(times), "dtheta": list(map(float, dth)),
+                      "note": "wall time of the synchronous pttk_grad call (loss, dL/dtheta, dL/dX)"}
+
+    # end to end through the public API: pinned host inputs copied in, one device->host read
+    # of the apply result per build
+    Xh = X32.cpu().pin_memory()
+    Yh = Y32.cpu().pin_memory()
+    wh = wv.cpu().pin_memory()
+    outh = torch.empty(N, dtype=torch.float32).pin_memory()
+    U, M, V = state["U"], state["M"], state["V"]
+    nb = 64
+    torch.cuda.synchronize()
+    a = ev()
+    Xd = Xh.to("cuda", non_blocking=True)
+    Yd = Yh.to("cuda", non_blocking=True)
+    wd = wh.to("cuda", non_blocking=True)
+    for th in thetas[:nb]:
+        P.instantiate(tt, th, Xd, Yd, FAST_FORM, U=U, M=M, V=V)
+        outd = P.apply(U, M, V, wd)
+        outh.copy_(outd, non_blocking=True)
+    b = ev()
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b)
+    out["e2e"] = {"value": nb / (e2e_ms / 1000.0), "unit": UNIT,
+                  "h2d_bytes_per_step": int((Xh.numel() + Yh.numel() + wh.numel()) * 4),
+                  "d2h_bytes_per_step": int(outh.numel() * 4 * nb), "builds_per_step": nb,
+                  "note": "step = H2D of X, Y, w then 64 x (instantiate + apply + D2H of the result)"}
+    return out
 
 
 if __name__ == "__main__":

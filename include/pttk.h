@@ -262,6 +262,8 @@ pttk_status pttk_profile_reset(void);
 /* Total milliseconds and launch count accumulated for one kernel name (synchronises on the
  * pending events of that kernel). Unknown names give 0 and 0. */
 pttk_status pttk_profile_get(const char* kernel_name, double* ms_total, int64_t* launches);
+/* Total number of kernels the library has launched in this process (all entry points). */
+int64_t pttk_launch_count(void);
 /* Names of the kernels timed so far, newline-separated, NUL-terminated, truncated to len. */
 pttk_status pttk_profile_names(char* buf, int64_t len);
 

@@ -233,8 +233,8 @@ pttk_status weighted_sum(const T* A, const T* w, int64_t N, int r, double* out, 
     PTTK_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * r, s));
     return PTTK_OK;
   }
-  weighted_colsum<T><<<nparts, 256, 0, s>>>(A, w, N, r, partial);
-  sum_partials<<<nblk(r), 256, 0, s>>>(partial, nparts, r, out);
+  weighted_colsum<T><<<nparts, 256, 0, s>>>(A, w, N, r, partial); pttk::count_launch();
+  sum_partials<<<nblk(r), 256, 0, s>>>(partial, nparts, r, out); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
 }
@@ -295,9 +295,9 @@ pttk_status grad_typed(const pttk_tt* tt, const double* theta, const T* X, int64
   }
   PTTK_TRY(weighted_sum<T>(U, w, N_s, rs, a, partial, nparts, s));
   PTTK_TRY(weighted_sum<T>(V, z, N_t, rt, b, partial, nparts, s));
-  matvec_rows<<<(unsigned)(((int64_t)rs * 32 + 255) / 256), 256, 0, s>>>(M, rs, rt, b, g);  // g = H b
+  matvec_rows<<<(unsigned)(((int64_t)rs * 32 + 255) / 256), 256, 0, s>>>(M, rs, rt, b, g); pttk::count_launch();  // g = H b
   double* Lbuf = small;
-  matvec_rows<<<1, 32, 0, s>>>(a, 1, rs, g, Lbuf);  // L = a . g
+  matvec_rows<<<1, 32, 0, s>>>(a, 1, rs, g, Lbuf); pttk::count_launch();  // L = a . g
 
   // dL/dtheta
   if (dtheta && dth > 0) {
@@ -311,19 +311,19 @@ pttk_status grad_typed(const pttk_tt* tt, const double* theta, const T* X, int64
     const double sc1 = 2.0 / (tt->box[d][0] - tt->box[d][1]);
     if (dth == 1) {
       // a^T H1' b: u = H1'^T a (r1), then u . b
-      core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G1, r0, n, r1, th[0], true, sc1, a, 0, u);
-      matvec_rows<<<1, 32, 0, s>>>(u, 1, r1, b, dth_dev);
+      core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G1, r0, n, r1, th[0], true, sc1, a, 0, u); pttk::count_launch();
+      matvec_rows<<<1, 32, 0, s>>>(u, 1, r1, b, dth_dev); pttk::count_launch();
     } else {
       const double* G2 = tt->cores64 + tt->core_off[d + 1];
       const int r2 = tt->ranks[d + 2];
       const double sc2 = 2.0 / (tt->box[d + 1][0] - tt->box[d + 1][1]);
       // u = H1'^T a, v = H2 b, u2 = H1^T a, v2 = H2' b; dtheta = (u . v, u2 . v2)
-      core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G1, r0, n, r1, th[0], true, sc1, a, 0, u);
-      core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G2, r1, n, r2, th[1], false, 1.0, b, 1, v);
-      core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G1, r0, n, r1, th[0], false, 1.0, a, 0, u2);
-      core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G2, r1, n, r2, th[1], true, sc2, b, 1, v2);
-      matvec_rows<<<1, 32, 0, s>>>(u, 1, r1, v, dth_dev);
-      matvec_rows<<<1, 32, 0, s>>>(u2, 1, r1, v2, dth_dev + 1);
+      { core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G1, r0, n, r1, th[0], true, sc1, a, 0, u); pttk::count_launch(); }
+      core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G2, r1, n, r2, th[1], false, 1.0, b, 1, v); pttk::count_launch();
+      core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G1, r0, n, r1, th[0], false, 1.0, a, 0, u2); pttk::count_launch();
+      core_vec<<<(unsigned)((r1 * 32 + 255) / 256), 256, 0, s>>>(G2, r1, n, r2, th[1], true, sc2, b, 1, v2); pttk::count_launch();
+      matvec_rows<<<1, 32, 0, s>>>(u, 1, r1, v, dth_dev); pttk::count_launch();
+      matvec_rows<<<1, 32, 0, s>>>(u2, 1, r1, v2, dth_dev + 1); pttk::count_launch();
     }
   }
 
@@ -342,7 +342,7 @@ pttk_status grad_typed(const pttk_tt* tt, const double* theta, const T* X, int64
     const T* Gs_last = static_cast<const T*>(oriented_core_ptr(tt, true, d - 1, fp64));
     T* q;
     PTTK_TRY(sc.get(&q, (size_t)n * rin));
-    core_times_vec<T><<<nblk((int64_t)n * rin), 256, 0, s>>>(Gs_last, n * rin, rout, g, q);
+    core_times_vec<T><<<nblk((int64_t)n * rin), 256, 0, s>>>(Gs_last, n * rin, rout, g, q); pttk::count_launch();
     T *gbar = nullptr, *gnext = nullptr, *Q = nullptr;
     size_t qmax = 0;
     for (int i = 0; i < d - 1; ++i) qmax = std::max<size_t>(qmax, (size_t)n * tt->ranks[i]);
@@ -358,12 +358,12 @@ pttk_status grad_typed(const pttk_tt* tt, const double* theta, const T* X, int64
       if (i < d - 1) {
         const T* Gs = static_cast<const T*>(oriented_core_ptr(tt, true, i, fp64));
         dim3 grid((unsigned)((K + 63) / 64), (unsigned)((N_s + 63) / 64));
-        gemm_gbar_core<T><<<grid, 256, 0, s>>>(gbar, Gs, N_s, rout, K, Q);
+        gemm_gbar_core<T><<<grid, 256, 0, s>>>(gbar, Gs, N_s, rout, K, Q); pttk::count_launch();
       }
       const size_t smem = sizeof(T) * 8 * (PTTK_MAX_N + rin);
       chain_back_step<T><<<(unsigned)((N_s + 7) / 8), 256, smem, s>>>(
           X, d, coord, lo, hi, n, N_s, rin, i > 0 ? Sbuf[i] : nullptr, i < d - 1 ? Q : nullptr, w,
-          i == d - 1 ? q : nullptr, i > 0 ? gnext : nullptr, dX);
+          i == d - 1 ? q : nullptr, i > 0 ? gnext : nullptr, dX); pttk::count_launch();
       std::swap(gbar, gnext);
     }
   }

@@ -85,7 +85,7 @@ static pttk_status prepare_oriented(pttk_tt_ext* t, cudaStream_t s) {
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, sm_count() * 8);
     orient_kernel<<<blocks, 256, 0, s>>>(t->cores64 + t->core_off[k], t->ranks[k], t->n,
                                          t->ranks[k + 1], t->tgt64 + t->core_off[k],
-                                         t->tgt32 + t->core_off[k]);
+                                         t->tgt32 + t->core_off[k]); pttk::count_launch();
   }
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;

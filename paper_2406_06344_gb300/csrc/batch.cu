@@ -231,24 +231,24 @@ pttk_status pttk_instantiate_batched(const pttk_batch* b, const double* thetas, 
   double* Hout = b->scratch;
   if (dth == 1) {
     theta_contract_batched<<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(
-        tt->cores64 + tt->core_off[d], rs, n, rt, thetas, B, 1, 0, tt->box[d][0], tt->box[d][1], Hout, status);
+        tt->cores64 + tt->core_off[d], rs, n, rt, thetas, B, 1, 0, tt->box[d][0], tt->box[d][1], Hout, status); pttk::count_launch();
     H = Hout;
   } else {
     const int rm = tt->ranks[d + 1];
     double* H1 = Hout + (size_t)B * rs * rt;
     double* H2 = H1 + (size_t)B * rs * rm;
     theta_contract_batched<<<blocks_for((int64_t)B * rs * rm), 256, 0, s>>>(
-        tt->cores64 + tt->core_off[d], rs, n, rm, thetas, B, 2, 0, tt->box[d][0], tt->box[d][1], H1, status);
+        tt->cores64 + tt->core_off[d], rs, n, rm, thetas, B, 2, 0, tt->box[d][0], tt->box[d][1], H1, status); pttk::count_launch();
     theta_contract_batched<<<blocks_for((int64_t)B * rm * rt), 256, 0, s>>>(
         tt->cores64 + tt->core_off[d + 1], rm, n, rt, thetas, B, 2, 1, tt->box[d + 1][0], tt->box[d + 1][1], H2,
-        status);
-    batched_product<<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(H1, H2, rs, rm, rt, B, Hout);
+        status); pttk::count_launch();
+    batched_product<<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(H1, H2, rs, rm, rt, B, Hout); pttk::count_launch();
     H = Hout;
   }
   if (b->prec == PTTK_FP64)
-    store_batched_rowmajor<double><<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(H, rs, rt, B, static_cast<double*>(M));
+    { store_batched_rowmajor<double><<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(H, rs, rt, B, static_cast<double*>(M)); pttk::count_launch(); }
   else
-    store_batched_rowmajor<float><<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(H, rs, rt, B, static_cast<float*>(M));
+    { store_batched_rowmajor<float><<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(H, rs, rt, B, static_cast<float*>(M)); pttk::count_launch(); }
   PTTK_CUDA(cudaGetLastError());
   if (tc_form(b->prec))
     return factor_build_tc(tt, tt_tc_cache(tt), static_cast<const float*>(X), b->Ns, static_cast<const float*>(Y),

@@ -647,7 +647,7 @@ static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, int KCB, Imag
       const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count() * 8);
       auto* kfn = bf16 ? core_image_kernel<true> : core_image_kernel<false>;
       kfn<<<blocks, 256, 0, s>>>(G, tt->n, rin, im.R_in_pad[side][i], rout, im.Npad[side][i], im.nchunks[side][i],
-                                 KCB, split, im.buf + im.hi_off[side][i], im.buf + im.lo_off[side][i]);
+                                 KCB, split, im.buf + im.hi_off[side][i], im.buf + im.lo_off[side][i]); pttk::count_launch();
     }
   PTTK_CUDA(cudaGetLastError());
   PTTK_CUDA(cudaStreamSynchronize(s));
@@ -685,7 +685,7 @@ static pttk_status launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
   auto kfn = chain_tc_kernel<BF16, SPLIT, KCB, NS>;
   PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned grid = (unsigned)std::min<int64_t>(a.ntiles, sm_count());
-  kfn<<<grid, TC_THREADS, smem, s>>>(a);
+  kfn<<<grid, TC_THREADS, smem, s>>>(a); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
 }

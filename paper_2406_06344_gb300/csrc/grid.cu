@@ -171,7 +171,7 @@ pttk_status launch_all(const GridArgs& a, T* C, cudaStream_t st) {
   const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)sm_count() * per_sm);
   {
     PTTK_PROF("grid_tile", st);
-    kfn<<<(unsigned)grid, threads, smem, st>>>(a, C);
+    kfn<<<(unsigned)grid, threads, smem, st>>>(a, C); pttk::count_launch();
   }
   PTTK_CUDA(cudaGetLastError());
   int64_t total = 1;
@@ -181,7 +181,7 @@ pttk_status launch_all(const GridArgs& a, T* C, cudaStream_t st) {
   for (int j = a.m1; j < a.D; ++j, s *= a.n) {
     const int64_t blocks = std::min<int64_t>((nfib + 255) / 256, (int64_t)sm_count() * 8);
     PTTK_PROF("mode_transform", st);
-    mode_transform_kernel<T, NB><<<(unsigned)blocks, 256, 0, st>>>(C, a.n, s, nfib);
+    mode_transform_kernel<T, NB><<<(unsigned)blocks, 256, 0, st>>>(C, a.n, s, nfib); pttk::count_launch();
     PTTK_CUDA(cudaGetLastError());
   }
   return PTTK_OK;

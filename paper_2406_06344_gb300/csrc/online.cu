@@ -263,14 +263,14 @@ pttk_status apply_typed(const T* U, const T* M, const T* V, int64_t N_s, int64_t
   T* sv = scratch + (size_t)nparts * rt;
   PTTK_PROF("apply", s);
   if (N_t > 0) {
-    vtw_partial_kernel<T><<<nparts, 256, 0, s>>>(V, N_t, rt, w, partial);
+    vtw_partial_kernel<T><<<nparts, 256, 0, s>>>(V, N_t, rt, w, partial); pttk::count_launch();
   } else {
     PTTK_CUDA(cudaMemsetAsync(partial, 0, sizeof(T) * (size_t)nparts * rt, s));
   }
-  reduce_mt_kernel<T><<<1, 256, sizeof(T) * rt, s>>>(partial, nparts, rs, rt, M, sv);
+  reduce_mt_kernel<T><<<1, 256, sizeof(T) * rt, s>>>(partial, nparts, rs, rt, M, sv); pttk::count_launch();
   if (N_s > 0) {
     const int64_t blocks = std::min<int64_t>((N_s * 32 + 255) / 256, (int64_t)sm_count() * 16);
-    us_kernel<T><<<(unsigned)blocks, 256, sizeof(T) * rs, s>>>(U, N_s, rs, sv, out);
+    us_kernel<T><<<(unsigned)blocks, 256, sizeof(T) * rs, s>>>(U, N_s, rs, sv, out); pttk::count_launch();
   }
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
@@ -304,7 +304,7 @@ pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64
   const int d = tt->d, dth = tt->dtheta, n = tt->n;
   const int rs = tt->ranks[d], rt = tt->ranks[d + dth];
   if (dth == 0) {
-    identity_rowmajor_kernel<<<64, 256, 0, s>>>(M, rs, fp64);
+    identity_rowmajor_kernel<<<64, 256, 0, s>>>(M, rs, fp64); pttk::count_launch();
     PTTK_CUDA(cudaGetLastError());
     return PTTK_OK;
   }
@@ -319,7 +319,7 @@ pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64
     const int64_t total = (int64_t)ra * rb;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, sm_count() * 8);
     contract_theta_kernel<<<blocks, 256, 0, s>>>(tt->cores64 + tt->core_off[d + j], ra, n, rb,
-                                                 theta_hat[j], Hj[j]);
+                                                 theta_hat[j], Hj[j]); pttk::count_launch();
   }
   const double* H = Hj[0];
   if (dth == 2) {
@@ -329,8 +329,8 @@ pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64
     H = Hp;
   }
   const unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)rs * rt + 255) / 256, sm_count() * 8);
-  if (fp64) store_rowmajor_kernel<double><<<blocks, 256, 0, s>>>(H, rs, rt, static_cast<double*>(M));
-  else store_rowmajor_kernel<float><<<blocks, 256, 0, s>>>(H, rs, rt, static_cast<float*>(M));
+  if (fp64) { store_rowmajor_kernel<double><<<blocks, 256, 0, s>>>(H, rs, rt, static_cast<double*>(M)); pttk::count_launch(); }
+  else { store_rowmajor_kernel<float><<<blocks, 256, 0, s>>>(H, rs, rt, static_cast<float*>(M)); pttk::count_launch(); }
   PTTK_CUDA(cudaGetLastError());
   PTTK_CUDA(cudaFreeAsync(work, s));
   return PTTK_OK;
@@ -343,7 +343,7 @@ static pttk_status launch_chain(const ChainArgs& a, const T* pts, T* out, cudaSt
   PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t blocks = (a.N + P - 1) / P;
   PTTK_PROF("chain", s);
-  kfn<<<(unsigned)blocks, (P / 4) * 16, smem, s>>>(a, pts, out);
+  kfn<<<(unsigned)blocks, (P / 4) * 16, smem, s>>>(a, pts, out); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
 }

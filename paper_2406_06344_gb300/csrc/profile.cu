@@ -1,4 +1,5 @@
 // Per-kernel timing with CUDA events recorded on the launching stream (off by default).
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -52,6 +53,9 @@ pttk_status drain(Entry& en) {
 }  // namespace
 
 bool prof_on() { return g_on; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void* prof_begin(const char* name, cudaStream_t s) {
   if (!g_on) return nullptr;
@@ -107,6 +111,8 @@ pttk_status pttk_profile_get(const char* name, double* ms_total, int64_t* launch
   *launches = it->second.launches;
   return PTTK_OK;
 }
+
+int64_t pttk_launch_count(void) { return (int64_t)g_launches.load(); }
 
 // Names of the kernels seen so far, separated by '\n', into buf (truncated to len).
 pttk_status pttk_profile_names(char* buf, int64_t len) {

@@ -50,6 +50,9 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 int sm_count();
 
+// Number of kernels the library has launched (every launch site increments it).
+void count_launch();
+
 // Kernel timing (profile.cu): when enabled, PTTK_PROF brackets a launch with CUDA events
 // recorded on its stream; results are read through pttk_profile_get.
 bool prof_on();

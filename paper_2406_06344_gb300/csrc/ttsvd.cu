@@ -482,16 +482,16 @@ pttk_status householder_r(double* A, int64_t M, int64_t N, double* R, double* no
   const int64_t nchunks = (M + RC - 1) / RC;
   PTTK_PROF("householder", s);
   PTTK_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * N * N, s));
-  hh_colnorm_kernel<<<(unsigned)nchunks, 256, 0, s>>>(A, M, 0, 1, norm_part);
+  hh_colnorm_kernel<<<(unsigned)nchunks, 256, 0, s>>>(A, M, 0, 1, norm_part); pttk::count_launch();
   for (int64_t j = 0; j < N; ++j) {
-    hh_scalar_kernel<<<1, 256, 0, s>>>(A, M, N, j, norm_part, nchunks, hs, R);
+    hh_scalar_kernel<<<1, 256, 0, s>>>(A, M, N, j, norm_part, nchunks, hs, R); pttk::count_launch();
     const int64_t trailing = N - j - 1;
     if (trailing <= 0) break;
     const unsigned gx = (unsigned)(nchunks - j / RC);
     const unsigned gy = (unsigned)((trailing + CG - 1) / CG);
-    hh_w_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, hs, w_part);
-    hh_wsum_kernel<<<(unsigned)trailing, 256, 0, s>>>(w_part, N, j, nchunks, hs, w);
-    hh_update_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, hs, w, R, norm_part);
+    hh_w_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, hs, w_part); pttk::count_launch();
+    hh_wsum_kernel<<<(unsigned)trailing, 256, 0, s>>>(w_part, N, j, nchunks, hs, w); pttk::count_launch();
+    hh_update_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, hs, w, R, norm_part); pttk::count_launch();
   }
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
@@ -504,7 +504,7 @@ pttk_status jacobi(double* A, int64_t rows, int ncols, double* V, int64_t nv, un
   if (ncols < 2) return PTTK_OK;
   Buf colsq;
   PTTK_TRY(colsq.alloc(ncols));
-  colsq_init_kernel<<<(unsigned)(((int64_t)ncols * 32 + 255) / 256), 256, 0, s>>>(A, rows, ncols, colsq.p);
+  colsq_init_kernel<<<(unsigned)(((int64_t)ncols * 32 + 255) / 256), 256, 0, s>>>(A, rows, ncols, colsq.p); pttk::count_launch();
   const double small2 = small * small;
   const double count2 = 100.0 * small2;
   const int p = ncols + (ncols & 1);
@@ -520,7 +520,7 @@ pttk_status jacobi(double* A, int64_t rows, int ncols, double* V, int64_t nv, un
     {
       PTTK_PROF("jacobi_round", s);
       jacobi_round_kernel<<<blocks, 256, 0, s>>>(A, rows, ncols, V, nv, p, r, tol, small2, count2,
-                                                 colsq.p, d_counter);
+                                                 colsq.p, d_counter); pttk::count_launch();
     }
     PTTK_CUDA(cudaGetLastError());
     unsigned h = 0;
@@ -555,11 +555,11 @@ void dgemm(bool tA, bool tB, int64_t M, int64_t N, int64_t K, double alpha, cons
   if (M <= 16) {
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((M + 15) / 16));
     dgemm_kernel<16, 128, 16, 2, 4><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, B, ldb,
-                                                         beta, C, ldc);
+                                                         beta, C, ldc); pttk::count_launch();
   } else {
     dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
     dgemm_kernel<64, 64, 16, 4, 4><<<grid, 256, 0, s>>>(tA, tB, M, N, K, alpha, A, lda, B, ldb,
-                                                        beta, C, ldc);
+                                                        beta, C, ldc); pttk::count_launch();
   }
 }
 
@@ -573,8 +573,8 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   const unsigned nb = grid1d(total, 256, 4);
   PTTK_TRY(part.alloc(nb));
   PTTK_TRY(scal.alloc(64));
-  sumsq_kernel<<<nb, 256, 0, s>>>(X, total, part.p);
-  sum_kernel<<<1, 256, 0, s>>>(part.p, (int)nb, scal.p);
+  sumsq_kernel<<<nb, 256, 0, s>>>(X, total, part.p); pttk::count_launch();
+  sum_kernel<<<1, 256, 0, s>>>(part.p, (int)nb, scal.p); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
   double sumsq = 0.0;
   PTTK_CUDA(cudaMemcpyAsync(&sumsq, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -618,14 +618,14 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
       int64_t len = m;
       if (wide) {
         dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
-        transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, nullptr, W.p);
+        transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, nullptr, W.p); pttk::count_launch();
         src = W.p;
         len = c;
       }
       const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (len * q) / (256 * 1024 * 8) + 1));
       PTTK_TRY(colpart.alloc((int64_t)nsplit * q));
-      colsq_partial_kernel<<<dim3((unsigned)nsplit, (unsigned)q), 256, 0, s>>>(src, len, nsplit, colpart.p);
-      colsq_final_kernel<<<(unsigned)((q + 255) / 256), 256, 0, s>>>(colpart.p, nsplit, (int)q, norms.p);
+      colsq_partial_kernel<<<dim3((unsigned)nsplit, (unsigned)q), 256, 0, s>>>(src, len, nsplit, colpart.p); pttk::count_launch();
+      colsq_final_kernel<<<(unsigned)((q + 255) / 256), 256, 0, s>>>(colpart.p, nsplit, (int)q, norms.p); pttk::count_launch();
     }
     std::vector<double> nv(q);
     PTTK_CUDA(cudaMemcpyAsync(nv.data(), norms.p, sizeof(double) * q, cudaMemcpyDeviceToHost, s));
@@ -639,9 +639,9 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
     PTTK_TRY(qrin.alloc(Mqr * q));
     if (wide) {
       dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
-      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, d_perm, qrin.p);
+      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, d_perm, qrin.p); pttk::count_launch();
     } else {
-      gather_cols_kernel<<<grid1d(m * c, 256), 256, 0, s>>>(cur, m, d_perm, (int)c, nullptr, qrin.p);
+      gather_cols_kernel<<<grid1d(m * c, 256), 256, 0, s>>>(cur, m, d_perm, (int)c, nullptr, qrin.p); pttk::count_launch();
     }
     // R (q x q) of the ordered matrix, then A = R^T
     const int64_t nchunks = (Mqr + RC - 1) / RC;
@@ -653,13 +653,13 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
     PTTK_TRY(householder_r(qrin.p, Mqr, q, R.p, part.p, wpart.p, wv.p, d_hs, s));
     {
       dim3 tg((unsigned)((q + 31) / 32), (unsigned)((q + 31) / 32));
-      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(R.p, q, q, nullptr, A.p);
+      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(R.p, q, q, nullptr, A.p); pttk::count_launch();
     }
     // one-sided Jacobi on R^T: R^T V = U' Sigma, so R = V Sigma U'^T and the right singular
     // vectors of R (= of the ordered QR input) are the normalised columns of the rotated R^T
     // columns below 1e-3 delta / sqrt(q) together carry < 1e-6 delta^2: pairs of them are skipped
     PTTK_TRY(jacobi(A.p, q, (int)q, nullptr, 0, d_counter, s, 1e-3 * delta / sqrt((double)q)));
-    colnorm_kernel<<<(unsigned)((q * 32 + 255) / 256), 256, 0, s>>>(A.p, q, (int)q, norms.p);
+    colnorm_kernel<<<(unsigned)((q * 32 + 255) / 256), 256, 0, s>>>(A.p, q, (int)q, norms.p); pttk::count_launch();
     std::vector<double> sigma(q);
     PTTK_CUDA(cudaMemcpyAsync(sigma.data(), norms.p, sizeof(double) * q, cudaMemcpyDeviceToHost, s));
     PTTK_CUDA(cudaStreamSynchronize(s));
@@ -672,9 +672,9 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
     // top-r right singular vectors (unit columns), in the ordered basis
     PTTK_TRY(U.alloc(q * r));
     PTTK_TRY(Y.alloc(q * r));
-    gather_cols_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(A.p, q, d_top, r, norms.p, Y.p);
+    gather_cols_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(A.p, q, d_top, r, norms.p, Y.p); pttk::count_launch();
     // back to the original order: row order[i] of the result is row i of Y
-    scatter_rows_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(Y.p, q, r, d_perm, U.p);
+    scatter_rows_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(Y.p, q, r, d_perm, U.p); pttk::count_launch();
     double* basis = U.p;  // m x r (wide): left singular vectors of X
     if (!wide) {
       // tall: U holds the top right singular vectors of X (c x r); Y = X U spans the top-r
@@ -689,7 +689,7 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
     {
       Buf bn;
       PTTK_TRY(bn.alloc(r));
-      colnorm_kernel<<<(unsigned)(((int64_t)r * 32 + 255) / 256), 256, 0, s>>>(basis, m, r, bn.p);
+      colnorm_kernel<<<(unsigned)(((int64_t)r * 32 + 255) / 256), 256, 0, s>>>(basis, m, r, bn.p); pttk::count_launch();
       std::vector<double> bnh(r);
       PTTK_CUDA(cudaMemcpyAsync(bnh.data(), bn.p, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
       PTTK_CUDA(cudaStreamSynchronize(s));
@@ -697,7 +697,7 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
       truncation(bnh, 0.0, bperm);
       PTTK_CUDA(cudaMemcpyAsync(d_top, bperm.data(), sizeof(int) * r, cudaMemcpyHostToDevice, s));
       PTTK_TRY(cores[k].alloc(m * r));
-      gather_cols_kernel<<<grid1d(m * r, 256), 256, 0, s>>>(basis, m, d_top, r, bn.p, cores[k].p);
+      gather_cols_kernel<<<grid1d(m * r, 256), 256, 0, s>>>(basis, m, d_top, r, bn.p, cores[k].p); pttk::count_launch();
       PTTK_CUDA(cudaStreamSynchronize(s));
     }
     // X <- G_k^T X  (r x c)
@@ -726,7 +726,7 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   for (int k = 0; k < D; ++k)
     PTTK_CUDA(cudaMemcpyAsync(tt->cores64 + tt->core_off[k], cores[k].p,
                               sizeof(double) * tt->core_elems(k), cudaMemcpyDeviceToDevice, s));
-  cast_f32_kernel<<<grid1d((int64_t)off, 256), 256, 0, s>>>(tt->cores64, (int64_t)off, tt->cores32);
+  cast_f32_kernel<<<grid1d((int64_t)off, 256), 256, 0, s>>>(tt->cores64, (int64_t)off, tt->cores32); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
   PTTK_CUDA(cudaStreamSynchronize(s));
   return PTTK_OK;
@@ -734,7 +734,7 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
 
 // FP32 tensor -> FP64 work buffer
 pttk_status widen_to_f64(const float* in, int64_t n, double* out, cudaStream_t s) {
-  widen_f32_kernel<<<grid1d(n, 256), 256, 0, s>>>(in, n, out);
+  widen_f32_kernel<<<grid1d(n, 256), 256, 0, s>>>(in, n, out); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
 }

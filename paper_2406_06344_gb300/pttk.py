@@ -61,6 +61,7 @@ SIGNATURES = [
     ("pttk_profile_reset", _int, []),
     ("pttk_profile_get", _int, [ctypes.c_char_p, _c_double_p, ctypes.POINTER(_i64)]),
     ("pttk_profile_names", _int, [ctypes.c_char_p, _i64]),
+    ("pttk_launch_count", _i64, []),
 ]
 
 _lib = None
@@ -416,3 +417,8 @@ def profile_names() -> list:
     buf = ctypes.create_string_buffer(4096)
     _check(load().pttk_profile_names(buf, 4096))
     return [s for s in buf.value.decode().split("\n") if s]
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().pttk_launch_count())
