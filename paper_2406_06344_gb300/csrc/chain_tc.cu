@@ -1,16 +1,18 @@
 // Factor chain of Algorithm 2, Phase 3 on the 5th-generation tensor cores (tcgen05).
 //
-// One CTA (4 warps) owns 128 points at a time (persistent over point tiles). Chain step i
-// computes S_out (128 x R_out) = A (128 x K) * Gs (K x R_out), K = n R_in, with
+// One persistent launch builds both factors: a CTA (10 warps, one per SM) takes 128-point
+// tiles of the source points, then of the target points. Chain step i computes
+// S_out (128 x R_out) = A (128 x K) * Gs (K x R_out), K = n R_in, with
 //   A[p, a + R_in j] = T_j(xhat_{p,i}) * S_in[p, a]
-// generated by the threads (thread t = point t) straight into shared memory in the UMMA
-// K-major layout, and Gs the oriented core, pre-laid out once per handle as per-chunk images
-// in the same layout and fetched chunk by chunk with one cp.async.bulk (TMA) copy. The
-// accumulator lives in tensor memory (TMEM, 128 lanes = points, N_pad columns); one elected
-// thread issues tcgen05.mma and commits to an mbarrier; after the last chunk the threads read
-// the accumulator back with tcgen05.ld: into S_in (FP32, shared memory) for the next step, or,
-// after the last step, into a shared-memory output tile that is copied to U/V with coalesced
-// 16-byte stores (a tile's 128 rows are contiguous in the row-major output).
+// generated by the generator warps (two threads per point row) straight into shared memory
+// in the UMMA K-major layout, and Gs the oriented core, pre-laid out once per handle as
+// per-chunk images in the same layout and fetched chunk by chunk by one cp.async.bulk (TMA)
+// copy into a ring of NSLOT operand slots. The accumulator lives in tensor memory (TMEM,
+// 128 lanes = points, N_pad columns); one lane of the MMA warp issues tcgen05.mma and commits
+// to mbarriers; after the last chunk of a step the generator warps read the accumulator back
+// with tcgen05.ld: into S_in (FP32, shared memory) for the next step, or, after the last step,
+// into a shared-memory output tile that is copied to U/V with coalesced 16-byte stores (a
+// tile's 128 rows are contiguous in the row-major output).
 //
 // Precision forms (FP32 accumulation throughout):
 //   TF32   kind::tf32, operands rounded to TF32 (10-bit mantissa);
@@ -20,10 +22,10 @@
 // Core images are split from the FP64 cores; A is split after its FP32 product.
 //
 // Shared-memory operand layout (UMMA "no swizzle" K-major): 16-byte units, a core matrix is
-// 8 rows x 16 bytes stored contiguously (128 B). Chunk of KC_BYTES = 128 bytes of K per row:
-// unit (row r, k-unit u) at byte (r / 8) * 1024 + u * 128 + (r % 8) * 16. Descriptor: leading
-// (K-direction) byte offset 128, stride (M/N-direction) byte offset 1024; one MMA consumes 32
-// bytes of K (8 TF32 or 16 BF16), so k-step s starts at +256 s.
+// 8 rows x 16 bytes stored contiguously (128 B). Chunk of KCB bytes of K per row (64 or 128,
+// a launch configuration): unit (row r, k-unit u) at byte (r / 8) * 8 KCB + u * 128 + (r % 8) * 16.
+// Descriptor: leading (K-direction) byte offset 128, stride (M/N-direction) byte offset 8 KCB;
+// one MMA consumes 32 bytes of K (8 TF32 or 16 BF16), so k-step s starts at +256 s.
 //
 // Waits: every mbarrier wait is bounded; on timeout the CTA records PTTK_ETIMEOUT in a device
 // status word, stops issuing work, waits (bounded) for its outstanding copies and MMAs, frees
@@ -45,8 +47,6 @@ const void* oriented_core_ptr(const pttk_tt* tt, bool source, int k, bool fp64);
 namespace {
 
 constexpr int TILE_M = 128;
-constexpr int KC_BYTES = 128;            // bytes of K per row per chunk
-constexpr int CHUNK_ROW_GROUP = 1024;    // bytes per 8-row group in a chunk
 
 // ---------------- PTX wrappers ------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
