@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--impl", default="pttk", choices=["pttk", "reference"])
     ap.add_argument("--n-theta", type=int, default=N_THETA)
     ap.add_argument("--no-extras", action="store_true", help="skip the per-form/batched/adjoint/CPU legs")
+    ap.add_argument("--online-only", type=int, default=0, metavar="BUILDS",
+                    help="profiling case: BUILDS instantiations at N = 1M on a handle made from seeded cores "
+                         "with the d = 3 workload's ranks (no grid, no TT-SVD); not a bench line")
+    ap.add_argument("--form", default=FAST_FORM, choices=FORMS)
     return ap.parse_args()
 
 
@@ -185,6 +189,8 @@ def main():
     rank, world, local = info.rank, info.world, info.local
     if args.impl == "reference":
         return reference_main(args, rank)
+    if args.online_only:
+        return online_only(args)
 
     import torch
     import torch.distributed as dist
@@ -342,6 +348,36 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def online_only(args):
+    """A small, launch-light case for kernel profiles: the online stage alone on cores of the
+    d = 3 workload's shapes (seeded values scaled to keep the chain O(1))."""
+    import torch
+    from paper_2406_06344_gb300 import pttk as P
+    from paper_2406_06344_gb300 import workloads as W
+    P.load()
+    w = W.C3
+    ranks = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_ranks.json")))["c3"]["ranks"]
+    rng = np.random.default_rng(7)
+    cores = [rng.standard_normal((ranks[k], w.n, ranks[k + 1])) / np.sqrt(ranks[k] * w.n) for k in range(w.D)]
+    tt = P.TT.from_cores(w.kernel, w.d, w.src_box, w.tgt_box, w.dtheta, w.theta_box, w.n, cores)
+    dt = torch.float64 if args.form == "fp64" else torch.float32
+    X = torch.tensor(W.sources(w), device="cuda", dtype=dt)
+    Y = torch.tensor(W.targets(w), device="cuda", dtype=dt)
+    th = W.thetas(w, 1)[0]
+    U, M, V = P.instantiate(tt, th, X, Y, args.form)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.online_only):
+        P.instantiate(tt, th, X, Y, args.form, U=U, M=M, V=V)
+    b.record()
+    torch.cuda.synchronize()
+    tt.check()
+    print(json.dumps({"case": "online stage only", "form": args.form, "builds": args.online_only,
+                      "ms_per_build": a.elapsed_time(b) / args.online_only, "ranks": ranks}), flush=True)
 
 
 def run_extras(torch, P, W, o, w, tt, X32, Y32, wv, thetas, state, flush, ev):

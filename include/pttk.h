@@ -136,6 +136,18 @@ pttk_status pttk_tt_get_core(const pttk_tt* tt, int k, double* host_out);
 pttk_status pttk_tt_save(const pttk_tt* tt, const char* path);
 pttk_status pttk_tt_load(const char* path, pttk_tt** out);
 
+/* A handle from given TT cores (the TT format of Section 2.3): for instance cores computed
+ * elsewhere, or cores with chosen ranks for timing the online stage. The problem arguments
+ * are those of pttk_grid_coeffs; ranks[0..D] with ranks[0] = ranks[D] = 1; `cores` is host
+ * memory holding the D cores one after another, core k as r_{k-1} x n x r_k doubles,
+ * column-major (the layout pttk_tt_get_core returns). The cores must be the Chebyshev
+ * coefficient form (contracted with T(xhat), not with nodal values). Copied; the caller
+ * keeps ownership of `cores`. Synchronous. Errors: PTTK_EINVAL (bad problem or ranks),
+ * PTTK_ENOMEM / PTTK_ECUDA. */
+pttk_status pttk_tt_from_cores(pttk_kernel kernel, int d, const double* src_box, const double* tgt_box,
+                               int d_theta, const double* theta_box, int n, const int* ranks,
+                               const double* cores, pttk_tt** out);
+
 /* Release a handle and its device memory (NULL is a no-op). */
 void pttk_tt_free(pttk_tt* tt);
 

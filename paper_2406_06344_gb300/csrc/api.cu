@@ -326,6 +326,38 @@ pttk_status pttk_tt_save(const pttk_tt* tt, const char* path) {
   return ok ? PTTK_OK : set_error(PTTK_EINVAL, std::string("write failed: ") + path);
 }
 
+// Copies host FP64 cores (packed in core order, each column-major) into a handle whose
+// metadata and ranks are set, and prepares its FP32 and oriented copies. Frees the handle
+// on failure.
+static pttk_status upload_cores(pttk_tt_ext* t, const double* host, pttk_tt** out) {
+  size_t off = 0;
+  for (int k = 0; k < t->D; ++k) {
+    t->core_off[k] = off;
+    off += t->core_elems(k);
+  }
+  t->core_total = off;
+  cudaGetDevice(&t->device);
+  cudaError_t e = cudaMalloc(&t->cores64, sizeof(double) * t->core_total);
+  if (e == cudaSuccess) e = cudaMalloc(&t->cores32, sizeof(float) * t->core_total);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(t->cores64, host, sizeof(double) * t->core_total, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    std::vector<float> h32(host, host + t->core_total);
+    e = cudaMemcpy(t->cores32, h32.data(), sizeof(float) * t->core_total, cudaMemcpyHostToDevice);
+  }
+  pttk_status st = e == cudaSuccess ? prepare_oriented(t, 0) : cuda_error(e, "uploading cores");
+  if (st == PTTK_OK) {
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_error(e, "uploading cores");
+  }
+  if (st != PTTK_OK) {
+    free_handle(t);
+    return st;
+  }
+  *out = t;
+  return PTTK_OK;
+}
+
 pttk_status pttk_tt_load(const char* path, pttk_tt** out) {
   clear_error();
   if (!path || !out) return set_error(PTTK_EINVAL, "NULL argument");
@@ -354,42 +386,34 @@ pttk_status pttk_tt_load(const char* path, pttk_tt** out) {
   ok = ok && t->ranks[0] == 1 && t->ranks[t->D] == 1;
   std::vector<double> host;
   if (ok) {
-    size_t off = 0;
-    for (int k = 0; k < t->D; ++k) {
-      t->core_off[k] = off;
-      off += t->core_elems(k);
-    }
-    t->core_total = off;
-    host.resize(off);
-    ok = fread(host.data(), sizeof(double), off, f) == off;
+    size_t total = 0;
+    for (int k = 0; k < t->D; ++k) total += t->core_elems(k);
+    host.resize(total);
+    ok = fread(host.data(), sizeof(double), total, f) == total;
   }
   fclose(f);
   if (!ok) {
     delete t;
     return set_error(PTTK_EINVAL, std::string("not a valid TT file: ") + path);
   }
-  cudaGetDevice(&t->device);
-  cudaError_t e = cudaMalloc(&t->cores64, sizeof(double) * t->core_total);
-  if (e == cudaSuccess) e = cudaMalloc(&t->cores32, sizeof(float) * t->core_total);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(t->cores64, host.data(), sizeof(double) * t->core_total, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    free_handle(t);
-    return cuda_error(e, "loading cores");
-  }
-  std::vector<float> h32(host.begin(), host.end());
-  e = cudaMemcpy(t->cores32, h32.data(), sizeof(float) * t->core_total, cudaMemcpyHostToDevice);
-  pttk_status st = e == cudaSuccess ? prepare_oriented(t, 0) : cuda_error(e, "loading cores");
-  if (st == PTTK_OK) {
-    e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) st = cuda_error(e, "loading cores");
-  }
-  if (st != PTTK_OK) {
-    free_handle(t);
-    return st;
-  }
-  *out = t;
-  return PTTK_OK;
+  return upload_cores(t, host.data(), out);
+}
+
+pttk_status pttk_tt_from_cores(pttk_kernel kernel, int d, const double* src_box, const double* tgt_box,
+                               int d_theta, const double* theta_box, int n, const int* ranks,
+                               const double* cores, pttk_tt** out) {
+  clear_error();
+  if (!out || !ranks || !cores) return set_error(PTTK_EINVAL, "NULL argument");
+  *out = nullptr;
+  PTTK_TRY(check_problem(kernel, d, src_box, tgt_box, d_theta, theta_box, n));
+  const int D = 2 * d + d_theta;
+  if (ranks[0] != 1 || ranks[D] != 1) return set_error(PTTK_EINVAL, "ranks[0] and ranks[D] must be 1");
+  for (int k = 1; k < D; ++k)
+    if (ranks[k] < 1 || ranks[k] > (1 << 20)) return set_error(PTTK_EINVAL, "TT rank out of range");
+  pttk_tt_ext* t = new pttk_tt_ext();
+  fill_meta(t, kernel, d, src_box, tgt_box, d_theta, theta_box, n);
+  for (int k = 0; k <= D; ++k) t->ranks[k] = ranks[k];
+  return upload_cores(t, cores, out);
 }
 
 void pttk_tt_free(pttk_tt* tt) { free_handle(static_cast<pttk_tt_ext*>(tt)); }

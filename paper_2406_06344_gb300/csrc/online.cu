@@ -74,6 +74,53 @@ __global__ void store_rowmajor_kernel(const double* __restrict__ H, int rs, int 
   }
 }
 
+// H = H1 H2 for two theta cores, split over the inner dimension so that the product spreads
+// over the whole GPU (FP64 issue is ~2 DFMA per clock per SM here, so a few output tiles on a
+// few SMs would take ~0.5 ms): block (tile, slice) writes
+//   part[slice][a + rs b] = sum_{c in slice} H1[a + rs c] H2[c + rm b]
+// and hprod_reduce_kernel sums the slices in a fixed order.
+constexpr int HP_T = 32;  // output tile edge and inner slice length
+__global__ void __launch_bounds__(256) hprod_splitk_kernel(const double* __restrict__ H1,
+                                                           const double* __restrict__ H2, int rs,
+                                                           int rm, int rt,
+                                                           double* __restrict__ part) {
+  __shared__ double a_s[HP_T][HP_T + 1], b_s[HP_T][HP_T + 1];
+  const int a0 = blockIdx.x * HP_T, b0 = blockIdx.y * HP_T, c0 = blockIdx.z * HP_T;
+  for (int e = threadIdx.x; e < HP_T * HP_T; e += blockDim.x) {
+    const int i = e % HP_T, j = e / HP_T;  // a_s[i][j] = H1[a0 + i, c0 + j]; b_s[i][j] = H2[c0 + i, b0 + j]
+    a_s[i][j] = (a0 + i < rs && c0 + j < rm) ? H1[(a0 + i) + (int64_t)rs * (c0 + j)] : 0.0;
+    b_s[i][j] = (c0 + i < rm && b0 + j < rt) ? H2[(c0 + i) + (int64_t)rm * (b0 + j)] : 0.0;
+  }
+  __syncthreads();
+  const int ti = threadIdx.x % HP_T, tj = threadIdx.x / HP_T;  // tj in [0, 8)
+  double acc[HP_T / 8] = {};
+  for (int c = 0; c < HP_T; ++c) {
+    const double av = a_s[ti][c];
+#pragma unroll
+    for (int q = 0; q < HP_T / 8; ++q) acc[q] = fma(av, b_s[c][tj + 8 * q], acc[q]);
+  }
+  double* out = part + (int64_t)blockIdx.z * rs * rt;
+#pragma unroll
+  for (int q = 0; q < HP_T / 8; ++q) {
+    const int a = a0 + ti, b = b0 + tj + 8 * q;
+    if (a < rs && b < rt) out[a + (int64_t)rs * b] = acc[q];
+  }
+}
+
+// M row-major (rs x rt) = sum over the slices of part, in slice order
+template <typename T>
+__global__ void hprod_reduce_kernel(const double* __restrict__ part, int nslices, int rs, int rt,
+                                    T* __restrict__ M) {
+  const int64_t total = (int64_t)rs * rt;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / rt, b = e % rt;
+    double acc = 0.0;
+    for (int sl = 0; sl < nslices; ++sl) acc += part[(int64_t)sl * total + a + (int64_t)rs * b];
+    M[e] = (T)acc;
+  }
+}
+
 __global__ void identity_rowmajor_kernel(void* M, int r, bool fp64) {
   const int64_t total = (int64_t)r * r;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -308,9 +355,12 @@ pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64
     PTTK_CUDA(cudaGetLastError());
     return PTTK_OK;
   }
+  PTTK_PROF("theta_core", s);
+  const int rm = tt->ranks[d + 1];
+  const int nslices = (rm + HP_T - 1) / HP_T;
   size_t need = 0;
   for (int j = 0; j < dth; ++j) need += (size_t)tt->ranks[d + j] * tt->ranks[d + j + 1];
-  need += (size_t)rs * rt * (dth > 1 ? 2 : 0);
+  need += (size_t)rs * rt * (dth > 1 ? nslices : 0);
   double* work = nullptr;
   PTTK_CUDA(cudaMallocAsync(&work, sizeof(double) * std::max<size_t>(need, 1), s));
   double* Hj[2] = {work, work + (size_t)tt->ranks[d] * tt->ranks[d + 1]};
@@ -321,16 +371,18 @@ pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64
     contract_theta_kernel<<<blocks, 256, 0, s>>>(tt->cores64 + tt->core_off[d + j], ra, n, rb,
                                                  theta_hat[j], Hj[j]); pttk::count_launch();
   }
-  const double* H = Hj[0];
-  if (dth == 2) {
-    double* Hp = Hj[1] + (size_t)tt->ranks[d + 1] * tt->ranks[d + 2];
-    dgemm(false, false, rs, rt, tt->ranks[d + 1], 1.0, Hj[0], rs, Hj[1], tt->ranks[d + 1], 0.0,
-          Hp, rs, s);
-    H = Hp;
-  }
   const unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)rs * rt + 255) / 256, sm_count() * 8);
-  if (fp64) { store_rowmajor_kernel<double><<<blocks, 256, 0, s>>>(H, rs, rt, static_cast<double*>(M)); pttk::count_launch(); }
-  else { store_rowmajor_kernel<float><<<blocks, 256, 0, s>>>(H, rs, rt, static_cast<float*>(M)); pttk::count_launch(); }
+  if (dth == 2) {
+    double* part = Hj[1] + (size_t)rm * rt;
+    const dim3 grid((unsigned)((rs + HP_T - 1) / HP_T), (unsigned)((rt + HP_T - 1) / HP_T), (unsigned)nslices);
+    hprod_splitk_kernel<<<grid, 256, 0, s>>>(Hj[0], Hj[1], rs, rm, rt, part); pttk::count_launch();
+    if (fp64) { hprod_reduce_kernel<double><<<blocks, 256, 0, s>>>(part, nslices, rs, rt, static_cast<double*>(M)); pttk::count_launch(); }
+    else { hprod_reduce_kernel<float><<<blocks, 256, 0, s>>>(part, nslices, rs, rt, static_cast<float*>(M)); pttk::count_launch(); }
+  } else if (fp64) {
+    store_rowmajor_kernel<double><<<blocks, 256, 0, s>>>(Hj[0], rs, rt, static_cast<double*>(M)); pttk::count_launch();
+  } else {
+    store_rowmajor_kernel<float><<<blocks, 256, 0, s>>>(Hj[0], rs, rt, static_cast<float*>(M)); pttk::count_launch();
+  }
   PTTK_CUDA(cudaGetLastError());
   PTTK_CUDA(cudaFreeAsync(work, s));
   return PTTK_OK;

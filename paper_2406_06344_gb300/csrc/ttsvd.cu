@@ -22,6 +22,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <chrono>
 #include <numeric>
 #include <vector>
 
@@ -90,70 +91,162 @@ __global__ void transpose_kernel(const double* __restrict__ X, int64_t m, int64_
   }
 }
 
-// ---------------- Householder QR, R factor only (A: M x N column-major, M >= N) --------
-// Reflector j: x = A[j:M, j], beta = -sign(x_0) ||x||, v = [1; x_{1:}/(x_0 - beta)],
-// tau = (beta - x_0) / beta, H_j = I - tau v v^T, H_j x = beta e_1 (LAPACK convention).
-struct HHScal {
+// ---------------- Householder QR with column pivoting, truncated --------------------------
+// A: M x N column-major (M >= N), overwritten. Step j picks, among the columns not yet
+// factored, the one with the largest norm in rows j..M-1 (ties: lowest position), moves it to
+// position j, and reflects it: x = A[j:M, p], beta = -sign(x_0) ||x||,
+// v = [1; x_{1:}/(x_0 - beta)], tau = (beta - x_0) / beta, H_j = I - tau v v^T,
+// H_j x = beta e_1 (LAPACK convention). The factorisation stops before step j as soon as
+// the remaining block A[j:M, j:N] (the R22 of A P = Q [R11 R12; 0 R22]) has Frobenius norm
+// <= `stop`: then A P = Q [R11 R12] + (a term of norm ||R22||_F), which is what the
+// truncated SVD downstream needs, and k = j rows of R are kept.
+//
+// Columns are never moved: perm[l] is the physical column at position l, the reflector data
+// of step j stays in physical column perm[j], and R is stored by physical column,
+// Rp[i + N * perm[l]] = R[i, l]. The norm of every remaining column below the next diagonal
+// row comes exactly from the update of the previous step (per 1024-row chunk, summed in a
+// fixed order), so pivots and the stopping test use exact norms, not downdated ones.
+struct HHState {
   double beta, scale, tau;
+  double tail2;  // ||R22||_F^2 at the stop (0 if every column was factored)
+  int done, k;
 };
 
-__global__ void hh_colnorm_kernel(const double* __restrict__ A, int64_t M, int64_t col,
-                                  int64_t row0, double* __restrict__ norm_part) {
-  __shared__ double red[8];
-  const int64_t c = blockIdx.x + row0 / RC;
-  const int64_t r_begin = std::max<int64_t>(c * RC, row0), r_end = std::min<int64_t>((c + 1) * RC, M);
-  double acc = 0.0;
-  for (int64_t i = r_begin + threadIdx.x; i < r_end; i += blockDim.x) {
-    const double a = A[i + col * M];
-    acc = fma(a, a, acc);
+// part[c * N + p] = sum of A[i, p]^2 over rows i >= 1 of chunk c, for every column p
+__global__ void __launch_bounds__(256) hh_init_norms_kernel(const double* __restrict__ A, int64_t M,
+                                                            int64_t N, double* __restrict__ part) {
+  const int64_t c = blockIdx.x;
+  const int64_t r_begin = std::max<int64_t>(c * RC, 1), r_end = std::min<int64_t>((c + 1) * RC, M);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t p = (int64_t)blockIdx.y * CG + warp; p < std::min<int64_t>(N, ((int64_t)blockIdx.y + 1) * CG); p += 8) {
+    const double* col = A + p * M;
+    double acc = 0.0;
+    for (int64_t i = r_begin + lane; i < r_end; i += 32) acc = fma(col[i], col[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) part[c * N + p] = acc;
   }
-  acc = block_sum<256>(acc, red);
-  if (threadIdx.x == 0) norm_part[c] = acc;
 }
 
-__global__ void hh_scalar_kernel(const double* __restrict__ A, int64_t M, int64_t N, int64_t j,
-                                 const double* __restrict__ norm_part, int64_t nchunks,
-                                 HHScal* __restrict__ hs, double* __restrict__ R) {
-  __shared__ double red[8];
+// below[perm[l]] = sum over chunks of part (rows > j), for positions l >= j; one warp per column
+__global__ void __launch_bounds__(256) hh_below_kernel(const double* __restrict__ part, int64_t N,
+                                                       int64_t j, int64_t nchunks,
+                                                       const int* __restrict__ perm,
+                                                       const HHState* __restrict__ st,
+                                                       double* __restrict__ below) {
+  if (st->done) return;
+  const int64_t l = j + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (l >= N) return;
+  const int p = perm[l];
   double acc = 0.0;
-  for (int64_t c = j / RC + threadIdx.x; c < nchunks; c += blockDim.x) acc += norm_part[c];
-  acc = block_sum<256>(acc, red);  // sum of squares strictly below the diagonal
-  if (threadIdx.x == 0) {
-    const double x0 = A[j + j * M];
-    HHScal h;
-    if (!(acc > 0.0)) {  // nothing below the diagonal: no reflection
-      h.beta = x0;
-      h.scale = 0.0;
-      h.tau = 0.0;
-    } else {
-      const double nrm = hypot(x0, sqrt(acc));
-      h.beta = (x0 >= 0.0) ? -nrm : nrm;
-      h.scale = 1.0 / (x0 - h.beta);
-      h.tau = (h.beta - x0) / h.beta;
+  for (int64_t c = j / RC + lane; c < nchunks; c += 32) acc += part[c * N + p];
+  acc = warp_sum(acc);
+  if (lane == 0) below[p] = acc;
+}
+
+// Pivot choice, stopping test and reflector of step j (one block).
+__global__ void __launch_bounds__(1024) hh_pivot_kernel(const double* __restrict__ A, int64_t M,
+                                                        int64_t N, int64_t j,
+                                                        const double* __restrict__ below,
+                                                        int* __restrict__ perm, double stop2,
+                                                        HHState* __restrict__ st,
+                                                        double* __restrict__ Rp) {
+  __shared__ double s_tot[32], s_max[32];
+  __shared__ int64_t s_arg[32];
+  if (st->done) return;
+  double tot = 0.0, best = -1.0;
+  int64_t arg = N;
+  for (int64_t l = j + threadIdx.x; l < N; l += blockDim.x) {
+    const int p = perm[l];
+    const double x = A[j + (int64_t)p * M];
+    const double t = fma(x, x, below[p]);
+    tot += t;
+    if (t > best) {  // strictly greater: the lowest position wins ties within a thread
+      best = t;
+      arg = l;
     }
-    *hs = h;
-    R[j + j * N] = h.beta;
   }
+  // fixed-order block reductions: sum, and max with the lowest position on ties
+  for (int o = 16; o; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int64_t oa = __shfl_xor_sync(0xffffffffu, arg, o);
+    if (ob > best || (ob == best && oa < arg)) {
+      best = ob;
+      arg = oa;
+    }
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_tot[w] = tot;
+    s_max[w] = best;
+    s_arg[w] = arg;
+  }
+  __syncthreads();
+  if (w != 0) return;
+  const int nw = blockDim.x >> 5;
+  tot = lane < nw ? s_tot[lane] : 0.0;
+  best = lane < nw ? s_max[lane] : -1.0;
+  arg = lane < nw ? s_arg[lane] : N;
+  for (int o = 16; o; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int64_t oa = __shfl_xor_sync(0xffffffffu, arg, o);
+    if (ob > best || (ob == best && oa < arg)) {
+      best = ob;
+      arg = oa;
+    }
+  }
+  if (lane != 0) return;
+  if (j > 0 && tot <= stop2) {
+    st->done = 1;
+    st->k = (int)j;
+    st->tail2 = tot;
+    return;
+  }
+  if (arg >= N) arg = j;
+  const int pj = perm[arg];
+  perm[arg] = perm[j];
+  perm[j] = pj;
+  const double x0 = A[j + (int64_t)pj * M];
+  const double acc = below[pj];  // sum of squares strictly below the diagonal
+  HHState h = *st;
+  if (!(acc > 0.0)) {  // nothing below the diagonal: no reflection
+    h.beta = x0;
+    h.scale = 0.0;
+    h.tau = 0.0;
+  } else {
+    const double nrm = hypot(x0, sqrt(acc));
+    h.beta = (x0 >= 0.0) ? -nrm : nrm;
+    h.scale = 1.0 / (x0 - h.beta);
+    h.tau = (h.beta - x0) / h.beta;
+  }
+  h.k = (int)(j + 1);
+  *st = h;
+  Rp[j + (int64_t)pj * N] = h.beta;
 }
 
-// w_part[c, l] = sum_{i in chunk c, i >= j} v_i A[i, l], l in (j, N)
+// w_part[c * N + l] = sum_{i in chunk c, i >= j} v_i A[i, perm[l]], l in (j, N)
 __global__ void __launch_bounds__(256) hh_w_kernel(const double* __restrict__ A, int64_t M,
                                                    int64_t N, int64_t j,
-                                                   const HHScal* __restrict__ hs,
+                                                   const int* __restrict__ perm,
+                                                   const HHState* __restrict__ st,
                                                    double* __restrict__ w_part) {
   __shared__ double v[RC];
+  if (st->done) return;
   const int64_t c = blockIdx.x + j / RC;
   const int64_t r_begin = std::max<int64_t>(c * RC, j), r_end = std::min<int64_t>((c + 1) * RC, M);
-  const double scale = hs->scale;
+  const double scale = st->scale;
+  const double* vj = A + (int64_t)perm[j] * M;
   for (int64_t i = r_begin + threadIdx.x; i < r_end; i += blockDim.x)
-    v[i - c * RC] = (i == j) ? 1.0 : A[i + j * M] * scale;
+    v[i - c * RC] = (i == j) ? 1.0 : vj[i] * scale;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t l0 = j + 1 + (int64_t)blockIdx.y * CG;
   for (int q = warp; q < CG; q += 8) {
     const int64_t l = l0 + q;
     if (l >= N) break;
-    const double* col = A + l * M;
+    const double* col = A + (int64_t)perm[l] * M;
     double acc = 0.0;
     for (int64_t i = r_begin + lane; i < r_end; i += 32) acc = fma(v[i - c * RC], col[i], acc);
     acc = warp_sum(acc);
@@ -161,50 +254,72 @@ __global__ void __launch_bounds__(256) hh_w_kernel(const double* __restrict__ A,
   }
 }
 
-// w[l] = tau * sum_c w_part[c, l]
+// w[l] = tau * sum_c w_part[c * N + l]
 __global__ void hh_wsum_kernel(const double* __restrict__ w_part, int64_t N, int64_t j,
-                               int64_t nchunks, const HHScal* __restrict__ hs,
+                               int64_t nchunks, const HHState* __restrict__ st,
                                double* __restrict__ w) {
   __shared__ double red[8];
+  if (st->done) return;
   const int64_t l = j + 1 + blockIdx.x;
   double acc = 0.0;
   for (int64_t c = j / RC + threadIdx.x; c < nchunks; c += blockDim.x) acc += w_part[c * N + l];
   acc = block_sum<256>(acc, red);
-  if (threadIdx.x == 0) w[l] = hs->tau * acc;
+  if (threadIdx.x == 0) w[l] = st->tau * acc;
 }
 
-// A[i, l] -= v_i w[l]; row j of the result is row j of R; partial norm of column j+1.
+// A[i, perm[l]] -= v_i w[l] for rows i >= j; row j of the result is row j of R; the squares
+// of rows i >= j+2 (below the next diagonal) go to part[c * N + perm[l]]. One warp per column.
 __global__ void __launch_bounds__(256) hh_update_kernel(double* __restrict__ A, int64_t M,
                                                         int64_t N, int64_t j,
-                                                        const HHScal* __restrict__ hs,
+                                                        const int* __restrict__ perm,
+                                                        const HHState* __restrict__ st,
                                                         const double* __restrict__ w,
-                                                        double* __restrict__ R,
-                                                        double* __restrict__ norm_part) {
+                                                        double* __restrict__ Rp,
+                                                        double* __restrict__ part) {
   __shared__ double v[RC];
-  __shared__ double red[8];
+  if (st->done) return;
   const int64_t c = blockIdx.x + j / RC;
   const int64_t r_begin = std::max<int64_t>(c * RC, j), r_end = std::min<int64_t>((c + 1) * RC, M);
-  const double scale = hs->scale;
+  const double scale = st->scale;
+  const double* vj = A + (int64_t)perm[j] * M;
   for (int64_t i = r_begin + threadIdx.x; i < r_end; i += blockDim.x)
-    v[i - c * RC] = (i == j) ? 1.0 : A[i + j * M] * scale;
+    v[i - c * RC] = (i == j) ? 1.0 : vj[i] * scale;
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t l0 = j + 1 + (int64_t)blockIdx.y * CG;
-  const int64_t l1 = std::min<int64_t>(l0 + CG, N);
-  double nacc = 0.0;
-  for (int64_t l = l0; l < l1; ++l) {
+  for (int q = warp; q < CG; q += 8) {
+    const int64_t l = l0 + q;
+    if (l >= N) break;
+    const int p = perm[l];
     const double wl = w[l];
-    double* col = A + l * M;
-    for (int64_t i = r_begin + threadIdx.x; i < r_end; i += blockDim.x) {
+    double* col = A + (int64_t)p * M;
+    double nacc = 0.0;
+    for (int64_t i = r_begin + lane; i < r_end; i += 32) {
       const double a = fma(-v[i - c * RC], wl, col[i]);
       col[i] = a;
-      if (i == j) R[j + l * N] = a;
-      if (l == j + 1 && i >= j + 2) nacc = fma(a, a, nacc);
+      if (i == j) Rp[j + (int64_t)p * N] = a;
+      if (i >= j + 2) nacc = fma(a, a, nacc);
     }
+    nacc = warp_sum(nacc);
+    if (lane == 0) part[c * N + p] = nacc;
   }
-  if (l0 == j + 1) {  // this column group holds column j+1
-    nacc = block_sum<256>(nacc, red);
-    if (threadIdx.x == 0) norm_part[c] = nacc;
+}
+
+// At[l + N * i] = R[i, l] = Rp[i + N * perm[l]] for l < N, i < k: the transpose of the kept rows
+__global__ void gather_rt_kernel(const double* __restrict__ Rp, int64_t N, int k,
+                                 const int* __restrict__ perm, double* __restrict__ At) {
+  const int64_t total = N * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e % N, i = e / N;
+    At[e] = Rp[i + N * (int64_t)perm[l]];
   }
+}
+
+__global__ void iota_kernel(int* __restrict__ p, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = (int)e;
 }
 
 // ---------------- one-sided Jacobi (Hestenes) with round-robin pairing -----------------
@@ -343,30 +458,6 @@ __global__ void gather_cols_kernel(const double* __restrict__ in, int64_t rows,
   }
 }
 
-// Column sums of squares of A (rows x ncols, column-major) in two deterministic levels:
-// partial[col * nsplit + split] over a contiguous slice of the column, then a fixed-order sum.
-__global__ void __launch_bounds__(256) colsq_partial_kernel(const double* __restrict__ A, int64_t rows,
-                                                            int nsplit, double* __restrict__ partial) {
-  __shared__ double red[8];
-  const int64_t col = blockIdx.y;
-  const int64_t per = (rows + nsplit - 1) / nsplit;
-  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = std::min<int64_t>(rows, r0 + per);
-  const double* a = A + col * rows;
-  double acc = 0.0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) acc = fma(a[i], a[i], acc);
-  acc = block_sum<256>(acc, red);
-  if (threadIdx.x == 0) partial[col * nsplit + blockIdx.x] = acc;
-}
-
-__global__ void colsq_final_kernel(const double* __restrict__ partial, int nsplit, int ncols,
-                                   double* __restrict__ norms) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= ncols) return;
-  double acc = 0.0;
-  for (int k = 0; k < nsplit; ++k) acc += partial[(int64_t)col * nsplit + k];
-  norms[col] = sqrt(acc);
-}
-
 // out[perm[i] + rows q] = in[i + rows q] (rows x ncols, column-major)
 __global__ void scatter_rows_kernel(const double* __restrict__ in, int64_t rows, int ncols,
                                     const int* __restrict__ perm, double* __restrict__ out) {
@@ -476,24 +567,42 @@ unsigned grid1d(int64_t work, int threads, int cap_per_sm = 8) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * cap_per_sm));
 }
 
-// R (N x N) of A (M x N, M >= N), A overwritten.
-pttk_status householder_r(double* A, int64_t M, int64_t N, double* R, double* norm_part,
-                          double* w_part, double* w, HHScal* hs, cudaStream_t s) {
+// Pivoted Householder QR of A (M x N, M >= N, overwritten), stopped once ||R22||_F^2 <= stop2
+// (at least one step is taken). On return perm[0..N) holds the column order, Rp the rows
+// 0..k-1 of R by physical column (Rp must be N x N and is zeroed here), *k_out the number of
+// rows kept and *tail2_out ||R22||_F^2 at the stop. Synchronises `s` every 16 steps to read the
+// stop flag; steps enqueued after the stop return at once.
+pttk_status householder_qrcp(double* A, int64_t M, int64_t N, double stop2, double* Rp, int* perm,
+                             double* part, double* below, double* w_part, double* w, HHState* st,
+                             int* k_out, double* tail2_out, cudaStream_t s) {
   const int64_t nchunks = (M + RC - 1) / RC;
   PTTK_PROF("householder", s);
-  PTTK_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * N * N, s));
-  hh_colnorm_kernel<<<(unsigned)nchunks, 256, 0, s>>>(A, M, 0, 1, norm_part); pttk::count_launch();
+  PTTK_CUDA(cudaMemsetAsync(Rp, 0, sizeof(double) * N * N, s));
+  PTTK_CUDA(cudaMemsetAsync(st, 0, sizeof(HHState), s));
+  iota_kernel<<<grid1d(N, 256), 256, 0, s>>>(perm, N); pttk::count_launch();
+  hh_init_norms_kernel<<<dim3((unsigned)nchunks, (unsigned)((N + CG - 1) / CG)), 256, 0, s>>>(A, M, N, part); pttk::count_launch();
+  HHState h{};
   for (int64_t j = 0; j < N; ++j) {
-    hh_scalar_kernel<<<1, 256, 0, s>>>(A, M, N, j, norm_part, nchunks, hs, R); pttk::count_launch();
+    hh_below_kernel<<<(unsigned)((N - j + 7) / 8), 256, 0, s>>>(part, N, j, nchunks, perm, st, below); pttk::count_launch();
+    hh_pivot_kernel<<<1, 1024, 0, s>>>(A, M, N, j, below, perm, stop2, st, Rp); pttk::count_launch();
     const int64_t trailing = N - j - 1;
-    if (trailing <= 0) break;
-    const unsigned gx = (unsigned)(nchunks - j / RC);
-    const unsigned gy = (unsigned)((trailing + CG - 1) / CG);
-    hh_w_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, hs, w_part); pttk::count_launch();
-    hh_wsum_kernel<<<(unsigned)trailing, 256, 0, s>>>(w_part, N, j, nchunks, hs, w); pttk::count_launch();
-    hh_update_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, hs, w, R, norm_part); pttk::count_launch();
+    if (trailing > 0) {
+      const unsigned gx = (unsigned)(nchunks - j / RC);
+      const unsigned gy = (unsigned)((trailing + CG - 1) / CG);
+      hh_w_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, perm, st, w_part); pttk::count_launch();
+      hh_wsum_kernel<<<(unsigned)trailing, 256, 0, s>>>(w_part, N, j, nchunks, st, w); pttk::count_launch();
+      hh_update_kernel<<<dim3(gx, gy), 256, 0, s>>>(A, M, N, j, perm, st, w, Rp, part); pttk::count_launch();
+    }
+    if ((j & 15) == 15 || j == N - 1) {
+      PTTK_CUDA(cudaGetLastError());
+      PTTK_CUDA(cudaMemcpyAsync(&h, st, sizeof(HHState), cudaMemcpyDeviceToHost, s));
+      PTTK_CUDA(cudaStreamSynchronize(s));
+      if (h.done) break;
+    }
   }
   PTTK_CUDA(cudaGetLastError());
+  *k_out = h.done ? h.k : (int)N;
+  *tail2_out = h.done ? h.tail2 : 0.0;
   return PTTK_OK;
 }
 
@@ -533,12 +642,14 @@ pttk_status jacobi(double* A, int64_t rows, int ncols, double* V, int64_t nv, un
 }
 
 // Sorted order of sigma (descending) and the truncation rank for threshold delta.
-int truncation(const std::vector<double>& sigma, double delta, std::vector<int>& perm) {
+// `extra2` is a squared norm already discarded (the R22 of a truncated QR), counted in every tail.
+int truncation(const std::vector<double>& sigma, double delta, std::vector<int>& perm, double extra2 = 0.0) {
   perm.resize(sigma.size());
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return sigma[x] > sigma[y]; });
   const int m = (int)sigma.size();
-  std::vector<double> tail(m + 1, 0.0);  // tail[r] = sum_{i >= r} sigma_(i)^2
+  std::vector<double> tail(m + 1, 0.0);  // tail[r] = extra2 + sum_{i >= r} sigma_(i)^2
+  tail[m] = extra2;
   for (int i = m - 1; i >= 0; --i) tail[i] = tail[i + 1] + sigma[perm[i]] * sigma[perm[i]];
   for (int r = 1; r <= m; ++r)
     if (sqrt(tail[r]) <= delta) return r;
@@ -563,8 +674,31 @@ void dgemm(bool tA, bool tB, int64_t M, int64_t N, int64_t K, double alpha, cons
   }
 }
 
+// Wall-clock stage timing of the TT-SVD, printed to stderr when PTTK_VERBOSE is set (it
+// synchronises the stream at every mark, so it is off otherwise).
+struct StageClock {
+  bool on;
+  cudaStream_t s;
+  std::chrono::steady_clock::time_point t0;
+  explicit StageClock(cudaStream_t st) : on(getenv("PTTK_VERBOSE") != nullptr), s(st) { reset(); }
+  void reset() {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    t0 = std::chrono::steady_clock::now();
+  }
+  void mark(int k, const char* what) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    const auto t1 = std::chrono::steady_clock::now();
+    fprintf(stderr, "pttk: tt-svd step %d %-10s %9.3f ms\n", k + 1, what,
+            std::chrono::duration<double, std::milli>(t1 - t0).count());
+    t0 = t1;
+  }
+};
+
 pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   const int D = tt->D, n = tt->n;
+  StageClock clk(s);
   int64_t total = 1;
   for (int k = 0; k < D; ++k) total *= n;
 
@@ -581,16 +715,15 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   PTTK_CUDA(cudaStreamSynchronize(s));
   const double delta = tol / sqrt((double)(D - 1)) * sqrt(sumsq);
 
-  Buf W, Xn, R, wpart, wv;
-  PTTK_TRY(W.alloc(total));
+  Buf Xn, R, wpart, wv, below;
   PTTK_TRY(Xn.alloc(total));
   int* d_perm = nullptr;
   unsigned* d_counter = nullptr;
-  HHScal* d_hs = nullptr;
+  HHState* d_hs = nullptr;
   PTTK_CUDA(cudaMalloc(&d_counter, sizeof(unsigned)));
-  PTTK_CUDA(cudaMalloc(&d_hs, sizeof(HHScal)));
+  PTTK_CUDA(cudaMalloc(&d_hs, sizeof(HHState)));
   struct Guard {
-    int*& a; unsigned*& b; HHScal*& c;
+    int*& a; unsigned*& b; HHState*& c;
     ~Guard() { if (a) cudaFree(a); if (b) cudaFree(b); if (c) cudaFree(c); }
   } guard{d_perm, d_counter, d_hs};
 
@@ -600,80 +733,70 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   double* cur = X;
   double* nxt = Xn.p;
   int64_t cur_elems = total;
-  Buf qrin, A, U, Y, Yt, norms, colpart;
+  Buf qrin, A, U, Y, Yt, norms;
   for (int k = 0; k < D - 1; ++k) {
     PTTK_CUDA(cudaStreamSynchronize(s));  // buffers below are reallocated per step
     const int64_t m = r_prev * n;
     const int64_t c = cur_elems / m;
     const bool wide = c >= m;
-    // QR input: wide -> W = (P X)^T (c x m), tall -> W = X P (m x c); P orders the rows
-    // (wide) or columns (tall) of X by decreasing norm, which makes the triangular factor
-    // graded so that one-sided Jacobi on R^T converges in a few sweeps.
-    const int64_t q = wide ? m : c;        // size of the square R
+    // QR input: wide -> W = X^T (c x m), tall -> a copy of X (m x c). The pivoted QR makes
+    // the triangular factor graded, so one-sided Jacobi on its transpose converges in a few
+    // sweeps, and stops once the remaining block is negligible next to delta.
+    const int64_t q = wide ? m : c;        // columns of the QR input
     const int64_t Mqr = wide ? c : m;      // rows of the QR input
+    if (clk.on) fprintf(stderr, "pttk: tt-svd step %d m %lld c %lld %s\n", k + 1, (long long)m, (long long)c, wide ? "wide" : "tall");
+    clk.reset();
     PTTK_TRY(norms.alloc(std::max<int64_t>(q, 1)));
-    {
-      // norms of the q vectors to be ordered: rows of X (wide, via W = X^T) or columns (tall)
-      const double* src = cur;
-      int64_t len = m;
-      if (wide) {
-        dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
-        transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, nullptr, W.p); pttk::count_launch();
-        src = W.p;
-        len = c;
-      }
-      const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (len * q) / (256 * 1024 * 8) + 1));
-      PTTK_TRY(colpart.alloc((int64_t)nsplit * q));
-      colsq_partial_kernel<<<dim3((unsigned)nsplit, (unsigned)q), 256, 0, s>>>(src, len, nsplit, colpart.p); pttk::count_launch();
-      colsq_final_kernel<<<(unsigned)((q + 255) / 256), 256, 0, s>>>(colpart.p, nsplit, (int)q, norms.p); pttk::count_launch();
-    }
-    std::vector<double> nv(q);
-    PTTK_CUDA(cudaMemcpyAsync(nv.data(), norms.p, sizeof(double) * q, cudaMemcpyDeviceToHost, s));
-    PTTK_CUDA(cudaStreamSynchronize(s));
-    std::vector<int> order;
-    truncation(nv, 0.0, order);  // descending order
     if (d_perm) cudaFree(d_perm);
     d_perm = nullptr;
     PTTK_CUDA(cudaMalloc(&d_perm, sizeof(int) * q));
-    PTTK_CUDA(cudaMemcpyAsync(d_perm, order.data(), sizeof(int) * q, cudaMemcpyHostToDevice, s));
     PTTK_TRY(qrin.alloc(Mqr * q));
     if (wide) {
       dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
-      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, d_perm, qrin.p); pttk::count_launch();
+      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, nullptr, qrin.p); pttk::count_launch();
     } else {
-      gather_cols_kernel<<<grid1d(m * c, 256), 256, 0, s>>>(cur, m, d_perm, (int)c, nullptr, qrin.p); pttk::count_launch();
+      PTTK_CUDA(cudaMemcpyAsync(qrin.p, cur, sizeof(double) * m * c, cudaMemcpyDeviceToDevice, s));
     }
-    // R (q x q) of the ordered matrix, then A = R^T
     const int64_t nchunks = (Mqr + RC - 1) / RC;
-    PTTK_TRY(part.alloc(nchunks));
+    PTTK_TRY(part.alloc(nchunks * q));
     PTTK_TRY(wpart.alloc(nchunks * q));
     PTTK_TRY(wv.alloc(q));
+    PTTK_TRY(below.alloc(q));
     PTTK_TRY(R.alloc(q * q));
-    PTTK_TRY(A.alloc(q * q));
-    PTTK_TRY(householder_r(qrin.p, Mqr, q, R.p, part.p, wpart.p, wv.p, d_hs, s));
-    {
-      dim3 tg((unsigned)((q + 31) / 32), (unsigned)((q + 31) / 32));
-      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(R.p, q, q, nullptr, A.p); pttk::count_launch();
-    }
-    // one-sided Jacobi on R^T: R^T V = U' Sigma, so R = V Sigma U'^T and the right singular
-    // vectors of R (= of the ordered QR input) are the normalised columns of the rotated R^T
-    // columns below 1e-3 delta / sqrt(q) together carry < 1e-6 delta^2: pairs of them are skipped
-    PTTK_TRY(jacobi(A.p, q, (int)q, nullptr, 0, d_counter, s, 1e-3 * delta / sqrt((double)q)));
-    colnorm_kernel<<<(unsigned)((q * 32 + 255) / 256), 256, 0, s>>>(A.p, q, (int)q, norms.p); pttk::count_launch();
-    std::vector<double> sigma(q);
-    PTTK_CUDA(cudaMemcpyAsync(sigma.data(), norms.p, sizeof(double) * q, cudaMemcpyDeviceToHost, s));
+    clk.mark(k, "layout");
+    // rows of R kept: the QR stops once the discarded block has ||R22||_F <= 1e-3 delta, so
+    // it changes the tails below by at most 1e-6 delta^2 (and is counted in them)
+    int kq = 0;
+    double tail2 = 0.0;
+    const double stop = 1e-3 * delta;
+    PTTK_TRY(householder_qrcp(qrin.p, Mqr, q, stop * stop, R.p, d_perm, part.p, below.p, wpart.p, wv.p, d_hs,
+                              &kq, &tail2, s));
+    clk.mark(k, "qr");
+    if (clk.on) fprintf(stderr, "pttk: tt-svd step %d kept %d of %lld rows of R, ||R22|| %.3e\n", k + 1, kq, (long long)q, sqrt(tail2));
+    // A = R1^T (q x kq), R1 = the kept rows of R in pivoted column order
+    PTTK_TRY(A.alloc(q * kq));
+    gather_rt_kernel<<<grid1d(q * kq, 256), 256, 0, s>>>(R.p, q, kq, d_perm, A.p); pttk::count_launch();
+    // one-sided Jacobi on R1^T: R1^T V = U' Sigma, so R1 = V Sigma U'^T and the right singular
+    // vectors of R1 (= of the pivoted QR input, up to the discarded R22) are the normalised
+    // columns of the rotated R1^T; columns below 1e-3 delta / sqrt(kq) together carry
+    // < 1e-6 delta^2, and pairs of them are skipped
+    PTTK_TRY(jacobi(A.p, q, kq, nullptr, 0, d_counter, s, 1e-3 * delta / sqrt((double)kq)));
+    clk.mark(k, "jacobi");
+    colnorm_kernel<<<(unsigned)(((int64_t)kq * 32 + 255) / 256), 256, 0, s>>>(A.p, q, kq, norms.p); pttk::count_launch();
+    std::vector<double> sigma(kq);
+    PTTK_CUDA(cudaMemcpyAsync(sigma.data(), norms.p, sizeof(double) * kq, cudaMemcpyDeviceToHost, s));
     PTTK_CUDA(cudaStreamSynchronize(s));
     std::vector<int> perm;
-    const int r = truncation(sigma, delta, perm);
+    const int r = truncation(sigma, delta, perm, tail2);
     int* d_top = nullptr;
-    PTTK_CUDA(cudaMalloc(&d_top, sizeof(int) * std::max<int64_t>(q, 1)));
+    PTTK_CUDA(cudaMalloc(&d_top, sizeof(int) * std::max<int64_t>(kq, 1)));
     struct TopGuard { int* p; ~TopGuard() { if (p) cudaFree(p); } } top_guard{d_top};
-    PTTK_CUDA(cudaMemcpyAsync(d_top, perm.data(), sizeof(int) * q, cudaMemcpyHostToDevice, s));
-    // top-r right singular vectors (unit columns), in the ordered basis
+    PTTK_CUDA(cudaMemcpyAsync(d_top, perm.data(), sizeof(int) * kq, cudaMemcpyHostToDevice, s));
+    // top-r right singular vectors (unit columns), in the pivoted order
     PTTK_TRY(U.alloc(q * r));
     PTTK_TRY(Y.alloc(q * r));
     gather_cols_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(A.p, q, d_top, r, norms.p, Y.p); pttk::count_launch();
-    // back to the original order: row order[i] of the result is row i of Y
+    // back to the original order: row perm[l] of the result is row l of Y
     scatter_rows_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(Y.p, q, r, d_perm, U.p); pttk::count_launch();
     double* basis = U.p;  // m x r (wide): left singular vectors of X
     if (!wide) {
@@ -685,7 +808,9 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
     }
     // make the m x r basis orthonormal to working precision: its columns are orthogonal up
     // to ~eps ||X|| / sigma_i, so one-sided Jacobi needs one or two sweeps
+    clk.mark(k, "basis");
     PTTK_TRY(jacobi(basis, m, r, nullptr, 0, d_counter, s));
+    clk.mark(k, "reorth");
     {
       Buf bn;
       PTTK_TRY(bn.alloc(r));
@@ -703,6 +828,8 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
     // X <- G_k^T X  (r x c)
     dgemm(true, false, r, c, m, 1.0, cores[k].p, m, cur, m, 0.0, nxt, r, s);
     PTTK_CUDA(cudaGetLastError());
+    clk.mark(k, "project");
+    if (clk.on) fprintf(stderr, "pttk: tt-svd step %d rank %d\n", k + 1, r);
     tt->ranks[k + 1] = r;
     std::swap(cur, nxt);
     cur_elems = (int64_t)r * c;

@@ -42,6 +42,8 @@ SIGNATURES = [
     ("pttk_tt_get_core", _int, [_vp, _int, _c_double_p]),
     ("pttk_tt_save", _int, [_vp, ctypes.c_char_p]),
     ("pttk_tt_load", _int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
+    ("pttk_tt_from_cores", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int, _c_int_p,
+                                  _c_double_p, ctypes.POINTER(_vp)]),
     ("pttk_tt_free", None, [_vp]),
     ("pttk_theta_core", _int, [_vp, _c_double_p, _int, _vp, _vp]),
     ("pttk_tt_check", _int, [_vp, _vp]),
@@ -178,6 +180,20 @@ class TT:
         _check(load().pttk_tt_from_coeffs(kernel, d, _dbl(_boxflat(src_box)), _dbl(_boxflat(tgt_box)),
                                           dtheta, _dbl(_boxflat(theta_box)), n, tol, _ptr(C), prec,
                                           _stream(stream), ctypes.byref(h)))
+        return cls(h.value)
+
+    @classmethod
+    def from_cores(cls, kernel: int, d: int, src_box, tgt_box, dtheta: int, theta_box, n: int, cores) -> "TT":
+        """pttk_tt_from_cores: a handle from host cores (core k: r_{k-1} x n x r_k, Chebyshev
+        coefficient form)."""
+        ranks = [int(cores[0].shape[0])] + [int(G.shape[2]) for G in cores]
+        packed = np.ascontiguousarray(np.concatenate(
+            [np.asarray(G, dtype=np.float64).reshape(-1, order="F") for G in cores]))
+        r = (_int * len(ranks))(*ranks)
+        h = _vp()
+        _check(load().pttk_tt_from_cores(kernel, d, _dbl(_boxflat(src_box)), _dbl(_boxflat(tgt_box)), dtheta,
+                                         _dbl(_boxflat(theta_box)), n, r, packed.ctypes.data_as(_c_double_p),
+                                         ctypes.byref(h)))
         return cls(h.value)
 
     @classmethod

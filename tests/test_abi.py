@@ -105,3 +105,18 @@ def test_load_rejects_garbage(so, tmp_path):
     h = ctypes.c_void_p()
     assert so.pttk_tt_load(str(p).encode(), ctypes.byref(h)) == pttk.EINVAL
     assert so.pttk_tt_load(str(tmp_path / "missing.tt").encode(), ctypes.byref(h)) == pttk.EINVAL
+
+
+def test_from_cores_rejects_bad_ranks_without_touching_the_device(so):
+    from paper_2406_06344_gb300 import pttk
+    s, t, p = _boxes()
+    h = ctypes.c_void_p()
+    cores = pttk._dbl([0.0] * 64)
+    bad_first = (ctypes.c_int * 4)(2, 3, 3, 1)
+    assert so.pttk_tt_from_cores(0, 1, s, t, 1, p, 8, bad_first, cores, ctypes.byref(h)) == pttk.EINVAL
+    assert "ranks[0]" in so.pttk_last_error().decode()
+    bad_mid = (ctypes.c_int * 4)(1, 0, 3, 1)
+    assert so.pttk_tt_from_cores(0, 1, s, t, 1, p, 8, bad_mid, cores, ctypes.byref(h)) == pttk.EINVAL
+    assert so.pttk_tt_from_cores(0, 1, s, t, 1, p, 8, None, cores, ctypes.byref(h)) == pttk.EINVAL
+    assert so.pttk_tt_from_cores(2, 1, s, t, 1, p, 8, bad_first, cores, ctypes.byref(h)) == pttk.EINVAL
+    assert not h.value

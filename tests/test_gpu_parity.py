@@ -273,6 +273,26 @@ def test_save_load_roundtrip(P, torch_cuda, tmp_path):
         assert torch_cuda.equal(a, b)
 
 
+def test_from_cores_with_oracle_cores(P, torch_cuda):
+    """A handle made from the oracle's own TT cores: the GPU online stage on them equals the
+    oracle's online stage (no GPU TT-SVD involved), and the cores come back unchanged."""
+    w = W.C2
+    cores, ranks, _ = o.build_offline(w.kernel, w.d, w.dtheta, w.mode_boxes(), 8, 1e-10)
+    tt = P.TT.from_cores(w.kernel, w.d, w.src_box, w.tgt_box, w.dtheta, w.theta_box, 8, cores)
+    assert tt.ranks == ranks
+    for a, b in zip(cores, tt.cores()):
+        assert np.array_equal(a, b)
+    X = W.sources(w, 777)
+    Y = W.targets(w, 555)
+    th = W.thetas(w, 1)[0]
+    U, M, V = P.instantiate(tt, th, torch_cuda.tensor(X, device="cuda"), torch_cuda.tensor(Y, device="cuda"), "fp64")
+    tt.check()
+    Uo, Mo, Vo = o.instantiate(cores, w.d, w.dtheta, w.mode_boxes(), th, X, Y)
+    Ko = Uo @ Mo @ Vo.T
+    assert o.rel_fro(Ko, U.cpu().numpy() @ M.cpu().numpy() @ V.cpu().numpy().T) <= 1e-12
+    tt.free()
+
+
 # --- full-size workloads (sampled checks) ---------------------------------------------
 
 def test_c3_full_size_fp64(P, torch_cuda):
