@@ -10,7 +10,8 @@ One timed step is one pass of the whole hot path over that batch:
      FP32 (the fast form);
   2. TT-SVD of the FP64 coefficient tensor at tol 1e-10 (pttk_tt_from_coeffs);
   3. 256 online instantiations (pttk_instantiate: H(theta), U(X), V(Y)) at N = 1M per side in
-     the fast online form (3xTF32 on the tensor cores);
+     the fast online form (3xFP16 on the tensor cores: two FP16 parts per operand, three
+     products, FP32 accumulation; ~22 significant bits, the accuracy of 3xTF32);
   4. pttk_apply of the last factors to a vector.
 `value` is online factor builds/s: builds of the fast form divided by their device time inside
 the timed steps. Beside it: grid entries/s (FP64 and FP32), every online form's build rate and
@@ -40,8 +41,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "online factor builds/s (N=1M) & grid entries/s vs FP64 plain at stated rel err"
 UNIT = "builds/s"
-FAST_FORM = "tf32x3"
-FORMS = ("fp64", "fp32", "tf32", "tf32x3", "bf16", "bf16x3")
+FAST_FORM = "fp16x3"
+FORMS = ("fp64", "fp32", "tf32", "tf32x3", "fp16", "fp16x3", "bf16", "bf16x3")
 N_THETA = 256
 WORKLOAD = "d3 matern-nu n12 (12^8 grid), N_s=N_t=1M, 256 theta"
 # nominal dense tensor rates (PFLOP/s) used to carry the measured BF16 peak to other dtypes
@@ -295,13 +296,14 @@ def main():
     roof = None
     if ctc_n:
         achieved = flops / (ctc_ms / ctc_n / 1000.0) / 1e12
-        peak = tf32_sus / 3.0
-        roof = {"kernel": "chain_tc (3xTF32 factor chain, both sides, N=1M each)", "bound": "tensor",
+        peak = (bf16_sus if FAST_FORM.startswith(("fp16", "bf16")) else tf32_sus) / (3.0 if FAST_FORM.endswith("x3") else 1.0)
+        roof = {"kernel": f"chain_tc ({FAST_FORM} factor chain, both sides, N=1M each)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "flops_per_launch": flops, "avg_launch_ms": ctc_ms / ctc_n, "launches": ctc_n,
-                "peak_note": (f"TF32 dense = {peak_src} sustained BF16 {bf16_sus} x nominal 1.1/2.25, divided "
-                              "by 3 (three TF32 products per algorithmic product); achieved counts "
-                              "algorithmic flops 2n sum r_{i-1} r_i per point per side")}
+                "peak_note": (f"{peak_src} sustained BF16 {bf16_sus} TFLOP/s (FP16 runs at the BF16 rate; TF32 at "
+                              "x 1.1/2.25 nominal), divided by 3 for the split forms (three products per "
+                              "algorithmic product); achieved counts algorithmic flops 2n sum r_{i-1} r_i "
+                              "per point per side")}
     gt_ms, gt_n = prof.get("grid_tile", (0.0, 0))
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
     prof_total = sum(v[0] for v in prof.values())
@@ -331,7 +333,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (3xTF32 tensor) online / f64 offline",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (3xFP16 tensor, FP32 accumulate) online / f64 offline",
             "data": "synthetic (seeded uniform points and theta, the paper's recipe)",
             "config": {"workload": WORKLOAD, "fast_form": FAST_FORM, "tol": w.tol, "ranks": ranks,
                        "l2": "each stage's data exceeds L2 (3.4 GB grid, 1.4 GB factors); 256 MB flush before the grid and the builds"},

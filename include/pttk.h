@@ -71,7 +71,9 @@ typedef enum pttk_prec {
   PTTK_TF32 = 2,
   PTTK_TF32X3 = 3,
   PTTK_BF16 = 4,
-  PTTK_BF16X3 = 5
+  PTTK_BF16X3 = 5,
+  PTTK_FP16 = 6,
+  PTTK_FP16X3 = 7
 } pttk_prec;
 
 typedef struct pttk_tt pttk_tt; /* opaque: TT cores on the device plus their metadata */
@@ -175,8 +177,10 @@ pttk_status pttk_tt_check(const pttk_tt* tt, void* stream);
  *   expected inside their boxes (a point outside is extrapolated, not rejected).
  *   N_s, N_t >= 0 (0 is allowed and writes nothing for that side).
  *   U, M, V: dev outputs (double for PTTK_FP64, float otherwise).
- *   prec: PTTK_FP64 / PTTK_FP32 run the SIMT chain; PTTK_TF32, PTTK_TF32X3, PTTK_BF16 and
- *   PTTK_BF16X3 run the tensor-core chain (tcgen05, FP32 accumulation; TMEM accumulator of
+ *   prec: PTTK_FP64 / PTTK_FP32 run the SIMT chain; PTTK_TF32, PTTK_TF32X3, PTTK_BF16,
+ *   PTTK_BF16X3, PTTK_FP16 and PTTK_FP16X3 run the tensor-core chain (tcgen05, FP32
+ *   accumulation; the X3 forms split both operands into two parts and sum three products;
+ *   the FP16 forms scale operands by exact powers of two to stay in FP16 range; TMEM accumulator of
  *   128 points x N_pad columns), which needs every TT rank it touches <= 256 and, on first
  *   use of a form with a handle, lays out that form's core images on the device
  *   (synchronising `stream` once). Check pttk_tt_check after tensor-core calls. */

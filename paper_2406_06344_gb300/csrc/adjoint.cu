@@ -389,7 +389,7 @@ extern "C" pttk_status pttk_grad(const pttk_tt* tt, const double* theta, const v
   if (!tt || !theta) return set_error(PTTK_EINVAL, "NULL argument");
   if (N_s < 0 || N_t < 0) return set_error(PTTK_EINVAL, "negative point count");
   if ((N_s > 0 && (!X || !w)) || (N_t > 0 && (!Y || !z))) return set_error(PTTK_EINVAL, "NULL point or weight buffer");
-  if (prec < PTTK_FP64 || prec > PTTK_BF16X3) return set_error(PTTK_EINVAL, "unknown precision");
+  if (prec < PTTK_FP64 || prec > PTTK_FP16X3) return set_error(PTTK_EINVAL, "unknown precision");
   for (int j = 0; j < tt->dtheta; ++j) {
     const double lo = tt->box[tt->d + j][0], hi = tt->box[tt->d + j][1];
     if (!(theta[j] >= lo - 1e-12 * (hi - lo) && theta[j] <= hi + 1e-12 * (hi - lo)))

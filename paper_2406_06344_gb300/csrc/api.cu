@@ -422,7 +422,7 @@ pttk_status pttk_theta_core(const pttk_tt* tt, const double* theta, pttk_prec pr
                             void* stream) {
   clear_error();
   if (!tt || !M) return set_error(PTTK_EINVAL, "NULL argument");
-  if (prec < PTTK_FP64 || prec > PTTK_BF16X3) return set_error(PTTK_EINVAL, "unknown precision");
+  if (prec < PTTK_FP64 || prec > PTTK_FP16X3) return set_error(PTTK_EINVAL, "unknown precision");
   double th[PTTK_MAX_D];
   PTTK_TRY(theta_hat(tt, theta, th));
   return theta_core_run(tt, th, prec == PTTK_FP64, M, as_stream(stream));
@@ -435,7 +435,7 @@ pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void*
   if (!tt || !M) return set_error(PTTK_EINVAL, "NULL argument");
   if (N_s < 0 || N_t < 0) return set_error(PTTK_EINVAL, "negative point count");
   if ((N_s > 0 && (!X || !U)) || (N_t > 0 && (!Y || !V))) return set_error(PTTK_EINVAL, "NULL point or factor buffer");
-  if (prec < PTTK_FP64 || prec > PTTK_BF16X3) return set_error(PTTK_EINVAL, "unknown precision");
+  if (prec < PTTK_FP64 || prec > PTTK_FP16X3) return set_error(PTTK_EINVAL, "unknown precision");
   double th[PTTK_MAX_D];
   PTTK_TRY(theta_hat(tt, theta, th));
   cudaStream_t s = as_stream(stream);

@@ -108,7 +108,7 @@ struct pttk_batch {
 using namespace pttk;
 
 static bool tc_form(pttk_prec p) {
-  return p == PTTK_TF32 || p == PTTK_TF32X3 || p == PTTK_BF16 || p == PTTK_BF16X3;
+  return p >= PTTK_TF32 && p <= PTTK_FP16X3;
 }
 
 extern "C" {
@@ -120,7 +120,7 @@ pttk_status pttk_batch_create(const pttk_tt* tt, int B, const int64_t* xoff, con
   *out = nullptr;
   if (!tt || !xoff || !yoff) return set_error(PTTK_EINVAL, "NULL argument");
   if (B < 1) return set_error(PTTK_EINVAL, "B must be >= 1");
-  if (prec < PTTK_FP64 || prec > PTTK_BF16X3) return set_error(PTTK_EINVAL, "unknown precision");
+  if (prec < PTTK_FP64 || prec > PTTK_FP16X3) return set_error(PTTK_EINVAL, "unknown precision");
   if (xoff[0] != 0 || yoff[0] != 0) return set_error(PTTK_EINVAL, "offsets must start at 0");
   for (int b = 0; b < B; ++b)
     if (xoff[b + 1] < xoff[b] || yoff[b + 1] < yoff[b]) return set_error(PTTK_EINVAL, "offsets must not decrease");

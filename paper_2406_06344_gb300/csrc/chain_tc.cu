@@ -18,8 +18,15 @@
 //   TF32   kind::tf32, operands rounded to TF32 (10-bit mantissa);
 //   TF32X3 a = a_hi + a_lo, b = b_hi + b_lo (each TF32), D += a_hi b_hi + a_hi b_lo + a_lo b_hi;
 //   BF16   kind::f16 with BF16 operands (7-bit mantissa);
-//   BF16X3 the same split with BF16 parts.
-// Core images are split from the FP64 cores; A is split after its FP32 product.
+//   BF16X3 the same split with BF16 parts;
+//   FP16   kind::f16 with FP16 operands (10-bit mantissa, like TF32, at half the bytes);
+//   FP16X3 the same split with FP16 parts.
+// Core images are split from the FP64 cores; A is split after its FP32 product. FP16 has a
+// narrow exponent range, so the FP16 forms scale by exact powers of two: each core image so
+// that its largest entry is <= 2^14, and each step's A operand (folded into the basis values)
+// by an a-priori bound on |S_in| (|S_out| <= max|S_in| times the largest column 1-norm of
+// the core, since |T_j| <= 1); the FP32 accumulator is unscaled when read back. Small
+// entries then lose only what lies below 2^-24 of 2^14, far under the form's rounding.
 //
 // Shared-memory operand layout (UMMA "no swizzle" K-major): 16-byte units, a core matrix is
 // 8 rows x 16 bytes stored contiguously (128 B). Chunk of KCB bytes of K per row (64 or 128,
@@ -31,11 +38,14 @@
 // status word, stops issuing work, waits (bounded) for its outstanding copies and MMAs, frees
 // its TMEM and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 #include <stdio.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "pttk_internal.cuh"
 
@@ -73,17 +83,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the completion of the phase with the given parity; gives up after ~2 s or
-// as soon as another thread of the CTA has raised the abort flag.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
-  for (uint32_t i = 0; i < (1u << 24); ++i) {
+// Bounded wait for the completion of the phase with the given parity: gives up after ~2 s
+// (2^32 SM clocks, or 2^30 polls) or as soon as another thread of the CTA has raised the
+// abort flag. try_wait itself suspends the thread for a while in hardware, so the loop polls
+// without sleeping in software: a software sleep adds its own wake-up delay to every hand-off.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
+  const long long t0 = clock64();
+  for (uint32_t i = 0; i < (1u << 30); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (i >= 32) {
-      if (*abort_flag) return false;
-      __nanosleep(128);
-    }
+    if ((i & 15) == 15 && (*abort_flag || clock64() - t0 > (4ll << 30))) return false;
   }
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
+  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, abort_flag);
 }
 __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -148,6 +161,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 16 consecutive TMEM columns of this warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -168,7 +195,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Instruction descriptor: FP32 accumulator, A/B format (TF32 = 2, BF16 = 1), K-major A and B.
+// Instruction descriptor: FP32 accumulator, A/B format (kind::tf32: TF32 = 2; kind::f16: FP16 = 0,
+// BF16 = 1), K-major A and B.
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, int M, int N) {
   return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
@@ -179,6 +207,8 @@ struct TcStep {
   const uint8_t* img_lo;  // same, or null for single-product forms
   int nchunks, R_in, R_in_pad, R_out, Npad, coord;
   float lo, hi;           // box of the coordinate
+  float a_scale;          // power of two applied to the A operand (folded into the basis)
+  float out_scale;        // power of two that unscales the accumulator
 };
 // One launch builds both factors: work item i < T0 is tile i of the source points (side 0),
 // item i >= T0 is tile i - T0 of the target points (side 1). Factor rows depend only on their
@@ -196,28 +226,34 @@ struct TcArgs {
   uint32_t b_slot_bytes;  // bytes reserved per B part per slot
 };
 
-constexpr int NGEN_WARPS = 8;              // A generators (2 threads per point row)
-constexpr int TC_THREADS = 64 + 32 * NGEN_WARPS;  // warp 0: TMA, warp 1: MMA, warps 2..9: A
-constexpr int STAGE_LD = 33;               // epilogue staging row stride (floats)
+constexpr int NGEN_WARPS = 16;             // A generators: NPART threads per point row
+constexpr int NPART = NGEN_WARPS / 4;      // generator warps per TMEM lane quarter
+constexpr int TC_THREADS = 64 + 32 * NGEN_WARPS;  // warp 0: TMA, warp 1: MMA, warps 2..17: A
+constexpr int STAGE_COLS = 16;             // epilogue staging: 32 rows x 16 columns per warp
+constexpr int STAGE_LD = STAGE_COLS + 1;   // its row stride (floats; odd: no bank conflicts)
 
 // Launch configurations: bytes of K per row per chunk (KCB) and operand ring depth (NS).
-template <bool BF16, bool SPLIT, int KCB_, int NS>
+// Operand formats of the tensor-core forms.
+constexpr int FMT_TF32 = 0, FMT_BF16 = 1, FMT_FP16 = 2;
+__host__ __device__ constexpr uint32_t fmt_code(int fmt) { return fmt == FMT_TF32 ? 2u : fmt == FMT_BF16 ? 1u : 0u; }
+
+template <int FMT, bool SPLIT, int KCB_, int NS>
 struct Cfg {
   static constexpr int KCB = KCB_;
   static constexpr int NSLOT = NS;
   static constexpr int PARTS = SPLIT ? 2 : 1;             // hi (and lo) operand parts
-  static constexpr int E = BF16 ? 8 : 4;                  // elements per 16-byte unit
+  static constexpr int E = FMT == FMT_TF32 ? 4 : 8;       // elements per 16-byte unit
   static constexpr int UNITS = KCB / 16;                  // units per row per chunk
-  static constexpr int KC = KCB / (BF16 ? 2 : 4);         // K elements per chunk
+  static constexpr int KC = KCB / (FMT == FMT_TF32 ? 4 : 2);  // K elements per chunk
   static constexpr uint32_t SBO = 8 * KCB;                // 8-row group stride
   static constexpr uint32_t A_PART = TILE_M * KCB;
   static constexpr int KSTEPS = KCB / 32;                 // MMAs (per product) per chunk
 };
 
 // 16-byte unit of the generated A operand from E consecutive S values times one basis value.
-template <bool BF16, bool SPLIT>
+template <int FMT, bool SPLIT>
 __device__ __forceinline__ void write_unit(float b, const float* sv, uint8_t* hi, uint8_t* lo) {
-  if constexpr (!BF16) {
+  if constexpr (FMT == FMT_TF32) {
     const float4 x = *reinterpret_cast<const float4*>(sv);
     const float v[4] = {b * x.x, b * x.y, b * x.z, b * x.w};
     float h[4], l[4];
@@ -228,7 +264,7 @@ __device__ __forceinline__ void write_unit(float b, const float* sv, uint8_t* hi
     }
     *reinterpret_cast<float4*>(hi) = make_float4(h[0], h[1], h[2], h[3]);
     if (SPLIT) *reinterpret_cast<float4*>(lo) = make_float4(l[0], l[1], l[2], l[3]);
-  } else {
+  } else if constexpr (FMT == FMT_BF16) {
     const float4 x0 = *reinterpret_cast<const float4*>(sv);
     const float4 x1 = *reinterpret_cast<const float4*>(sv + 4);
     const float v[8] = {b * x0.x, b * x0.y, b * x0.z, b * x0.w, b * x1.x, b * x1.y, b * x1.z, b * x1.w};
@@ -243,10 +279,25 @@ __device__ __forceinline__ void write_unit(float b, const float* sv, uint8_t* hi
     }
     *reinterpret_cast<uint4*>(hi) = *reinterpret_cast<uint4*>(h);
     if (SPLIT) *reinterpret_cast<uint4*>(lo) = *reinterpret_cast<uint4*>(l);
+  } else {
+    const float4 x0 = *reinterpret_cast<const float4*>(sv);
+    const float4 x1 = *reinterpret_cast<const float4*>(sv + 4);
+    const float v[8] = {b * x0.x, b * x0.y, b * x0.z, b * x0.w, b * x1.x, b * x1.y, b * x1.z, b * x1.w};
+    __half2 h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      h[e] = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+      if (SPLIT) {
+        const float2 hf = __half22float2(h[e]);
+        l[e] = __floats2half2_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+      }
+    }
+    *reinterpret_cast<uint4*>(hi) = *reinterpret_cast<uint4*>(h);
+    if (SPLIT) *reinterpret_cast<uint4*>(lo) = *reinterpret_cast<uint4*>(l);
   }
 }
 
-__device__ __forceinline__ void gen_barrier() {  // the 256 generator threads only
+__device__ __forceinline__ void gen_barrier() {  // the generator threads only
   asm volatile("bar.sync 1, %0;" ::"n"(32 * NGEN_WARPS) : "memory");
 }
 
@@ -257,18 +308,19 @@ struct StepS {
   uint32_t bytes;   // bytes of one chunk part (Npad x KCB)
   uint32_t idesc;
   int nchunks, R_in_pad, R_out, Npad, coord;
-  float lo_box, hi_box;
+  float lo_box, hi_box, a_scale, out_scale;
 };
 
 // Warp-specialised factor chain over both sides. Warp 0 (one lane) loads the core chunks with
-// TMA into an NSLOT-deep ring; warp 1 (one lane) issues the MMAs; warps 2..9 generate the A
-// chunks (two threads per point row, each writing half of the row's units) and run the
+// TMA into an NSLOT-deep ring; warp 1 (one lane) issues the MMAs; warps 2..17 generate the A
+// chunks (NPART = 4 threads per point row, each writing a quarter of the row's units: enough
+// warps per scheduler to hide the shared-memory latency of the generation) and run the
 // epilogues. Barriers per slot: full_a (8 generator warps arrive), full_b (TMA transaction
 // bytes), empty (tcgen05.commit of the slot's MMAs); acc_ready is committed after each step's
 // last chunk.
-template <bool BF16, bool SPLIT, int KCB_, int NS>
+template <int FMT, bool SPLIT, int KCB_, int NS>
 __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
-  using C = Cfg<BF16, SPLIT, KCB_, NS>;
+  using C = Cfg<FMT, SPLIT, KCB_, NS>;
   constexpr int NSLOT = C::NSLOT;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int bv_ld = (a.n + 1) | 1;                                   // odd row stride > n
@@ -305,7 +357,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     v.hi = st.img_hi;
     v.lo = st.img_lo;
     v.bytes = (uint32_t)st.Npad * C::KCB;
-    v.idesc = instr_desc(BF16 ? 1u : 2u, TILE_M, st.Npad);
+    v.idesc = instr_desc(fmt_code(FMT), TILE_M, st.Npad);
     v.nchunks = st.nchunks;
     v.R_in_pad = st.R_in_pad;
     v.R_out = st.R_out;
@@ -313,6 +365,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     v.coord = st.coord;
     v.lo_box = st.lo;
     v.hi_box = st.hi;
+    v.a_scale = st.a_scale;
+    v.out_scale = st.out_scale;
     steps[sd * 3 + si] = v;
   }
   if (warp == 1) {
@@ -378,7 +432,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
             for (int k = 0; k < C::KSTEPS; ++k) {
               const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
               const uint64_t ah = smem_desc2(sa + k * 256, C::SBO), bh = smem_desc2(sb + k * 256, C::SBO);
-              if constexpr (BF16) {
+              if constexpr (FMT != FMT_TF32) {
                 umma_f16(tmem, ah, bh, st.idesc, acc);
                 if (SPLIT) {
                   umma_f16(tmem, ah, smem_desc2(sb + a.b_slot_bytes + k * 256, C::SBO), st.idesc, 1u);
@@ -409,20 +463,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     // ---------------- generator warps: A chunks and epilogues ----------------
     // Every generator thread runs the same sequence of named barriers whatever happens: a wait
     // that gives up only marks the warp dead (warp-uniform), after which its work is skipped.
-    const int gw = warp - 2;                   // 0..7
+    const int gw = warp - 2;                   // 0..NGEN_WARPS-1
     const int row = 32 * (warp & 3) + lane;    // TMEM lane quarter of this warp
-    const int half = gw >> 2;                  // which half of the row's units
+    const int part = gw >> 2;                  // which part of the row's units
     uint32_t g = 0, steps_done = 0;
     bool dead = false;
-    // basis of step si of side sd into Bv buffer `buf` (threads of half 0; zero from index n on)
+    // basis of step si of side sd into Bv buffer `buf` (threads of part 0; zero from index n on)
     auto basis = [&](int sd, int si, int buf, float x) {
       const StepS& st = steps[sd * 3 + si];
       const float xh = (2.f * x - st.lo_box - st.hi_box) / (st.lo_box - st.hi_box);
       float* bv = Bv + ((size_t)buf * TILE_M + row) * bv_ld;
+      const float sc = st.a_scale;
       float t0 = 1.f, t1 = xh;
-      bv[0] = 1.f;
+      bv[0] = sc;
       for (int k = 1; k < a.n; ++k) {
-        bv[k] = t1;
+        bv[k] = t1 * sc;
         const float t2 = 2.f * xh * t1 - t0;
         t0 = t1;
         t1 = t2;
@@ -436,7 +491,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
       return gp < a.N[sd] ? a.pts[sd][gp * a.d + st.coord] : st.lo_box;
     };
     float xn[3] = {0.f, 0.f, 0.f};  // coordinates of this row for the next tile to build
-    if (half == 0 && blockIdx.x < ntiles) {
+    if (part == 0 && blockIdx.x < ntiles) {
       for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
       basis(blockIdx.x >= a.T0 ? 1 : 0, 0, 0, xn[0]);
     }
@@ -447,9 +502,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
       const int rows = (int)std::min<int64_t>(TILE_M, a.N[sd] - row0);
       float xcur[3] = {xn[0], xn[1], xn[2]};
       const int64_t itn = it + gridDim.x;  // next item: prefetch its coordinates
-      if (half == 0 && itn < ntiles)
+      if (part == 0 && itn < ntiles)
         for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
-      if (half == 0) {
+      if (part == 0) {
         float4* s4 = reinterpret_cast<float4*>(S + (size_t)row * a.ld_s);
         s4[0] = make_float4(1.f, 0.f, 0.f, 0.f);  // S_0 = 1 (r_0 = 1), zero padding
         s4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -468,14 +523,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
           if (!dead) {
             uint8_t* ah = a_base + (size_t)slot * C::PARTS * C::A_PART;
             const uint32_t row_off = (uint32_t)(row >> 3) * C::SBO + (uint32_t)(row & 7) * 16;
-            constexpr int UH = C::UNITS / 2;  // units of this thread
-            const int k = c * C::KC + half * UH * C::E;
+            constexpr int UH = C::UNITS / NPART;  // units of this thread
+            static_assert(C::UNITS % NPART == 0, "units per chunk row must split evenly");
+            const int k = c * C::KC + part * UH * C::E;
             int j = k / st.R_in_pad;
             int ai = k - j * st.R_in_pad;
 #pragma unroll
             for (int u = 0; u < UH; ++u) {
-              const uint32_t off = row_off + (uint32_t)(half * UH + u) * 128;
-              write_unit<BF16, SPLIT>(bvrow[j < a.n ? j : a.n], srow + ai, ah + off, ah + C::A_PART + off);
+              const uint32_t off = row_off + (uint32_t)(part * UH + u) * 128;
+              write_unit<FMT, SPLIT>(bvrow[j < a.n ? j : a.n], srow + ai, ah + off, ah + C::A_PART + off);
               ai += C::E;
               if (ai == st.R_in_pad) {
                 ai = 0;
@@ -490,7 +546,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
         // the next basis (next step, or step 0 of the next item) goes to the other buffer
         // while this step's MMAs drain
         const bool last = si == nsteps - 1;
-        if (half == 0) {
+        if (part == 0) {
           if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
           else if (itn < ntiles) basis(itn >= a.T0 ? 1 : 0, 0, bufsel ^ 1, xn[0]);
         }
@@ -503,33 +559,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
         tc_fence_after();
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
         if (!last) {
-          // S for the next step: columns [0, Npad) (zero beyond R_out); this thread's half of
+          // S for the next step: columns [0, Npad) (zero beyond R_out); this thread's share of
           // the 32-column blocks
           if (!dead)
-            for (int cb = 32 * half; cb < st.Npad; cb += 64) {
+            for (int cb = 32 * part; cb < st.Npad; cb += 32 * NPART) {
               float v[32];
               tmem_ld32(lane_addr + (uint32_t)cb, v);
               float* dst = S + (size_t)row * a.ld_s + cb;
+              const float osc = st.out_scale;
 #pragma unroll
               for (int i = 0; i < 32; i += 4)
                 if (cb + i < a.ld_s)
-                  *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                  *reinterpret_cast<float4*>(dst + i) =
+                      make_float4(v[i] * osc, v[i + 1] * osc, v[i + 2] * osc, v[i + 3] * osc);
             }
         } else if (!dead) {
-          // output rows: each warp stages 32 rows x 32 columns, then writes row segments
+          // output rows: each warp stages 32 rows x 16 columns, then writes two row segments
+          // of 16 columns per store instruction
           float* stg = stage + (size_t)gw * 32 * STAGE_LD;
           const int R = st.R_out;
           float* outbase = a.out[sd] + (row0 + 32 * (warp & 3)) * R;
           const int wrows = std::max(0, std::min(32, rows - 32 * (warp & 3)));
-          for (int cb = 32 * half; cb < st.Npad; cb += 64) {
-            float v[32];
-            tmem_ld32(lane_addr + (uint32_t)cb, v);
+          const int sub = lane >> 4, lc = lane & 15;
+          for (int cb = STAGE_COLS * part; cb < st.Npad; cb += STAGE_COLS * NPART) {
+            float v[STAGE_COLS];
+            tmem_ld16(lane_addr + (uint32_t)cb, v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) stg[lane * STAGE_LD + i] = v[i];
+            for (int i = 0; i < STAGE_COLS; ++i) stg[lane * STAGE_LD + i] = v[i] * st.out_scale;
             __syncwarp();
-            const int col = cb + lane;
+            const int col = cb + lc;
             if (col < R)
-              for (int rr = 0; rr < wrows; ++rr) outbase[(int64_t)rr * R + col] = stg[rr * STAGE_LD + lane];
+              for (int rr = sub; rr < wrows; rr += 2) outbase[(int64_t)rr * R + col] = stg[rr * STAGE_LD + lc];
             __syncwarp();
           }
         }
@@ -553,12 +613,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
 // Image of the oriented core (K x R_out, column-major, FP64; K = n R_in) for one chain step in
 // the padded K order k' = a + R_in_pad j (zero rows for a >= R_in): chunk c holds rows o < Npad
 // and K'-elements [c KC, (c+1) KC) in the K-major no-swizzle layout (row group stride 8 KCB).
-template <bool BF16>
+template <int FMT>
 __global__ void core_image_kernel(const double* __restrict__ G, int n, int R_in, int R_in_pad, int R_out,
-                                  int Npad, int nchunks, int KCB, bool split, uint8_t* __restrict__ hi,
-                                  uint8_t* __restrict__ lo) {
-  constexpr int E = BF16 ? 8 : 4;
-  const int KC = KCB / (BF16 ? 2 : 4);
+                                  int Npad, int nchunks, int KCB, bool split, double scale,
+                                  uint8_t* __restrict__ hi, uint8_t* __restrict__ lo) {
+  constexpr int E = FMT == FMT_TF32 ? 4 : 8;
+  const int KC = KCB / (FMT == FMT_TF32 ? 4 : 2);
   const int K = n * R_in;
   const int64_t total = (int64_t)nchunks * Npad * KC;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -568,13 +628,17 @@ __global__ void core_image_kernel(const double* __restrict__ G, int n, int R_in,
     const int c = (int)(e / ((int64_t)KC * Npad));
     const int kp = c * KC + kk;
     const int j = kp / R_in_pad, ai = kp - j * R_in_pad;
-    const double v = (ai < R_in && j < n && o < R_out) ? G[(ai + R_in * j) + (int64_t)K * o] : 0.0;
+    const double v = (ai < R_in && j < n && o < R_out) ? scale * G[(ai + R_in * j) + (int64_t)K * o] : 0.0;
     const size_t off = (size_t)c * Npad * KCB + (size_t)(o >> 3) * (8 * KCB) + (size_t)(kk / E) * 128 +
                        (size_t)(o & 7) * 16;
-    if constexpr (BF16) {
+    if constexpr (FMT == FMT_BF16) {
       const __nv_bfloat16 h = __double2bfloat16(v);
       reinterpret_cast<__nv_bfloat16*>(hi + off)[kk % E] = h;
       if (split) reinterpret_cast<__nv_bfloat16*>(lo + off)[kk % E] = __double2bfloat16(v - (double)__bfloat162float(h));
+    } else if constexpr (FMT == FMT_FP16) {
+      const __half h = __double2half(v);
+      reinterpret_cast<__half*>(hi + off)[kk % E] = h;
+      if (split) reinterpret_cast<__half*>(lo + off)[kk % E] = __double2half(v - (double)__half2float(h));
     } else {
       const float h = to_tf32((float)v);
       reinterpret_cast<float*>(hi + off)[kk % E] = h;
@@ -587,6 +651,7 @@ struct Images {
   uint8_t* buf = nullptr;
   size_t hi_off[2][3] = {}, lo_off[2][3] = {};
   int Npad[2][3] = {}, nchunks[2][3] = {}, R_in_pad[2][3] = {};
+  float a_scale[2][3] = {}, out_scale[2][3] = {};
 };
 
 std::mutex g_img_mu;
@@ -595,7 +660,7 @@ std::mutex g_img_mu;
 
 // Per-handle image cache, indexed by form and chunk width (64 or 128 bytes of K per row).
 struct TcImageCache {
-  Images img[4][2];
+  Images img[6][2];
 };
 
 static int form_index(pttk_prec p) {
@@ -604,6 +669,8 @@ static int form_index(pttk_prec p) {
     case PTTK_TF32X3: return 1;
     case PTTK_BF16: return 2;
     case PTTK_BF16X3: return 3;
+    case PTTK_FP16: return 4;
+    case PTTK_FP16X3: return 5;
     default: return -1;
   }
 }
@@ -617,11 +684,56 @@ void tc_cache_free(TcImageCache* c) {
   delete c;
 }
 
+static int form_fmt(pttk_prec p) {
+  return (p == PTTK_BF16 || p == PTTK_BF16X3) ? FMT_BF16 : (p == PTTK_FP16 || p == PTTK_FP16X3) ? FMT_FP16 : FMT_TF32;
+}
+static bool form_split(pttk_prec p) { return p == PTTK_TF32X3 || p == PTTK_BF16X3 || p == PTTK_FP16X3; }
+
+// Power-of-two scales of the FP16 forms (1 for the others): per chain step, the image scale
+// 2^sB with max|G| 2^sB <= 2^14 and the A scale 2^sA with bound(|S_in|) 2^sA <= 2^14, where
+// bound(S_in of step 0) = 1 and bound(S_out) = bound(S_in) * max over columns of sum |G|.
+static pttk_status step_scales(const pttk_tt* tt, pttk_prec prec, Images& im, double img_scale[2][3]) {
+  for (int side = 0; side < 2; ++side) {
+    double bound = 1.0;
+    for (int i = 0; i < tt->d; ++i) {
+      img_scale[side][i] = 1.0;
+      im.a_scale[side][i] = 1.f;
+      im.out_scale[side][i] = 1.f;
+      if (form_fmt(prec) != FMT_FP16) continue;
+      int rin, rout, coord;
+      const int k = oriented_core_dims(tt, side == 0, i, &rin, &rout, &coord);
+      const int64_t K = (int64_t)tt->n * rin;
+      std::vector<double> G((size_t)(K * rout));
+      PTTK_CUDA(cudaMemcpy(G.data(), oriented_core_ptr(tt, side == 0, k, true), sizeof(double) * G.size(),
+                           cudaMemcpyDeviceToHost));
+      double gmax = 0.0, colmax = 0.0;
+      for (int o = 0; o < rout; ++o) {
+        double cs = 0.0;
+        for (int64_t q = 0; q < K; ++q) {
+          const double g = fabs(G[(size_t)(q + K * o)]);
+          gmax = std::max(gmax, g);
+          cs += g;
+        }
+        colmax = std::max(colmax, cs);
+      }
+      const int sB = gmax > 0.0 ? 14 - (int)ceil(log2(gmax)) : 0;
+      const int sA = bound > 0.0 ? 14 - (int)ceil(log2(bound)) : 0;
+      img_scale[side][i] = ldexp(1.0, sB);
+      im.a_scale[side][i] = (float)ldexp(1.0, sA);
+      im.out_scale[side][i] = (float)ldexp(1.0, -(sA + sB));
+      bound *= std::max(colmax, 1e-300);
+    }
+  }
+  return PTTK_OK;
+}
+
 static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, int KCB, Images& im, cudaStream_t s) {
-  const bool bf16 = prec == PTTK_BF16 || prec == PTTK_BF16X3;
-  const bool split = prec == PTTK_TF32X3 || prec == PTTK_BF16X3;
-  const int KC = KCB / (bf16 ? 2 : 4);
-  const int E = bf16 ? 8 : 4;
+  const int fmt = form_fmt(prec);
+  const bool split = form_split(prec);
+  const int KC = KCB / (fmt == FMT_TF32 ? 4 : 2);
+  const int E = fmt == FMT_TF32 ? 4 : 8;
+  double img_scale[2][3];
+  PTTK_TRY(step_scales(tt, prec, im, img_scale));
   size_t total = 0;
   for (int side = 0; side < 2; ++side)
     for (int i = 0; i < tt->d; ++i) {
@@ -645,9 +757,11 @@ static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, int KCB, Imag
       const double* G = static_cast<const double*>(oriented_core_ptr(tt, side == 0, k, true));
       const int64_t work = (int64_t)im.nchunks[side][i] * im.Npad[side][i] * KC;
       const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count() * 8);
-      auto* kfn = bf16 ? core_image_kernel<true> : core_image_kernel<false>;
+      auto* kfn = fmt == FMT_BF16 ? core_image_kernel<FMT_BF16>
+                                  : fmt == FMT_FP16 ? core_image_kernel<FMT_FP16> : core_image_kernel<FMT_TF32>;
       kfn<<<blocks, 256, 0, s>>>(G, tt->n, rin, im.R_in_pad[side][i], rout, im.Npad[side][i], im.nchunks[side][i],
-                                 KCB, split, im.buf + im.hi_off[side][i], im.buf + im.lo_off[side][i]); pttk::count_launch();
+                                 KCB, split, img_scale[side][i], im.buf + im.hi_off[side][i],
+                                 im.buf + im.lo_off[side][i]); pttk::count_launch();
     }
   PTTK_CUDA(cudaGetLastError());
   PTTK_CUDA(cudaStreamSynchronize(s));
@@ -656,12 +770,12 @@ static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, int KCB, Imag
 
 // Launch configurations per form: {KCB, NSLOT}. Configuration 0 is the default.
 static const int kTcConfigs[2][2] = {{128, 4}, {64, 4}};
-static const int kTcConfigsSplit[2][2] = {{64, 4}, {128, 2}};
+static const int kTcConfigsSplit[2][2] = {{128, 2}, {64, 4}};
 
 int tc_config_count() { return 2; }
 
 static void tc_config(pttk_prec prec, int cfg, int* KCB, int* NS) {
-  const bool split = prec == PTTK_TF32X3 || prec == PTTK_BF16X3;
+  const bool split = form_split(prec);
   const int (*t)[2] = split ? kTcConfigsSplit : kTcConfigs;
   cfg = (cfg < 0 || cfg > 1) ? 0 : cfg;
   *KCB = t[cfg][0];
@@ -680,9 +794,9 @@ pttk_status tc_prepare(const pttk_tt* tt, TcImageCache* cache, pttk_prec prec, i
   return PTTK_OK;
 }
 
-template <bool BF16, bool SPLIT, int KCB, int NS>
+template <int FMT, bool SPLIT, int KCB, int NS>
 static pttk_status launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
-  auto kfn = chain_tc_kernel<BF16, SPLIT, KCB, NS>;
+  auto kfn = chain_tc_kernel<FMT, SPLIT, KCB, NS>;
   PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned grid = (unsigned)std::min<int64_t>(a.ntiles, sm_count());
   kfn<<<grid, TC_THREADS, smem, s>>>(a); pttk::count_launch();
@@ -700,8 +814,8 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
   int KCB, NS;
   tc_config(prec, cfg, &KCB, &NS);
   const Images& im = cache->img[fi][KCB == 64 ? 0 : 1];
-  const bool bf16 = prec == PTTK_BF16 || prec == PTTK_BF16X3;
-  const bool split = prec == PTTK_TF32X3 || prec == PTTK_BF16X3;
+  const int fmt = form_fmt(prec);
+  const bool split = form_split(prec);
   TcArgs a{};
   a.nsteps = tt->d;
   a.n = tt->n;
@@ -732,6 +846,8 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
       const int bj = side == 0 ? coord : tt->d + tt->dtheta + coord;
       st.lo = (float)tt->box[bj][0];
       st.hi = (float)tt->box[bj][1];
+      st.a_scale = im.a_scale[side][i];
+      st.out_scale = im.out_scale[side][i];
       npad_max = std::max(npad_max, st.Npad);
       // S must hold every R_in_pad (read) and, for non-last steps, Npad columns (written)
       spad_max = std::max(spad_max, st.R_in_pad);
@@ -739,7 +855,7 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
     }
   if (npad_max > 256) return set_error(PTTK_ENOTSUP, "tensor-core chain: a rank above 256");
   // row stride of S: a multiple of 4 floats, = 4 (mod 32) so float4 rows fall in distinct banks;
-  // it also holds the last step's 8 x 32 x 33 staging floats
+  // it also holds the last step's NGEN_WARPS x 32 x STAGE_LD staging floats
   int ld_s = ((spad_max + 31) / 32) * 32 + 4;
   while ((size_t)TILE_M * ld_s < (size_t)NGEN_WARPS * 32 * STAGE_LD) ld_s += 32;
   a.ld_s = ld_s;
@@ -755,12 +871,14 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
   if (smem > 227 * 1024) return set_error(PTTK_ENOTSUP, "tensor-core chain: ranks too large for shared memory");
   const size_t smem_req = std::max<size_t>(smem, 116 * 1024);  // one CTA (one TMEM allocation) per SM
   PTTK_PROF("chain_tc", s);
-  if (bf16) {
-    if (split) return KCB == 64 ? launch_tc<true, true, 64, 4>(a, smem_req, s) : launch_tc<true, true, 128, 2>(a, smem_req, s);
-    return KCB == 128 ? launch_tc<true, false, 128, 4>(a, smem_req, s) : launch_tc<true, false, 64, 4>(a, smem_req, s);
-  }
-  if (split) return KCB == 64 ? launch_tc<false, true, 64, 4>(a, smem_req, s) : launch_tc<false, true, 128, 2>(a, smem_req, s);
-  return KCB == 128 ? launch_tc<false, false, 128, 4>(a, smem_req, s) : launch_tc<false, false, 64, 4>(a, smem_req, s);
+  // configurations: split forms {128, 2} and {64, 4}; single forms {128, 4} and {64, 4}
+#define PTTK_TC_LAUNCH(F)                                                                        \
+  if (split) return KCB == 64 ? launch_tc<F, true, 64, 4>(a, smem_req, s) : launch_tc<F, true, 128, 2>(a, smem_req, s); \
+  return KCB == 128 ? launch_tc<F, false, 128, 4>(a, smem_req, s) : launch_tc<F, false, 64, 4>(a, smem_req, s);
+  if (fmt == FMT_BF16) { PTTK_TC_LAUNCH(FMT_BF16) }
+  if (fmt == FMT_FP16) { PTTK_TC_LAUNCH(FMT_FP16) }
+  PTTK_TC_LAUNCH(FMT_TF32)
+#undef PTTK_TC_LAUNCH
 }
 
 }  // namespace pttk

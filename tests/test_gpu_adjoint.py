@@ -74,7 +74,7 @@ def test_grad_fp64_matches_oracle_and_fd(env, name, n):
     assert float(np.sum(dX.cpu().numpy() * v)) == pytest.approx((Lp - Lm) / (2 * h), rel=1e-6, abs=1e-9)
 
 
-@pytest.mark.parametrize("form", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("form", ["fp32", "tf32x3", "fp16x3"])
 @pytest.mark.parametrize("name,n", CASES)
 def test_grad_fp32_forms(env, form, name, n):
     torch, P = env

@@ -12,7 +12,8 @@ from paper_2406_06344_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 3e-5, "tf32": 2e-3, "bf16": 2e-2}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-5, "fp16x3": 1e-5, "bf16x3": 3e-5, "tf32": 2e-3, "fp16": 2e-3,
+       "bf16": 2e-2}
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +38,7 @@ def _instances(w, sizes_s, sizes_t, seed=0):
     return X.reshape(-1, w.d), Y.reshape(-1, w.d), th, xoff, yoff
 
 
-@pytest.mark.parametrize("form", ["fp64", "fp32", "tf32x3", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("form", ["fp64", "fp32", "tf32x3", "fp16x3", "bf16x3", "tf32", "fp16", "bf16"])
 def test_batched_matches_oracle_per_instance(env, form):
     torch, P, w, tt, gc = env
     sizes_s = [300, 1, 0, 129, 777, 64, 2000, 5]

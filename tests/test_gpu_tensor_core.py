@@ -1,9 +1,11 @@
 """Tensor-core (tcgen05) factor chain against the FP64 oracle's chain on the same cores.
 
 Tolerances (relative Frobenius error of U, V and of K~ = U M V^T):
-  TF32X3 / BF16X3  1e-5 and 3e-5: the split forms carry ~22 / ~16 mantissa bits per operand,
-                   and the 1e-5 FP32 target is claimed for TF32X3;
-  TF32 / BF16      2e-3 / 2e-2: single-product forms, 10 / 7 mantissa bits per operand.
+  TF32X3 / FP16X3 / BF16X3  1e-5, 1e-5 and 3e-5: the split forms carry ~22 / ~22 / ~16
+                            mantissa bits per operand, and the 1e-5 FP32 target is claimed
+                            for TF32X3 and FP16X3;
+  TF32 / FP16 / BF16        2e-3 / 2e-3 / 2e-2: single-product forms, 10 / 10 / 7 mantissa
+                            bits per operand.
 """
 import dataclasses
 
@@ -15,7 +17,7 @@ from paper_2406_06344_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"tf32x3": 1e-5, "bf16x3": 3e-5, "tf32": 2e-3, "bf16": 2e-2}
+TOL = {"tf32x3": 1e-5, "fp16x3": 1e-5, "bf16x3": 3e-5, "tf32": 2e-3, "fp16": 2e-3, "bf16": 2e-2}
 
 
 @pytest.fixture(scope="module")
@@ -58,7 +60,7 @@ def _run(env, w, form, ns, nt, th_index=0):
     return U.double().cpu().numpy(), M.double().cpu().numpy(), V.double().cpu().numpy(), Uo, Mo, Vo
 
 
-@pytest.mark.parametrize("form", ["tf32", "tf32x3", "bf16", "bf16x3"])
+@pytest.mark.parametrize("form", ["tf32", "tf32x3", "bf16", "bf16x3", "fp16", "fp16x3"])
 @pytest.mark.parametrize("name,n", [("c1", None), ("c2", None), ("c3", 6)])
 def test_tensor_core_chain_matches_oracle(env, form, name, n):
     w = _case(name, n)
@@ -90,3 +92,30 @@ def test_tensor_core_repeated_calls_are_identical(env):
     tt.check()
     for a, b in zip(r1, r2):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("form", ["fp16", "fp16x3"])
+@pytest.mark.parametrize("scales", [(1e6, 1.0), (1.0, 1e-7), (1e-5, 1e5)])
+def test_fp16_forms_keep_range_by_scaling(env, form, scales):
+    """FP16 overflows at 65504 and loses precision below 6e-5: cores scaled far outside that
+    range (source chain by scales[0], target chain by scales[1]) must give the same relative
+    accuracy, because the FP16 forms scale operands by powers of two."""
+    torch, P = env
+    w = _case("c2")
+    base = tt_for(P, w).cores()
+    cores = [G.copy() for G in base]
+    cores[0] *= scales[0]             # first core: the source chain and H
+    cores[-1] *= scales[1]            # last core: the target chain
+    tt = P.TT.from_cores(w.kernel, w.d, w.src_box, w.tgt_box, w.dtheta, w.theta_box, w.n, cores)
+    X = torch.tensor(W.sources(w, 2000), device="cuda", dtype=torch.float32)
+    Y = torch.tensor(W.targets(w, 1500), device="cuda", dtype=torch.float32)
+    th = W.thetas(w, 1)[0]
+    U, M, V = P.instantiate(tt, th, X, Y, form)
+    tt.check()
+    Uo, Mo, Vo = o.instantiate(cores, w.d, w.dtheta, w.mode_boxes(), th, X.double().cpu().numpy(),
+                               Y.double().cpu().numpy())
+    Uh, Vh = U.double().cpu().numpy(), V.double().cpu().numpy()
+    assert np.isfinite(Uh).all() and np.isfinite(Vh).all()
+    assert o.rel_fro(Uo, Uh) <= TOL[form]
+    assert o.rel_fro(Vo, Vh) <= TOL[form]
+    tt.free()
