@@ -323,9 +323,10 @@ __global__ void iota_kernel(int* __restrict__ p, int64_t n) {
 }
 
 // ---------------- one-sided Jacobi (Hestenes) with round-robin pairing -----------------
-// One launch per round; each warp rotates one column pair (a, b) of A (rows x ncols,
-// column-major) and, if V is given, the same pair of V (nv x ncols) so that the pair becomes
-// orthogonal. Rotation (Rutishauser): zeta = (beta - alpha) / (2 gamma),
+// All sweeps of one call run in a single cooperative launch with one block per SM. Round r of
+// a sweep pairs the columns (a, b) of the round-robin tournament on p = ncols (+1 if odd)
+// players; each warp rotates one pair at a time, and the rounds are separated by a grid
+// barrier. Rotation (Rutishauser): zeta = (beta - alpha) / (2 gamma),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t,
 // [a, b] <- [c a - s b, s a + c b].
 // colsq[] holds every column's squared norm (refreshed for the two columns of each
@@ -336,76 +337,129 @@ __global__ void iota_kernel(int* __restrict__ p, int64_t n) {
 // small2 = (1e-3 delta)^2 / q and count2 = (1e-2 delta)^2 / q the columns left unsettled carry
 // < 1e-4 delta^2 in total, so they change neither the kept subspace nor, except within that
 // margin of the threshold, the truncation rank.
-__global__ void __launch_bounds__(256) jacobi_round_kernel(double* __restrict__ A, int64_t rows,
-                                                           int ncols, double* __restrict__ V,
-                                                           int64_t nv, int p, int round,
-                                                           double tol, double small2,
-                                                           double count2,
-                                                           double* __restrict__ colsq,
-                                                           unsigned* __restrict__ counter) {
-  const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+// Columns and norms written by other blocks in earlier rounds are read through L2 (ld.cg),
+// never from a possibly stale L1 line.
+constexpr int JB = 256;            // threads per block
+constexpr int JMAX_SWEEPS = 60;
+
+struct JacobiSync {                // device state of one call (zeroed before the launch)
+  alignas(128) unsigned count;     // grid-barrier arrivals
+  alignas(128) unsigned gen;       // grid-barrier generation (polled: its own line)
+  alignas(128) int err;            // a barrier wait gave up
+  int sweeps;                      // sweeps run; JMAX_SWEEPS + 1 if not converged
+  unsigned rot[JMAX_SWEEPS];       // counted rotations per sweep
+};
+
+// Bounded grid barrier (the launch is cooperative, so every block is resident): gives up
+// after ~2 s (2^32 SM clocks) or once another block has given up; returns false then.
+__device__ bool grid_barrier(JacobiSync* js, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &js->gen;
+    volatile int* verr = &js->err;
+    const unsigned gen = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&js->count, 1u) == nblocks - 1) {
+      atomicExch(&js->count, 0u);
+      __threadfence();
+      atomicAdd(&js->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        __nanosleep(32);
+        if (*verr) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > (4ll << 30)) {
+          atomicExch(&js->err, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok && !*verr;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(JB) jacobi_kernel(double* __restrict__ A, int64_t rows, int ncols,
+                                                    int p, double tol, double small2, double count2,
+                                                    double* __restrict__ colsq,
+                                                    JacobiSync* __restrict__ js) {
+  const unsigned nb = gridDim.x;
+  const int npairs = p / 2;
   const int lane = threadIdx.x & 31;
-  if (gw >= p / 2) return;
-  int a, b;
-  if (gw == 0) {
-    a = p - 1;
-    b = round;
-  } else {
-    a = (round + gw) % (p - 1);
-    b = (round - gw + (p - 1)) % (p - 1);
-  }
-  if (a > b) {
-    const int t = a;
-    a = b;
-    b = t;
-  }
-  if (b >= ncols) return;  // dummy player when ncols is odd
-  if (colsq[a] < small2 && colsq[b] < small2) return;
-  double* ca = A + (int64_t)a * rows;
-  double* cb = A + (int64_t)b * rows;
-  double al = 0.0, be = 0.0, ga = 0.0;
-  for (int64_t i = lane; i < rows; i += 32) {
-    const double x = ca[i], y = cb[i];
-    al = fma(x, x, al);
-    be = fma(y, y, be);
-    ga = fma(x, y, ga);
-  }
-  al = warp_sum(al);
-  be = warp_sum(be);
-  ga = warp_sum(ga);
-  if (!(al > 0.0) || !(be > 0.0) || !(fabs(ga) > tol * sqrt(al) * sqrt(be))) return;
-  const double zeta = (be - al) / (2.0 * ga);
-  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-  double na = 0.0, nb = 0.0;
-  for (int64_t i = lane; i < rows; i += 32) {
-    const double x = ca[i], y = cb[i];
-    const double xa = cs * x - sn * y, yb = sn * x + cs * y;
-    ca[i] = xa;
-    cb[i] = yb;
-    na = fma(xa, xa, na);
-    nb = fma(yb, yb, nb);
-  }
-  na = warp_sum(na);
-  nb = warp_sum(nb);
-  if (V) {
-    double* va = V + (int64_t)a * nv;
-    double* vb = V + (int64_t)b * nv;
-    for (int64_t i = lane; i < nv; i += 32) {
-      const double x = va[i], y = vb[i];
-      va[i] = cs * x - sn * y;
-      vb[i] = sn * x + cs * y;
+  const int gw0 = (int)(blockIdx.x * (JB / 32) + (threadIdx.x >> 5));
+  const int nwarps = (int)(nb * (JB / 32));
+  for (int sweep = 0; sweep < JMAX_SWEEPS; ++sweep) {
+    for (int r = 0; r < p - 1; ++r) {
+      for (int pr = gw0; pr < npairs; pr += nwarps) {
+        int a, b;
+        if (pr == 0) {
+          a = p - 1;
+          b = r;
+        } else {
+          a = (r + pr) % (p - 1);
+          b = (r - pr + (p - 1)) % (p - 1);
+        }
+        if (a > b) {
+          const int t = a;
+          a = b;
+          b = t;
+        }
+        if (b >= ncols) continue;  // dummy player when ncols is odd
+        if (__ldcg(colsq + a) < small2 && __ldcg(colsq + b) < small2) continue;
+        double* ca = A + (int64_t)a * rows;
+        double* cb = A + (int64_t)b * rows;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int64_t i = lane; i < rows; i += 32) {
+          const double x = __ldcg(ca + i), y = __ldcg(cb + i);
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (!(al > 0.0) || !(be > 0.0) || !(fabs(ga) > tol * sqrt(al) * sqrt(be))) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        double na = 0.0, nbb = 0.0;
+        for (int64_t i = lane; i < rows; i += 32) {
+          const double x = __ldcg(ca + i), y = __ldcg(cb + i);
+          const double xa = cs * x - sn * y, yb = sn * x + cs * y;
+          ca[i] = xa;
+          cb[i] = yb;
+          na = fma(xa, xa, na);
+          nbb = fma(yb, yb, nbb);
+        }
+        na = warp_sum(na);
+        nbb = warp_sum(nbb);
+        if (lane == 0) {
+          colsq[a] = na;
+          colsq[b] = nbb;
+          // the rotation counts toward convergence if it moved a column of squared norm
+          // >= count2 by more than rounding: column a changes by ~|t| ||b||, column b by ~|t| ||a||
+          const double move_a = al >= count2 ? fabs(t) * sqrt(be / al) : 0.0;
+          const double move_b = be >= count2 ? fabs(t) * sqrt(al / be) : 0.0;
+          if (fmax(move_a, move_b) > 4.0 * 2.220446049250313e-16) atomicAdd(&js->rot[sweep], 1u);
+        }
+      }
+      if (!grid_barrier(js, nb)) return;
+    }
+    // after the sweep's last barrier every block reads the same final count
+    if (*(volatile unsigned*)&js->rot[sweep] == 0) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) js->sweeps = sweep + 1;
+      return;
     }
   }
-  if (lane == 0) {
-    colsq[a] = na;
-    colsq[b] = nb;
-    // the rotation counts toward convergence if it moved a column of squared norm >= count2
-    // by more than rounding: column a changes by ~|t| ||b||, column b by ~|t| ||a||
-    const double move_a = al >= count2 ? fabs(t) * sqrt(be / al) : 0.0;
-    const double move_b = be >= count2 ? fabs(t) * sqrt(al / be) : 0.0;
-    if (fmax(move_a, move_b) > 4.0 * 2.220446049250313e-16) atomicAdd(counter, 1u);
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) js->sweeps = JMAX_SWEEPS + 1;
 }
 
 __global__ void colsq_init_kernel(const double* __restrict__ A, int64_t rows, int ncols,
@@ -420,11 +474,6 @@ __global__ void colsq_init_kernel(const double* __restrict__ A, int64_t rows, in
   if (lane == 0) colsq[gw] = acc;
 }
 
-__global__ void set_identity_kernel(double* __restrict__ V, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    V[e] = (e % n == e / n) ? 1.0 : 0.0;
-}
 
 // norms[c] = ||A[:, c]||_2, one warp per column
 __global__ void colnorm_kernel(const double* __restrict__ A, int64_t rows, int ncols,
@@ -606,13 +655,30 @@ pttk_status householder_qrcp(double* A, int64_t M, int64_t N, double stop2, doub
   return PTTK_OK;
 }
 
-// One-sided Jacobi on A (rows x ncols) accumulating V (nv x ncols). Synchronises `s` once
-// per sweep to read the rotation count.
-pttk_status jacobi(double* A, int64_t rows, int ncols, double* V, int64_t nv, unsigned* d_counter,
-                   cudaStream_t s, double small = 0.0) {
+static pttk_status launch_jacobi(double* A, int64_t rows, int ncols, int p, double tol, double small2,
+                                 double count2, double* colsq, JacobiSync* js, cudaStream_t s) {
+  int per_sm = 0;
+  PTTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JB, 0));
+  if (per_sm < 1) return set_error(PTTK_ECUDA, "Jacobi kernel cannot be resident");
+  // one block (8 warps, 8 pairs at a time) per SM, fewer when there are fewer pairs
+  const int want = (p / 2 + JB / 32 - 1) / (JB / 32);
+  const unsigned grid = (unsigned)std::max(1, std::min(want, sm_count()));
+  void* args[] = {&A, &rows, &ncols, &p, &tol, &small2, &count2, &colsq, &js};
+  PTTK_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(JB), args, 0, s));
+  pttk::count_launch();
+  return PTTK_OK;
+}
+
+// One-sided Jacobi on the columns of A (rows x ncols), all sweeps in one cooperative launch;
+// synchronises `s` once to read the outcome.
+pttk_status jacobi(double* A, int64_t rows, int ncols, cudaStream_t s, double small = 0.0) {
   if (ncols < 2) return PTTK_OK;
-  Buf colsq;
+  Buf colsq, state;
   PTTK_TRY(colsq.alloc(ncols));
+  PTTK_TRY(state.alloc((sizeof(JacobiSync) + sizeof(double) - 1) / sizeof(double)));
+  static_assert(alignof(JacobiSync) <= 256, "cudaMalloc alignment");
+  JacobiSync* js = reinterpret_cast<JacobiSync*>(state.p);
+  PTTK_CUDA(cudaMemsetAsync(js, 0, sizeof(JacobiSync), s));
   colsq_init_kernel<<<(unsigned)(((int64_t)ncols * 32 + 255) / 256), 256, 0, s>>>(A, rows, ncols, colsq.p); pttk::count_launch();
   const double small2 = small * small;
   const double count2 = 100.0 * small2;
@@ -621,24 +687,20 @@ pttk_status jacobi(double* A, int64_t rows, int ncols, double* V, int64_t nv, un
   // level of a computed dot product. The singular subspaces are then accurate to that level,
   // which the 1e-12 parity of K~ needs (a looser rows * eps stops ~20x earlier in accuracy).
   const double tol = sqrt((double)std::max<int64_t>(rows, 16)) * 2.220446049250313e-16;
-  const unsigned blocks = (unsigned)((p / 2 * 32 + 255) / 256);
-  static const bool verbose = getenv("PTTK_VERBOSE") != nullptr;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    PTTK_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s));
-    for (int r = 0; r < p - 1; ++r)
-    {
-      PTTK_PROF("jacobi_round", s);
-      jacobi_round_kernel<<<blocks, 256, 0, s>>>(A, rows, ncols, V, nv, p, r, tol, small2, count2,
-                                                 colsq.p, d_counter); pttk::count_launch();
-    }
-    PTTK_CUDA(cudaGetLastError());
-    unsigned h = 0;
-    PTTK_CUDA(cudaMemcpyAsync(&h, d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    PTTK_CUDA(cudaStreamSynchronize(s));
-    if (verbose) fprintf(stderr, "pttk: jacobi %lld x %d sweep %d rotations %u\n", (long long)rows, ncols, sweep, h);
-    if (h == 0) return PTTK_OK;
+  {
+    PTTK_PROF("jacobi", s);
+    PTTK_TRY(launch_jacobi(A, rows, ncols, p, tol, small2, count2, colsq.p, js, s));
   }
-  return set_error(PTTK_ECUDA, "one-sided Jacobi SVD did not converge in 60 sweeps");
+  JacobiSync h{};
+  PTTK_CUDA(cudaMemcpyAsync(&h, js, sizeof(JacobiSync), cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  static const bool verbose = getenv("PTTK_VERBOSE") != nullptr;
+  if (verbose)
+    for (int sw = 0; sw < std::min(h.sweeps, JMAX_SWEEPS); ++sw)
+      fprintf(stderr, "pttk: jacobi %lld x %d sweep %d rotations %u\n", (long long)rows, ncols, sw, h.rot[sw]);
+  if (h.err) return set_error(PTTK_ETIMEOUT, "one-sided Jacobi: a grid barrier timed out");
+  if (h.sweeps > JMAX_SWEEPS) return set_error(PTTK_ECUDA, "one-sided Jacobi SVD did not converge in 60 sweeps");
+  return PTTK_OK;
 }
 
 // Sorted order of sigma (descending) and the truncation rank for threshold delta.
@@ -718,14 +780,12 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   Buf Xn, R, wpart, wv, below;
   PTTK_TRY(Xn.alloc(total));
   int* d_perm = nullptr;
-  unsigned* d_counter = nullptr;
   HHState* d_hs = nullptr;
-  PTTK_CUDA(cudaMalloc(&d_counter, sizeof(unsigned)));
   PTTK_CUDA(cudaMalloc(&d_hs, sizeof(HHState)));
   struct Guard {
-    int*& a; unsigned*& b; HHState*& c;
-    ~Guard() { if (a) cudaFree(a); if (b) cudaFree(b); if (c) cudaFree(c); }
-  } guard{d_perm, d_counter, d_hs};
+    int*& a; HHState*& c;
+    ~Guard() { if (a) cudaFree(a); if (c) cudaFree(c); }
+  } guard{d_perm, d_hs};
 
   std::vector<Buf> cores(D);
   tt->ranks[0] = 1;
@@ -780,7 +840,7 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
     // vectors of R1 (= of the pivoted QR input, up to the discarded R22) are the normalised
     // columns of the rotated R1^T; columns below 1e-3 delta / sqrt(kq) together carry
     // < 1e-6 delta^2, and pairs of them are skipped
-    PTTK_TRY(jacobi(A.p, q, kq, nullptr, 0, d_counter, s, 1e-3 * delta / sqrt((double)kq)));
+    PTTK_TRY(jacobi(A.p, q, kq, s, 1e-3 * delta / sqrt((double)kq)));
     clk.mark(k, "jacobi");
     colnorm_kernel<<<(unsigned)(((int64_t)kq * 32 + 255) / 256), 256, 0, s>>>(A.p, q, kq, norms.p); pttk::count_launch();
     std::vector<double> sigma(kq);
@@ -809,7 +869,7 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
     // make the m x r basis orthonormal to working precision: its columns are orthogonal up
     // to ~eps ||X|| / sigma_i, so one-sided Jacobi needs one or two sweeps
     clk.mark(k, "basis");
-    PTTK_TRY(jacobi(basis, m, r, nullptr, 0, d_counter, s));
+    PTTK_TRY(jacobi(basis, m, r, s));
     clk.mark(k, "reorth");
     {
       Buf bn;
