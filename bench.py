@@ -49,6 +49,9 @@ WORKLOAD = "d3 matern-nu n12 (12^8 grid), N_s=N_t=1M, 256 theta"
 NOMINAL = {"bf16": 2.25, "tf32": 1.1}
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12   # FFMA lanes/SM x 2 x SMs x max clock
 FP64_PEAK_TFLOPS = 1.25                             # nominal FP64 rate of the part
+# DRAM bytes (read + write) of one chain_tc launch of the fast form on this workload, from the
+# ncu capture summarised in profiles/chain_tc_fp16x3_c3_online.md (None for other forms)
+NCU_TRAFFIC = {"fp16x3": 27.414016e6 + 1.372644e9}
 
 
 def parse():
@@ -298,7 +301,9 @@ def main():
         achieved = flops / (ctc_ms / ctc_n / 1000.0) / 1e12
         peak = (bf16_sus if FAST_FORM.startswith(("fp16", "bf16")) else tf32_sus) / (3.0 if FAST_FORM.endswith("x3") else 1.0)
         roof = {"kernel": f"chain_tc ({FAST_FORM} factor chain, both sides, N=1M each)", "bound": "tensor",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get(FAST_FORM), "traffic_unit": "bytes per launch (ncu dram read+write)",
+                "algorithmic_bytes": float(N * 4 * (w.d + ranks[w.d]) + N * 4 * (w.d + ranks[w.d + w.dtheta])),
                 "flops_per_launch": flops, "avg_launch_ms": ctc_ms / ctc_n, "launches": ctc_n,
                 "peak_note": (f"{peak_src} sustained BF16 {bf16_sus} TFLOP/s (FP16 runs at the BF16 rate; TF32 at "
                               "x 1.1/2.25 nominal), divided by 3 for the split forms (three products per "
