@@ -314,7 +314,7 @@ def main():
     prof_total = sum(v[0] for v in prof.values())
     roof_dominant = {"kernel": dom[0], "ms_total": dom[1][0], "launches": dom[1][1],
                      "share_of_timed_kernel_time": dom[1][0] / max(prof_total, 1e-9),
-                     "bound": "alu (FP64)" if dom[0] in ("jacobi_round", "householder", "dgemm") else None,
+                     "bound": "alu (FP64)" if dom[0] in ("jacobi", "householder", "dgemm", "grid_tile") else "tensor",
                      "note": "the FP64 TT-SVD of the offline stage dominates the step; see the kernel_ms split"}
     roof_grid = {"fp64_entries_per_s": total * args.steps * world / (g64_ms / 1000.0),
                  "fp32_entries_per_s": total * args.steps * world / (g32_ms / 1000.0),
