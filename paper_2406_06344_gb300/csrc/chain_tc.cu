@@ -216,6 +216,10 @@ struct TcStep {
 struct TcArgs {
   TcStep st[2][3];
   int nsteps, n, d;
+  // S of the first step: 1 (s0_coord < 0) or the basis vector T(xhat) of coordinate s0_coord
+  // on [s0_lo, s0_hi] (the first two chain steps merged into one)
+  int s0_coord[2];
+  float s0_lo[2], s0_hi[2];
   int64_t N[2];
   int64_t T0, ntiles;
   const float* pts[2];
@@ -490,9 +494,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
       const StepS& st = steps[sd * 3 + si];
       return gp < a.N[sd] ? a.pts[sd][gp * a.d + st.coord] : st.lo_box;
     };
-    float xn[3] = {0.f, 0.f, 0.f};  // coordinates of this row for the next tile to build
+    // coordinate of the seed basis (merged first steps) of this row in item `it`
+    auto seed_coord_of = [&](int64_t it) -> float {
+      const int sd = it >= a.T0 ? 1 : 0;
+      const int64_t gp = (sd ? it - a.T0 : it) * TILE_M + row;
+      return (a.s0_coord[sd] >= 0 && gp < a.N[sd]) ? a.pts[sd][gp * a.d + a.s0_coord[sd]] : a.s0_lo[sd];
+    };
+    // coordinates of this row for the next tile to build; xn[3]: the seed coordinate
+    float xn[4] = {0.f, 0.f, 0.f, 0.f};
     if (part == 0 && blockIdx.x < ntiles) {
       for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
+      xn[3] = seed_coord_of(blockIdx.x);
       basis(blockIdx.x >= a.T0 ? 1 : 0, 0, 0, xn[0]);
     }
     uint32_t bufsel = 0;
@@ -501,13 +513,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
       const int64_t row0 = (sd ? it - a.T0 : it) * TILE_M;
       const int rows = (int)std::min<int64_t>(TILE_M, a.N[sd] - row0);
       float xcur[3] = {xn[0], xn[1], xn[2]};
+      const float xseed = xn[3];
       const int64_t itn = it + gridDim.x;  // next item: prefetch its coordinates
-      if (part == 0 && itn < ntiles)
+      if (part == 0 && itn < ntiles) {
         for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
+        xn[3] = seed_coord_of(itn);
+      }
       if (part == 0) {
-        float4* s4 = reinterpret_cast<float4*>(S + (size_t)row * a.ld_s);
-        s4[0] = make_float4(1.f, 0.f, 0.f, 0.f);  // S_0 = 1 (r_0 = 1), zero padding
-        s4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float* srow_w = S + (size_t)row * a.ld_s;
+        const int pad = steps[sd * 3].R_in_pad;
+        if (a.s0_coord[sd] >= 0) {
+          // S of the merged first step: T_0..T_{n-1}(xhat) of the seed coordinate, zero padding
+          const float lo = a.s0_lo[sd], hi = a.s0_hi[sd];
+          const float xh = (2.f * xseed - lo - hi) / (lo - hi);
+          float t0 = 1.f, t1 = xh;
+          srow_w[0] = 1.f;
+          for (int k = 1; k < pad; ++k) {
+            srow_w[k] = k < a.n ? t1 : 0.f;
+            const float t2 = 2.f * xh * t1 - t0;
+            t0 = t1;
+            t1 = t2;
+          }
+        } else {
+          srow_w[0] = 1.f;  // S_0 = 1 (r_0 = 1), zero padding
+          for (int k = 1; k < pad; ++k) srow_w[k] = 0.f;
+        }
       }
       gen_barrier();
       for (int si = 0; si < nsteps; ++si) {
@@ -661,6 +691,7 @@ std::mutex g_img_mu;
 // Per-handle image cache, indexed by form and chunk width (64 or 128 bytes of K per row).
 struct TcImageCache {
   Images img[6][2];
+  double* L[2] = {nullptr, nullptr};  // merged first two cores per side (see tc_chain_steps)
 };
 
 static int form_index(pttk_prec p) {
@@ -681,7 +712,78 @@ void tc_cache_free(TcImageCache* c) {
   for (auto& f : c->img)
     for (auto& im : f)
       if (im.buf) cudaFree(im.buf);
+  for (double* L : c->L)
+    if (L) cudaFree(L);
   delete c;
+}
+
+// Steps of the tensor-core chain on one side (0: source, 1: target). With d >= 2 the first two
+// steps of Algorithm 2, Phase 3 are merged: S_2 = (B_2 face-split B_1) L with
+// L[i + n (j + n b)] = sum_a G_1[i, a] G_2[a, j, b] (G_1, G_2 the first two oriented cores), one
+// chain step whose input S is the basis vector of the first coordinate (R_in = n). It has the
+// K and N of the second step, so it adds no MMA work, and each tile runs one step (one pipeline
+// drain and epilogue) fewer. Returns the step count; *s0_coord is the seed coordinate, or -1
+// when S starts as 1.
+struct TcChainStep {
+  int R_in, R_out, coord;
+  const double* G;  // FP64 oriented core (R_in x n x R_out, column-major) on the device
+};
+static int tc_chain_steps(const pttk_tt* tt, const TcImageCache* cache, int side, TcChainStep* st,
+                          int* s0_coord) {
+  const bool src = side == 0;
+  const bool merged = tt->d >= 2 && cache->L[side] != nullptr;
+  int nst = 0;
+  for (int i = merged ? 1 : 0; i < tt->d; ++i) {
+    int rin, rout, coord;
+    const int k = oriented_core_dims(tt, src, i, &rin, &rout, &coord);
+    TcChainStep c{rin, rout, coord, static_cast<const double*>(oriented_core_ptr(tt, src, k, true))};
+    if (merged && i == 1) {
+      c.R_in = tt->n;
+      c.G = cache->L[side];
+    }
+    st[nst++] = c;
+  }
+  *s0_coord = -1;
+  if (merged) {
+    int rin, rout, coord;
+    oriented_core_dims(tt, src, 0, &rin, &rout, &coord);
+    *s0_coord = coord;
+  }
+  return nst;
+}
+
+// The merged cores L of both sides, formed once per handle in FP64 on the host.
+static pttk_status ensure_merged(const pttk_tt* tt, TcImageCache* cache) {
+  if (tt->d < 2) return PTTK_OK;
+  const int n = tt->n;
+  for (int side = 0; side < 2; ++side) {
+    if (cache->L[side]) continue;
+    int r0in, r0, c0, r1in, r1, c1;
+    const int k0 = oriented_core_dims(tt, side == 0, 0, &r0in, &r0, &c0);
+    const int k1 = oriented_core_dims(tt, side == 0, 1, &r1in, &r1, &c1);
+    if (r0in != 1 || r1in != r0) return set_error(PTTK_ECUDA, "unexpected TT ranks at the chain ends");
+    std::vector<double> G0((size_t)n * r0), G1((size_t)r0 * n * r1), L((size_t)n * n * r1, 0.0);
+    PTTK_CUDA(cudaMemcpy(G0.data(), oriented_core_ptr(tt, side == 0, k0, true), sizeof(double) * G0.size(),
+                         cudaMemcpyDeviceToHost));
+    PTTK_CUDA(cudaMemcpy(G1.data(), oriented_core_ptr(tt, side == 0, k1, true), sizeof(double) * G1.size(),
+                         cudaMemcpyDeviceToHost));
+    for (int b = 0; b < r1; ++b)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          double acc = 0.0;
+          for (int a = 0; a < r0; ++a) acc += G0[(size_t)i + (size_t)n * a] * G1[(size_t)a + (size_t)r0 * (j + (size_t)n * b)];
+          L[(size_t)i + (size_t)n * (j + (size_t)n * b)] = acc;
+        }
+    double* dL = nullptr;
+    PTTK_CUDA(cudaMalloc(&dL, sizeof(double) * L.size()));
+    const cudaError_t e = cudaMemcpy(dL, L.data(), sizeof(double) * L.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(dL);
+      return cuda_error(e, "merged chain core");
+    }
+    cache->L[side] = dL;
+  }
+  return PTTK_OK;
 }
 
 static int form_fmt(pttk_prec p) {
@@ -692,20 +794,22 @@ static bool form_split(pttk_prec p) { return p == PTTK_TF32X3 || p == PTTK_BF16X
 // Power-of-two scales of the FP16 forms (1 for the others): per chain step, the image scale
 // 2^sB with max|G| 2^sB <= 2^14 and the A scale 2^sA with bound(|S_in|) 2^sA <= 2^14, where
 // bound(S_in of step 0) = 1 and bound(S_out) = bound(S_in) * max over columns of sum |G|.
-static pttk_status step_scales(const pttk_tt* tt, pttk_prec prec, Images& im, double img_scale[2][3]) {
+static pttk_status step_scales(const pttk_tt* tt, const TcImageCache* cache, pttk_prec prec, Images& im,
+                               double img_scale[2][3]) {
   for (int side = 0; side < 2; ++side) {
-    double bound = 1.0;
-    for (int i = 0; i < tt->d; ++i) {
+    double bound = 1.0;  // |S| of the first step: 1, or |T_j| <= 1 for a seed basis
+    TcChainStep cs[3];
+    int s0;
+    const int nst = tc_chain_steps(tt, cache, side, cs, &s0);
+    for (int i = 0; i < nst; ++i) {
       img_scale[side][i] = 1.0;
       im.a_scale[side][i] = 1.f;
       im.out_scale[side][i] = 1.f;
       if (form_fmt(prec) != FMT_FP16) continue;
-      int rin, rout, coord;
-      const int k = oriented_core_dims(tt, side == 0, i, &rin, &rout, &coord);
+      const int rin = cs[i].R_in, rout = cs[i].R_out;
       const int64_t K = (int64_t)tt->n * rin;
       std::vector<double> G((size_t)(K * rout));
-      PTTK_CUDA(cudaMemcpy(G.data(), oriented_core_ptr(tt, side == 0, k, true), sizeof(double) * G.size(),
-                           cudaMemcpyDeviceToHost));
+      PTTK_CUDA(cudaMemcpy(G.data(), cs[i].G, sizeof(double) * G.size(), cudaMemcpyDeviceToHost));
       double gmax = 0.0, colmax = 0.0;
       for (int o = 0; o < rout; ++o) {
         double cs = 0.0;
@@ -727,18 +831,21 @@ static pttk_status step_scales(const pttk_tt* tt, pttk_prec prec, Images& im, do
   return PTTK_OK;
 }
 
-static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, int KCB, Images& im, cudaStream_t s) {
+static pttk_status build_images(const pttk_tt* tt, const TcImageCache* cache, pttk_prec prec, int KCB,
+                                Images& im, cudaStream_t s) {
   const int fmt = form_fmt(prec);
   const bool split = form_split(prec);
   const int KC = KCB / (fmt == FMT_TF32 ? 4 : 2);
   const int E = fmt == FMT_TF32 ? 4 : 8;
   double img_scale[2][3];
-  PTTK_TRY(step_scales(tt, prec, im, img_scale));
+  PTTK_TRY(step_scales(tt, cache, prec, im, img_scale));
+  TcChainStep cs[2][3];
+  int s0[2], nst = 0;
+  for (int side = 0; side < 2; ++side) nst = tc_chain_steps(tt, cache, side, cs[side], &s0[side]);
   size_t total = 0;
   for (int side = 0; side < 2; ++side)
-    for (int i = 0; i < tt->d; ++i) {
-      int rin, rout, coord;
-      oriented_core_dims(tt, side == 0, i, &rin, &rout, &coord);
+    for (int i = 0; i < nst; ++i) {
+      const int rin = cs[side][i].R_in, rout = cs[side][i].R_out;
       im.R_in_pad[side][i] = ((rin + E - 1) / E) * E;
       im.Npad[side][i] = ((rout + 15) / 16) * 16;
       im.nchunks[side][i] = (tt->n * im.R_in_pad[side][i] + KC - 1) / KC;
@@ -751,10 +858,9 @@ static pttk_status build_images(const pttk_tt* tt, pttk_prec prec, int KCB, Imag
   PTTK_CUDA(cudaMalloc(&im.buf, std::max<size_t>(total, 16)));
   PTTK_CUDA(cudaMemsetAsync(im.buf, 0, std::max<size_t>(total, 16), s));
   for (int side = 0; side < 2; ++side)
-    for (int i = 0; i < tt->d; ++i) {
-      int rin, rout, coord;
-      const int k = oriented_core_dims(tt, side == 0, i, &rin, &rout, &coord);
-      const double* G = static_cast<const double*>(oriented_core_ptr(tt, side == 0, k, true));
+    for (int i = 0; i < nst; ++i) {
+      const int rin = cs[side][i].R_in, rout = cs[side][i].R_out;
+      const double* G = cs[side][i].G;
       const int64_t work = (int64_t)im.nchunks[side][i] * im.Npad[side][i] * KC;
       const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count() * 8);
       auto* kfn = fmt == FMT_BF16 ? core_image_kernel<FMT_BF16>
@@ -790,7 +896,8 @@ pttk_status tc_prepare(const pttk_tt* tt, TcImageCache* cache, pttk_prec prec, i
   tc_config(prec, cfg, &KCB, &NS);
   Images& im = cache->img[fi][KCB == 64 ? 0 : 1];
   std::lock_guard<std::mutex> lk(g_img_mu);
-  if (!im.buf) PTTK_TRY(build_images(tt, prec, KCB, im, s));
+  PTTK_TRY(ensure_merged(tt, cache));
+  if (!im.buf) PTTK_TRY(build_images(tt, cache, prec, KCB, im, s));
   return PTTK_OK;
 }
 
@@ -830,10 +937,16 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
   a.out[1] = V;
   a.status = d_status;
   int npad_max = 16, spad_max = 8;
-  for (int side = 0; side < 2; ++side)
-    for (int i = 0; i < tt->d; ++i) {
-      int rin, rout, coord;
-      oriented_core_dims(tt, side == 0, i, &rin, &rout, &coord);
+  for (int side = 0; side < 2; ++side) {
+    TcChainStep cs[3];
+    int s0;
+    a.nsteps = tc_chain_steps(tt, cache, side, cs, &s0);
+    a.s0_coord[side] = s0;
+    const int b0 = s0 < 0 ? 0 : (side == 0 ? s0 : tt->d + tt->dtheta + s0);
+    a.s0_lo[side] = (float)tt->box[b0][0];
+    a.s0_hi[side] = (float)tt->box[b0][1];
+    for (int i = 0; i < a.nsteps; ++i) {
+      const int rin = cs[i].R_in, rout = cs[i].R_out, coord = cs[i].coord;
       TcStep& st = a.st[side][i];
       st.img_hi = im.buf + im.hi_off[side][i];
       st.img_lo = split ? im.buf + im.lo_off[side][i] : nullptr;
@@ -851,8 +964,9 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
       npad_max = std::max(npad_max, st.Npad);
       // S must hold every R_in_pad (read) and, for non-last steps, Npad columns (written)
       spad_max = std::max(spad_max, st.R_in_pad);
-      if (i < tt->d - 1) spad_max = std::max(spad_max, st.Npad);
+      if (i < a.nsteps - 1) spad_max = std::max(spad_max, st.Npad);
     }
+  }
   if (npad_max > 256) return set_error(PTTK_ENOTSUP, "tensor-core chain: a rank above 256");
   // row stride of S: a multiple of 4 floats, = 4 (mod 32) so float4 rows fall in distinct banks;
   // it also holds the last step's NGEN_WARPS x 32 x STAGE_LD staging floats
