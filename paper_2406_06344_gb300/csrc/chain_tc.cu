@@ -226,6 +226,8 @@ struct TcArgs {
   float* out[2];
   int* status;
   int ld_s;               // row stride of S (floats, multiple of 4)
+  int ld_seed;            // row stride of the first step's input (floats, multiple of 4)
+  int acc1_col;           // TMEM column of the first step's accumulator when it has its own
   int tmem_cols;
   uint32_t b_slot_bytes;  // bytes reserved per B part per slot
 };
@@ -332,14 +334,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
   uint8_t* b_base = a_base + (size_t)NSLOT * C::PARTS * C::A_PART;    // NSLOT x PARTS x b_slot_bytes
   float* S = reinterpret_cast<float*>(b_base + (size_t)NSLOT * C::PARTS * a.b_slot_bytes);  // 128 x ld_s
   float* Bv = S + (size_t)TILE_M * a.ld_s;                           // 2 x 128 x bv_ld
+  float* Sseed = Bv + (size_t)2 * TILE_M * bv_ld;                     // 128 x ld_seed: step 0's input
   StepS* steps = reinterpret_cast<StepS*>(
-      (reinterpret_cast<uintptr_t>(Bv + (size_t)2 * TILE_M * bv_ld) + 15) & ~uintptr_t(15));  // [2][3]
+      (reinterpret_cast<uintptr_t>(Sseed + (size_t)TILE_M * a.ld_seed) + 15) & ~uintptr_t(15));  // [2][3]
   uint64_t* bars = reinterpret_cast<uint64_t*>(steps + 6);
   uint64_t* full_a = bars;
   uint64_t* full_b = bars + NSLOT;
   uint64_t* empty = bars + 2 * NSLOT;
-  uint64_t* acc_ready = bars + 3 * NSLOT;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * NSLOT + 1);
+  uint64_t* acc_ready = bars + 3 * NSLOT;  // [0]: accumulator 0, [1]: the first step's own
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * NSLOT + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* stage = S;  // epilogue staging of the last step aliases S (8 x 32 x STAGE_LD floats)
 
@@ -350,7 +353,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
       mbar_init(&full_b[i], 1);
       mbar_init(&empty[i], 1);
     }
-    mbar_init(acc_ready, 1);
+    mbar_init(&acc_ready[0], 1);
+    mbar_init(&acc_ready[1], 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -423,6 +427,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
         const int sd = it >= a.T0 ? 1 : 0;
         for (int si = 0; si < nsteps && ok; ++si) {
           const StepS st = steps[sd * 3 + si];
+          // the first step has its own accumulator when there are later steps
+          const int ab = (si == 0 && nsteps > 1) ? 1 : 0;
+          const uint32_t dacc = tmem + (ab ? (uint32_t)a.acc1_col : 0u);
           for (int c = 0; c < st.nchunks; ++c, ++g) {
             const uint32_t slot = g % NSLOT, par = (g / NSLOT) & 1;
             if (!mbar_wait(&full_a[slot], par, abort_flag) || !mbar_wait(&full_b[slot], par, abort_flag)) {
@@ -437,21 +444,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
               const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
               const uint64_t ah = smem_desc2(sa + k * 256, C::SBO), bh = smem_desc2(sb + k * 256, C::SBO);
               if constexpr (FMT != FMT_TF32) {
-                umma_f16(tmem, ah, bh, st.idesc, acc);
+                umma_f16(dacc, ah, bh, st.idesc, acc);
                 if (SPLIT) {
-                  umma_f16(tmem, ah, smem_desc2(sb + a.b_slot_bytes + k * 256, C::SBO), st.idesc, 1u);
-                  umma_f16(tmem, smem_desc2(sa + C::A_PART + k * 256, C::SBO), bh, st.idesc, 1u);
+                  umma_f16(dacc, ah, smem_desc2(sb + a.b_slot_bytes + k * 256, C::SBO), st.idesc, 1u);
+                  umma_f16(dacc, smem_desc2(sa + C::A_PART + k * 256, C::SBO), bh, st.idesc, 1u);
                 }
               } else {
-                umma_tf32(tmem, ah, bh, st.idesc, acc);
+                umma_tf32(dacc, ah, bh, st.idesc, acc);
                 if (SPLIT) {
-                  umma_tf32(tmem, ah, smem_desc2(sb + a.b_slot_bytes + k * 256, C::SBO), st.idesc, 1u);
-                  umma_tf32(tmem, smem_desc2(sa + C::A_PART + k * 256, C::SBO), bh, st.idesc, 1u);
+                  umma_tf32(dacc, ah, smem_desc2(sb + a.b_slot_bytes + k * 256, C::SBO), st.idesc, 1u);
+                  umma_tf32(dacc, smem_desc2(sa + C::A_PART + k * 256, C::SBO), bh, st.idesc, 1u);
                 }
               }
             }
             umma_commit(&empty[slot]);
-            if (c == st.nchunks - 1) umma_commit(acc_ready);
+            if (c == st.nchunks - 1) umma_commit(&acc_ready[ab]);
           }
         }
       }
@@ -470,7 +477,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     const int gw = warp - 2;                   // 0..NGEN_WARPS-1
     const int row = 32 * (warp & 3) + lane;    // TMEM lane quarter of this warp
     const int part = gw >> 2;                  // which part of the row's units
-    uint32_t g = 0, steps_done = 0;
+    uint32_t g = 0;
     bool dead = false;
     // basis of step si of side sd into Bv buffer `buf` (threads of part 0; zero from index n on)
     auto basis = [&](int sd, int si, int buf, float x) {
@@ -500,50 +507,92 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
       const int64_t gp = (sd ? it - a.T0 : it) * TILE_M + row;
       return (a.s0_coord[sd] >= 0 && gp < a.N[sd]) ? a.pts[sd][gp * a.d + a.s0_coord[sd]] : a.s0_lo[sd];
     };
+    // input of the first step for item `it` into Sseed (threads of part 0): the seed basis
+    // T_0..T_{n-1}(xhat) of the merged first steps, or S_0 = 1; zero padding
+    auto write_seed = [&](int64_t it, float x) {
+      const int sd = it >= a.T0 ? 1 : 0;
+      float* w = Sseed + (size_t)row * a.ld_seed;
+      const int pad = steps[sd * 3].R_in_pad;
+      if (a.s0_coord[sd] >= 0) {
+        const float lo = a.s0_lo[sd], hi = a.s0_hi[sd];
+        const float xh = (2.f * x - lo - hi) / (lo - hi);
+        float t0 = 1.f, t1 = xh;
+        w[0] = 1.f;
+        for (int k = 1; k < pad; ++k) {
+          w[k] = k < a.n ? t1 : 0.f;
+          const float t2 = 2.f * xh * t1 - t0;
+          t0 = t1;
+          t1 = t2;
+        }
+      } else {
+        w[0] = 1.f;
+        for (int k = 1; k < pad; ++k) w[k] = 0.f;
+      }
+    };
+    // output rows of the last step of item (osd, orow0, orows) from accumulator 0: each warp
+    // stages 32 rows x 16 columns, then writes two row segments of 16 columns per store
+    auto write_output = [&](int osd, int64_t orow0, int orows, uint32_t lane_addr) {
+      const StepS& st = steps[osd * 3 + nsteps - 1];
+      float* stg = stage + (size_t)gw * 32 * STAGE_LD;
+      const int R = st.R_out;
+      float* outbase = a.out[osd] + (orow0 + 32 * (warp & 3)) * R;
+      const int wrows = std::max(0, std::min(32, orows - 32 * (warp & 3)));
+      const int sub = lane >> 4, lc = lane & 15;
+      for (int cb = STAGE_COLS * part; cb < st.Npad; cb += STAGE_COLS * NPART) {
+        float v[STAGE_COLS];
+        tmem_ld16(lane_addr + (uint32_t)cb, v);
+#pragma unroll
+        for (int i = 0; i < STAGE_COLS; ++i) stg[lane * STAGE_LD + i] = v[i] * st.out_scale;
+        __syncwarp();
+        const int col = cb + lc;
+        if (col < R)
+          for (int rr = sub; rr < wrows; rr += 2) outbase[(int64_t)rr * R + col] = stg[rr * STAGE_LD + lc];
+        __syncwarp();
+      }
+    };
+    // Each accumulator barrier completes one phase per step that uses it; a waiter is never
+    // more than one phase behind, because the next step on that accumulator needs chunks that
+    // are generated only after the wait.
+    uint32_t done_acc[2] = {0u, 0u};
+    auto wait_acc = [&](int ab) {
+      if (!dead && !*abort_flag) dead = !mbar_wait(&acc_ready[ab], done_acc[ab] & 1, abort_flag);
+      ++done_acc[ab];
+      dead = __any_sync(0xffffffffu, dead || *abort_flag);
+      if (dead && lane == 0) *abort_flag = 1;
+      tc_fence_after();
+    };
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+    // With two or more steps the last step's output is written after the next item's first
+    // step has been generated: the tensor cores run that step (into its own accumulator)
+    // while the output leaves.
+    const bool defer = nsteps > 1;
     // coordinates of this row for the next tile to build; xn[3]: the seed coordinate
     float xn[4] = {0.f, 0.f, 0.f, 0.f};
     if (part == 0 && blockIdx.x < ntiles) {
       for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
       xn[3] = seed_coord_of(blockIdx.x);
       basis(blockIdx.x >= a.T0 ? 1 : 0, 0, 0, xn[0]);
+      write_seed(blockIdx.x, xn[3]);
     }
+    gen_barrier();
     uint32_t bufsel = 0;
+    bool out_pending = false;
+    int out_sd = 0, out_rows = 0;
+    int64_t out_row0 = 0;
     for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x) {
       const int sd = it >= a.T0 ? 1 : 0;
       const int64_t row0 = (sd ? it - a.T0 : it) * TILE_M;
       const int rows = (int)std::min<int64_t>(TILE_M, a.N[sd] - row0);
       float xcur[3] = {xn[0], xn[1], xn[2]};
-      const float xseed = xn[3];
       const int64_t itn = it + gridDim.x;  // next item: prefetch its coordinates
       if (part == 0 && itn < ntiles) {
         for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
         xn[3] = seed_coord_of(itn);
       }
-      if (part == 0) {
-        float* srow_w = S + (size_t)row * a.ld_s;
-        const int pad = steps[sd * 3].R_in_pad;
-        if (a.s0_coord[sd] >= 0) {
-          // S of the merged first step: T_0..T_{n-1}(xhat) of the seed coordinate, zero padding
-          const float lo = a.s0_lo[sd], hi = a.s0_hi[sd];
-          const float xh = (2.f * xseed - lo - hi) / (lo - hi);
-          float t0 = 1.f, t1 = xh;
-          srow_w[0] = 1.f;
-          for (int k = 1; k < pad; ++k) {
-            srow_w[k] = k < a.n ? t1 : 0.f;
-            const float t2 = 2.f * xh * t1 - t0;
-            t0 = t1;
-            t1 = t2;
-          }
-        } else {
-          srow_w[0] = 1.f;  // S_0 = 1 (r_0 = 1), zero padding
-          for (int k = 1; k < pad; ++k) srow_w[k] = 0.f;
-        }
-      }
-      gen_barrier();
       for (int si = 0; si < nsteps; ++si) {
         const StepS st = steps[sd * 3 + si];
         const float* bvrow = Bv + ((size_t)bufsel * TILE_M + row) * bv_ld;
-        const float* srow = S + (size_t)row * a.ld_s;
+        const float* srow = si == 0 ? Sseed + (size_t)row * a.ld_seed : S + (size_t)row * a.ld_s;
         for (int c = 0; c < st.nchunks; ++c, ++g) {
           const uint32_t slot = g % NSLOT, use = g / NSLOT;
           dead = dead || *abort_flag;
@@ -580,14 +629,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
           if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
           else if (itn < ntiles) basis(itn >= a.T0 ? 1 : 0, 0, bufsel ^ 1, xn[0]);
         }
+        if (si == 0 && out_pending) {
+          // the previous item's output, while this item's first step runs; its staging aliases
+          // S, which the epilogue below writes, hence the barrier
+          wait_acc(0);
+          if (!dead) write_output(out_sd, out_row0, out_rows, tmem + lanes);
+          out_pending = false;
+          gen_barrier();
+        }
+        if (last && defer && itn < ntiles) {
+          // this item's output is written during the next item's first step; the first
+          // step's input of the next item goes to Sseed (its last reader was step 0 of this
+          // item, finished before the barrier that ended step 0)
+          out_pending = true;
+          out_sd = sd;
+          out_row0 = row0;
+          out_rows = rows;
+          if (part == 0) write_seed(itn, xn[3]);
+          bufsel ^= 1;
+          tc_fence_before();
+          gen_barrier();
+          continue;
+        }
         // accumulator of this step is complete (all A chunks of the step, hence all reads of
-        // S for it, are done once it is)
-        if (!dead && !*abort_flag) dead = !mbar_wait(acc_ready, steps_done & 1, abort_flag);
-        ++steps_done;
-        dead = __any_sync(0xffffffffu, dead || *abort_flag);
-        if (dead && lane == 0) *abort_flag = 1;
-        tc_fence_after();
-        const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        // its input, are done once it is)
+        const int ab = (si == 0 && defer) ? 1 : 0;
+        wait_acc(ab);
+        const uint32_t lane_addr = tmem + lanes + (ab ? (uint32_t)a.acc1_col : 0u);
         if (!last) {
           // S for the next step: columns [0, Npad) (zero beyond R_out); this thread's share of
           // the 32-column blocks
@@ -604,28 +672,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
                       make_float4(v[i] * osc, v[i + 1] * osc, v[i + 2] * osc, v[i + 3] * osc);
             }
         } else if (!dead) {
-          // output rows: each warp stages 32 rows x 16 columns, then writes two row segments
-          // of 16 columns per store instruction
-          float* stg = stage + (size_t)gw * 32 * STAGE_LD;
-          const int R = st.R_out;
-          float* outbase = a.out[sd] + (row0 + 32 * (warp & 3)) * R;
-          const int wrows = std::max(0, std::min(32, rows - 32 * (warp & 3)));
-          const int sub = lane >> 4, lc = lane & 15;
-          for (int cb = STAGE_COLS * part; cb < st.Npad; cb += STAGE_COLS * NPART) {
-            float v[STAGE_COLS];
-            tmem_ld16(lane_addr + (uint32_t)cb, v);
-#pragma unroll
-            for (int i = 0; i < STAGE_COLS; ++i) stg[lane * STAGE_LD + i] = v[i] * st.out_scale;
-            __syncwarp();
-            const int col = cb + lc;
-            if (col < R)
-              for (int rr = sub; rr < wrows; rr += 2) outbase[(int64_t)rr * R + col] = stg[rr * STAGE_LD + lc];
-            __syncwarp();
-          }
+          write_output(sd, row0, rows, lane_addr);
         }
         bufsel ^= 1;
         tc_fence_before();
         gen_barrier();
+        if (last && !defer && itn < ntiles) {
+          // a single step: its input is read until the barrier above
+          if (part == 0) write_seed(itn, xn[3]);
+          gen_barrier();
+        }
       }
     }
     if (dead && lane == 0) {
@@ -973,15 +1029,31 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
   int ld_s = ((spad_max + 31) / 32) * 32 + 4;
   while ((size_t)TILE_M * ld_s < (size_t)NGEN_WARPS * 32 * STAGE_LD) ld_s += 32;
   a.ld_s = ld_s;
+  // the first step's input (Sseed) row stride: its padded width rounded to 8, plus 4, so the
+  // 16-byte reads of consecutive rows fall in distinct banks
+  int pad0 = 4, npad0 = 16, npad_rest = 16;
+  for (int side = 0; side < 2; ++side) {
+    pad0 = std::max(pad0, a.st[side][0].R_in_pad);
+    npad0 = std::max(npad0, a.st[side][0].Npad);
+    for (int i = 1; i < a.nsteps; ++i) npad_rest = std::max(npad_rest, a.st[side][i].Npad);
+  }
+  a.ld_seed = ((pad0 + 7) / 8) * 8 + 4;
+  // TMEM: accumulator 0 at column 0; with two or more steps the first step has its own
+  // accumulator after it, so that the next item's first step can run while the last step's
+  // accumulator is read out
+  a.acc1_col = a.nsteps > 1 ? ((npad_rest + 31) / 32) * 32 : 0;
+  const int tmem_need = a.nsteps > 1 ? a.acc1_col + npad0 : npad_max;
   int cols = 32;
-  while (cols < npad_max) cols <<= 1;
+  while (cols < tmem_need) cols <<= 1;
+  if (cols > 512) return set_error(PTTK_ENOTSUP, "tensor-core chain: accumulators exceed tensor memory");
   a.tmem_cols = cols;
   a.b_slot_bytes = (uint32_t)npad_max * KCB;
   const int bv_ld = (tt->n + 1) | 1;
   const size_t parts = split ? 2 : 1;
   const size_t smem = (size_t)NS * parts * TILE_M * KCB + (size_t)NS * parts * a.b_slot_bytes +
-                      sizeof(float) * ((size_t)TILE_M * a.ld_s + (size_t)2 * TILE_M * bv_ld) + 16 +
-                      sizeof(StepS) * 6 + 8 * (3 * NS + 1) + 16;
+                      sizeof(float) * ((size_t)TILE_M * a.ld_s + (size_t)2 * TILE_M * bv_ld +
+                                       (size_t)TILE_M * a.ld_seed) + 16 +
+                      sizeof(StepS) * 6 + 8 * (3 * NS + 2) + 16;
   if (smem > 227 * 1024) return set_error(PTTK_ENOTSUP, "tensor-core chain: ranks too large for shared memory");
   const size_t smem_req = std::max<size_t>(smem, 116 * 1024);  // one CTA (one TMEM allocation) per SM
   PTTK_PROF("chain_tc", s);
