@@ -50,9 +50,9 @@ NOMINAL = {"bf16": 2.25, "tf32": 1.1}
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12   # FFMA lanes/SM x 2 x SMs x max clock
 FP64_PEAK_TFLOPS = 1.25                             # nominal FP64 rate of the part
 # DRAM bytes (read + write) of one chain_tc launch of the fast form on this workload, from the
-# ncu capture summarised in profiles/chain_tc_fp16x3_c3_online.md; empty while the kernel has
-# changed since that capture
-NCU_TRAFFIC = {}
+# ncu capture summarised in profiles/chain_tc_fp16x3_c3_online.md (to be emptied whenever the
+# kernel changes after that capture)
+NCU_TRAFFIC = {"fp16x3": 26.541056e6 + 1.373002e9}
 
 
 def parse():
