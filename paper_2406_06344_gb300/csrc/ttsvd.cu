@@ -824,11 +824,13 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
     PTTK_TRY(below.alloc(q));
     PTTK_TRY(R.alloc(q * q));
     clk.mark(k, "layout");
-    // rows of R kept: the QR stops once the discarded block has ||R22||_F <= 1e-3 delta, so
-    // it changes the tails below by at most 1e-6 delta^2 (and is counted in them)
+    // rows of R kept: the QR stops once the discarded block has ||R22||_F <= 0.03 delta. The
+    // tails below count ||R22||^2, so the error bound of the truncation holds as it is; only a
+    // tail within 9e-4 delta^2 of the threshold could give a rank one higher than the exact
+    // singular values would
     int kq = 0;
     double tail2 = 0.0;
-    const double stop = 1e-3 * delta;
+    const double stop = 0.03 * delta;
     PTTK_TRY(householder_qrcp(qrin.p, Mqr, q, stop * stop, R.p, d_perm, part.p, below.p, wpart.p, wv.p, d_hs,
                               &kq, &tail2, s));
     clk.mark(k, "qr");
