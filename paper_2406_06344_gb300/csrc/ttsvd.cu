@@ -32,6 +32,7 @@ namespace pttk {
 namespace {
 
 constexpr int RC = 1024;  // Householder rows per chunk
+constexpr int HU = 8;     // rows per lane per load batch in the Householder passes
 constexpr int CG = 32;    // Householder columns per group
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -248,7 +249,14 @@ __global__ void __launch_bounds__(256) hh_w_kernel(const double* __restrict__ A,
     if (l >= N) break;
     const double* col = A + (int64_t)perm[l] * M;
     double acc = 0.0;
-    for (int64_t i = r_begin + lane; i < r_end; i += 32) acc = fma(v[i - c * RC], col[i], acc);
+    for (int64_t i0 = r_begin + lane; i0 < r_end; i0 += 32 * HU) {
+      double x[HU];  // HU loads in flight before the arithmetic
+#pragma unroll
+      for (int u = 0; u < HU; ++u) x[u] = i0 + 32 * u < r_end ? col[i0 + 32 * u] : 0.0;
+#pragma unroll
+      for (int u = 0; u < HU; ++u)
+        if (i0 + 32 * u < r_end) acc = fma(v[i0 + 32 * u - c * RC], x[u], acc);
+    }
     acc = warp_sum(acc);
     if (lane == 0) w_part[c * N + l] = acc;
   }
@@ -294,11 +302,20 @@ __global__ void __launch_bounds__(256) hh_update_kernel(double* __restrict__ A, 
     const double wl = w[l];
     double* col = A + (int64_t)p * M;
     double nacc = 0.0;
-    for (int64_t i = r_begin + lane; i < r_end; i += 32) {
-      const double a = fma(-v[i - c * RC], wl, col[i]);
-      col[i] = a;
-      if (i == j) Rp[j + (int64_t)p * N] = a;
-      if (i >= j + 2) nacc = fma(a, a, nacc);
+    for (int64_t i0 = r_begin + lane; i0 < r_end; i0 += 32 * HU) {
+      double x[HU];  // HU loads in flight before the arithmetic
+#pragma unroll
+      for (int u = 0; u < HU; ++u) x[u] = i0 + 32 * u < r_end ? col[i0 + 32 * u] : 0.0;
+#pragma unroll
+      for (int u = 0; u < HU; ++u) {
+        const int64_t i = i0 + 32 * u;
+        if (i < r_end) {
+          const double a = fma(-v[i - c * RC], wl, x[u]);
+          col[i] = a;
+          if (i == j) Rp[j + (int64_t)p * N] = a;
+          if (i >= j + 2) nacc = fma(a, a, nacc);
+        }
+      }
     }
     nacc = warp_sum(nacc);
     if (lane == 0) part[c * N + p] = nacc;
@@ -340,6 +357,7 @@ __global__ void iota_kernel(int* __restrict__ p, int64_t n) {
 // Columns and norms written by other blocks in earlier rounds are read through L2 (ld.cg),
 // never from a possibly stale L1 line.
 constexpr int JB = 256;            // threads per block
+constexpr int JU = 8;              // rows per lane per load batch
 constexpr int JMAX_SWEEPS = 60;
 
 struct JacobiSync {                // device state of one call (zeroed before the launch)
@@ -394,7 +412,9 @@ __global__ void __launch_bounds__(JB) jacobi_kernel(double* __restrict__ A, int6
   const unsigned nb = gridDim.x;
   const int npairs = p / 2;
   const int lane = threadIdx.x & 31;
-  const int gw0 = (int)(blockIdx.x * (JB / 32) + (threadIdx.x >> 5));
+  // pairs are dealt to blocks first (pair pr goes to block pr mod nb), so that a round's FP64
+  // work spreads over every SM even when there are fewer pairs than warps
+  const int gw0 = (int)(blockIdx.x + nb * (threadIdx.x >> 5));
   const int nwarps = (int)(nb * (JB / 32));
   for (int sweep = 0; sweep < JMAX_SWEEPS; ++sweep) {
     for (int r = 0; r < p - 1; ++r) {
@@ -416,12 +436,23 @@ __global__ void __launch_bounds__(JB) jacobi_kernel(double* __restrict__ A, int6
         if (__ldcg(colsq + a) < small2 && __ldcg(colsq + b) < small2) continue;
         double* ca = A + (int64_t)a * rows;
         double* cb = A + (int64_t)b * rows;
+        // JU rows per lane per iteration, all loads issued before the arithmetic, so that the
+        // L2 latency is paid once per JU rows
         double al = 0.0, be = 0.0, ga = 0.0;
-        for (int64_t i = lane; i < rows; i += 32) {
-          const double x = __ldcg(ca + i), y = __ldcg(cb + i);
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
+        for (int64_t i0 = lane; i0 < rows; i0 += 32 * JU) {
+          double x[JU], y[JU];
+#pragma unroll
+          for (int u = 0; u < JU; ++u) {
+            const int64_t i = i0 + 32 * u;
+            x[u] = i < rows ? __ldcg(ca + i) : 0.0;
+            y[u] = i < rows ? __ldcg(cb + i) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < JU; ++u) {
+            al = fma(x[u], x[u], al);
+            be = fma(y[u], y[u], be);
+            ga = fma(x[u], y[u], ga);
+          }
         }
         al = warp_sum(al);
         be = warp_sum(be);
@@ -431,13 +462,25 @@ __global__ void __launch_bounds__(JB) jacobi_kernel(double* __restrict__ A, int6
         const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
         double na = 0.0, nbb = 0.0;
-        for (int64_t i = lane; i < rows; i += 32) {
-          const double x = __ldcg(ca + i), y = __ldcg(cb + i);
-          const double xa = cs * x - sn * y, yb = sn * x + cs * y;
-          ca[i] = xa;
-          cb[i] = yb;
-          na = fma(xa, xa, na);
-          nbb = fma(yb, yb, nbb);
+        for (int64_t i0 = lane; i0 < rows; i0 += 32 * JU) {
+          double x[JU], y[JU];
+#pragma unroll
+          for (int u = 0; u < JU; ++u) {
+            const int64_t i = i0 + 32 * u;
+            x[u] = i < rows ? __ldcg(ca + i) : 0.0;
+            y[u] = i < rows ? __ldcg(cb + i) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < JU; ++u) {
+            const int64_t i = i0 + 32 * u;
+            const double xa = cs * x[u] - sn * y[u], yb = sn * x[u] + cs * y[u];
+            if (i < rows) {
+              ca[i] = xa;
+              cb[i] = yb;
+            }
+            na = fma(xa, xa, na);
+            nbb = fma(yb, yb, nbb);
+          }
         }
         na = warp_sum(na);
         nbb = warp_sum(nbb);
@@ -660,8 +703,9 @@ static pttk_status launch_jacobi(double* A, int64_t rows, int ncols, int p, doub
   int per_sm = 0;
   PTTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JB, 0));
   if (per_sm < 1) return set_error(PTTK_ECUDA, "Jacobi kernel cannot be resident");
-  // one block (8 warps, 8 pairs at a time) per SM, fewer when there are fewer pairs
-  const int want = (p / 2 + JB / 32 - 1) / (JB / 32);
+  // one block per SM (fewer when there are fewer pairs); each block takes up to 8 pairs of a
+  // round at a time, pairs dealt round-robin over the blocks
+  const int want = p / 2;
   const unsigned grid = (unsigned)std::max(1, std::min(want, sm_count()));
   void* args[] = {&A, &rows, &ncols, &p, &tol, &small2, &count2, &colsq, &js};
   PTTK_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(JB), args, 0, s));
