@@ -19,7 +19,7 @@ Conventions (all from Section 2 of the paper):
     (r_{k-1} n) x r_k unfolding and G^{1} its r_{k-1} x (n r_k) unfolding;
   * the variable order is xi = (x, theta, y) (Eq. fkappa), D = 2d + dtheta.
 
-Readings of the paper taken here (each is also listed in the design notes):
+Readings of the paper taken here (where the paper is silent, ambiguous or garbled):
   R1  The interval map is used exactly as printed in Section 2.4,
       phi_[a,b](t) = ((a-b)/2) t + (a+b)/2 (it sends +1 to a). The
       interpolant does not depend on this orientation (test pin).
