@@ -280,6 +280,14 @@ pttk_status pttk_profile_reset(void);
 pttk_status pttk_profile_get(const char* kernel_name, double* ms_total, int64_t* launches);
 /* Total number of kernels the library has launched in this process (all entry points). */
 int64_t pttk_launch_count(void);
+
+/* Self-test of failure detection (the paper has no counterpart). Every wait inside the
+ * library's kernels (pipeline barriers, grid barriers) is bounded: after ~2 s it gives up,
+ * the kernel records PTTK_ETIMEOUT and returns, and the CUDA context stays usable. This call
+ * runs one such wait on a barrier that nothing ever completes and reports the outcome:
+ * PTTK_ETIMEOUT when the wait gave up as designed (the expected result), PTTK_ECUDA
+ * otherwise. Takes ~2 s; synchronises `stream`. */
+pttk_status pttk_selftest_wait_timeout(void* stream);
 /* Names of the kernels timed so far, newline-separated, NUL-terminated, truncated to len. */
 pttk_status pttk_profile_names(char* buf, int64_t len);
 

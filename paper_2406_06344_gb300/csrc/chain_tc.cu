@@ -1068,3 +1068,39 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
 }
 
 }  // namespace pttk
+
+namespace pttk {
+namespace {
+// One thread waits, with the kernels' bounded wait, on an mbarrier that nothing arrives on:
+// the wait must give up (after ~2 s) and the kernel must report PTTK_ETIMEOUT and return.
+__global__ void selftest_wait_kernel(int* __restrict__ status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+    const bool ok = mbar_wait(&bar, 0, &abort_flag);
+    *status = ok ? (int)PTTK_OK : (int)PTTK_ETIMEOUT;
+  }
+}
+}  // namespace
+}  // namespace pttk
+
+extern "C" pttk_status pttk_selftest_wait_timeout(void* stream) {
+  using namespace pttk;
+  clear_error();
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* d_status = nullptr;
+  PTTK_CUDA(cudaMalloc(&d_status, sizeof(int)));
+  PTTK_CUDA(cudaMemsetAsync(d_status, 0xff, sizeof(int), s));
+  selftest_wait_kernel<<<1, 32, 0, s>>>(d_status); pttk::count_launch();
+  int h = -1;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_status);
+  if (e != cudaSuccess) return cuda_error(e, "self-test of the bounded wait");
+  if (h == (int)PTTK_ETIMEOUT) return set_error(PTTK_ETIMEOUT, "self-test: the bounded wait gave up as it should");
+  return set_error(PTTK_ECUDA, "self-test: the bounded wait did not give up");
+}

@@ -65,6 +65,7 @@ SIGNATURES = [
     ("pttk_profile_get", _int, [ctypes.c_char_p, _c_double_p, ctypes.POINTER(_i64)]),
     ("pttk_profile_names", _int, [ctypes.c_char_p, _i64]),
     ("pttk_launch_count", _i64, []),
+    ("pttk_selftest_wait_timeout", _int, [_vp]),
 ]
 
 _lib = None
@@ -439,3 +440,9 @@ def profile_names() -> list:
 def launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().pttk_launch_count())
+
+
+def selftest_wait_timeout(stream=None) -> int:
+    """Runs a kernel whose bounded wait can never complete; returns the library status
+    (ETIMEOUT when the wait gave up as designed)."""
+    return int(load().pttk_selftest_wait_timeout(_stream(stream)))
