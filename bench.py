@@ -53,6 +53,7 @@ FP64_PEAK_TFLOPS = 1.25                             # nominal FP64 rate of the p
 # ncu capture summarised in profiles/chain_tc_fp16x3_c3_online.md (to be emptied whenever the
 # kernel changes after that capture)
 NCU_TRAFFIC = {"fp16x3": 26.541056e6 + 1.373002e9}
+GRID_FP64_FLOPS_PER_ENTRY = 944.0
 
 
 def parse():
@@ -313,10 +314,19 @@ def main():
     gt_ms, gt_n = prof.get("grid_tile", (0.0, 0))
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
     prof_total = sum(v[0] for v in prof.values())
+    # FP64 flops per entry of the FP64 grid kernel (K_nu quadrature + in-tile transform), from
+    # the instruction counts summarised in profiles/grid_tile_fp64_c3n5.md
+    grid_fp64_flops = GRID_FP64_FLOPS_PER_ENTRY * total * args.steps * world
+    roof_grid_fp64 = {"kernel": "grid_tile_kernel (FP64)", "bound": "alu (FP64)",
+                      "achieved": grid_fp64_flops / (g64_ms / 1000.0) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                      "unit": "TFLOP/s", "frac": grid_fp64_flops / (g64_ms / 1000.0) / 1e12 / FP64_PEAK_TFLOPS,
+                      "peak_note": "nominal FP64 rate of the part (not measured); flops per entry from ncu "
+                                   "instruction counts on the n = 5 grid of the same workload"}
     roof_dominant = {"kernel": dom[0], "ms_total": dom[1][0], "launches": dom[1][1],
                      "share_of_timed_kernel_time": dom[1][0] / max(prof_total, 1e-9),
                      "bound": "alu (FP64)" if dom[0] in ("jacobi", "householder", "dgemm", "grid_tile") else "tensor",
-                     "note": "the FP64 TT-SVD of the offline stage dominates the step; see the kernel_ms split"}
+                     "note": "the FP64 offline stage (grid, pivoted QR, Jacobi) holds most of the step; see kernel_ms "
+                             "and roofline_grid_fp64"}
     roof_grid = {"fp64_entries_per_s": total * args.steps * world / (g64_ms / 1000.0),
                  "fp32_entries_per_s": total * args.steps * world / (g32_ms / 1000.0),
                  "bound": "alu (K_nu by quadrature)",
@@ -347,6 +357,7 @@ def main():
             "stage_ms_per_step": {k: tot(k) / args.steps for k in
                                   ("grid64_ms", "grid32_ms", "ttsvd_ms", "inst_ms", "apply_ms")},
             "roofline": roof, "roofline_dominant": roof_dominant, "roofline_grid": roof_grid,
+            "roofline_grid_fp64": roof_grid_fp64,
             "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()},
             "gpu_launches": int(launches),
             "clocks": clock_info,
