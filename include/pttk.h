@@ -58,12 +58,34 @@ typedef enum pttk_status {
   PTTK_ENOTSUP = 6   /* combination not implemented (e.g. a precision for this shape) */
 } pttk_status;
 
-/* Kernels of Table kern-table (r = ||x - y||_2):
- *   PTTK_GAUSS      theta = (l):      exp(-(r/l)^2)
- *   PTTK_MATERN32   theta = (l):      (1 + sqrt(3) r/l) exp(-sqrt(3) r/l)
- *   PTTK_MATERN_NU  theta = (l, nu):  2^(1-nu)/Gamma(nu) (sqrt(2 nu) r/l)^nu K_nu(sqrt(2 nu) r/l)
+/* Kernels of Table kern-table (r = ||x - y||_2, a = r / l):
+ *   PTTK_GAUSS              theta = (l):      exp(-a^2)
+ *   PTTK_MATERN32           theta = (l):      (1 + sqrt(3) a) exp(-sqrt(3) a)
+ *   PTTK_MATERN_NU          theta = (l, nu):  2^(1-nu)/Gamma(nu) (sqrt(2 nu) a)^nu K_nu(sqrt(2 nu) a)
+ *   PTTK_EXPONENTIAL        theta = (l):      exp(-a)
+ *   PTTK_MATERN52           theta = (l):      (1 + sqrt(5) a + 5 a^2 / 3) exp(-sqrt(5) a)
+ *   PTTK_MULTIQUADRIC       theta = (l):      (1 + a^2)^(1/2)
+ *   PTTK_THIN_PLATE_SPLINE  theta = (l):      a^2 log(a^2)
+ * and, without a parameter (d_theta = 0, the TTK variant of Section 3.3; the boxes must be
+ * admissible, dist(source box, target box) > 0, since these are singular at r = 0):
+ *   PTTK_BIHARMONIC         r^-2
+ *   PTTK_LAPLACE3D          r^-1
+ *   PTTK_LAPLACE2D          -log(r)
+ *   PTTK_THIN_PLATE         r^2 log(r)
  * (the table prints Gamma(l) in the Matern normalisation; Gamma(nu) is used). */
-typedef enum pttk_kernel { PTTK_GAUSS = 0, PTTK_MATERN32 = 1, PTTK_MATERN_NU = 2 } pttk_kernel;
+typedef enum pttk_kernel {
+  PTTK_GAUSS = 0,
+  PTTK_MATERN32 = 1,
+  PTTK_MATERN_NU = 2,
+  PTTK_EXPONENTIAL = 3,
+  PTTK_MATERN52 = 4,
+  PTTK_MULTIQUADRIC = 5,
+  PTTK_THIN_PLATE_SPLINE = 6,
+  PTTK_BIHARMONIC = 7,
+  PTTK_LAPLACE3D = 8,
+  PTTK_LAPLACE2D = 9,
+  PTTK_THIN_PLATE = 10
+} pttk_kernel;
 
 typedef enum pttk_prec {
   PTTK_FP64 = 0,

@@ -46,6 +46,8 @@ import numpy as np
 from scipy import special
 
 GAUSS, MATERN32, MATERN_NU = 0, 1, 2
+EXPONENTIAL, MATERN52, MULTIQUADRIC, THIN_PLATE_SPLINE = 3, 4, 5, 6
+BIHARMONIC, LAPLACE3D, LAPLACE2D, THIN_PLATE = 7, 8, 9, 10     # no parameter (d_theta = 0)
 
 
 # ---------------------------------------------------------------------------
@@ -118,9 +120,17 @@ def basis_q(x, a: float, b: float, n: int) -> np.ndarray:
 def kernel_of_r(kind: int, r, theta) -> np.ndarray:
     """kappa as a function of r = ||x - y||_2 and theta (Table kern-table, reading R5).
 
-    GAUSS      theta = (l,):      exp(-(r/l)^2)
-    MATERN32   theta = (l,):      (1 + sqrt(3) r/l) exp(-sqrt(3) r/l)
-    MATERN_NU  theta = (l, nu):   2^(1-nu)/Gamma(nu) (sqrt(2 nu) r/l)^nu K_nu(sqrt(2 nu) r/l)
+    GAUSS              theta = (l,):      exp(-(r/l)^2)
+    MATERN32           theta = (l,):      (1 + sqrt(3) r/l) exp(-sqrt(3) r/l)
+    MATERN_NU          theta = (l, nu):   2^(1-nu)/Gamma(nu) (sqrt(2 nu) r/l)^nu K_nu(sqrt(2 nu) r/l)
+    EXPONENTIAL        theta = (l,):      exp(-r/l)
+    MATERN52           theta = (l,):      (1 + sqrt(5) r/l + 5 (r/l)^2 / 3) exp(-sqrt(5) r/l)
+    MULTIQUADRIC       theta = (l,):      (1 + (r/l)^2)^(1/2)
+    THIN_PLATE_SPLINE  theta = (l,):      (r/l)^2 log((r/l)^2)
+    BIHARMONIC         theta = ():        r^-2
+    LAPLACE3D          theta = ():        r^-1
+    LAPLACE2D          theta = ():        -log(r)
+    THIN_PLATE         theta = ():        r^2 log(r)
     """
     r = np.asarray(r, dtype=np.float64)
     if kind == GAUSS:
@@ -130,6 +140,25 @@ def kernel_of_r(kind: int, r, theta) -> np.ndarray:
         l = theta[0]
         a = math.sqrt(3.0) * r / l
         return (1.0 + a) * np.exp(-a)
+    if kind == EXPONENTIAL:
+        return np.exp(-r / theta[0])
+    if kind == MATERN52:
+        a = math.sqrt(5.0) * r / theta[0]
+        return (1.0 + a + a * a / 3.0) * np.exp(-a)
+    if kind == MULTIQUADRIC:
+        return np.sqrt(1.0 + (r / theta[0]) ** 2)
+    if kind == THIN_PLATE_SPLINE:
+        q = (r / theta[0]) ** 2
+        with np.errstate(divide="ignore", invalid="ignore"):
+            return np.where(q > 0.0, q * np.log(np.where(q > 0.0, q, 1.0)), 0.0)
+    if kind == BIHARMONIC:
+        return r ** -2.0
+    if kind == LAPLACE3D:
+        return 1.0 / r
+    if kind == LAPLACE2D:
+        return -np.log(r)
+    if kind == THIN_PLATE:
+        return r * r * np.log(r)
     if kind == MATERN_NU:
         l, nu = theta[0], theta[1]
         z = np.sqrt(2.0 * nu) * r / l
@@ -186,7 +215,7 @@ def kernel_f(kind: int):
             l, nu = th
             z = np.sqrt(2.0 * nu) * r / l
             return np.power(2.0, 1.0 - nu) / special.gamma(nu) * np.power(z, nu) * special.kv(nu, z)
-        return kernel_of_r(kind, r, (th[0],))
+        return kernel_of_r(kind, r, tuple(th[:1]))
     return f
 
 

@@ -104,22 +104,27 @@ static void free_handle(pttk_tt_ext* t) {
 
 static pttk_status check_problem(int kernel, int d, const double* src_box, const double* tgt_box,
                                  int d_theta, const double* theta_box, int n) {
-  if (kernel < PTTK_GAUSS || kernel > PTTK_MATERN_NU) return set_error(PTTK_EINVAL, "unknown kernel");
+  if (kernel < PTTK_GAUSS || kernel > PTTK_THIN_PLATE) return set_error(PTTK_EINVAL, "unknown kernel");
   if (d < 1 || d > 3) return set_error(PTTK_EINVAL, "d must be 1, 2 or 3");
-  const int need_dth = kernel == PTTK_MATERN_NU ? 2 : 1;
+  const int need_dth = kernel_dtheta(kernel);
   if (d_theta != need_dth)
-    return set_error(PTTK_EINVAL, kernel == PTTK_MATERN_NU
-                                      ? "the general-nu Matern kernel takes theta = (l, nu): d_theta = 2"
-                                      : "this kernel takes theta = (l): d_theta = 1");
+    return set_error(PTTK_EINVAL, need_dth == 2   ? "the general-nu Matern kernel takes theta = (l, nu): d_theta = 2"
+                                  : need_dth == 1 ? "this kernel takes theta = (l): d_theta = 1"
+                                                  : "this kernel has no parameter: d_theta = 0");
   if (n < 2 || n > PTTK_MAX_N) return set_error(PTTK_EINVAL, "n must be in [2, 32]");
-  if (!src_box || !tgt_box || !theta_box) return set_error(PTTK_EINVAL, "NULL box");
+  if (!src_box || !tgt_box || (d_theta > 0 && !theta_box)) return set_error(PTTK_EINVAL, "NULL box");
+  double gap2 = 0.0;  // squared distance between the source and target boxes
   for (int j = 0; j < d; ++j) {
     if (!(src_box[2 * j] < src_box[2 * j + 1]) || !(tgt_box[2 * j] < tgt_box[2 * j + 1]))
       return set_error(PTTK_EINVAL, "box with lo >= hi");
+    const double g = std::max({0.0, tgt_box[2 * j] - src_box[2 * j + 1], src_box[2 * j] - tgt_box[2 * j + 1]});
+    gap2 += g * g;
   }
+  if (d_theta == 0 && !(gap2 > 0.0))
+    return set_error(PTTK_EINVAL, "this kernel is singular at r = 0: the boxes must be apart (dist > 0)");
   for (int j = 0; j < d_theta; ++j)
     if (!(theta_box[2 * j] < theta_box[2 * j + 1])) return set_error(PTTK_EINVAL, "theta box with lo >= hi");
-  if (!(theta_box[0] > 0.0)) return set_error(PTTK_EINVAL, "length scale box must be positive");
+  if (d_theta > 0 && !(theta_box[0] > 0.0)) return set_error(PTTK_EINVAL, "length scale box must be positive");
   if (kernel == PTTK_MATERN_NU && !(theta_box[2] > 0.0))
     return set_error(PTTK_EINVAL, "nu box must be positive");
   double prod = 1.0;
@@ -375,7 +380,8 @@ pttk_status pttk_tt_load(const char* path, pttk_tt** out) {
     t->n = hdr[3];
     t->D = hdr[4];
     ok = t->d >= 1 && t->d <= 3 && t->dtheta >= 0 && t->dtheta <= 2 && t->D == 2 * t->d + t->dtheta &&
-         t->n >= 2 && t->n <= PTTK_MAX_N && t->kernel >= 0 && t->kernel <= 2;
+         t->n >= 2 && t->n <= PTTK_MAX_N && t->kernel >= 0 && t->kernel <= PTTK_THIN_PLATE &&
+         t->dtheta == kernel_dtheta(t->kernel);
   }
   for (int j = 0; ok && j < t->D; ++j) ok = fread(t->box[j], sizeof(double), 2, f) == 2;
   for (int k = 0; ok && k <= t->D; ++k) {

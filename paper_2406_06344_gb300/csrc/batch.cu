@@ -75,6 +75,16 @@ __global__ void batched_product(const double* __restrict__ H1, const double* __r
   }
 }
 
+// H[b] = identity (r x r): kernels without a parameter (d_theta = 0) have H(theta) = I
+__global__ void identity_batched(int r, int B, double* __restrict__ H) {
+  const int64_t total = (int64_t)B * r * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e % ((int64_t)r * r);
+    H[e] = (q % r == q / r) ? 1.0 : 0.0;
+  }
+}
+
 // M[b] row-major (rs x rt) from H[b] column-major
 template <typename T>
 __global__ void store_batched_rowmajor(const double* __restrict__ H, int rs, int rt, int B, T* __restrict__ M) {
@@ -220,7 +230,7 @@ pttk_status pttk_batch_autotune(pttk_batch* b, const void* X, const void* Y, voi
 pttk_status pttk_instantiate_batched(const pttk_batch* b, const double* thetas, const void* X, const void* Y,
                                      void* U, void* M, void* V, void* stream) {
   clear_error();
-  if (!b || !thetas || !M) return set_error(PTTK_EINVAL, "NULL argument");
+  if (!b || !M || (b->tt->dtheta > 0 && !thetas)) return set_error(PTTK_EINVAL, "NULL argument");
   if ((b->Ns > 0 && (!X || !U)) || (b->Nt > 0 && (!Y || !V))) return set_error(PTTK_EINVAL, "NULL point or factor buffer");
   const pttk_tt* tt = b->tt;
   cudaStream_t s = as_stream(stream);
@@ -229,7 +239,10 @@ pttk_status pttk_instantiate_batched(const pttk_batch* b, const double* thetas, 
   int* status = tt_status_word(tt);
   const double* H = nullptr;
   double* Hout = b->scratch;
-  if (dth == 1) {
+  if (dth == 0) {
+    identity_batched<<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(rs, B, Hout); pttk::count_launch();
+    H = Hout;
+  } else if (dth == 1) {
     theta_contract_batched<<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(
         tt->cores64 + tt->core_off[d], rs, n, rt, thetas, B, 1, 0, tt->box[d][0], tt->box[d][1], Hout, status); pttk::count_launch();
     H = Hout;

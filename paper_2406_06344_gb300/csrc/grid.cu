@@ -59,7 +59,7 @@ __device__ __forceinline__ T eval_entry(const GridArgs& a, const int* idx, const
     const T diff = eta[j * n + idx[j]] - eta[(a.d + a.dtheta + j) * n + idx[a.d + a.dtheta + j]];
     r2 += diff * diff;
   }
-  const T l = eta[a.d * n + idx[a.d]];
+  const T l = a.dtheta > 0 ? eta[a.d * n + idx[a.d]] : T(1);
   if (a.kind == K_MATERN_NU) {
     const int inu = idx[a.d + 1];
     return kappa_matern_nu<T>(r2, l, eta[(a.d + 1) * n + inu], cnu[inu], snu[inu], stab);

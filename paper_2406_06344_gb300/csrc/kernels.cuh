@@ -77,14 +77,45 @@ __device__ __forceinline__ void kv_table_fill(T* stab) {
   }
 }
 
-enum { K_GAUSS = 0, K_MATERN32 = 1, K_MATERN_NU = 2 };
+enum {
+  K_GAUSS = 0,
+  K_MATERN32 = 1,
+  K_MATERN_NU = 2,
+  K_EXPONENTIAL = 3,
+  K_MATERN52 = 4,
+  K_MULTIQUADRIC = 5,
+  K_THIN_PLATE_SPLINE = 6,
+  K_BIHARMONIC = 7,
+  K_LAPLACE3D = 8,
+  K_LAPLACE2D = 9,
+  K_THIN_PLATE = 10
+};
 
-// kappa(r; l) for the Gaussian and Matern-3/2 kernels, from r^2.
+// kappa(r; l) of the closed-form kernels, from r^2 (l is unused by the kernels without a
+// parameter, whose boxes are apart, so r > 0 there).
 template <typename T>
 __device__ __forceinline__ T kappa_l(int kind, T r2, T l) {
-  if (kind == K_GAUSS) return exp(-r2 / (l * l));
-  const T a = T(1.7320508075688772) * sqrt(r2) / l;
-  return (T(1) + a) * exp(-a);
+  switch (kind) {
+    case K_GAUSS: return exp(-r2 / (l * l));
+    case K_MATERN32: {
+      const T a = T(1.7320508075688772) * sqrt(r2) / l;
+      return (T(1) + a) * exp(-a);
+    }
+    case K_EXPONENTIAL: return exp(-sqrt(r2) / l);
+    case K_MATERN52: {
+      const T a = T(2.23606797749979) * sqrt(r2) / l;
+      return (T(1) + a + a * a / T(3)) * exp(-a);
+    }
+    case K_MULTIQUADRIC: return sqrt(T(1) + r2 / (l * l));
+    case K_THIN_PLATE_SPLINE: {
+      const T q = r2 / (l * l);
+      return q > T(0) ? q * log(q) : T(0);
+    }
+    case K_BIHARMONIC: return T(1) / r2;
+    case K_LAPLACE3D: return T(1) / sqrt(r2);
+    case K_LAPLACE2D: return T(-0.5) * log(r2);
+    default: return T(0.5) * r2 * log(r2);  // K_THIN_PLATE: r^2 log r
+  }
 }
 
 // Matern general nu: 2^(1-nu)/Gamma(nu) z^nu K_nu(z), z = sqrt(2 nu) r / l.

@@ -13,6 +13,12 @@
 #include "../../include/pttk.h"
 
 #define PTTK_MAX_D 8
+
+// Parameters of each kernel: theta = (l, nu) for the general-nu Matern kernel, (l) for the
+// other length-scale kernels, none for the singular kernels of the TTK variant.
+inline int kernel_dtheta(int kernel) {
+  return kernel == PTTK_MATERN_NU ? 2 : (kernel >= PTTK_BIHARMONIC && kernel <= PTTK_THIN_PLATE) ? 0 : 1;
+}
 #define PTTK_MAX_N 32
 
 struct pttk_tt {

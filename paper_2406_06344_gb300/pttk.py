@@ -19,6 +19,8 @@ OK, EINVAL, EDOMAIN, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP = range(7)
 STATUS_NAMES = {0: "PTTK_OK", 1: "PTTK_EINVAL", 2: "PTTK_EDOMAIN", 3: "PTTK_ENOMEM",
                 4: "PTTK_ECUDA", 5: "PTTK_ETIMEOUT", 6: "PTTK_ENOTSUP"}
 GAUSS, MATERN32, MATERN_NU = 0, 1, 2
+EXPONENTIAL, MATERN52, MULTIQUADRIC, THIN_PLATE_SPLINE = 3, 4, 5, 6
+BIHARMONIC, LAPLACE3D, LAPLACE2D, THIN_PLATE = 7, 8, 9, 10      # no parameter (d_theta = 0)
 FP64, FP32, TF32, TF32X3, BF16, BF16X3, FP16, FP16X3 = range(8)
 PREC_NAMES = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "tf32x3": TF32X3, "bf16": BF16, "bf16x3": BF16X3,
               "fp16": FP16, "fp16x3": FP16X3}

@@ -27,7 +27,11 @@ from dataclasses import dataclass, field
 import numpy as np
 
 GAUSS, MATERN32, MATERN_NU = 0, 1, 2
-KERNEL_NAMES = {GAUSS: "gaussian", MATERN32: "matern32", MATERN_NU: "matern_nu"}
+EXPONENTIAL, MATERN52, MULTIQUADRIC, THIN_PLATE_SPLINE = 3, 4, 5, 6
+BIHARMONIC, LAPLACE3D, LAPLACE2D, THIN_PLATE = 7, 8, 9, 10      # no parameter (d_theta = 0)
+KERNEL_NAMES = {GAUSS: "gaussian", MATERN32: "matern32", MATERN_NU: "matern_nu", EXPONENTIAL: "exponential",
+                MATERN52: "matern52", MULTIQUADRIC: "multiquadric", THIN_PLATE_SPLINE: "thin_plate_spline",
+                BIHARMONIC: "biharmonic", LAPLACE3D: "laplace3d", LAPLACE2D: "laplace2d", THIN_PLATE: "thin_plate"}
 
 SEED_X, SEED_Y, SEED_THETA, SEED_SUB, SEED_WZ, SEED_SIZES = 1, 2, 3, 4, 5, 6
 

@@ -54,7 +54,9 @@ def _boxes():
 
 
 @pytest.mark.parametrize("kernel,d,dth,n,expect", [
-    (7, 1, 1, 16, "unknown kernel"),
+    (11, 1, 1, 16, "unknown kernel"),
+    (7, 1, 1, 16, "d_theta = 0"),
+    (3, 1, 0, 16, "d_theta = 1"),
     (0, 0, 1, 16, "d must be"),
     (0, 4, 1, 16, "d must be"),
     (0, 1, 2, 16, "d_theta = 1"),
@@ -119,4 +121,13 @@ def test_from_cores_rejects_bad_ranks_without_touching_the_device(so):
     assert so.pttk_tt_from_cores(0, 1, s, t, 1, p, 8, bad_mid, cores, ctypes.byref(h)) == pttk.EINVAL
     assert so.pttk_tt_from_cores(0, 1, s, t, 1, p, 8, None, cores, ctypes.byref(h)) == pttk.EINVAL
     assert so.pttk_tt_from_cores(2, 1, s, t, 1, p, 8, bad_first, cores, ctypes.byref(h)) == pttk.EINVAL
+    assert not h.value
+
+
+def test_kernels_without_parameter_need_boxes_apart(so):
+    from paper_2406_06344_gb300 import pttk
+    h = ctypes.c_void_p()
+    touching = so.pttk_build_offline(pttk.LAPLACE3D, 1, pttk._dbl([0, 1]), pttk._dbl([1, 2]), 0, None, 8,
+                                     1e-10, 0, None, ctypes.byref(h))
+    assert touching == pttk.EINVAL and "apart" in so.pttk_last_error().decode()
     assert not h.value

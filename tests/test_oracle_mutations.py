@@ -106,6 +106,18 @@ def _chebT_shifted(k, t):
     return _orig["cheb_T"](np.asarray(k) + 1, t)
 
 
+def _laplace2d_sign(kind, r, theta):
+    if kind == o.LAPLACE2D:
+        return np.log(np.asarray(r))
+    return _orig["kernel_of_r"](kind, r, theta)
+
+
+def _biharmonic_power(kind, r, theta):
+    if kind == o.BIHARMONIC:
+        return 1.0 / np.asarray(r)
+    return _orig["kernel_of_r"](kind, r, theta)
+
+
 # name -> (replacements, pins that should catch it as (function, kwargs))
 CASES = {
     "transform c_0 = 2": ({"cheb_transform_matrix": _transform_c0_two},
@@ -148,6 +160,10 @@ CASES = {
                                        [(pins.test_apply_matches_dense_product, {})]),
     "Chebyshev index off by one": ({"cheb_T": _chebT_shifted},
                                    [(pins.test_transform_inverts_node_values, {"n": 12})]),
+    "Laplace-2D with the wrong sign": ({"kernel_of_r": _laplace2d_sign},
+                                       [(pins.test_multiquadric_and_thin_plate_family_identities, {})]),
+    "bi-harmonic as r^-1": ({"kernel_of_r": _biharmonic_power},
+                            [(pins.test_multiquadric_and_thin_plate_family_identities, {})]),
 }
 
 

@@ -363,3 +363,45 @@ def test_gradients_match_dense_matern32_closed_form():
     assert gth[0] == pytest.approx(w @ dK_dl @ z, rel=1e-9)
     gx = w * (dK_dx @ z)
     assert np.linalg.norm(gX[:, 0] - gx) <= 1e-10 * np.linalg.norm(gx)
+
+
+# --- the other kernels of Table kern-table --------------------------------------
+
+@pytest.mark.parametrize("l", [0.5, 1.3])
+def test_exponential_and_matern52_are_matern_at_half_and_five_halves(l):
+    # the closed forms against the general-nu Matern evaluated through scipy's K_nu
+    r = np.linspace(0.05, 6.0, 101)
+    assert np.allclose(o.kernel_of_r(o.EXPONENTIAL, r, (l,)), o.kernel_of_r(o.MATERN_NU, r, (l, 0.5)),
+                       rtol=1e-13, atol=0)
+    assert np.allclose(o.kernel_of_r(o.MATERN52, r, (l,)), o.kernel_of_r(o.MATERN_NU, r, (l, 2.5)),
+                       rtol=1e-13, atol=0)
+
+
+def test_multiquadric_and_thin_plate_family_identities():
+    r = np.linspace(0.1, 5.0, 50)
+    for l in (0.4, 1.0, 2.5):
+        # multiquadric = hypot(1, r/l)
+        assert np.allclose(o.kernel_of_r(o.MULTIQUADRIC, r, (l,)), np.hypot(1.0, r / l), rtol=1e-15)
+        # thin-plate spline (r/l)^2 log((r/l)^2) = 2 x thin-plate at r/l
+        assert np.allclose(o.kernel_of_r(o.THIN_PLATE_SPLINE, r, (l,)), 2.0 * o.kernel_of_r(o.THIN_PLATE, r / l, ()),
+                           rtol=1e-13, atol=1e-15)
+    # thin-plate r^2 log r = -r^2 x Laplace-2D; bi-harmonic = Laplace-3D squared
+    assert np.allclose(o.kernel_of_r(o.THIN_PLATE, r, ()), -r * r * o.kernel_of_r(o.LAPLACE2D, r, ()), rtol=1e-15)
+    assert np.allclose(o.kernel_of_r(o.BIHARMONIC, r, ()), o.kernel_of_r(o.LAPLACE3D, r, ()) ** 2, rtol=1e-15)
+    assert o.kernel_of_r(o.THIN_PLATE_SPLINE, np.array([0.0]), (1.0,))[0] == 0.0   # the limit at r = 0
+
+
+def test_kernel_without_parameter_end_to_end():
+    # TTK (d_theta = 0): the pipeline runs with an empty theta and H = I; the interpolation of
+    # the Laplace-3D kernel on admissible boxes converges to the dense matrix
+    d, boxes = 2, [(0.0, 1.0), (0.0, 1.0), (2.0, 3.0), (0.0, 1.0)]
+    X = np.random.default_rng(11).random((60, 2))
+    Y = np.column_stack([2 + np.random.default_rng(12).random(50), np.random.default_rng(13).random(50)])
+    K = o.kernel_matrix(o.LAPLACE3D, X, Y, ())
+    errs = []
+    for n in (6, 10, 14):
+        cores, r, C = o.build_offline(o.LAPLACE3D, d, 0, boxes, n, 1e-13)
+        U, M, V = o.instantiate(cores, d, 0, boxes, (), X, Y)
+        assert M.shape[0] == M.shape[1] and np.array_equal(M, np.eye(M.shape[0]))
+        errs.append(o.rel_fro(K, U @ M @ V.T))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-8
