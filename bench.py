@@ -513,6 +513,34 @@ def run_extras(torch, P, W, o, w, tt, X32, Y32, wv, thetas, state, flush, ev):
                       "ms": 1000.0 * statistics.median(times), "dtheta": list(map(float, dth)),
                       "note": "wall time of the synchronous pttk_grad call (loss, dL/dtheta, dL/dX)"}
 
+    # the other kernels of the table at d = 3: grid + transform rate (FP64, FP32) and the TT
+    kern = {}
+    for kid in (W.EXPONENTIAL, W.MATERN52, W.MULTIQUADRIC, W.THIN_PLATE_SPLINE,
+                W.BIHARMONIC, W.LAPLACE3D, W.LAPLACE2D, W.THIN_PLATE):
+        par = kid <= W.THIN_PLATE_SPLINE
+        nk = 12 if par else 16
+        dth = 1 if par else 0
+        sb, tb = ((0.0, 1.0),) * 3, ((3.0, 4.0), (0.0, 1.0), (0.0, 1.0))
+        thb = ((0.5, 2.0),) if par else ()
+        ent = nk ** (6 + dth)
+        rec = {"d": 3, "d_theta": dth, "n": nk, "entries": ent}
+        for prec in ("fp64", "fp32"):
+            Ck = P.grid_coeffs(kid, 3, sb, tb, dth, thb, nk, prec)
+            a = ev()
+            Ck = P.grid_coeffs(kid, 3, sb, tb, dth, thb, nk, prec, out=Ck)
+            b = ev()
+            torch.cuda.synchronize()
+            rec[prec + "_entries_per_s"] = ent / (a.elapsed_time(b) / 1000.0)
+        a = ev()
+        ttk = P.TT.build_offline(kid, 3, sb, tb, dth, thb, nk, 1e-10, "fp64")
+        b = ev()
+        torch.cuda.synchronize()
+        rec["build_offline_s"] = a.elapsed_time(b) / 1000.0
+        rec["ranks"] = ttk.ranks
+        ttk.free()
+        kern[W.KERNEL_NAMES[kid]] = rec
+    out["kernels"] = kern
+
     # end to end through the public API: pinned host inputs copied in, one device->host read
     # of the apply result per build
     Xh = X32.cpu().pin_memory()
