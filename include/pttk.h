@@ -168,6 +168,15 @@ pttk_status pttk_tt_load(const char* path, pttk_tt** out);
  * coefficient form (contracted with T(xhat), not with nodal values). Copied; the caller
  * keeps ownership of `cores`. Synchronous. Errors: PTTK_EINVAL (bad problem or ranks),
  * PTTK_ENOMEM / PTTK_ECUDA. */
+/* TT-Round (Algorithm 1): a new handle holding a TT of the same tensor with ranks reduced so
+ * that ||X - X_rounded||_F <= tol ||X||_F (X the tensor `in` represents): right-to-left
+ * orthogonalisation of the cores, then a left-to-right sweep of truncated SVDs with
+ * delta = tol / sqrt(D - 1) ||X||_F, in FP64 with the factorisation of the TT-SVD. For TTs
+ * whose ranks are inflated (given cores, sums or products of TTs). `in` is unchanged; the
+ * caller frees both. tol in (0, 1). Synchronises `stream`. Errors: PTTK_EINVAL, PTTK_ENOMEM,
+ * PTTK_ECUDA, PTTK_ETIMEOUT. */
+pttk_status pttk_tt_round(const pttk_tt* in, double tol, void* stream, pttk_tt** out);
+
 pttk_status pttk_tt_from_cores(pttk_kernel kernel, int d, const double* src_box, const double* tgt_box,
                                int d_theta, const double* theta_box, int n, const int* ranks,
                                const double* cores, pttk_tt** out);

@@ -270,6 +270,32 @@ def tt_svd(C: np.ndarray, eps: float):
     return cores, ranks
 
 
+def tt_round(cores, eps: float):
+    """TT-Round (Algorithm 1, Section 2.3): right-to-left orthogonalisation by thin QR of
+    (G_i^{1})^T, then left-to-right truncated SVDs of G_i^{2} with delta = eps/sqrt(N-1) ||X||_F.
+    Reading: the update of G_{i-1} is the one that leaves the tensor unchanged,
+    G_{i-1}^{2} <- G_{i-1}^{2} R^T (G_i^{1} = R^T Q^T).
+    Returns (cores, ranks)."""
+    G = [np.array(c, dtype=np.float64) for c in cores]
+    N = len(G)
+    for i in range(N - 1, 0, -1):
+        r0, n, r1 = G[i].shape
+        Q, R = np.linalg.qr(unfold1(G[i]).T)                 # (n r1) x k, k x r0
+        k = Q.shape[1]
+        G[i] = Q.T.reshape(k, n, r1, order="F")
+        a, m, _ = G[i - 1].shape
+        G[i - 1] = (unfold2(G[i - 1]) @ R.T).reshape(a, m, k, order="F")
+    delta = eps / math.sqrt(N - 1) * float(np.linalg.norm(G[0])) if N > 1 else 0.0
+    for i in range(N - 1):
+        r0, n, r1 = G[i].shape
+        U, s, Vt = np.linalg.svd(unfold2(G[i]), full_matrices=False)
+        r = truncation_rank(s, delta)
+        G[i] = U[:, :r].reshape(r0, n, r, order="F")
+        _, n2, r2 = G[i + 1].shape
+        G[i + 1] = ((s[:r, None] * Vt[:r]) @ unfold1(G[i + 1])).reshape(r, n2, r2, order="F")
+    return G, [1] + [g.shape[2] for g in G]
+
+
 def tt_full(cores) -> np.ndarray:
     """x_{i_1..i_N} = sum_s G_1[1,i_1,s_1] G_2[s_1,i_2,s_2] ... G_N[s_{N-1},i_N,1] (Section 2.3)."""
     T = cores[0]                                  # (1, n_1, r_1)

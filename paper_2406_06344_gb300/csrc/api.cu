@@ -422,6 +422,37 @@ pttk_status pttk_tt_from_cores(pttk_kernel kernel, int d, const double* src_box,
   return upload_cores(t, cores, out);
 }
 
+pttk_status pttk_tt_round(const pttk_tt* in, double tol, void* stream, pttk_tt** out) {
+  clear_error();
+  if (!in || !out) return set_error(PTTK_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (!(tol > 0.0) || !(tol < 1.0)) return set_error(PTTK_EINVAL, "tol must be in (0, 1)");
+  cudaStream_t s = as_stream(stream);
+  pttk_tt_ext* t = new pttk_tt_ext();
+  t->kernel = in->kernel;
+  t->d = in->d;
+  t->dtheta = in->dtheta;
+  t->D = in->D;
+  t->n = in->n;
+  for (int j = 0; j < in->D; ++j) {
+    t->box[j][0] = in->box[j][0];
+    t->box[j][1] = in->box[j][1];
+  }
+  cudaGetDevice(&t->device);
+  pttk_status st = tt_round_run(in, tol, t, s);
+  if (st == PTTK_OK) st = prepare_oriented(t, s);
+  if (st == PTTK_OK) {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_error(e, "TT-Round");
+  }
+  if (st != PTTK_OK) {
+    free_handle(t);
+    return st;
+  }
+  *out = t;
+  return PTTK_OK;
+}
+
 void pttk_tt_free(pttk_tt* tt) { free_handle(static_cast<pttk_tt_ext*>(tt)); }
 
 pttk_status pttk_theta_core(const pttk_tt* tt, const double* theta, pttk_prec prec, void* M,

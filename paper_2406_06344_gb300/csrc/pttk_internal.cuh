@@ -80,6 +80,7 @@ pttk_status grid_coeffs_launch(int kernel, int d, int dtheta, int n, const doubl
 // TT-SVD of the FP64 tensor in `X` (n^D elements, modified). Fills tt->ranks and
 // allocates tt->cores64 / cores32. Synchronises `s`.
 pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s);
+pttk_status tt_round_run(const pttk_tt* in, double tol, pttk_tt* out, cudaStream_t s);
 pttk_status widen_to_f64(const float* in, int64_t n, double* out, cudaStream_t s);
 
 // FP64 column-major GEMM: C[M x N] = alpha * op(A) * op(B) + beta * C.

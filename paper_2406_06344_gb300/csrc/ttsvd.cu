@@ -802,6 +802,148 @@ struct StageClock {
   }
 };
 
+// Working buffers of svd_basis, reused (reallocated) from call to call.
+struct StepWork {
+  Buf qrin, A, U, Y, Yt, norms, part, wpart, wv, below, R;
+  int* d_perm = nullptr;
+  HHState* d_hs = nullptr;
+  ~StepWork() {
+    if (d_perm) cudaFree(d_perm);
+    if (d_hs) cudaFree(d_hs);
+  }
+};
+
+// Orthonormal basis (m x r, unit columns in decreasing singular value, column-major, into
+// `core`) of the top-r left singular subspace of X (m x c, column-major, not modified), r the
+// smallest rank >= 1 whose discarded tail sqrt(sum_{i>r} sigma_i^2) is <= delta; delta = 0
+// keeps every direction X has (an orthonormal basis of its range).
+static pttk_status svd_basis(const double* X, int64_t m, int64_t c, double delta, StepWork& wk, Buf& core,
+                             int* r_out, StageClock& clk, int k, cudaStream_t s) {
+  if (!wk.d_hs) PTTK_CUDA(cudaMalloc(&wk.d_hs, sizeof(HHState)));
+  const bool wide = c >= m;
+  // QR input: wide -> W = X^T (c x m), tall -> a copy of X (m x c). The pivoted QR makes
+  // the triangular factor graded, so one-sided Jacobi on its transpose converges in a few
+  // sweeps, and stops once the remaining block is negligible next to delta.
+  const int64_t q = wide ? m : c;        // columns of the QR input
+  const int64_t Mqr = wide ? c : m;      // rows of the QR input
+  if (clk.on) fprintf(stderr, "pttk: tt-svd step %d m %lld c %lld %s\n", k + 1, (long long)m, (long long)c, wide ? "wide" : "tall");
+  clk.reset();
+  PTTK_TRY(wk.norms.alloc(std::max<int64_t>(q, 1)));
+  if (wk.d_perm) cudaFree(wk.d_perm);
+  wk.d_perm = nullptr;
+  PTTK_CUDA(cudaMalloc(&wk.d_perm, sizeof(int) * q));
+  PTTK_TRY(wk.qrin.alloc(Mqr * q));
+  if (wide) {
+    dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
+    transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(X, m, c, nullptr, wk.qrin.p); pttk::count_launch();
+  } else {
+    PTTK_CUDA(cudaMemcpyAsync(wk.qrin.p, X, sizeof(double) * m * c, cudaMemcpyDeviceToDevice, s));
+  }
+  const int64_t nchunks = (Mqr + RC - 1) / RC;
+  PTTK_TRY(wk.part.alloc(nchunks * q));
+  PTTK_TRY(wk.wpart.alloc(nchunks * q));
+  PTTK_TRY(wk.wv.alloc(q));
+  PTTK_TRY(wk.below.alloc(q));
+  PTTK_TRY(wk.R.alloc(q * q));
+  clk.mark(k, "layout");
+  // rows of R kept: the QR stops once the discarded block has ||R22||_F <= 0.03 delta. The
+  // tails below count ||R22||^2, so the error bound of the truncation holds as it is; only a
+  // tail within 9e-4 delta^2 of the threshold could give a rank one higher than the exact
+  // singular values would
+  int kq = 0;
+  double tail2 = 0.0;
+  const double stop = 0.03 * delta;
+  PTTK_TRY(householder_qrcp(wk.qrin.p, Mqr, q, stop * stop, wk.R.p, wk.d_perm, wk.part.p, wk.below.p,
+                            wk.wpart.p, wk.wv.p, wk.d_hs, &kq, &tail2, s));
+  clk.mark(k, "qr");
+  if (clk.on) fprintf(stderr, "pttk: tt-svd step %d kept %d of %lld rows of R, ||R22|| %.3e\n", k + 1, kq, (long long)q, sqrt(tail2));
+  // A = R1^T (q x kq), R1 = the kept rows of R in pivoted column order
+  PTTK_TRY(wk.A.alloc(q * kq));
+  gather_rt_kernel<<<grid1d(q * kq, 256), 256, 0, s>>>(wk.R.p, q, kq, wk.d_perm, wk.A.p); pttk::count_launch();
+  // one-sided Jacobi on R1^T: R1^T V = U' Sigma, so R1 = V Sigma U'^T and the right singular
+  // vectors of R1 (= of the pivoted QR input, up to the discarded R22) are the normalised
+  // columns of the rotated R1^T; columns below 1e-3 delta / sqrt(kq) together carry
+  // < 1e-6 delta^2, and pairs of them are skipped
+  PTTK_TRY(jacobi(wk.A.p, q, kq, s, 1e-3 * delta / sqrt((double)kq)));
+  clk.mark(k, "jacobi");
+  colnorm_kernel<<<(unsigned)(((int64_t)kq * 32 + 255) / 256), 256, 0, s>>>(wk.A.p, q, kq, wk.norms.p); pttk::count_launch();
+  std::vector<double> sigma(kq);
+  PTTK_CUDA(cudaMemcpyAsync(sigma.data(), wk.norms.p, sizeof(double) * kq, cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> perm;
+  const int r = truncation(sigma, delta, perm, tail2);
+  int* d_top = nullptr;
+  PTTK_CUDA(cudaMalloc(&d_top, sizeof(int) * std::max<int64_t>(kq, 1)));
+  struct TopGuard { int* p; ~TopGuard() { if (p) cudaFree(p); } } top_guard{d_top};
+  PTTK_CUDA(cudaMemcpyAsync(d_top, perm.data(), sizeof(int) * kq, cudaMemcpyHostToDevice, s));
+  // top-r right singular vectors (unit columns), in the pivoted order
+  PTTK_TRY(wk.U.alloc(q * r));
+  PTTK_TRY(wk.Y.alloc(q * r));
+  gather_cols_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(wk.A.p, q, d_top, r, wk.norms.p, wk.Y.p); pttk::count_launch();
+  // back to the original order: row perm[l] of the result is row l of Y
+  scatter_rows_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(wk.Y.p, q, r, wk.d_perm, wk.U.p); pttk::count_launch();
+  double* basis = wk.U.p;  // m x r (wide): left singular vectors of X
+  if (!wide) {
+    // tall: U holds the top right singular vectors of X (c x r); Y = X U spans the top-r
+    // left singular subspace
+    PTTK_TRY(wk.Yt.alloc(m * r));
+    dgemm(false, false, m, r, c, 1.0, X, m, wk.U.p, c, 0.0, wk.Yt.p, m, s);
+    basis = wk.Yt.p;
+  }
+  // make the m x r basis orthonormal to working precision: its columns are orthogonal up
+  // to ~eps ||X|| / sigma_i, so one-sided Jacobi needs one or two sweeps
+  clk.mark(k, "basis");
+  PTTK_TRY(jacobi(basis, m, r, s));
+  clk.mark(k, "reorth");
+  Buf bn;
+  PTTK_TRY(bn.alloc(r));
+  colnorm_kernel<<<(unsigned)(((int64_t)r * 32 + 255) / 256), 256, 0, s>>>(basis, m, r, bn.p); pttk::count_launch();
+  std::vector<double> bnh(r);
+  PTTK_CUDA(cudaMemcpyAsync(bnh.data(), bn.p, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> bperm;
+  truncation(bnh, 0.0, bperm);
+  PTTK_CUDA(cudaMemcpyAsync(d_top, bperm.data(), sizeof(int) * r, cudaMemcpyHostToDevice, s));
+  PTTK_TRY(core.alloc(m * r));
+  gather_cols_kernel<<<grid1d(m * r, 256), 256, 0, s>>>(basis, m, d_top, r, bn.p, core.p); pttk::count_launch();
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  *r_out = r;
+  return PTTK_OK;
+}
+
+// Packs device cores (core k: ranks[k] x n x ranks[k+1], column-major) into the handle.
+static pttk_status pack_cores(pttk_tt* tt, std::vector<Buf>& cores, cudaStream_t s) {
+  size_t off = 0;
+  for (int k = 0; k < tt->D; ++k) {
+    tt->core_off[k] = off;
+    off += tt->core_elems(k);
+  }
+  tt->core_total = off;
+  PTTK_CUDA(cudaMalloc(&tt->cores64, sizeof(double) * off));
+  PTTK_CUDA(cudaMalloc(&tt->cores32, sizeof(float) * off));
+  for (int k = 0; k < tt->D; ++k)
+    PTTK_CUDA(cudaMemcpyAsync(tt->cores64 + tt->core_off[k], cores[k].p,
+                              sizeof(double) * tt->core_elems(k), cudaMemcpyDeviceToDevice, s));
+  cast_f32_kernel<<<grid1d((int64_t)off, 256), 256, 0, s>>>(tt->cores64, (int64_t)off, tt->cores32); pttk::count_launch();
+  PTTK_CUDA(cudaGetLastError());
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  return PTTK_OK;
+}
+
+// squared Frobenius norm of x (n doubles), synchronous
+static pttk_status sumsq_host(const double* x, int64_t n, double* out, cudaStream_t s) {
+  Buf part, scal;
+  const unsigned nb = grid1d(n, 256, 4);
+  PTTK_TRY(part.alloc(nb));
+  PTTK_TRY(scal.alloc(1));
+  sumsq_kernel<<<nb, 256, 0, s>>>(x, n, part.p); pttk::count_launch();
+  sum_kernel<<<1, 256, 0, s>>>(part.p, (int)nb, scal.p); pttk::count_launch();
+  PTTK_CUDA(cudaGetLastError());
+  PTTK_CUDA(cudaMemcpyAsync(out, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  return PTTK_OK;
+}
+
 pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   const int D = tt->D, n = tt->n;
   StageClock clk(s);
@@ -809,128 +951,25 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   for (int k = 0; k < D; ++k) total *= n;
 
   // ||C||_F
-  Buf part, scal;
-  const unsigned nb = grid1d(total, 256, 4);
-  PTTK_TRY(part.alloc(nb));
-  PTTK_TRY(scal.alloc(64));
-  sumsq_kernel<<<nb, 256, 0, s>>>(X, total, part.p); pttk::count_launch();
-  sum_kernel<<<1, 256, 0, s>>>(part.p, (int)nb, scal.p); pttk::count_launch();
-  PTTK_CUDA(cudaGetLastError());
   double sumsq = 0.0;
-  PTTK_CUDA(cudaMemcpyAsync(&sumsq, scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-  PTTK_CUDA(cudaStreamSynchronize(s));
+  PTTK_TRY(sumsq_host(X, total, &sumsq, s));
   const double delta = tol / sqrt((double)(D - 1)) * sqrt(sumsq);
 
-  Buf Xn, R, wpart, wv, below;
+  Buf Xn;
   PTTK_TRY(Xn.alloc(total));
-  int* d_perm = nullptr;
-  HHState* d_hs = nullptr;
-  PTTK_CUDA(cudaMalloc(&d_hs, sizeof(HHState)));
-  struct Guard {
-    int*& a; HHState*& c;
-    ~Guard() { if (a) cudaFree(a); if (c) cudaFree(c); }
-  } guard{d_perm, d_hs};
-
+  StepWork wk;
   std::vector<Buf> cores(D);
   tt->ranks[0] = 1;
   int64_t r_prev = 1;
   double* cur = X;
   double* nxt = Xn.p;
   int64_t cur_elems = total;
-  Buf qrin, A, U, Y, Yt, norms;
   for (int k = 0; k < D - 1; ++k) {
-    PTTK_CUDA(cudaStreamSynchronize(s));  // buffers below are reallocated per step
+    PTTK_CUDA(cudaStreamSynchronize(s));  // buffers are reallocated per step
     const int64_t m = r_prev * n;
     const int64_t c = cur_elems / m;
-    const bool wide = c >= m;
-    // QR input: wide -> W = X^T (c x m), tall -> a copy of X (m x c). The pivoted QR makes
-    // the triangular factor graded, so one-sided Jacobi on its transpose converges in a few
-    // sweeps, and stops once the remaining block is negligible next to delta.
-    const int64_t q = wide ? m : c;        // columns of the QR input
-    const int64_t Mqr = wide ? c : m;      // rows of the QR input
-    if (clk.on) fprintf(stderr, "pttk: tt-svd step %d m %lld c %lld %s\n", k + 1, (long long)m, (long long)c, wide ? "wide" : "tall");
-    clk.reset();
-    PTTK_TRY(norms.alloc(std::max<int64_t>(q, 1)));
-    if (d_perm) cudaFree(d_perm);
-    d_perm = nullptr;
-    PTTK_CUDA(cudaMalloc(&d_perm, sizeof(int) * q));
-    PTTK_TRY(qrin.alloc(Mqr * q));
-    if (wide) {
-      dim3 tg((unsigned)((c + 31) / 32), (unsigned)((m + 31) / 32));
-      transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(cur, m, c, nullptr, qrin.p); pttk::count_launch();
-    } else {
-      PTTK_CUDA(cudaMemcpyAsync(qrin.p, cur, sizeof(double) * m * c, cudaMemcpyDeviceToDevice, s));
-    }
-    const int64_t nchunks = (Mqr + RC - 1) / RC;
-    PTTK_TRY(part.alloc(nchunks * q));
-    PTTK_TRY(wpart.alloc(nchunks * q));
-    PTTK_TRY(wv.alloc(q));
-    PTTK_TRY(below.alloc(q));
-    PTTK_TRY(R.alloc(q * q));
-    clk.mark(k, "layout");
-    // rows of R kept: the QR stops once the discarded block has ||R22||_F <= 0.03 delta. The
-    // tails below count ||R22||^2, so the error bound of the truncation holds as it is; only a
-    // tail within 9e-4 delta^2 of the threshold could give a rank one higher than the exact
-    // singular values would
-    int kq = 0;
-    double tail2 = 0.0;
-    const double stop = 0.03 * delta;
-    PTTK_TRY(householder_qrcp(qrin.p, Mqr, q, stop * stop, R.p, d_perm, part.p, below.p, wpart.p, wv.p, d_hs,
-                              &kq, &tail2, s));
-    clk.mark(k, "qr");
-    if (clk.on) fprintf(stderr, "pttk: tt-svd step %d kept %d of %lld rows of R, ||R22|| %.3e\n", k + 1, kq, (long long)q, sqrt(tail2));
-    // A = R1^T (q x kq), R1 = the kept rows of R in pivoted column order
-    PTTK_TRY(A.alloc(q * kq));
-    gather_rt_kernel<<<grid1d(q * kq, 256), 256, 0, s>>>(R.p, q, kq, d_perm, A.p); pttk::count_launch();
-    // one-sided Jacobi on R1^T: R1^T V = U' Sigma, so R1 = V Sigma U'^T and the right singular
-    // vectors of R1 (= of the pivoted QR input, up to the discarded R22) are the normalised
-    // columns of the rotated R1^T; columns below 1e-3 delta / sqrt(kq) together carry
-    // < 1e-6 delta^2, and pairs of them are skipped
-    PTTK_TRY(jacobi(A.p, q, kq, s, 1e-3 * delta / sqrt((double)kq)));
-    clk.mark(k, "jacobi");
-    colnorm_kernel<<<(unsigned)(((int64_t)kq * 32 + 255) / 256), 256, 0, s>>>(A.p, q, kq, norms.p); pttk::count_launch();
-    std::vector<double> sigma(kq);
-    PTTK_CUDA(cudaMemcpyAsync(sigma.data(), norms.p, sizeof(double) * kq, cudaMemcpyDeviceToHost, s));
-    PTTK_CUDA(cudaStreamSynchronize(s));
-    std::vector<int> perm;
-    const int r = truncation(sigma, delta, perm, tail2);
-    int* d_top = nullptr;
-    PTTK_CUDA(cudaMalloc(&d_top, sizeof(int) * std::max<int64_t>(kq, 1)));
-    struct TopGuard { int* p; ~TopGuard() { if (p) cudaFree(p); } } top_guard{d_top};
-    PTTK_CUDA(cudaMemcpyAsync(d_top, perm.data(), sizeof(int) * kq, cudaMemcpyHostToDevice, s));
-    // top-r right singular vectors (unit columns), in the pivoted order
-    PTTK_TRY(U.alloc(q * r));
-    PTTK_TRY(Y.alloc(q * r));
-    gather_cols_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(A.p, q, d_top, r, norms.p, Y.p); pttk::count_launch();
-    // back to the original order: row perm[l] of the result is row l of Y
-    scatter_rows_kernel<<<grid1d(q * r, 256), 256, 0, s>>>(Y.p, q, r, d_perm, U.p); pttk::count_launch();
-    double* basis = U.p;  // m x r (wide): left singular vectors of X
-    if (!wide) {
-      // tall: U holds the top right singular vectors of X (c x r); Y = X U spans the top-r
-      // left singular subspace
-      PTTK_TRY(Yt.alloc(m * r));
-      dgemm(false, false, m, r, c, 1.0, cur, m, U.p, c, 0.0, Yt.p, m, s);
-      basis = Yt.p;
-    }
-    // make the m x r basis orthonormal to working precision: its columns are orthogonal up
-    // to ~eps ||X|| / sigma_i, so one-sided Jacobi needs one or two sweeps
-    clk.mark(k, "basis");
-    PTTK_TRY(jacobi(basis, m, r, s));
-    clk.mark(k, "reorth");
-    {
-      Buf bn;
-      PTTK_TRY(bn.alloc(r));
-      colnorm_kernel<<<(unsigned)(((int64_t)r * 32 + 255) / 256), 256, 0, s>>>(basis, m, r, bn.p); pttk::count_launch();
-      std::vector<double> bnh(r);
-      PTTK_CUDA(cudaMemcpyAsync(bnh.data(), bn.p, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
-      PTTK_CUDA(cudaStreamSynchronize(s));
-      std::vector<int> bperm;
-      truncation(bnh, 0.0, bperm);
-      PTTK_CUDA(cudaMemcpyAsync(d_top, bperm.data(), sizeof(int) * r, cudaMemcpyHostToDevice, s));
-      PTTK_TRY(cores[k].alloc(m * r));
-      gather_cols_kernel<<<grid1d(m * r, 256), 256, 0, s>>>(basis, m, d_top, r, bn.p, cores[k].p); pttk::count_launch();
-      PTTK_CUDA(cudaStreamSynchronize(s));
-    }
+    int r = 0;
+    PTTK_TRY(svd_basis(cur, m, c, delta, wk, cores[k], &r, clk, k, s));
     // X <- G_k^T X  (r x c)
     dgemm(true, false, r, c, m, 1.0, cores[k].p, m, cur, m, 0.0, nxt, r, s);
     PTTK_CUDA(cudaGetLastError());
@@ -946,23 +985,64 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
   PTTK_TRY(cores[D - 1].alloc(r_prev * n));
   PTTK_CUDA(cudaMemcpyAsync(cores[D - 1].p, cur, sizeof(double) * r_prev * n,
                             cudaMemcpyDeviceToDevice, s));
+  return pack_cores(tt, cores, s);
+}
 
-  // pack into the handle
-  size_t off = 0;
+// TT-Round (Algorithm 1): right-to-left orthogonalisation, then a left-to-right sweep of
+// truncated SVDs with delta = tol / sqrt(D-1) ||X||_F. Each factorisation is svd_basis: with
+// delta = 0 for the orthogonalisation (an orthonormal basis of the whole range, in place of the
+// thin QR; any orthonormal factor serves), with delta for the truncation.
+pttk_status tt_round_run(const pttk_tt* in, double tol, pttk_tt* out, cudaStream_t s) {
+  const int D = in->D, n = in->n;
+  StageClock clk(s);
+  std::vector<Buf> G(D), nb(D);
+  std::vector<int64_t> r(D + 1);
+  for (int k = 0; k <= D; ++k) r[k] = in->ranks[k];
   for (int k = 0; k < D; ++k) {
-    tt->core_off[k] = off;
-    off += tt->core_elems(k);
+    PTTK_TRY(G[k].alloc(in->core_elems(k)));
+    PTTK_CUDA(cudaMemcpyAsync(G[k].p, in->cores64 + in->core_off[k], sizeof(double) * in->core_elems(k),
+                              cudaMemcpyDeviceToDevice, s));
   }
-  tt->core_total = off;
-  PTTK_CUDA(cudaMalloc(&tt->cores64, sizeof(double) * off));
-  PTTK_CUDA(cudaMalloc(&tt->cores32, sizeof(float) * off));
-  for (int k = 0; k < D; ++k)
-    PTTK_CUDA(cudaMemcpyAsync(tt->cores64 + tt->core_off[k], cores[k].p,
-                              sizeof(double) * tt->core_elems(k), cudaMemcpyDeviceToDevice, s));
-  cast_f32_kernel<<<grid1d((int64_t)off, 256), 256, 0, s>>>(tt->cores64, (int64_t)off, tt->cores32); pttk::count_launch();
-  PTTK_CUDA(cudaGetLastError());
-  PTTK_CUDA(cudaStreamSynchronize(s));
-  return PTTK_OK;
+  StepWork wk;
+  Buf A, W, T;
+  // right to left: (G_i^{1})^T = U W, G_i <- U^T, G_{i-1} <- G_{i-1} x_3 W^T
+  for (int i = D - 1; i >= 1; --i) {
+    const int64_t m = n * r[i + 1], c = r[i];
+    PTTK_TRY(A.alloc(m * c));
+    dim3 tg((unsigned)((m + 31) / 32), (unsigned)((c + 31) / 32));
+    transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(G[i].p, c, m, nullptr, A.p); pttk::count_launch();
+    int k = 0;
+    PTTK_TRY(svd_basis(A.p, m, c, 0.0, wk, nb[i], &k, clk, i, s));
+    PTTK_TRY(W.alloc((int64_t)k * c));
+    dgemm(true, false, k, c, m, 1.0, nb[i].p, m, A.p, m, 0.0, W.p, k, s);   // W = U^T A (k x c)
+    PTTK_TRY(G[i].alloc((int64_t)k * m));
+    dim3 tg2((unsigned)((k + 31) / 32), (unsigned)((m + 31) / 32));
+    transpose_kernel<<<tg2, dim3(32, 8), 0, s>>>(nb[i].p, m, k, nullptr, G[i].p); pttk::count_launch();
+    const int64_t mp = r[i - 1] * n;                                       // G_{i-1}^{2}: mp x c
+    PTTK_TRY(T.alloc(mp * k));
+    dgemm(false, true, mp, k, c, 1.0, G[i - 1].p, mp, W.p, k, 0.0, T.p, mp, s);
+    std::swap(G[i - 1].p, T.p);
+    r[i] = k;
+  }
+  double sumsq = 0.0;
+  PTTK_TRY(sumsq_host(G[0].p, r[0] * n * r[1], &sumsq, s));
+  const double delta = D > 1 ? tol / sqrt((double)(D - 1)) * sqrt(sumsq) : 0.0;
+  // left to right: G_i^{2} = U W (truncated), G_i <- U, G_{i+1} <- W x_1 G_{i+1}
+  for (int i = 0; i < D - 1; ++i) {
+    const int64_t m = r[i] * n, c = r[i + 1];
+    int k = 0;
+    PTTK_TRY(svd_basis(G[i].p, m, c, delta, wk, nb[i], &k, clk, i, s));
+    PTTK_TRY(W.alloc((int64_t)k * c));
+    dgemm(true, false, k, c, m, 1.0, nb[i].p, m, G[i].p, m, 0.0, W.p, k, s);
+    std::swap(G[i].p, nb[i].p);
+    const int64_t cn = n * r[i + 2];                                       // G_{i+1}^{1}: c x cn
+    PTTK_TRY(T.alloc((int64_t)k * cn));
+    dgemm(false, false, k, cn, c, 1.0, W.p, k, G[i + 1].p, c, 0.0, T.p, k, s);
+    std::swap(G[i + 1].p, T.p);
+    r[i + 1] = k;
+  }
+  for (int k = 0; k <= D; ++k) out->ranks[k] = (int)r[k];
+  return pack_cores(out, G, s);
 }
 
 // FP32 tensor -> FP64 work buffer

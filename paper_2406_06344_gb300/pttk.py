@@ -45,6 +45,7 @@ SIGNATURES = [
     ("pttk_tt_get_core", _int, [_vp, _int, _c_double_p]),
     ("pttk_tt_save", _int, [_vp, ctypes.c_char_p]),
     ("pttk_tt_load", _int, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
+    ("pttk_tt_round", _int, [_vp, ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
     ("pttk_tt_from_cores", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int, _c_int_p,
                                   _c_double_p, ctypes.POINTER(_vp)]),
     ("pttk_tt_free", None, [_vp]),
@@ -199,6 +200,13 @@ class TT:
                                          _dbl(_boxflat(theta_box)), n, r, packed.ctypes.data_as(_c_double_p),
                                          ctypes.byref(h)))
         return cls(h.value)
+
+    def round(self, tol: float, stream=None) -> "TT":
+        """pttk_tt_round: a new TT of the same tensor with ranks reduced to relative
+        Frobenius accuracy tol (Algorithm 1, TT-Round)."""
+        h = _vp()
+        _check(load().pttk_tt_round(self.handle, tol, _stream(stream), ctypes.byref(h)))
+        return TT(h.value)
 
     @classmethod
     def load(cls, path: str) -> "TT":

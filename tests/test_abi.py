@@ -131,3 +131,10 @@ def test_kernels_without_parameter_need_boxes_apart(so):
                                      1e-10, 0, None, ctypes.byref(h))
     assert touching == pttk.EINVAL and "apart" in so.pttk_last_error().decode()
     assert not h.value
+
+
+def test_round_rejects_bad_arguments(so):
+    from paper_2406_06344_gb300 import pttk
+    h = ctypes.c_void_p()
+    assert so.pttk_tt_round(None, 1e-6, None, ctypes.byref(h)) == pttk.EINVAL
+    assert not h.value

@@ -1,0 +1,67 @@
+"""TT-Round (Algorithm 1) on the GPU against the oracle's TT-Round.
+
+The GPU rounds in FP64 with the TT-SVD's factorisation (pivoted QR, one-sided Jacobi); the
+oracle with numpy's QR and SVD. Cores differ by rotations, so the tests compare ranks, the
+represented tensor and the instantiated K~.
+"""
+import numpy as np
+import pytest
+
+import oracle.pttk_oracle as o
+from paper_2406_06344_gb300 import workloads as W
+from tests.test_oracle_pins import tt_sum
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_06344_gb300 import pttk as P
+    P.load()
+    w = W.Workload("c2n8", W.MATERN32, 2, 1, 8, W.C2.src_box, W.C2.tgt_box, W.C2.theta_box, 2000, 4)
+    cores, ranks, _ = o.build_offline(w.kernel, w.d, w.dtheta, w.mode_boxes(), w.n, 1e-10)
+    return torch, P, w, cores, ranks
+
+
+def _from_cores(P, w, cores):
+    return P.TT.from_cores(w.kernel, w.d, w.src_box, w.tgt_box, w.dtheta, w.theta_box, w.n, cores)
+
+
+def test_round_undoes_rank_inflation(env):
+    torch, P, w, cores, ranks = env
+    S = tt_sum(cores, cores)                         # a TT of 2X with doubled ranks
+    tt = _from_cores(P, w, S)
+    rt = tt.round(1e-10)
+    _, oranks = o.tt_round(S, 1e-10)
+    # the original is itself truncated at 1e-10, so rounding 2X at 1e-10 may drop one more
+    # direction at the middle bonds (the oracle gives 52 where the TT-SVD kept 53)
+    assert rt.ranks == oranks
+    assert all(a <= b for a, b in zip(oranks, ranks))
+    X2 = 2.0 * o.tt_full(cores)
+    assert o.rel_fro(X2, o.tt_full(rt.cores())) <= 2e-10
+    # the rounded handle instantiates like the original, doubled
+    X, Y = W.sources(w, 300), W.targets(w, 200)
+    th = W.thetas(w, 1)[0]
+    U, M, V = P.instantiate(rt, th, torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"), "fp64")
+    rt.check()
+    Uo, Mo, Vo = o.instantiate(cores, w.d, w.dtheta, w.mode_boxes(), th, X, Y)
+    assert o.rel_fro(2 * Uo @ Mo @ Vo.T, U.cpu().numpy() @ M.cpu().numpy() @ V.cpu().numpy().T) <= 2e-10
+    rt.free()
+    tt.free()
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-7])
+def test_round_to_a_looser_tolerance(env, tol):
+    torch, P, w, cores, ranks = env
+    tt = _from_cores(P, w, cores)
+    rt = tt.round(tol)
+    _, oranks = o.tt_round(cores, tol)
+    assert rt.ranks == oranks
+    assert all(a <= b for a, b in zip(rt.ranks, ranks))
+    X = o.tt_full(cores)
+    assert o.rel_fro(X, o.tt_full(rt.cores())) <= tol
+    rt.free()
+    tt.free()

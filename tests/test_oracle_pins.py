@@ -405,3 +405,53 @@ def test_kernel_without_parameter_end_to_end():
         assert M.shape[0] == M.shape[1] and np.array_equal(M, np.eye(M.shape[0]))
         errs.append(o.rel_fro(K, U @ M @ V.T))
     assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-8
+
+
+# --- TT-Round (Algorithm 1) -------------------------------------------------------
+
+def tt_sum(a, b):
+    """Cores of the TT of X_a + X_b: concatenated end cores, block-diagonal middle cores."""
+    N = len(a)
+    out = []
+    for i, (A, B) in enumerate(zip(a, b)):
+        if i == 0:
+            out.append(np.concatenate([A, B], axis=2))
+        elif i == N - 1:
+            out.append(np.concatenate([A, B], axis=0))
+        else:
+            C = np.zeros((A.shape[0] + B.shape[0], A.shape[1], A.shape[2] + B.shape[2]))
+            C[:A.shape[0], :, :A.shape[2]] = A
+            C[A.shape[0]:, :, A.shape[2]:] = B
+            out.append(C)
+    return out
+
+
+def test_tt_round_undoes_rank_inflation():
+    # X + X has a TT with doubled ranks; rounding finds the ranks of X and the tensor 2X
+    rng = np.random.default_rng(21)
+    dims, ranks = (4, 5, 3, 6, 4), [1, 3, 4, 3, 2, 1]
+    G = _random_tt(dims, ranks, rng)
+    X = o.tt_full(G)
+    S = tt_sum(G, G)
+    assert [c.shape[2] for c in S][:-1] == [2 * r for r in ranks[1:-1]]
+    R, rr = o.tt_round(S, 1e-12)
+    assert rr == ranks
+    assert o.rel_fro(2 * X, o.tt_full(R)) < 1e-13
+    for g in R[:-1]:                                       # left-orthonormal cores
+        g2 = o.unfold2(g)
+        assert np.allclose(g2.T @ g2, np.eye(g2.shape[1]), atol=1e-12)
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-5])
+def test_tt_round_meets_its_tolerance(eps):
+    # a low-rank tensor plus small noise in TT format with inflated ranks: the rounded TT
+    # stays within eps of it and its ranks do not exceed the input's
+    rng = np.random.default_rng(22)
+    dims = (5, 4, 6, 5)
+    G = _random_tt(dims, [1, 2, 3, 2, 1], rng)
+    Nz = [0.01 * c for c in _random_tt(dims, [1, 4, 5, 3, 1], rng)]
+    S = tt_sum(G, Nz)
+    X = o.tt_full(S)
+    R, rr = o.tt_round(S, eps)
+    assert o.rel_fro(X, o.tt_full(R)) <= eps
+    assert all(a <= b for a, b in zip(rr, [1] + [c.shape[2] for c in S]))
