@@ -513,6 +513,38 @@ def run_extras(torch, P, W, o, w, tt, X32, Y32, wv, thetas, state, flush, ev):
                       "ms": 1000.0 * statistics.median(times), "dtheta": list(map(float, dth)),
                       "note": "wall time of the synchronous pttk_grad call (loss, dL/dtheta, dL/dX)"}
 
+    # TT-Round (Algorithm 1) of the d = 3 TT: to looser tolerances, and of its sum with itself
+    # (ranks doubled), back to 1e-10
+    rnd = {}
+    for tol_r in (1e-6, 1e-4):
+        a = ev()
+        rt = tt.round(tol_r)
+        b = ev()
+        torch.cuda.synchronize()
+        rnd[f"tol_{tol_r:g}"] = {"ms": a.elapsed_time(b), "ranks": rt.ranks}
+        rt.free()
+    blk = []
+    gcs = tt.cores()
+    for i, (A_, B_) in enumerate(zip(gcs, gcs)):
+        if i == 0:
+            blk.append(np.concatenate([A_, B_], axis=2))
+        elif i == len(gcs) - 1:
+            blk.append(np.concatenate([A_, B_], axis=0))
+        else:
+            Cb = np.zeros((A_.shape[0] * 2, A_.shape[1], A_.shape[2] * 2))
+            Cb[:A_.shape[0], :, :A_.shape[2]] = A_
+            Cb[A_.shape[0]:, :, A_.shape[2]:] = B_
+            blk.append(Cb)
+    ts = P.TT.from_cores(w.kernel, w.d, w.src_box, w.tgt_box, w.dtheta, w.theta_box, w.n, blk)
+    a = ev()
+    rt = ts.round(1e-10)
+    b = ev()
+    torch.cuda.synchronize()
+    rnd["sum_with_itself_tol_1e-10"] = {"ms": a.elapsed_time(b), "ranks_in": ts.ranks, "ranks": rt.ranks}
+    rt.free()
+    ts.free()
+    out["tt_round"] = rnd
+
     # the other kernels of the table at d = 3: grid + transform rate (FP64, FP32) and the TT
     kern = {}
     for kid in (W.EXPONENTIAL, W.MATERN52, W.MULTIQUADRIC, W.THIN_PLATE_SPLINE,
