@@ -118,6 +118,42 @@ def _biharmonic_power(kind, r, theta):
     return _orig["kernel_of_r"](kind, r, theta)
 
 
+def _tt_round_variant(cores, eps, r_update="RT", sqrt_d=True, orthogonalise=True, delta_first=False):
+    """The oracle's TT-Round with one step changed: the update of the left neighbour, the
+    sqrt(N-1) of the threshold, the orthogonalisation sweep, or the norm delta is taken from."""
+    G = [np.array(c, dtype=np.float64) for c in cores]
+    N = len(G)
+    norm_before = float(np.linalg.norm(G[0]))
+    if orthogonalise:
+        for i in range(N - 1, 0, -1):
+            r0, n, r1 = G[i].shape
+            Q, R = np.linalg.qr(o.unfold1(G[i]).T)
+            k = Q.shape[1]
+            G[i] = Q.T.reshape(k, n, r1, order="F")
+            a, m, _ = G[i - 1].shape
+            G[i - 1] = (o.unfold2(G[i - 1]) @ (R.T if r_update == "RT" else R)).reshape(a, m, k, order="F")
+    nrm = norm_before if delta_first else float(np.linalg.norm(G[0]))
+    delta = eps / (math.sqrt(N - 1) if sqrt_d else 1.0) * nrm
+    for i in range(N - 1):
+        r0, n, r1 = G[i].shape
+        U, s, Vt = np.linalg.svd(o.unfold2(G[i]), full_matrices=False)
+        r = o.truncation_rank(s, delta)
+        G[i] = U[:, :r].reshape(r0, n, r, order="F")
+        _, n2, r2 = G[i + 1].shape
+        G[i + 1] = ((s[:r, None] * Vt[:r]) @ o.unfold1(G[i + 1])).reshape(r, n2, r2, order="F")
+    return G, [1] + [g.shape[2] for g in G]
+
+
+def _round_with(**kw):
+    return lambda cores, eps: _tt_round_variant(cores, eps, **kw)
+
+
+_ROUND_PINS = [(pins.test_tt_round_undoes_rank_inflation, {}),
+               (pins.test_tt_round_meets_its_tolerance, {"eps": 1e-2}),
+               (pins.test_tt_round_matches_tt_svd_of_the_full_tensor, {"eps": 1e-3}),
+               (pins.test_tt_round_matches_tt_svd_of_the_full_tensor, {"eps": 1e-6})]
+
+
 # name -> (replacements, pins that should catch it as (function, kwargs))
 CASES = {
     "transform c_0 = 2": ({"cheb_transform_matrix": _transform_c0_two},
@@ -164,6 +200,11 @@ CASES = {
                                        [(pins.test_multiquadric_and_thin_plate_family_identities, {})]),
     "bi-harmonic as r^-1": ({"kernel_of_r": _biharmonic_power},
                             [(pins.test_multiquadric_and_thin_plate_family_identities, {})]),
+    "TT-Round: left neighbour times R, not R^T": ({"tt_round": _round_with(r_update="R")}, _ROUND_PINS),
+    "TT-Round: threshold without sqrt(N-1)": ({"tt_round": _round_with(sqrt_d=False)}, _ROUND_PINS),
+    "TT-Round: no orthogonalisation sweep": ({"tt_round": _round_with(orthogonalise=False)}, _ROUND_PINS),
+    "TT-Round: delta from the first core before the sweep": (
+        {"tt_round": _round_with(delta_first=True)}, _ROUND_PINS),
 }
 
 

@@ -455,3 +455,21 @@ def test_tt_round_meets_its_tolerance(eps):
     R, rr = o.tt_round(S, eps)
     assert o.rel_fro(X, o.tt_full(R)) <= eps
     assert all(a <= b for a, b in zip(rr, [1] + [c.shape[2] for c in S]))
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6])
+def test_tt_round_matches_tt_svd_of_the_full_tensor(eps):
+    # After the right-to-left orthogonalisation, the left-to-right sweep of TT-Round sees the
+    # singular values of the full tensor's unfoldings, as the TT-SVD does, and both cut at the
+    # same delta. So rounding a TT of X with inflated ranks gives the TT-SVD's ranks and error.
+    # Test tensor: 1/(1 + i1 + i2 + 1.3 i3 + i4 + i5), whose unfoldings decay gradually.
+    dims = (6, 5, 7, 6, 5)
+    idx = np.indices(dims)
+    X = 1.0 / (1.0 + idx.sum(axis=0) + 0.3 * idx[2])
+    G, ranks = o.tt_svd(X, eps)
+    E, _ = o.tt_svd(X, 1e-15)
+    S = tt_sum([E[0] / 3] + E[1:], [2 * E[0] / 3] + E[1:])        # X with doubled ranks
+    R, rr = o.tt_round(S, eps)
+    assert rr == ranks
+    e_svd, e_round = o.rel_fro(X, o.tt_full(G)), o.rel_fro(X, o.tt_full(R))
+    assert abs(e_svd - e_round) <= 1e-6 * e_svd
