@@ -38,6 +38,11 @@ Readings of the paper taken here (where the paper is silent, ambiguous or garble
       Gamma(l)); SE is exp(-(r/l)^2) without a factor 1/2 (Table kern-table).
   R6  Phase 3 of Algorithm 2 (the factor chain) runs per instantiation:
       instantiate(TT, theta, X, Y) -> (U, M, V) = (S, H(theta), T).
+  R7  PTTK-Global (Algorithm 4): the compression test compares with
+      S H(theta) T^T (the printed S H(theta) T lacks the transpose). The
+      eigenpairs kept are a prefix of the order |lambda_1| >= |lambda_2| >= ...
+      (negative eigenvalues removed first when the kernel is definite), the
+      shortest prefix that meets the test; all of them when none does.
 """
 from __future__ import annotations
 
@@ -488,3 +493,65 @@ def loss_grad(cores, d: int, dtheta: int, mode_boxes, theta, X, Y, w, z):
         Bi[i] = cheb_dvector(interval_map_inv(X[:, i], lo, hi), n) * (2.0 / (lo - hi))
         dX[:, i] = w * (source_factor(cores, d, Bi) @ g)
     return dtheta_out, dX
+
+
+# --- PTTK-Global (Algorithm 4, Section 3 "Global low-rank approximation") ----------------
+
+def global_offline(S: np.ndarray, T: np.ndarray):
+    """Offline stage of PTTK-Global (Algorithm 4): with X = Y and B_s = B_t, S = U(X) and
+    T = V(X) are the two factors of Algorithm 2 on the one point set; the thin QR
+    [S T] = Q R is stored. Returns (Q, R), Q: N x k orthonormal, R: k x (r_s + r_t)."""
+    Q, R = np.linalg.qr(np.hstack([S, T]), mode="reduced")
+    return Q, R
+
+
+def global_hhat(H: np.ndarray) -> np.ndarray:
+    """H^ of Eq. pttk1: the symmetric block matrix [[0, H/2], [H^T/2, 0]], so that
+    [S T] H^ [S T]^T = (S H T^T + T H^T S^T) / 2."""
+    rs, rt = H.shape
+    Hh = np.zeros((rs + rt, rs + rt))
+    Hh[:rs, rs:] = 0.5 * H
+    Hh[rs:, :rs] = 0.5 * H.T
+    return Hh
+
+
+def global_online(R: np.ndarray, H: np.ndarray, eps: float = 0.0, compress: bool = False,
+                  definite: bool = True):
+    """Online stage of PTTK-Global (Algorithm 4) for H = H(theta) (r_s x r_t).
+
+    Eigendecomposition R H^ R^T = U Lambda U^T, eigenpairs ordered by decreasing |lambda|;
+    for a definite kernel the negative eigenvalues are zeroed and their eigenvectors dropped
+    (the paper drops this step for indefinite kernels such as the Multiquadric).
+    Without compression: returns (None, W), W = U Lambda U^T (k x k), K ~= Q W Q^T.
+    With compression: keeps the shortest prefix of eigenpairs with
+    ||Q U^ Lambda^ (Q U^)^T - S H T^T||_F <= eps ||S H T^T||_F (reading R7; with Q orthonormal
+    and S H T^T = Q (R E R^T) Q^T, E = [[0, H], [0, 0]], both norms are taken on k x k
+    matrices); returns (U^, Lambda^) with K ~= (Q U^) Lambda^ (Q U^)^T."""
+    rs = H.shape[0]
+    lam, U = np.linalg.eigh(R @ global_hhat(H) @ R.T)
+    order = np.argsort(-np.abs(lam), kind="stable")
+    lam, U = lam[order], U[:, order]
+    if definite:
+        keep = lam > 0
+        lam, U = lam[keep], U[:, keep]
+    if not compress:
+        return None, U @ np.diag(lam) @ U.T
+    E = np.zeros((R.shape[1], R.shape[1]))
+    E[:rs, rs:] = H
+    target = R @ E @ R.T
+    bound = eps * np.linalg.norm(target)
+    m = len(lam)
+    for j in range(len(lam) + 1):
+        if np.linalg.norm(U[:, :j] @ np.diag(lam[:j]) @ U[:, :j].T - target) <= bound:
+            m = j
+            break
+    return U[:, :m], np.diag(lam[:m])
+
+
+def global_factors(S: np.ndarray, T: np.ndarray, H: np.ndarray, eps: float = 0.0,
+                   compress: bool = False, definite: bool = True):
+    """Both stages of Algorithm 4 on one point set: returns (Z, W) with K(X, X; theta) ~=
+    Z W Z^T; Z = Q (PTTK-Global-1, compress False) or Q U^ (PTTK-Global-2)."""
+    Q, R = global_offline(S, T)
+    Uh, W = global_online(R, H, eps, compress, definite)
+    return (Q if Uh is None else Q @ Uh), W

@@ -154,6 +154,34 @@ _ROUND_PINS = [(pins.test_tt_round_undoes_rank_inflation, {}),
                (pins.test_tt_round_matches_tt_svd_of_the_full_tensor, {"eps": 1e-6})]
 
 
+def _hhat_no_half(H):
+    return 2.0 * _orig["global_hhat"](H)
+
+
+def _hhat_h_twice(H):
+    rs, rt = H.shape
+    Hh = np.zeros((rs + rt, rs + rt))
+    Hh[:rs, rs:] = 0.5 * H
+    Hh[rs:, :rs] = 0.5 * H            # H where H^T belongs
+    return Hh
+
+
+def _global_keeps_negatives(R, H, eps=0.0, compress=False, definite=True):
+    return _orig["global_online"](R, H, eps, compress, False)
+
+
+def _global_one_term_short(R, H, eps=0.0, compress=False, definite=True):
+    Uh, W = _orig["global_online"](R, H, eps, compress, definite)
+    if Uh is None:
+        return Uh, W
+    return Uh[:, :-1], W[:-1, :-1]
+
+
+_GLOBAL_PINS = [(pins.test_global_1_is_the_psd_part_of_the_symmetric_part, {}),
+                (pins.test_global_2_keeps_the_fewest_terms, {"definite": True, "eps": 1e-3}),
+                (pins.test_global_2_keeps_the_fewest_terms, {"definite": False, "eps": 3e-2})]
+
+
 # name -> (replacements, pins that should catch it as (function, kwargs))
 CASES = {
     "transform c_0 = 2": ({"cheb_transform_matrix": _transform_c0_two},
@@ -205,6 +233,11 @@ CASES = {
     "TT-Round: no orthogonalisation sweep": ({"tt_round": _round_with(orthogonalise=False)}, _ROUND_PINS),
     "TT-Round: delta from the first core before the sweep": (
         {"tt_round": _round_with(delta_first=True)}, _ROUND_PINS),
+    "PTTK-Global: H^ without the 1/2": ({"global_hhat": _hhat_no_half}, _GLOBAL_PINS),
+    "PTTK-Global: H in place of H^T in H^": ({"global_hhat": _hhat_h_twice}, _GLOBAL_PINS),
+    "PTTK-Global: negative eigenvalues kept for a definite kernel": (
+        {"global_online": _global_keeps_negatives}, _GLOBAL_PINS),
+    "PTTK-Global: compression one term short": ({"global_online": _global_one_term_short}, _GLOBAL_PINS),
 }
 
 

@@ -473,3 +473,97 @@ def test_tt_round_matches_tt_svd_of_the_full_tensor(eps):
     assert rr == ranks
     e_svd, e_round = o.rel_fro(X, o.tt_full(G)), o.rel_fro(X, o.tt_full(R))
     assert abs(e_svd - e_round) <= 1e-6 * e_svd
+
+
+# --- PTTK-Global (Algorithm 4) --------------------------------------------------------------
+
+def test_global_1_is_the_psd_part_of_the_symmetric_part():
+    # Q W Q^T of PTTK-Global-1 is the symmetric part (S H T^T + T H^T S^T)/2 of the plain
+    # approximation with its negative eigenvalues set to zero; without that step (an indefinite
+    # kernel) it is the symmetric part itself. Checked against an eigendecomposition of the
+    # N x N matrix, a different and larger problem than the k x k one the oracle solves.
+    rng = np.random.default_rng(30)
+    N, rs, rt = 40, 5, 7
+    S, T, H = rng.standard_normal((N, rs)), rng.standard_normal((N, rt)), rng.standard_normal((rs, rt))
+    K1 = S @ H @ T.T
+    Ks = 0.5 * (K1 + K1.T)
+    lam, V = np.linalg.eigh(Ks)
+    assert lam.min() < -1e-3 * lam.max()                      # the case has negative eigenvalues
+    Kpsd = V @ np.diag(np.maximum(lam, 0.0)) @ V.T
+    Z, W = o.global_factors(S, T, H)
+    assert o.rel_fro(Kpsd, Z @ W @ Z.T) <= 1e-12
+    Z, W = o.global_factors(S, T, H, definite=False)
+    assert o.rel_fro(Ks, Z @ W @ Z.T) <= 1e-12
+    Q, R = o.global_offline(S, T)
+    assert np.allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-13)
+    assert o.rel_fro(np.hstack([S, T]), Q @ R) <= 1e-14
+
+
+@pytest.mark.parametrize("definite", [True, False])
+@pytest.mark.parametrize("eps", [3e-2, 1e-3])
+def test_global_2_keeps_the_fewest_terms(definite, eps):
+    # PTTK-Global-2 keeps the shortest prefix (by |lambda|) of eigenpairs of the symmetric part
+    # meeting ||Z W Z^T - S H T^T||_F <= eps ||S H T^T||_F. Brute force on the N x N matrices:
+    # for each m, the m largest eigenpairs of (S H T^T + T H^T S^T)/2 (the positive ones only
+    # for a definite kernel), and the error measured directly.
+    # S H T^T = F C F^T + 1e-4 F B F2^T: symmetric with a graded, partly negative spectrum, plus a
+    # small non-symmetric part, the structure of the kernel case
+    rng = np.random.default_rng(32)
+    N, rs, rt = 50, 6, 8
+    F = rng.standard_normal((N, rs))
+    Qc, _ = np.linalg.qr(rng.standard_normal((rs, rs)))
+    C = Qc @ np.diag([4.0, 2.0, -0.002, 1.0, 0.3, 0.05]) @ Qc.T
+    S, T = F, np.hstack([F, rng.standard_normal((N, rt - rs))])
+    H = np.hstack([C, 1e-4 * rng.standard_normal((rs, rt - rs))])
+    K1 = S @ H @ T.T
+    lam, V = np.linalg.eigh(0.5 * (K1 + K1.T))
+    order = np.argsort(-np.abs(lam), kind="stable")
+    lam, V = lam[order], V[:, order]
+    if definite:
+        lam, V = lam[lam > 0], V[:, lam > 0]
+    errs = [np.linalg.norm(V[:, :m] @ np.diag(lam[:m]) @ V[:, :m].T - K1) for m in range(len(lam) + 1)]
+    ok = [m for m, e in enumerate(errs) if e <= eps * np.linalg.norm(K1)]
+    m_brute = ok[0] if ok else len(lam)
+    assert 0 < m_brute < len(lam)                               # a real choice at this eps
+    Z, W = o.global_factors(S, T, H, eps, compress=True, definite=definite)
+    assert Z.shape[1] == m_brute
+    assert np.allclose(W, np.diag(np.diag(W)))                  # W = Lambda^, diagonal
+    assert abs(np.linalg.norm(Z @ W @ Z.T - K1) - errs[m_brute]) <= 1e-10 * np.linalg.norm(K1)
+    assert np.allclose(Z.T @ Z, np.eye(Z.shape[1]), atol=1e-12)  # Q U^ has orthonormal columns
+
+
+def _global_case(kind):
+    boxes = [(0.0, 1.0), (0.0, 1.0), (0.3, 1.4), (0.0, 1.0), (0.0, 1.0)]
+    cores, _, _ = o.build_offline(kind, 2, 1, boxes, 12, 1e-10)
+    X = np.random.default_rng(31).uniform(0.0, 1.0, (300, 2))
+    th = (0.7,)
+    S, H, T = o.instantiate(cores, 2, 1, boxes, th, X, X)
+    return S, H, T, o.kernel_matrix(kind, X, X, th)
+
+
+def test_global_on_the_squared_exponential_kernel():
+    # SE is positive definite: PTTK-Global-1 is symmetric positive semi-definite and as close to
+    # K as the plain interpolant S H T^T is (the symmetric PSD part can only move it closer)
+    S, H, T, K = _global_case(o.GAUSS)
+    plain = o.rel_fro(K, S @ H @ T.T)
+    Z, W = o.global_factors(S, T, H)
+    Kg = Z @ W @ Z.T
+    assert o.rel_fro(K, Kg) <= plain * (1 + 1e-9)
+    assert np.abs(Kg - Kg.T).max() <= 1e-14 * np.abs(Kg).max()
+    ev = np.linalg.eigvalsh(0.5 * (Kg + Kg.T))
+    assert ev.min() >= -1e-13 * ev.max()
+    # PTTK-Global-2 at eps = 1e-4: far fewer terms, within the tolerance of S H T^T
+    Z2, W2 = o.global_factors(S, T, H, 1e-4, compress=True)
+    assert Z2.shape[1] < Z.shape[1] // 4
+    assert o.rel_fro(S @ H @ T.T, Z2 @ W2 @ Z2.T) <= 1e-4
+
+
+def test_global_on_the_indefinite_multiquadric_kernel():
+    # The Multiquadric matrix is indefinite: zeroing negative eigenvalues loses > 10 % of it,
+    # and without that step PTTK-Global-1 is as accurate as the plain interpolant
+    S, H, T, K = _global_case(o.MULTIQUADRIC)
+    plain = o.rel_fro(K, S @ H @ T.T)
+    Z, W = o.global_factors(S, T, H, definite=False)
+    assert o.rel_fro(K, Z @ W @ Z.T) <= plain * (1 + 1e-6)
+    Z, W = o.global_factors(S, T, H, definite=True)
+    assert o.rel_fro(K, Z @ W @ Z.T) >= 0.1
