@@ -184,6 +184,60 @@ pttk_status pttk_tt_from_cores(pttk_kernel kernel, int d, const double* src_box,
 /* Release a handle and its device memory (NULL is a no-op). */
 void pttk_tt_free(pttk_tt* tt);
 
+/* ---- PTTK-Global (Algorithm 4, Section 3 "Global low-rank approximation") ------------------
+ * The global case: one point set X in one box (source box = target box) and a kernel symmetric
+ * in its arguments. K(X, X; theta) ~= Z W Z^T with W symmetric, positive semi-definite when
+ * the negative eigenvalues are dropped (a definite kernel). */
+typedef struct pttk_global pttk_global;
+
+/* Offline stage of Algorithm 4. S = U(X) and T = V(X) come from the FP64 factor chains of
+ * Algorithm 2 (Phase 3) on the one point set. Then the thin QR [S T] = Q R:
+ *   - Q: N x k with orthonormal columns, k <= r_s + r_t (r_s = r_d, r_t = r_{d+d_theta});
+ *   - R = Q^T [S T], k x (r_s + r_t).
+ * Q is an orthonormal basis of the range of [S T], computed with the pivoted Householder QR
+ * and one-sided Jacobi of the TT-SVD. R need not be triangular: any pair with orthonormal Q
+ * and Q R = [S T] gives the same Q R H^ R^T Q^T, which is all the method uses.
+ *   tt: a handle whose source and target boxes are equal (else PTTK_EINVAL). It may be freed
+ *       afterwards: the new handle keeps its own copy of the cores.
+ *   X:  dev, N x d row-major doubles, N >= 1, points inside the box.
+ * Synchronises `stream`. The handle holds Q (8 N k bytes) and R. The call needs scratch of
+ * about five N x (r_s + r_t) doubles.
+ * Errors: PTTK_EINVAL, PTTK_ENOMEM, PTTK_ENOTSUP (ranks too large for the FP64 chain),
+ * PTTK_ECUDA, PTTK_ETIMEOUT. */
+pttk_status pttk_global_create(const pttk_tt* tt, const double* X, int64_t N, void* stream,
+                               pttk_global** out);
+
+/* N, k (columns of Q), r_s and r_t of a handle. Any output pointer may be NULL. */
+pttk_status pttk_global_dims(const pttk_global* g, int64_t* N, int* k, int* r_s, int* r_t);
+
+/* Copies Q (N x k, row-major doubles) into the caller's device buffer Q, asynchronously on
+ * `stream`. */
+pttk_status pttk_global_get_q(const pttk_global* g, double* Q, void* stream);
+
+/* Copies R (k x (r_s + r_t), column-major doubles) into host memory. Synchronous. */
+pttk_status pttk_global_get_r(const pttk_global* g, double* R_host);
+
+/* Online stage of Algorithm 4 at theta (host [d_theta], inside its box, else PTTK_EDOMAIN).
+ * First H = H(theta), then the eigendecomposition R H^ R^T = U Lambda U^T, where
+ * H^ = [[0, H/2], [H^T/2, 0]] (Eq. pttk1). Eigenpairs are taken in order of decreasing
+ * |lambda|.
+ *   definite = 1: negative eigenvalues are dropped (a positive definite kernel).
+ *   definite = 0: they are kept (an indefinite kernel such as the Multiquadric).
+ *   compress = 0 (PTTK-Global-1): W (dev, k x k doubles) = U Lambda U^T and *rank = k.
+ *     K ~= Q W Q^T, with Q from pttk_global_get_q. Z is not used and may be NULL.
+ *   compress = 1 (PTTK-Global-2): keeps the fewest leading eigenpairs such that
+ *     ||Z W Z^T - S H T^T||_F <= eps ||S H T^T||_F, or all of them when no prefix meets it.
+ *     Z (dev, N x rank, row-major; capacity N x k) = Q U^.
+ *     W (dev, rank x rank; capacity k x k) = diag(lambda^). *rank = the terms kept.
+ * eps in [0, 1). FP64 throughout. Synchronises `stream`.
+ * Errors: PTTK_EINVAL, PTTK_EDOMAIN, PTTK_ENOMEM, PTTK_ECUDA, PTTK_ETIMEOUT (a bounded grid
+ * barrier of the Jacobi eigensolver ran out). */
+pttk_status pttk_global_instantiate(const pttk_global* g, const double* theta, double eps, int compress,
+                                    int definite, double* Z, double* W, int* rank, void* stream);
+
+/* Release a handle and its device memory (NULL is a no-op). */
+void pttk_global_free(pttk_global* g);
+
 /* ---- online stage ------------------------------------------------------------------ */
 
 /* Core matrix H(theta) = H_1(theta_1) ... H_{d_theta}(theta_{d_theta}),

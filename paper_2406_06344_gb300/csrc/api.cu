@@ -167,7 +167,7 @@ static pttk_status from_work(pttk_tt_ext* t, double* X, double tol, cudaStream_t
   return PTTK_OK;
 }
 
-static pttk_status theta_hat(const pttk_tt* tt, const double* theta, double* th) {
+pttk_status theta_hat(const pttk_tt* tt, const double* theta, double* th) {
   if (!theta && tt->dtheta > 0) return set_error(PTTK_EINVAL, "NULL theta");
   for (int j = 0; j < tt->dtheta; ++j) {
     const double lo = tt->box[tt->d + j][0], hi = tt->box[tt->d + j][1];

@@ -72,6 +72,11 @@ struct ProfScope {
 };
 #define PTTK_PROF(name, stream) pttk::ProfScope pttk_prof_scope__(name, stream)
 
+// --- api.cu ----------------------------------------------------------------------------
+// theta -> theta_hat (the inverse of the printed interval map) per parameter; PTTK_EDOMAIN when
+// theta lies outside its box beyond a relative slack of 1e-12.
+pttk_status theta_hat(const pttk_tt* tt, const double* theta, double* th);
+
 // --- grid.cu ---------------------------------------------------------------------------
 pttk_status grid_coeffs_launch(int kernel, int d, int dtheta, int n, const double (*box)[2],
                                bool fp64, void* C, cudaStream_t s);
@@ -82,6 +87,10 @@ pttk_status grid_coeffs_launch(int kernel, int d, int dtheta, int n, const doubl
 pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s);
 pttk_status tt_round_run(const pttk_tt* in, double tol, pttk_tt* out, cudaStream_t s);
 pttk_status widen_to_f64(const float* in, int64_t n, double* out, cudaStream_t s);
+// Orthonormal basis (allocated here, m x r column-major) of the range of X (m x c, column-major).
+pttk_status range_basis(const double* X, int64_t m, int64_t c, double** basis, int* r, cudaStream_t s);
+// One-sided Jacobi on the columns of A (rows x ncols, column-major), in place.
+pttk_status jacobi_columns(double* A, int64_t rows, int ncols, cudaStream_t s);
 
 // FP64 column-major GEMM: C[M x N] = alpha * op(A) * op(B) + beta * C.
 void dgemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,

@@ -1045,6 +1045,25 @@ pttk_status tt_round_run(const pttk_tt* in, double tol, pttk_tt* out, cudaStream
   return pack_cores(out, G, s);
 }
 
+// Orthonormal basis of the range of X (m x c, column-major, not modified): svd_basis with
+// delta = 0. *basis is allocated here (cudaMalloc, m x r column-major, r <= min(m, c)); the
+// caller frees it with cudaFree. Synchronises `s`.
+pttk_status range_basis(const double* X, int64_t m, int64_t c, double** basis, int* r, cudaStream_t s) {
+  StageClock clk(s);
+  StepWork wk;
+  Buf core;
+  PTTK_TRY(svd_basis(X, m, c, 0.0, wk, core, r, clk, 0, s));
+  *basis = core.p;
+  core.p = nullptr;
+  return PTTK_OK;
+}
+
+// One-sided Jacobi on the columns of A (rows x ncols, column-major), in place: on return the
+// columns are orthogonal, A V = U Sigma. Synchronises `s`.
+pttk_status jacobi_columns(double* A, int64_t rows, int ncols, cudaStream_t s) {
+  return jacobi(A, rows, ncols, s, 0.0);
+}
+
 // FP32 tensor -> FP64 work buffer
 pttk_status widen_to_f64(const float* in, int64_t n, double* out, cudaStream_t s) {
   widen_f32_kernel<<<grid1d(n, 256), 256, 0, s>>>(in, n, out); pttk::count_launch();

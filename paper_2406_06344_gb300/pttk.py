@@ -69,6 +69,12 @@ SIGNATURES = [
     ("pttk_profile_names", _int, [ctypes.c_char_p, _i64]),
     ("pttk_launch_count", _i64, []),
     ("pttk_selftest_wait_timeout", _int, [_vp]),
+    ("pttk_global_create", _int, [_vp, _vp, _i64, _vp, ctypes.POINTER(_vp)]),
+    ("pttk_global_dims", _int, [_vp, ctypes.POINTER(_i64), _c_int_p, _c_int_p, _c_int_p]),
+    ("pttk_global_get_q", _int, [_vp, _vp, _vp]),
+    ("pttk_global_get_r", _int, [_vp, _c_double_p]),
+    ("pttk_global_instantiate", _int, [_vp, _c_double_p, ctypes.c_double, _int, _int, _vp, _vp, _c_int_p, _vp]),
+    ("pttk_global_free", None, [_vp]),
 ]
 
 _lib = None
@@ -409,6 +415,78 @@ class Batch:
         if getattr(self, "_h", None):
             load().pttk_batch_free(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Global:
+    """PTTK-Global (Algorithm 4) on one point set X (source box = target box): owns a
+    pttk_global handle holding Q and R of the thin QR of [S T] = [U(X) V(X)]."""
+
+    def __init__(self, tt: TT, X, stream=None):
+        import torch
+        d = tt.dims[0]
+        if X.dtype != torch.float64 or X.dim() != 2 or X.shape[1] != d:
+            raise ValueError(f"points must be (N, {d}) float64")
+        h = _vp()
+        _check(load().pttk_global_create(tt.handle, _ptr(X), X.shape[0], _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("PTTK-Global handle already freed")
+        return self._h
+
+    @property
+    def dims(self):
+        """(N, k, r_s, r_t): points, columns of Q, columns of S and of T."""
+        N, k, rs, rt = _i64(), _int(), _int(), _int()
+        _check(load().pttk_global_dims(self.handle, ctypes.byref(N), ctypes.byref(k), ctypes.byref(rs),
+                                       ctypes.byref(rt)))
+        return N.value, k.value, rs.value, rt.value
+
+    def Q(self, stream=None):
+        """Q (N x k float64 CUDA tensor, orthonormal columns)."""
+        import torch
+        N, k, _, _ = self.dims
+        Q = torch.empty(N, k, dtype=torch.float64, device="cuda")
+        _check(load().pttk_global_get_q(self.handle, _ptr(Q), _stream(stream)))
+        return Q
+
+    def R(self) -> np.ndarray:
+        """R = Q^T [S T] (k x (r_s + r_t)) as a numpy array."""
+        _, k, rs, rt = self.dims
+        buf = np.empty(k * (rs + rt), dtype=np.float64)
+        _check(load().pttk_global_get_r(self.handle, buf.ctypes.data_as(_c_double_p)))
+        return buf.reshape(k, rs + rt, order="F")
+
+    def instantiate(self, theta, eps: float = 0.0, compress: bool = False, definite: bool = True,
+                    stream=None):
+        """pttk_global_instantiate: returns (Z, W) with K(X, X; theta) ~= Z W Z^T.
+        PTTK-Global-1 (compress False): Z = Q (N x k), W = U Lambda U^T (k x k).
+        PTTK-Global-2 (compress True): Z = Q U^ (N x rank), W = diag(lambda^) (rank x rank)."""
+        import torch
+        N, k, _, _ = self.dims
+        W = torch.empty(k * k, dtype=torch.float64, device="cuda")
+        Z = torch.empty(N * k, dtype=torch.float64, device="cuda") if compress else None
+        rank = _int()
+        _check(load().pttk_global_instantiate(self.handle, _dbl(theta), float(eps), 1 if compress else 0,
+                                              1 if definite else 0, _ptr(Z), _ptr(W), ctypes.byref(rank),
+                                              _stream(stream)))
+        r = rank.value
+        if not compress:
+            return self.Q(stream), W.view(k, k)
+        return Z[:N * r].view(N, r), W[:r * r].view(r, r)
+
+    def free(self):
+        if self._h:
+            load().pttk_global_free(self._h)
+            self._h = _vp()
 
     def __del__(self):
         try:

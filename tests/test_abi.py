@@ -138,3 +138,17 @@ def test_round_rejects_bad_arguments(so):
     h = ctypes.c_void_p()
     assert so.pttk_tt_round(None, 1e-6, None, ctypes.byref(h)) == pttk.EINVAL
     assert not h.value
+
+
+def test_global_rejects_bad_arguments_without_touching_the_device(so):
+    from paper_2406_06344_gb300 import pttk
+    h = ctypes.c_void_p()
+    assert so.pttk_global_create(None, None, 10, None, ctypes.byref(h)) == pttk.EINVAL
+    assert not h.value
+    N, k = ctypes.c_int64(), ctypes.c_int()
+    assert so.pttk_global_dims(None, ctypes.byref(N), ctypes.byref(k), None, None) == pttk.EINVAL
+    assert so.pttk_global_get_q(None, None, None) == pttk.EINVAL
+    assert so.pttk_global_get_r(None, None) == pttk.EINVAL
+    r = ctypes.c_int()
+    assert so.pttk_global_instantiate(None, None, 0.0, 0, 1, None, None, ctypes.byref(r), None) == pttk.EINVAL
+    so.pttk_global_free(None)  # no-op
