@@ -119,6 +119,26 @@ __global__ void __launch_bounds__(1024) sumsq_block_kernel(const double* __restr
   if (threadIdx.x == 0) *out = part[0];
 }
 
+// *out = ||(C - C^T) / 2||_F^2 (C: k x k, column-major), one block of 1024 threads
+__global__ void __launch_bounds__(1024) asym_sumsq_block_kernel(const double* __restrict__ C, int k,
+                                                                double* __restrict__ out) {
+  __shared__ double part[1024];
+  double acc = 0.0;
+  const int64_t total = (int64_t)k * k;
+  for (int64_t e = threadIdx.x; e < total; e += 1024) {
+    const int i = (int)(e % k), j = (int)(e / k);
+    const double a = 0.5 * (C[e] - C[j + (int64_t)i * k]);
+    acc = fma(a, a, acc);
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = part[0];
+}
+
 // norms[c] = ||A[:, c]||_2 (rows x ncols, column-major), one warp per column
 __global__ void col_norms_kernel(const double* __restrict__ A, int64_t rows, int ncols,
                                  double* __restrict__ norms) {
@@ -221,17 +241,20 @@ static pttk_status global_online_run(const pttk_global* g, const double* th, dou
   PTTK_TRY(C1.alloc((size_t)k * k));
   PTTK_TRY(B.alloc((size_t)k * k));
   PTTK_TRY(nrm.alloc(k));
-  PTTK_TRY(t2d.alloc(1));
+  PTTK_TRY(t2d.alloc(2));
   PTTK_TRY(theta_core_run(&g->tt, th, true, H.p, s));  // H(theta), rs x rt row-major
   // P = R_s H (k x rt); H row-major is H^T column-major with leading dimension rt
   dgemm(false, true, k, rt, rs, 1.0, g->R, k, H.p, rt, 0.0, P.p, k, s);
   // C1 = P R_t^T (k x k) = R E R^T, E = [[0, H], [0, 0]]: Q C1 Q^T = S H T^T
   dgemm(false, true, k, k, rt, 1.0, P.p, k, g->R + (size_t)k * rs, k, 0.0, C1.p, k, s);
+  // ||C1||_F^2 and ||(C1 - C1^T)/2||_F^2
   sumsq_block_kernel<<<1, 1024, 0, s>>>(C1.p, (int64_t)k * k, t2d.p); pttk::count_launch();
+  asym_sumsq_block_kernel<<<1, 1024, 0, s>>>(C1.p, k, t2d.p + 1); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
-  double t2 = 0.0;
-  PTTK_CUDA(cudaMemcpyAsync(&t2, t2d.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  double t2a[2] = {0.0, 0.0};
+  PTTK_CUDA(cudaMemcpyAsync(t2a, t2d.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   PTTK_CUDA(cudaStreamSynchronize(s));
+  const double t2 = t2a[0], a2 = t2a[1];
   if (!(t2 > 0.0)) {
     // S H T^T = 0: W = 0 (Global-1) or no term (Global-2)
     if (!compress) PTTK_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)k * k, s));
@@ -262,16 +285,22 @@ static pttk_status global_online_run(const pttk_global* g, const double* th, dou
     if (!definite || lam[i] > 0.0) kept.push_back(i);
   int m = (int)kept.size();
   if (compress) {
-    // ||Q U_j Lambda_j U_j^T Q^T - S H T^T||_F^2 = ||C1||_F^2 - sum_{i < j} lambda_i^2: the
-    // eigen-part is the orthogonal projection of C1 onto span{u_i u_i^T, i < j}
+    // ||Q U_j Lambda_j U_j^T Q^T - S H T^T||_F^2 = ||C1 - U_j Lambda_j U_j^T||_F^2
+    //   = ||(C1 - C1^T)/2||_F^2 + (sum of lambda_i^2 over the eigenpairs not kept),
+    // the symmetric and antisymmetric parts being orthogonal. Summed from the discarded terms
+    // themselves: ||C1||^2 - (sum of the kept lambda^2) would cancel, and the eigenvalues carry
+    // an absolute error of order 1e-14 ||C1||_F (they are singular values of sym(C1) + c I,
+    // minus c), which in the large kept terms alone exceeds eps^2 ||C1||^2 for eps <= 1e-6.
     const double bound2 = eps * eps * t2;
-    double kept2 = 0.0;
+    double excl2 = 0.0;  // eigenvalues not eligible: the negative ones of a definite kernel
+    if (definite)
+      for (int i = 0; i < k; ++i)
+        if (!(lam[i] > 0.0)) excl2 += lam[i] * lam[i];
+    std::vector<double> tail(kept.size() + 1, 0.0);  // tail[j] = sum over kept[j..] of lambda^2
+    for (int q = (int)kept.size() - 1; q >= 0; --q) tail[q] = tail[q + 1] + lam[kept[q]] * lam[kept[q]];
     int j = 0;
-    for (; j <= (int)kept.size(); ++j) {
-      if (std::max(t2 - kept2, 0.0) <= bound2) break;
-      if (j < (int)kept.size()) kept2 += lam[kept[j]] * lam[kept[j]];
-    }
-    m = std::min(j, (int)kept.size());
+    while (j < (int)kept.size() && a2 + excl2 + tail[j] > bound2) ++j;
+    m = j;
   }
   *rank = compress ? m : k;
   if (m == 0) {
