@@ -114,6 +114,35 @@ def test_global_needs_one_box(env):
     tt.free()
 
 
+@pytest.mark.parametrize("N", [1, 100])
+def test_global_small_point_sets(env, N):
+    # fewer points than columns of [S T] (r_s + r_t = 280): Q is N x N and [S T] is wide
+    torch, P, _, cases = env
+    cores, _ = cases[o.GAUSS]
+    X = np.random.default_rng(42).uniform(0.0, 1.0, (N, 2))
+    tt = P.TT.from_cores(o.GAUSS, 2, BOXES2[:2], BOXES2[3:], 1, BOXES2[2:3], 12, cores)
+    g = P.Global(tt, torch.tensor(X, device="cuda"))
+    tt.free()
+    n_, k, rs, rt = g.dims
+    assert n_ == N and k == min(N, rs + rt)
+    S, H, T = _oracle(cores, X, (0.8,))
+    Zo, Wo = o.global_factors(S, T, H)
+    Z, W = g.instantiate((0.8,))
+    Kg = (Z @ W @ Z.T).cpu().numpy()
+    assert o.rel_fro(Zo @ Wo @ Zo.T, Kg) <= 1e-10
+    g.free()
+
+
+def test_global_needs_a_point(env):
+    torch, P, _, cases = env
+    cores, _ = cases[o.GAUSS]
+    tt = P.TT.from_cores(o.GAUSS, 2, BOXES2[:2], BOXES2[3:], 1, BOXES2[2:3], 12, cores)
+    with pytest.raises(P.PttkError) as ei:
+        P.Global(tt, torch.empty(0, 2, dtype=torch.float64, device="cuda"))
+    assert ei.value.status == P.EINVAL
+    tt.free()
+
+
 def test_global_full_size_sampled(env):
     # the paper's synthetic setting in d = 3 (SE kernel, B_s = B_t = [0,1]^3,
     # l in [0.2 sqrt(3), sqrt(3)], N = 1e5, TT tol 1e-5) with n = 12 nodes per mode: Q is 1e5 x 828.
