@@ -238,6 +238,14 @@ pttk_status pttk_global_instantiate(const pttk_global* g, const double* theta, d
 /* Release a handle and its device memory (NULL is a no-op). */
 void pttk_global_free(pttk_global* g);
 
+/* ---- random numbers of the TT greedy-cross (Algorithms 5-7) ----------------------------
+ * The greedy-cross draws random index vectors, sample sets, a row-or-column bit and check
+ * points. They all come from SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) in counter-based
+ * form, so that two implementations draw the same numbers. Returns output number `counter`
+ * (0-based) of the stream seeded with `key`: the state key + (counter + 1) * 0x9E3779B97F4A7C15
+ * through the variant-13 mix. Pure host function: no device, no error. */
+uint64_t pttk_splitmix64(uint64_t key, uint64_t counter);
+
 /* ---- online stage ------------------------------------------------------------------ */
 
 /* Core matrix H(theta) = H_1(theta_1) ... H_{d_theta}(theta_{d_theta}),

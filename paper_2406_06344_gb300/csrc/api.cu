@@ -487,6 +487,8 @@ pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void*
                          static_cast<float*>(U), static_cast<float*>(V), t->dstatus, 0, s);
 }
 
+uint64_t pttk_splitmix64(uint64_t key, uint64_t counter) { return splitmix64(key, counter); }
+
 pttk_status pttk_tt_check(const pttk_tt* tt, void* stream) {
   clear_error();
   if (!tt) return set_error(PTTK_EINVAL, "NULL handle");

@@ -72,6 +72,17 @@ struct ProfScope {
 };
 #define PTTK_PROF(name, stream) pttk::ProfScope pttk_prof_scope__(name, stream)
 
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) in counter-based form: output number
+// `counter` (0-based) of the stream seeded with `key`, i.e. the state after counter + 1
+// increments by the golden gamma, through the variant-13 mix. The TT greedy-cross draws all of
+// its random numbers from it.
+__host__ __device__ inline uint64_t splitmix64(uint64_t key, uint64_t counter) {
+  uint64_t z = key + (counter + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 // --- api.cu ----------------------------------------------------------------------------
 // theta -> theta_hat (the inverse of the printed interval map) per parameter; PTTK_EDOMAIN when
 // theta lies outside its box beyond a relative slack of 1e-12.

@@ -75,6 +75,7 @@ SIGNATURES = [
     ("pttk_global_get_r", _int, [_vp, _c_double_p]),
     ("pttk_global_instantiate", _int, [_vp, _c_double_p, ctypes.c_double, _int, _int, _vp, _vp, _c_int_p, _vp]),
     ("pttk_global_free", None, [_vp]),
+    ("pttk_splitmix64", ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
 ]
 
 _lib = None
@@ -502,6 +503,11 @@ def apply_noalloc(U, M, V, w, out, stream=None):
     _check(load().pttk_apply_noalloc(_ptr(U), _ptr(M), _ptr(V), U.shape[0], V.shape[0], U.shape[1],
                                      V.shape[1], prec, _ptr(w), _ptr(out), _stream(stream)))
     return out
+
+
+def splitmix64(key: int, counter: int) -> int:
+    """pttk_splitmix64: output `counter` of the SplitMix64 stream seeded with `key`."""
+    return int(load().pttk_splitmix64(key & ((1 << 64) - 1), counter & ((1 << 64) - 1)))
 
 
 def profile_enable(on: bool = True):

@@ -152,3 +152,19 @@ def test_global_rejects_bad_arguments_without_touching_the_device(so):
     r = ctypes.c_int()
     assert so.pttk_global_instantiate(None, None, 0.0, 0, 1, None, None, ctypes.byref(r), None) == pttk.EINVAL
     so.pttk_global_free(None)  # no-op
+
+
+def test_splitmix64_is_the_published_generator_and_the_oracles(so):
+    # host-only entry point: the library's stream equals the reference outputs and the
+    # oracle's generator, so both sides of the TT greedy-cross draw the same numbers
+    import json
+    import numpy as np
+    from oracle import pttk_cross as x
+    from paper_2406_06344_gb300 import pttk
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "splitmix64.json")))["outputs"]
+    for seed, outs in g.items():
+        for c, v in enumerate(outs):
+            assert pttk.splitmix64(int(seed), c) == int(v, 0)
+    rng = np.random.default_rng(60)
+    for key, c in zip(rng.integers(0, 2**63, 50, dtype=np.int64), rng.integers(0, 2**40, 50, dtype=np.int64)):
+        assert pttk.splitmix64(int(key), int(c)) == x.splitmix64(int(key), int(c))
