@@ -122,6 +122,20 @@ pttk_status pttk_grid_coeffs(pttk_kernel kernel, int d, const double* src_box,
                              const double* tgt_box, int d_theta, const double* theta_box, int n,
                              pttk_prec grid_prec, void* C, void* stream);
 
+/* Entries of the grid tensor M (Eq. mdc) at given multi-indices, without the grid: the entry
+ * access the TT greedy-cross (Algorithms 5-7) works from.
+ *   out[e] = f_kappa(eta^(1)_{idx[e,0]}, ..., eta^(D)_{idx[e,D-1]}), variables in the order
+ *   (x, theta, y) of Eq. fkappa, eta^(j) the Chebyshev nodes of mode j mapped to its box.
+ *   idx: dev, M x D row-major int32, each in [0, n) (0-based node index).
+ *   out: dev, M entries (double for PTTK_FP64, float for PTTK_FP32).
+ *   Kernel, boxes and n as for pttk_grid_coeffs, except that n^D may exceed 4e9 (no grid is
+ *   formed).
+ * An index outside [0, n) writes NaN for that entry and returns PTTK_EINVAL; no node is read
+ * with it. M = 0 is a no-op. Synchronises `stream`. */
+pttk_status pttk_grid_entries(pttk_kernel kernel, int d, const double* src_box,
+                              const double* tgt_box, int d_theta, const double* theta_box, int n,
+                              const int32_t* idx, int64_t M, pttk_prec prec, void* out, void* stream);
+
 /* TT-SVD of a coefficient tensor (Section 2.3; Oseledets 2011, Algorithm 1) with the
  * truncation threshold delta = tol / sqrt(D-1) * ||C||_F of Algorithm 1 (TT-Round):
  * r_k is the smallest r >= 1 whose discarded singular values satisfy

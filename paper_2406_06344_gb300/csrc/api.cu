@@ -103,7 +103,7 @@ static void free_handle(pttk_tt_ext* t) {
 }
 
 static pttk_status check_problem(int kernel, int d, const double* src_box, const double* tgt_box,
-                                 int d_theta, const double* theta_box, int n) {
+                                 int d_theta, const double* theta_box, int n, bool whole_grid = true) {
   if (kernel < PTTK_GAUSS || kernel > PTTK_THIN_PLATE) return set_error(PTTK_EINVAL, "unknown kernel");
   if (d < 1 || d > 3) return set_error(PTTK_EINVAL, "d must be 1, 2 or 3");
   const int need_dth = kernel_dtheta(kernel);
@@ -129,7 +129,7 @@ static pttk_status check_problem(int kernel, int d, const double* src_box, const
     return set_error(PTTK_EINVAL, "nu box must be positive");
   double prod = 1.0;
   for (int j = 0; j < 2 * d + d_theta; ++j) prod *= n;
-  if (prod > 4e9) return set_error(PTTK_EINVAL, "n^D above 4e9 entries");
+  if (whole_grid && prod > 4e9) return set_error(PTTK_EINVAL, "n^D above 4e9 entries");
   return PTTK_OK;
 }
 
@@ -204,6 +204,36 @@ pttk_status pttk_grid_coeffs(pttk_kernel kernel, int d, const double* src_box,
   fill_meta(&meta, kernel, d, src_box, tgt_box, d_theta, theta_box, n);
   return grid_coeffs_launch(kernel, d, d_theta, n, meta.box, grid_prec == PTTK_FP64, C,
                             as_stream(stream));
+}
+
+pttk_status pttk_grid_entries(pttk_kernel kernel, int d, const double* src_box,
+                              const double* tgt_box, int d_theta, const double* theta_box, int n,
+                              const int32_t* idx, int64_t M, pttk_prec prec, void* out, void* stream) {
+  clear_error();
+  PTTK_TRY(check_problem(kernel, d, src_box, tgt_box, d_theta, theta_box, n, false));
+  if (prec != PTTK_FP64 && prec != PTTK_FP32) return set_error(PTTK_EINVAL, "entry precision must be FP64 or FP32");
+  if (M < 0) return set_error(PTTK_EINVAL, "negative entry count");
+  if (M > 0 && (!idx || !out)) return set_error(PTTK_EINVAL, "NULL index or output buffer");
+  if (M == 0) return PTTK_OK;
+  pttk_tt meta;
+  fill_meta(&meta, kernel, d, src_box, tgt_box, d_theta, theta_box, n);
+  cudaStream_t s = as_stream(stream);
+  int* dstat = nullptr;
+  PTTK_CUDA(cudaMallocAsync(&dstat, sizeof(int), s));
+  pttk_status st = PTTK_OK;
+  int h = 0;
+  if (cudaMemsetAsync(dstat, 0, sizeof(int), s) != cudaSuccess) st = cuda_error(cudaGetLastError(), "memset");
+  if (st == PTTK_OK)
+    st = grid_entries_launch(kernel, d, d_theta, n, meta.box, idx, M, prec == PTTK_FP64, out, dstat, s);
+  if (st == PTTK_OK) {
+    const cudaError_t e = cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || e2 != cudaSuccess) st = cuda_error(e != cudaSuccess ? e : e2, "grid entries");
+  }
+  cudaFreeAsync(dstat, s);
+  if (st != PTTK_OK) return st;
+  if (h != 0) return set_error(PTTK_EINVAL, "a multi-index lies outside [0, n)");
+  return PTTK_OK;
 }
 
 pttk_status pttk_tt_from_coeffs(pttk_kernel kernel, int d, const double* src_box,

@@ -203,7 +203,72 @@ pttk_status dispatch_nb(const GridArgs& a, T* C, cudaStream_t st) {
   return set_error(PTTK_EINVAL, "n out of range");
 }
 
+// Entries of the grid tensor M (Eq. mdc) at a list of multi-indices (the entry access the
+// TT greedy-cross works from): out[e] = f_kappa(eta^(1)_{idx[e,0]}, ..., eta^(D)_{idx[e,D-1]}),
+// idx row-major M x D. An index outside [0, n) gives NaN and records PTTK_EINVAL in *status;
+// no node is read with it.
+template <typename T>
+__global__ void __launch_bounds__(256) entries_kernel(GridArgs a, const int* __restrict__ idx, int64_t M,
+                                                      T* __restrict__ out, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* eta = reinterpret_cast<T*>(smem_raw);
+  T* Amat = eta + a.D * a.n;
+  T* cnu = Amat + a.n * a.n;
+  T* snu = cnu + a.n;
+  T* stab = snu + a.n;
+  fill_tables<T>(a, eta, Amat, cnu, snu, stab);
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < M;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int row[PTTK_MAX_D];
+    bool ok = true;
+    for (int j = 0; j < a.D; ++j) {
+      const int v = idx[e * a.D + j];
+      ok = ok && v >= 0 && v < a.n;
+      row[j] = ok ? v : 0;
+    }
+    if (!ok) {
+      out[e] = T(NAN);
+      atomicExch(status, (int)PTTK_EINVAL);
+      continue;
+    }
+    out[e] = eval_entry<T>(a, row, eta, cnu, snu, stab);
+  }
+}
+
+template <typename T>
+pttk_status launch_entries(const GridArgs& a, const int* idx, int64_t M, T* out, int* status,
+                           cudaStream_t st) {
+  const size_t smem = sizeof(T) * ((size_t)a.D * a.n + (size_t)a.n * a.n + 2 * a.n +
+                                   (a.kind == K_MATERN_NU ? KV_TABLE : 0));
+  auto kfn = entries_kernel<T>;
+  PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((M + 255) / 256, (int64_t)sm_count() * 8));
+  PTTK_PROF("grid_entries", st);
+  kfn<<<(unsigned)blocks, 256, smem, st>>>(a, idx, M, out, status); pttk::count_launch();
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
 }  // namespace
+
+pttk_status grid_entries_launch(int kernel, int d, int dtheta, int n, const double (*box)[2],
+                                const int* idx, int64_t M, bool fp64, void* out, int* status,
+                                cudaStream_t s) {
+  if (M == 0) return PTTK_OK;
+  GridArgs a{};
+  a.kind = kernel;
+  a.d = d;
+  a.dtheta = dtheta;
+  a.D = 2 * d + dtheta;
+  a.n = n;
+  for (int j = 0; j < a.D; ++j) {
+    a.lo[j] = box[j][0];
+    a.hi[j] = box[j][1];
+  }
+  if (fp64) return launch_entries<double>(a, idx, M, static_cast<double*>(out), status, s);
+  return launch_entries<float>(a, idx, M, static_cast<float*>(out), status, s);
+}
 
 pttk_status grid_coeffs_launch(int kernel, int d, int dtheta, int n, const double (*box)[2],
                                bool fp64, void* C, cudaStream_t s) {

@@ -91,6 +91,11 @@ pttk_status theta_hat(const pttk_tt* tt, const double* theta, double* th);
 // --- grid.cu ---------------------------------------------------------------------------
 pttk_status grid_coeffs_launch(int kernel, int d, int dtheta, int n, const double (*box)[2],
                                bool fp64, void* C, cudaStream_t s);
+// Grid-tensor entries at M multi-indices (dev, M x D row-major int32); a bad index records
+// PTTK_EINVAL in *status (dev int).
+pttk_status grid_entries_launch(int kernel, int d, int dtheta, int n, const double (*box)[2],
+                                const int* idx, int64_t M, bool fp64, void* out, int* status,
+                                cudaStream_t s);
 
 // --- ttsvd.cu --------------------------------------------------------------------------
 // TT-SVD of the FP64 tensor in `X` (n^D elements, modified). Fills tt->ranks and

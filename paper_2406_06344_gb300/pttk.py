@@ -36,6 +36,8 @@ SIGNATURES = [
     ("pttk_last_error", ctypes.c_char_p, []),
     ("pttk_version", _int, []),
     ("pttk_grid_coeffs", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int, _int, _vp, _vp]),
+    ("pttk_grid_entries", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int, _vp, _i64,
+                                 _int, _vp, _vp]),
     ("pttk_tt_from_coeffs", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int,
                                    ctypes.c_double, _vp, _int, _vp, ctypes.POINTER(_vp)]),
     ("pttk_build_offline", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int,
@@ -159,6 +161,22 @@ def grid_coeffs(kernel: int, d: int, src_box, tgt_box, dtheta: int, theta_box, n
         out = torch.empty(n ** D, dtype=_dtype(prec), device="cuda")
     _check(load().pttk_grid_coeffs(kernel, d, _dbl(_boxflat(src_box)), _dbl(_boxflat(tgt_box)), dtheta,
                                    _dbl(_boxflat(theta_box)), n, prec, _ptr(out), _stream(stream)))
+    return out
+
+
+def grid_entries(kernel: int, d: int, src_box, tgt_box, dtheta: int, theta_box, n: int, idx,
+                 prec="fp64", out=None, stream=None):
+    """pttk_grid_entries: kernel values at the multi-indices idx (M x D int32 CUDA tensor,
+    0-based node indices, variable order (x, theta, y)) of the grid tensor M."""
+    import torch
+    prec = _prec(prec)
+    if idx.dtype != torch.int32 or idx.dim() != 2 or idx.shape[1] != 2 * d + dtheta:
+        raise ValueError(f"idx must be (M, {2 * d + dtheta}) int32")
+    if out is None:
+        out = torch.empty(idx.shape[0], dtype=_dtype(prec), device="cuda")
+    _check(load().pttk_grid_entries(kernel, d, _dbl(_boxflat(src_box)), _dbl(_boxflat(tgt_box)), dtheta,
+                                    _dbl(_boxflat(theta_box)), n, _ptr(idx), idx.shape[0], prec, _ptr(out),
+                                    _stream(stream)))
     return out
 
 

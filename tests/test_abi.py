@@ -168,3 +168,20 @@ def test_splitmix64_is_the_published_generator_and_the_oracles(so):
     rng = np.random.default_rng(60)
     for key, c in zip(rng.integers(0, 2**63, 50, dtype=np.int64), rng.integers(0, 2**40, 50, dtype=np.int64)):
         assert pttk.splitmix64(int(key), int(c)) == x.splitmix64(int(key), int(c))
+
+
+def test_grid_entries_rejects_bad_arguments_without_touching_the_device(so):
+    from paper_2406_06344_gb300 import pttk
+    box = (ctypes.c_double * 2)(0.0, 1.0)
+    tbox = (ctypes.c_double * 2)(2.0, 3.0)
+    lbox = (ctypes.c_double * 2)(0.5, 2.0)
+    # M > 0 with NULL buffers, a negative count, a bad precision
+    assert so.pttk_grid_entries(0, 1, box, tbox, 1, lbox, 8, None, 5, 0, None, None) == pttk.EINVAL
+    assert so.pttk_grid_entries(0, 1, box, tbox, 1, lbox, 8, None, -1, 0, None, None) == pttk.EINVAL
+    assert so.pttk_grid_entries(0, 1, box, tbox, 1, lbox, 8, None, 0, 2, None, None) == pttk.EINVAL
+    # M = 0 is a no-op, also for an n^D far above the whole-grid limit (no grid is formed)
+    assert so.pttk_grid_entries(0, 1, box, tbox, 1, lbox, 8, None, 0, 0, None, None) == pttk.OK
+    b3 = (ctypes.c_double * 6)(0.0, 1.0, 0.0, 1.0, 0.0, 1.0)
+    t3 = (ctypes.c_double * 6)(3.0, 4.0, 0.0, 1.0, 0.0, 1.0)
+    p2 = (ctypes.c_double * 4)(0.5, 2.0, 0.5, 2.5)
+    assert so.pttk_grid_entries(2, 3, b3, t3, 2, p2, 32, None, 0, 0, None, None) == pttk.OK
