@@ -112,6 +112,18 @@ def _laplace2d_sign(kind, r, theta):
     return _orig["kernel_of_r"](kind, r, theta)
 
 
+def _H_theta_swapped(cores, d, dtheta, theta, theta_box):
+    # theta_1 contracted with the core of theta_2 and the other way round
+    th = list(theta)[::-1]
+    box = list(theta_box)[::-1]
+    n = cores[d].shape[1]
+    H = np.eye(cores[d].shape[0])
+    that = o.theta_hat(th, box)
+    for j in range(dtheta):
+        H = H @ np.tensordot(cores[d + j], o.cheb_vector(that[j], n), axes=([1], [0]))
+    return H
+
+
 def _biharmonic_power(kind, r, theta):
     if kind == o.BIHARMONIC:
         return 1.0 / np.asarray(r)
@@ -226,6 +238,8 @@ CASES = {
                                    [(pins.test_transform_inverts_node_values, {"n": 12})]),
     "Laplace-2D with the wrong sign": ({"kernel_of_r": _laplace2d_sign},
                                        [(pins.test_multiquadric_and_thin_plate_family_identities, {})]),
+    "theta components swapped in H": ({"core_matrix_H": _H_theta_swapped},
+                                      [(pins.test_factor_chain_equals_full_interpolant, {})]),
     "bi-harmonic as r^-1": ({"kernel_of_r": _biharmonic_power},
                             [(pins.test_multiquadric_and_thin_plate_family_identities, {})]),
     "TT-Round: left neighbour times R, not R^T": ({"tt_round": _round_with(r_update="R")}, _ROUND_PINS),
