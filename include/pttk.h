@@ -51,7 +51,7 @@ extern "C" {
 typedef enum pttk_status {
   PTTK_OK = 0,
   PTTK_EINVAL = 1,   /* bad argument: size, box, pointer, precision, rank mismatch */
-  PTTK_EDOMAIN = 2,  /* theta outside its box */
+  PTTK_EDOMAIN = 2,  /* theta, or a point, outside its box */
   PTTK_ENOMEM = 3,   /* a device or host allocation failed */
   PTTK_ECUDA = 4,    /* a CUDA runtime error; pttk_last_error() has its text */
   PTTK_ETIMEOUT = 5, /* a bounded device-side wait ran out */
@@ -182,6 +182,10 @@ pttk_status pttk_tt_load(const char* path, pttk_tt** out);
  * coefficient form (contracted with T(xhat), not with nodal values). Copied; the caller
  * keeps ownership of `cores`. Synchronous. Errors: PTTK_EINVAL (bad problem or ranks),
  * PTTK_ENOMEM / PTTK_ECUDA. */
+pttk_status pttk_tt_from_cores(pttk_kernel kernel, int d, const double* src_box, const double* tgt_box,
+                               int d_theta, const double* theta_box, int n, const int* ranks,
+                               const double* cores, pttk_tt** out);
+
 /* TT-Round (Algorithm 1): a new handle holding a TT of the same tensor with ranks reduced so
  * that ||X - X_rounded||_F <= tol ||X||_F (X the tensor `in` represents): right-to-left
  * orthogonalisation of the cores, then a left-to-right sweep of truncated SVDs with
@@ -190,10 +194,6 @@ pttk_status pttk_tt_load(const char* path, pttk_tt** out);
  * caller frees both. tol in (0, 1). Synchronises `stream`. Errors: PTTK_EINVAL, PTTK_ENOMEM,
  * PTTK_ECUDA, PTTK_ETIMEOUT. */
 pttk_status pttk_tt_round(const pttk_tt* in, double tol, void* stream, pttk_tt** out);
-
-pttk_status pttk_tt_from_cores(pttk_kernel kernel, int d, const double* src_box, const double* tgt_box,
-                               int d_theta, const double* theta_box, int n, const int* ranks,
-                               const double* cores, pttk_tt** out);
 
 /* Release a handle and its device memory (NULL is a no-op). */
 void pttk_tt_free(pttk_tt* tt);
@@ -272,7 +272,9 @@ pttk_status pttk_theta_core(const pttk_tt* tt, const double* theta, pttk_prec pr
 
 /* Synchronise `stream` and report the handle's device status word, then clear it:
  * PTTK_ETIMEOUT if a kernel working with this handle gave up a bounded wait, PTTK_EDOMAIN if a
- * batched call met a theta outside its box, else PTTK_OK. The tensor-core factor chain records
+ * batched call met a theta outside its box or any call met a point outside its box (a
+ * coordinate beyond its interval by more than 1e-12 of the interval's length; FP32 points
+ * are compared with the FP32-rounded ends), else PTTK_OK. The tensor-core factor chain records
  * such timeouts instead of spinning; its outputs are unspecified when it does. */
 pttk_status pttk_tt_check(const pttk_tt* tt, void* stream);
 
@@ -280,8 +282,10 @@ pttk_status pttk_tt_check(const pttk_tt* tt, void* stream);
  * Phase 3 for the given points: U = S(X) (N_s x r_d) by S <- B_1 G_1^{2},
  * S <- (B_i face-split S) G_i^{2}; V = T(Y) (N_t x r_{d+d_theta}) by the mirrored
  * Khatri-Rao chain; B_i[p, k] = T_k(phi^{-1}(x_{p,i})). K(X, Y; theta) ~= U M V^T.
- *   X: dev N_s x d, Y: dev N_t x d (double for PTTK_FP64, float otherwise); points are
- *   expected inside their boxes (a point outside is extrapolated, not rejected).
+ *   X: dev N_s x d, Y: dev N_t x d (double for PTTK_FP64, float otherwise); points must lie
+ *   in their boxes (Section 1: X in B_s, Y in B_t), a point on a face is valid. One pass over
+ *   X and Y checks it on the device; a point outside records PTTK_EDOMAIN in the handle's
+ *   status word (reported by pttk_tt_check) and its factor row is an extrapolation.
  *   N_s, N_t >= 0 (0 is allowed and writes nothing for that side).
  *   U, M, V: dev outputs (double for PTTK_FP64, float otherwise).
  *   prec: PTTK_FP64 / PTTK_FP32 run the SIMT chain; PTTK_TF32, PTTK_TF32X3, PTTK_BF16,
@@ -351,7 +355,9 @@ pttk_status pttk_grad(const pttk_tt* tt, const double* theta, const void* X, int
 /* Low-rank product out = U (M (V^T w)) (Eq. paramlowrank applied to a vector).
  *   U: dev N_s x rs, M: dev rs x rt, V: dev N_t x rt, row-major; w: dev [N_t];
  *   out: dev [N_s]. prec: PTTK_FP64 (all double) or PTTK_FP32 (all float; reductions
- *   accumulate in FP32). The library allocates a small temporary for V^T w and M (V^T w). */
+ *   accumulate in FP32). Any ranks rs, rt >= 1: no shared memory is sized by a rank. The
+ *   library allocates a small stream-ordered temporary for the partial sums of V^T w and for
+ *   M (V^T w). */
 pttk_status pttk_apply(const void* U, const void* M, const void* V, int64_t N_s, int64_t N_t,
                        int rs, int rt, pttk_prec prec, const void* w, void* out, void* stream);
 
@@ -363,7 +369,9 @@ pttk_status pttk_apply(const void* U, const void* M, const void* V, int64_t N_s,
  * file-scope device array inside libpttk, held by every device that loads the library until
  * the process exits. The paper has no counterpart; arguments and results are those of
  * pttk_apply, and it uses fewer partial-sum blocks when they would not fit.
- *   Limit: rs + rt <= 131072 (FP64) or 262144 (FP32); larger ranks give PTTK_EINVAL.
+ *   Limit: rs + rt <= 131072 (FP64) or 262144 (FP32), the scratch's size in elements (at
+ *   least one partial-sum block of rt values plus the rs values of M (V^T w) must fit);
+ *   larger ranks give PTTK_EINVAL. Below the limit any N_s, N_t is accepted.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *   with that device current; make that first call before any stream capture.
  *   All calls share the one array, which keeps the last call's contents: calls whose work
@@ -397,6 +405,28 @@ int64_t pttk_launch_count(void);
 pttk_status pttk_selftest_wait_timeout(void* stream);
 /* Names of the kernels timed so far, newline-separated, NUL-terminated, truncated to len. */
 pttk_status pttk_profile_names(char* buf, int64_t len);
+
+/* ---- peak probes (measurement helpers; the paper has no counterpart) -------------------
+ * Rooflines of kernels bound by an arithmetic pipe need that pipe's peak on this GPU. Each
+ * probe runs one loop kernel of the given kind for `iters` trips (tens of ms for the sizes
+ * the bench uses) and returns its rate: *tflops = executed flops / CUDA-event time, *ms (may
+ * be NULL) = that time. Kinds:
+ *   PTTK_PROBE_DFMA  FP64 FMA, 256-thread blocks, 8 per SM, 32 dependent-free FMAs per trip;
+ *   PTTK_PROBE_FFMA  FP32 FMA, the same shape;
+ *   PTTK_PROBE_DMMA  FP64 mma.sync m8n8k4, 4 independent accumulators per warp per trip;
+ *   PTTK_PROBE_TF32  tcgen05.mma kind::tf32 M = 128, N = 256, K = 8, one CTA per SM, one MMA
+ *                    per trip;
+ *   PTTK_PROBE_F16   tcgen05.mma kind::f16 (FP16 operands) M = 128, N = 256, K = 16.
+ * Operands are seeded nonzero values. iters in [1, 2^32]. Synchronises `stream`.
+ * Errors: PTTK_EINVAL, PTTK_ECUDA, PTTK_ETIMEOUT (an MMA loop's bounded final wait ran out). */
+typedef enum pttk_probe {
+  PTTK_PROBE_DFMA = 0,
+  PTTK_PROBE_FFMA = 1,
+  PTTK_PROBE_DMMA = 2,
+  PTTK_PROBE_TF32 = 3,
+  PTTK_PROBE_F16 = 4
+} pttk_probe;
+pttk_status pttk_peak_probe(int kind, int64_t iters, void* stream, double* tflops, double* ms);
 
 #ifdef __cplusplus
 }

@@ -507,6 +507,8 @@ pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void*
   PTTK_TRY(theta_hat(tt, theta, th));
   cudaStream_t s = as_stream(stream);
   PTTK_TRY(theta_core_run(tt, th, prec == PTTK_FP64, M, s));
+  PTTK_TRY(point_domain_check(tt, true, X, N_s, prec == PTTK_FP64, tt_status_word(tt), s));
+  PTTK_TRY(point_domain_check(tt, false, Y, N_t, prec == PTTK_FP64, tt_status_word(tt), s));
   if (prec == PTTK_FP64 || prec == PTTK_FP32) {
     PTTK_TRY(factor_build_run(tt, true, X, N_s, prec, U, s));
     PTTK_TRY(factor_build_run(tt, false, Y, N_t, prec, V, s));
@@ -529,6 +531,8 @@ pttk_status pttk_tt_check(const pttk_tt* tt, void* stream) {
   PTTK_CUDA(cudaMemcpy(&h, t->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
   if (h != 0) {
     PTTK_CUDA(cudaMemset(t->dstatus, 0, sizeof(int)));
+    if (h == (int)PTTK_EDOMAIN)
+      return set_error(PTTK_EDOMAIN, "a kernel using this handle met a point or a theta outside its box");
     return set_error((pttk_status)h, "a bounded device-side wait ran out in a kernel using this handle");
   }
   return PTTK_OK;

@@ -264,40 +264,43 @@ __global__ void __launch_bounds__(256) vtw_partial_kernel(const T* __restrict__ 
   }
 }
 
-// t = sum over partial rows; s = M t (one CTA)
+// t = sum over the partial rows, written in place into row 0 of `partial` (one thread per
+// column; the rows it reads belong to no other thread). Grid-stride over the rt columns.
 template <typename T>
-__global__ void __launch_bounds__(256) reduce_mt_kernel(const T* __restrict__ partial, int nparts,
-                                                        int rs, int rt, const T* __restrict__ M,
-                                                        T* __restrict__ s_out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* t = reinterpret_cast<T*>(smem_raw);
-  for (int c = threadIdx.x; c < rt; c += blockDim.x) {
-    T acc = T(0);
-    for (int b = 0; b < nparts; ++b) acc += partial[(int64_t)b * rt + c];
-    t[c] = acc;
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < rs; r += blockDim.x) {
-    T acc = T(0);
-    for (int c = 0; c < rt; ++c) acc = fma(M[(int64_t)r * rt + c], t[c], acc);
-    s_out[r] = acc;
+__global__ void __launch_bounds__(256) reduce_parts_kernel(T* __restrict__ partial, int nparts, int rt) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < rt; c += (int64_t)gridDim.x * blockDim.x) {
+    T acc = partial[c];
+    for (int b = 1; b < nparts; ++b) acc += partial[(int64_t)b * rt + c];
+    partial[c] = acc;
   }
 }
 
-// out[p] = U[p, :] . s, one warp per row
+// s = M t, one warp per row of M (rs x rt, row-major); t is read through the L1 cache, so
+// no shared memory is sized by a rank.
+template <typename T>
+__global__ void __launch_bounds__(256) mt_kernel(const T* __restrict__ M, int rs, int rt,
+                                                 const T* __restrict__ t, T* __restrict__ s_out) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rs;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const T* m = M + r * rt;
+    T acc = T(0);
+    for (int c = lane; c < rt; c += 32) acc = fma(m[c], __ldg(t + c), acc);
+    acc = warp_sum<T>(acc);
+    if (lane == 0) s_out[r] = acc;
+  }
+}
+
+// out[p] = U[p, :] . s, one warp per row; s is read through the L1 cache
 template <typename T>
 __global__ void __launch_bounds__(256) us_kernel(const T* __restrict__ U, int64_t N, int rs,
                                                  const T* __restrict__ s, T* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sv = reinterpret_cast<T*>(smem_raw);
-  for (int c = threadIdx.x; c < rs; c += blockDim.x) sv[c] = s[c];
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N;
        row += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const T* u = U + row * rs;
     T acc = T(0);
-    for (int c = lane; c < rs; c += 32) acc = fma(u[c], sv[c], acc);
+    for (int c = lane; c < rs; c += 32) acc = fma(u[c], __ldg(s + c), acc);
     acc = warp_sum<T>(acc);
     if (lane == 0) out[row] = acc;
   }
@@ -314,10 +317,15 @@ pttk_status apply_typed(const T* U, const T* M, const T* V, int64_t N_s, int64_t
   } else {
     PTTK_CUDA(cudaMemsetAsync(partial, 0, sizeof(T) * (size_t)nparts * rt, s));
   }
-  reduce_mt_kernel<T><<<1, 256, sizeof(T) * rt, s>>>(partial, nparts, rs, rt, M, sv); pttk::count_launch();
+  if (nparts > 1) {
+    const int64_t rblocks = std::min<int64_t>((rt + 255) / 256, (int64_t)sm_count() * 4);
+    reduce_parts_kernel<T><<<(unsigned)rblocks, 256, 0, s>>>(partial, nparts, rt); pttk::count_launch();
+  }
+  const int64_t mblocks = std::min<int64_t>(((int64_t)rs * 32 + 255) / 256, (int64_t)sm_count() * 16);
+  mt_kernel<T><<<(unsigned)mblocks, 256, 0, s>>>(M, rs, rt, partial, sv); pttk::count_launch();
   if (N_s > 0) {
     const int64_t blocks = std::min<int64_t>((N_s * 32 + 255) / 256, (int64_t)sm_count() * 16);
-    us_kernel<T><<<(unsigned)blocks, 256, sizeof(T) * rs, s>>>(U, N_s, rs, sv, out); pttk::count_launch();
+    us_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(U, N_s, rs, sv, out); pttk::count_launch();
   }
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
@@ -328,6 +336,46 @@ int apply_parts(int64_t N_t) {
 }
 
 }  // namespace
+
+// ---------------- point domain ---------------------------------------------------------
+// The problem is stated for X in B_s and Y in B_t (Section 1). One pass over a point set
+// records PTTK_EDOMAIN in the handle's status word if any coordinate lies outside its
+// interval by more than a relative slack of 1e-12. FP32 points are compared with the
+// FP32-rounded interval ends: rounding is monotone, so a point inside the box stays inside
+// the rounded box when it is cast.
+struct PointBox {
+  double lo[PTTK_MAX_D], hi[PTTK_MAX_D];
+};
+template <typename T>
+__global__ void __launch_bounds__(256) point_domain_kernel(const T* __restrict__ P, int64_t total, int d,
+                                                           PointBox box, int* __restrict__ status) {
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % d);
+    const double x = (double)P[e];
+    bad |= !(x >= box.lo[c] && x <= box.hi[c]);  // also catches NaN
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(status, 0, (int)PTTK_EDOMAIN);
+}
+
+pttk_status point_domain_check(const pttk_tt* tt, bool source, const void* P, int64_t N, bool fp64, int* status,
+                               cudaStream_t s) {
+  if (N <= 0) return PTTK_OK;
+  PointBox b{};
+  for (int c = 0; c < tt->d; ++c) {
+    const int bj = source ? c : tt->d + tt->dtheta + c;
+    const double lo = tt->box[bj][0], hi = tt->box[bj][1], slack = 1e-12 * (hi - lo);
+    b.lo[c] = (fp64 ? lo : (double)(float)lo) - slack;
+    b.hi[c] = (fp64 ? hi : (double)(float)hi) + slack;
+  }
+  const int64_t total = N * tt->d;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 4);
+  if (fp64) point_domain_kernel<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(P), total, tt->d, b, status);
+  else point_domain_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(P), total, tt->d, b, status);
+  pttk::count_launch();
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
 
 // Step `step` of a side's chain: dimensions of its oriented core and the point coordinate.
 int oriented_core_dims(const pttk_tt* tt, bool source, int step, int* R_in, int* R_out,

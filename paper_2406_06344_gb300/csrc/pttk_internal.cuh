@@ -54,6 +54,14 @@ void clear_error();
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Diagnostic logging to stderr (stage times, sweep counts): compiled in only by a build with
+// -DPTTK_DEBUG, the library's one build switch; release builds read no environment.
+#ifdef PTTK_DEBUG
+constexpr bool kDebugLog = true;
+#else
+constexpr bool kDebugLog = false;
+#endif
+
 int sm_count();
 
 // Number of kernels the library has launched (every launch site increments it).
@@ -132,6 +140,10 @@ pttk_status theta_core_run(const pttk_tt* tt, const double* theta_hat, bool fp64
 pttk_status factor_build_run(const pttk_tt* tt, bool source, const void* P, int64_t N,
                              pttk_prec prec, void* out, cudaStream_t s, int nsteps = 0);
 int oriented_core_dims(const pttk_tt* tt, bool source, int step, int* R_in, int* R_out, int* coord);
+// One pass over N points (N x d row-major, double if fp64 else float) of the source (or
+// target) side: records PTTK_EDOMAIN in *status if a coordinate lies outside its box.
+pttk_status point_domain_check(const pttk_tt* tt, bool source, const void* P, int64_t N, bool fp64, int* status,
+                               cudaStream_t s);
 const void* oriented_core_ptr(const pttk_tt* tt, bool source, int k, bool fp64);
 int* tt_status_word(const pttk_tt* tt);
 struct TcImageCache;

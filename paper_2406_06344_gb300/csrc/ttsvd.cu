@@ -738,8 +738,7 @@ pttk_status jacobi(double* A, int64_t rows, int ncols, cudaStream_t s, double sm
   JacobiSync h{};
   PTTK_CUDA(cudaMemcpyAsync(&h, js, sizeof(JacobiSync), cudaMemcpyDeviceToHost, s));
   PTTK_CUDA(cudaStreamSynchronize(s));
-  static const bool verbose = getenv("PTTK_VERBOSE") != nullptr;
-  if (verbose)
+  if (kDebugLog)
     for (int sw = 0; sw < std::min(h.sweeps, JMAX_SWEEPS); ++sw)
       fprintf(stderr, "pttk: jacobi %lld x %d sweep %d rotations %u\n", (long long)rows, ncols, sw, h.rot[sw]);
   if (h.err) return set_error(PTTK_ETIMEOUT, "one-sided Jacobi: a grid barrier timed out");
@@ -780,13 +779,13 @@ void dgemm(bool tA, bool tB, int64_t M, int64_t N, int64_t K, double alpha, cons
   }
 }
 
-// Wall-clock stage timing of the TT-SVD, printed to stderr when PTTK_VERBOSE is set (it
-// synchronises the stream at every mark, so it is off otherwise).
+// Wall-clock stage timing of the TT-SVD, printed to stderr in a PTTK_DEBUG build (it
+// synchronises the stream at every mark, so release builds compile it out).
 struct StageClock {
   bool on;
   cudaStream_t s;
   std::chrono::steady_clock::time_point t0;
-  explicit StageClock(cudaStream_t st) : on(getenv("PTTK_VERBOSE") != nullptr), s(st) { reset(); }
+  explicit StageClock(cudaStream_t st) : on(kDebugLog), s(st) { reset(); }
   void reset() {
     if (!on) return;
     cudaStreamSynchronize(s);

@@ -78,6 +78,7 @@ SIGNATURES = [
     ("pttk_global_instantiate", _int, [_vp, _c_double_p, ctypes.c_double, _int, _int, _vp, _vp, _c_int_p, _vp]),
     ("pttk_global_free", None, [_vp]),
     ("pttk_splitmix64", ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
+    ("pttk_peak_probe", _int, [_int, _i64, _vp, _c_double_p, _c_double_p]),
 ]
 
 _lib = None
@@ -316,9 +317,29 @@ def instantiate(tt: TT, theta, X, Y, prec="fp64", U=None, M=None, V=None, stream
     return U, M, V
 
 
+def _check_apply_args(U, M, V, w, out):
+    """Shapes and dtypes of an apply call: the library reads and writes these buffers by raw
+    pointer, so a mismatch would run past the end of one of them."""
+    import torch
+    if U.dtype not in (torch.float64, torch.float32):
+        raise ValueError("U must be float64 or float32")
+    if U.dim() != 2 or M.dim() != 2 or V.dim() != 2:
+        raise ValueError("U, M and V must be matrices")
+    for name, t in (("M", M), ("V", V), ("w", w), ("out", out)):
+        if t is not None and t.dtype != U.dtype:
+            raise ValueError(f"{name} must have U's dtype {U.dtype}")
+    if tuple(M.shape) != (U.shape[1], V.shape[1]):
+        raise ValueError(f"M must be {U.shape[1]} x {V.shape[1]}, got {tuple(M.shape)}")
+    if w.numel() != V.shape[0]:
+        raise ValueError(f"w must have {V.shape[0]} entries, got {w.numel()}")
+    if out is not None and out.numel() != U.shape[0]:
+        raise ValueError(f"out must have {U.shape[0]} entries, got {out.numel()}")
+
+
 def apply(U, M, V, w, out=None, stream=None):
     """pttk_apply: out = U (M (V^T w))."""
     import torch
+    _check_apply_args(U, M, V, w, out)
     prec = FP64 if U.dtype == torch.float64 else FP32
     if out is None:
         out = torch.empty(U.shape[0], dtype=U.dtype, device="cuda")
@@ -517,10 +538,23 @@ class Global:
 def apply_noalloc(U, M, V, w, out, stream=None):
     """pttk_apply_noalloc: out = U (M (V^T w)) with no device allocation (fixed library scratch)."""
     import torch
+    _check_apply_args(U, M, V, w, out)
     prec = FP64 if U.dtype == torch.float64 else FP32
     _check(load().pttk_apply_noalloc(_ptr(U), _ptr(M), _ptr(V), U.shape[0], V.shape[0], U.shape[1],
                                      V.shape[1], prec, _ptr(w), _ptr(out), _stream(stream)))
     return out
+
+
+PROBE_DFMA, PROBE_FFMA, PROBE_DMMA, PROBE_TF32, PROBE_F16 = range(5)
+PROBE_NAMES = {"dfma": PROBE_DFMA, "ffma": PROBE_FFMA, "dmma": PROBE_DMMA, "tf32": PROBE_TF32, "f16": PROBE_F16}
+
+
+def peak_probe(kind, iters: int, stream=None):
+    """pttk_peak_probe: (TFLOP/s, ms) of one loop kernel of the given kind."""
+    k = PROBE_NAMES[kind] if isinstance(kind, str) else int(kind)
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().pttk_peak_probe(k, int(iters), _stream(stream), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def splitmix64(key: int, counter: int) -> int:

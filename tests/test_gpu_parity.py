@@ -228,6 +228,41 @@ def test_points_on_box_faces_and_theta_on_edges(P, torch_cuda):
         assert o.rel_fro(K, Uo @ Mo @ Vo.T) < 1e-3
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16x3"])
+def test_points_outside_box_record_a_domain_error(P, torch_cuda, prec):
+    """Section 1 states the problem for X in B_s and Y in B_t: a point on a face is valid, a
+    point beyond it by more than the 1e-12 relative slack records PTTK_EDOMAIN in the status
+    word (pttk_tt_check), single and batched."""
+    torch = torch_cuda
+    w = W.C2
+    tt = _gpu_tt(P, w)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    th = W.thetas(w, 1)[0]
+    Xin = np.array([[0.0, 0.0], [1.0, 1.0], [0.5, 0.25]])
+    Yin = np.array([[2.0, 0.0], [3.0, 1.0], [2.5, 0.5]])
+    eps_out = 1e-9 if prec == "fp64" else 1e-6
+    cases = [(Xin, Yin, P.OK)]
+    for side, j, v in ((0, 0, 1.0 + eps_out), (0, 1, -eps_out), (1, 0, 2.0 - 2 * eps_out), (1, 1, 1.0 + eps_out)):
+        X, Y = Xin.copy(), Yin.copy()
+        (X if side == 0 else Y)[1, j] = v
+        cases.append((X, Y, P.EDOMAIN))
+    for X, Y, want in cases:
+        Xd, Yd = torch.tensor(X, device="cuda", dtype=dt), torch.tensor(Y, device="cuda", dtype=dt)
+        P.instantiate(tt, th, Xd, Yd, prec)
+        st = P.load().pttk_tt_check(tt.handle, None)
+        assert st == want, (X, Y, prec)
+        b = P.Batch(tt, [0, 3], [0, 3], prec)
+        thetas = torch.tensor([th], device="cuda", dtype=torch.float64)
+        b.instantiate(thetas, Xd, Yd)
+        st = P.load().pttk_tt_check(tt.handle, None)
+        assert st == want, ("batched", X, Y, prec)
+        b.free()
+    # the status word is cleared by the check: a valid call afterwards reports OK
+    P.instantiate(tt, th, torch.tensor(Xin, device="cuda", dtype=dt), torch.tensor(Yin, device="cuda", dtype=dt),
+                  prec)
+    assert P.load().pttk_tt_check(tt.handle, None) == P.OK
+
+
 def test_theta_outside_box_is_a_domain_error(P, torch_cuda):
     w = W.C1
     tt = _gpu_tt(P, w)
@@ -254,6 +289,37 @@ def test_apply_matches_oracle(P, torch_cuda, prec):
     ref = o.apply(U.double().cpu().numpy(), M.double().cpu().numpy(), V.double().cpu().numpy(), wv)
     tol = 1e-13 if prec == "fp64" else 1e-5
     assert np.linalg.norm(out.double().cpu().numpy() - ref) <= tol * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("rs,rt", [(7000, 8000), (3, 13000)])
+def test_apply_large_ranks_matches_oracle(P, torch_cuda, rs, rt):
+    """Ranks whose vectors exceed what one CTA could hold in 48 KB of shared memory (6144 FP64
+    values): the reduction and both products must still run and agree with the oracle."""
+    torch = torch_cuda
+    rng = np.random.default_rng(11)
+    Ns, Nt = 700, 900
+    U, M, V = rng.standard_normal((Ns, rs)), rng.standard_normal((rs, rt)), rng.standard_normal((Nt, rt))
+    wv = rng.standard_normal(Nt)
+    dev = [torch.tensor(a, device="cuda") for a in (U, M, V, wv)]
+    out = P.apply(*dev)
+    ref = o.apply(U, M, V, wv)
+    assert np.linalg.norm(out.cpu().numpy() - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_apply_rejects_mismatched_buffers(P, torch_cuda):
+    torch = torch_cuda
+    U = torch.zeros(5, 3, dtype=torch.float64, device="cuda")
+    M = torch.zeros(3, 4, dtype=torch.float64, device="cuda")
+    V = torch.zeros(6, 4, dtype=torch.float64, device="cuda")
+    w = torch.zeros(6, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        P.apply(U, M.float(), V, w)
+    with pytest.raises(ValueError):
+        P.apply(U, M[:2], V, w)
+    with pytest.raises(ValueError):
+        P.apply(U, M, V, w[:5])
+    with pytest.raises(ValueError):
+        P.apply(U, M, V, w, out=torch.zeros(4, dtype=torch.float64, device="cuda"))
 
 
 def test_save_load_roundtrip(P, torch_cuda, tmp_path):

@@ -44,6 +44,32 @@ def test_noalloc_apply_matches_apply_on_two_calls(env, prec, tol):
         assert err.item() <= tol
 
 
+@pytest.mark.parametrize("rs,rt,Nt", [(10, 2000, 200_000), (7000, 8000, 900)])
+def test_noalloc_apply_matches_apply_with_fewer_blocks_and_large_ranks(env, rs, rt, Nt):
+    """(10, 2000, 200k): the fixed scratch holds (131072 - rs) / rt = 65 partial sums of
+    V^T w, fewer than the 608 blocks pttk_apply uses at this N_t, so the call runs with fewer
+    blocks. (7000, 8000, 900): ranks beyond what 48 KB of shared memory could stage. Two calls
+    in a row against pttk_apply, in FP64."""
+    torch, P, W = env
+    lib = P.load()
+    g = torch.Generator(device="cuda").manual_seed(rs + rt)
+    Ns = 1500
+    U = torch.randn(Ns, rs, generator=g, device="cuda", dtype=torch.float64)
+    M = torch.randn(rs, rt, generator=g, device="cuda", dtype=torch.float64)
+    V = torch.randn(Nt, rt, generator=g, device="cuda", dtype=torch.float64)
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        wv = torch.randn(Nt, generator=g, device="cuda", dtype=torch.float64)
+        ref = P.apply(U, M, V, wv)
+        out = torch.full_like(ref, float("nan"))
+        st = lib.pttk_apply_noalloc(U.data_ptr(), M.data_ptr(), V.data_ptr(), Ns, Nt, rs, rt, P.FP64,
+                                    wv.data_ptr(), out.data_ptr(), stream)
+        assert st == P.OK, lib.pttk_last_error().decode()
+        torch.cuda.synchronize()
+        err = (out - ref).norm() / ref.norm()
+        assert err.item() <= 1e-13
+
+
 def test_noalloc_apply_rejects_ranks_beyond_its_scratch(env):
     torch, P, W = env
     lib = P.load()
