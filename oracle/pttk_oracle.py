@@ -409,6 +409,30 @@ def instantiate(cores, d: int, dtheta: int, mode_boxes, theta, X, Y):
     return U, M, V
 
 
+def twisted_tt(S: np.ndarray, theta_cores, T: np.ndarray) -> list:
+    """[T^(1)(S), G_{d+1}, ..., G_{d+dtheta}, T^(3)(T^T)] (Eq. twist; Section 3.1, Phase 4):
+    an order-(dtheta + 2) TT with mode sizes (N_s, n, ..., n, N_t) whose first core holds S
+    ([T^(1)(S)]_{1,i,j} = s_ij) and whose last holds T^T ([T^(3)(T^T)]_{i,j,1} = t_ji)."""
+    first = S.reshape(1, S.shape[0], S.shape[1])
+    last = T.T.reshape(T.shape[1], T.shape[0], 1)
+    return [first] + [np.array(g, dtype=np.float64) for g in theta_cores] + [last]
+
+
+def phase4(S: np.ndarray, theta_cores, T: np.ndarray, eps: float):
+    """Phase 4 of Algorithm 2: TT-Round (Algorithm 1) of the twisted TT of S, the theta cores
+    and T^T at tolerance eps. Returns (S', theta cores', T', ranks): the compressed factors
+    with K(X, Y; theta) ~= S' H'(theta) T'^T, H' from the rounded theta cores by Eq. hmat."""
+    G, ranks = tt_round(twisted_tt(S, theta_cores, T), eps)
+    S2 = G[0].reshape(G[0].shape[1], G[0].shape[2])
+    T2 = G[-1].reshape(G[-1].shape[0], G[-1].shape[1]).T
+    return S2, G[1:-1], T2, ranks
+
+
+def theta_core_matrix(theta_cores, theta, theta_box) -> np.ndarray:
+    """H(theta) of Eq. hmat from the theta cores alone (Algorithm 3)."""
+    return core_matrix_H(list(theta_cores), 0, len(theta_cores), theta, theta_box)
+
+
 def apply(U, M, V, w) -> np.ndarray:
     """out = U (M (V^T w)): the low-rank matrix-vector product of Eq. paramlowrank."""
     return U @ (M @ (V.T @ w))

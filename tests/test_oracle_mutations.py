@@ -194,6 +194,22 @@ _GLOBAL_PINS = [(pins.test_global_1_is_the_psd_part_of_the_symmetric_part, {}),
                 (pins.test_global_2_keeps_the_fewest_terms, {"definite": False, "eps": 3e-2})]
 
 
+def _twisted_last_untransposed(S, theta_cores, T):
+    # the last core filled from T instead of T^T (same shape only when the ranks allow it:
+    # a reshape of T's memory as r_t x N_t)
+    last = np.asarray(T).reshape(T.shape[1], T.shape[0], 1)
+    return [S.reshape(1, S.shape[0], S.shape[1])] + [np.array(g) for g in theta_cores] + [last]
+
+
+def _twisted_first_transposed(S, theta_cores, T):
+    first = np.asarray(S).T.reshape(1, S.shape[0], S.shape[1])
+    return [first] + [np.array(g) for g in theta_cores] + [T.T.reshape(T.shape[1], T.shape[0], 1)]
+
+
+_PHASE4_PINS = [(pins.test_twisted_tt_represents_S_H_T, {"dtheta": 1}),
+                (pins.test_twisted_tt_represents_S_H_T, {"dtheta": 2})]
+
+
 # name -> (replacements, pins that should catch it as (function, kwargs))
 CASES = {
     "transform c_0 = 2": ({"cheb_transform_matrix": _transform_c0_two},
@@ -252,6 +268,8 @@ CASES = {
     "PTTK-Global: negative eigenvalues kept for a definite kernel": (
         {"global_online": _global_keeps_negatives}, _GLOBAL_PINS),
     "PTTK-Global: compression one term short": ({"global_online": _global_one_term_short}, _GLOBAL_PINS),
+    "Phase 4: last core from T, not T^T": ({"twisted_tt": _twisted_last_untransposed}, _PHASE4_PINS),
+    "Phase 4: first core from S read transposed": ({"twisted_tt": _twisted_first_transposed}, _PHASE4_PINS),
 }
 
 

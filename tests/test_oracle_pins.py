@@ -567,3 +567,76 @@ def test_global_on_the_indefinite_multiquadric_kernel():
     assert o.rel_fro(K, Z @ W @ Z.T) <= plain * (1 + 1e-6)
     Z, W = o.global_factors(S, T, H, definite=True)
     assert o.rel_fro(K, Z @ W @ Z.T) >= 0.1
+
+
+# --- Algorithm 2, Phase 4: TT-Round of the twisted TT [T1(S), G_theta.., T3(T^T)] ----------
+
+def _phase4_case(dtheta=1, Ns=23, Nt=19, n=6, seed=5):
+    """Factors S (Ns x rs) and T (Nt x rt) and theta cores with known structure: S and T have
+    more columns than rank (products through a smaller inner dimension), so rounding must
+    reduce them."""
+    rng = np.random.default_rng(seed)
+    rs, rt, inner = 7, 6, 3
+    S = rng.standard_normal((Ns, inner)) @ rng.standard_normal((inner, rs))
+    T = rng.standard_normal((Nt, inner)) @ rng.standard_normal((inner, rt))
+    ranks = [rs] + [5] * (dtheta - 1) + [rt]
+    cores = [rng.standard_normal((ranks[j], n, ranks[j + 1])) for j in range(dtheta)]
+    return S, cores, T
+
+
+def _full_twisted(S, cores, T):
+    """x[i, k.., j] = sum S[i,a] G_1[a,k_1,b] .. T[j,c] by brute-force einsum (not tt_full)."""
+    if len(cores) == 1:
+        return np.einsum("ia,akb,jb->ikj", S, cores[0], T)
+    return np.einsum("ia,akb,blc,jc->iklj", S, cores[0], cores[1], T)
+
+
+@pytest.mark.parametrize("dtheta", [1, 2])
+def test_twisted_tt_represents_S_H_T(dtheta):
+    S, cores, T = _phase4_case(dtheta)
+    tw = o.twisted_tt(S, cores, T)
+    assert np.allclose(o.tt_full(tw), _full_twisted(S, cores, T), atol=1e-12)
+    # contracting the theta modes with the Chebyshev vectors gives S H(theta) T^T (Eq. hmat)
+    box = [(0.5, 2.0)] * dtheta
+    th = [0.8, 1.7][:dtheta]
+    full = _full_twisted(S, cores, T)
+    n = cores[0].shape[1]
+    for j, (t, (a, b)) in enumerate(zip(th, box)):
+        v = np.polynomial.chebyshev.chebvander(np.array([(2 * t - a - b) / (a - b)]), n - 1)[0]
+        full = np.tensordot(full, v, axes=([1], [0]))
+    assert np.allclose(full, S @ o.theta_core_matrix(cores, th, box) @ T.T, atol=1e-10)
+
+
+@pytest.mark.parametrize("eps", [1e-12, 1e-3])
+def test_phase4_meets_its_tolerance_and_tt_svd_ranks(eps):
+    S, cores, T = _phase4_case(2)
+    X = _full_twisted(S, cores, T)
+    S2, c2, T2, ranks = o.phase4(S, cores, T, eps)
+    X2 = _full_twisted(S2, c2, T2)
+    assert np.linalg.norm(X2 - X) <= eps * np.linalg.norm(X) * (1 + 1e-10) + 1e-13
+    assert ranks == o.tt_svd(X, eps)[1]
+    # the first core is left-orthonormal after the left-to-right sweep
+    assert np.allclose(S2.T @ S2, np.eye(S2.shape[1]), atol=1e-12)
+
+
+def test_phase4_removes_redundant_columns():
+    # S and T have 7 and 6 columns but rank 3: at a tight tolerance the outer ranks become 3
+    S, cores, T = _phase4_case(1)
+    S2, c2, T2, ranks = o.phase4(S, cores, T, 1e-12)
+    assert S2.shape[1] == 3 and T2.shape[1] == 3
+    assert ranks == [1, 3, 3, 1]
+
+
+def test_phase4_per_theta_error_bound():
+    # |T_k| <= 1 on [-1, 1], so the matrix at any theta moves by at most
+    # sqrt(n^dtheta) ||X - X'||_F <= sqrt(n^dtheta) eps ||X||_F
+    S, cores, T = _phase4_case(2, seed=9)
+    eps = 1e-2
+    X = _full_twisted(S, cores, T)
+    S2, c2, T2, _ = o.phase4(S, cores, T, eps)
+    box = [(0.5, 2.0), (0.5, 2.5)]
+    n = cores[0].shape[1]
+    for th in ([0.5, 0.5], [1.3, 2.2], [2.0, 2.5]):
+        K = S @ o.theta_core_matrix(cores, th, box) @ T.T
+        K2 = S2 @ o.theta_core_matrix(c2, th, box) @ T2.T
+        assert np.linalg.norm(K - K2) <= math.sqrt(n ** 2) * eps * np.linalg.norm(X)
