@@ -48,13 +48,18 @@ N_THETA = 256
 WORKLOAD = "d3 matern-nu n12 (12^8 grid), N_s=N_t=1M, 256 theta"
 # nominal dense tensor rates (PFLOP/s) used to carry the measured BF16 peak to other dtypes
 NOMINAL = {"bf16": 2.25, "tf32": 1.1}
-FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12   # FFMA lanes/SM x 2 x SMs x max clock
-FP64_PEAK_TFLOPS = 1.25                             # nominal FP64 rate of the part
-# DRAM bytes (read + write) of one chain_tc launch of the fast form on this workload, from the
-# ncu capture summarised in profiles/chain_tc_fp16x3_c3_online.md (to be emptied whenever the
-# kernel changes after that capture)
-NCU_TRAFFIC = {"fp16x3": 26.541056e6 + 1.373002e9}
+# DRAM bytes (read + write) of one chain_tc launch of the fast form on this workload, from one
+# ncu capture of the kernel source whose SHA-256 prefix is given: the figure is reported only
+# while the source is unchanged, and null otherwise.
+NCU_TRAFFIC = {"fp16x3": {"src_sha16": None, "bytes": None}}
+CHAIN_SRC = os.path.join(ROOT, "paper_2406_06344_gb300", "csrc", "chain_tc.cu")
+# executed FP64 flops per entry of the FP64 grid kernel (K_nu quadrature + in-tile transform),
+# from ncu instruction counts (DFMA x 2 + DADD + DMUL) on the n = 5 grid of the same workload
 GRID_FP64_FLOPS_PER_ENTRY = 944.0
+# peak probes (pttk_peak_probe): loop trips per run, sized for tens of milliseconds
+PROBES = (("dfma", 20000), ("ffma", 200000), ("dmma", 20000), ("tf32", 200000), ("f16", 200000))
+N_ERR_THETA = 8
+N_ERR_SUB = 2000
 
 
 def parse():
@@ -124,6 +129,22 @@ class Clocks:
                         reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def src_sha16(path: str):
+    import hashlib
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def measure_peaks(P):
+    """Rates of the arithmetic pipes on this GPU from the library's peak probes (median of three
+    runs each, TFLOP/s): FP64 FMA, FP32 FMA, FP64 mma.sync, tcgen05 TF32 and FP16."""
+    out = {}
+    for kind, iters in PROBES:
+        P.peak_probe(kind, iters // 10)
+        vals = [P.peak_probe(kind, iters)[0] for _ in range(3)]
+        out[kind] = statistics.median(vals)
+    return out
 
 
 def chain_flops(ranks, d, dtheta, n, N):
@@ -290,6 +311,7 @@ def main():
 
     for _ in range(args.warmup):
         step()
+    pk = measure_peaks(P)
     P.profile_reset()
     P.profile_enable(True)
     if world > 1:
@@ -319,48 +341,60 @@ def main():
     tt = state["tt"]
     hbm, bf16, bf16_sus, peak_src = peaks()
 
-    # roofline of the online factor build (the metric's kernel): chain_tc, both sides per launch
+    # roofline of the online factor build (the metric's kernel): chain_tc, both sides per launch.
+    # achieved = the method's flops (2n sum r_{i-1} r_i per point per side) / the kernel's mean
+    # launch time; peak = the measured dense FP16 rate (FP16 runs at the BF16 rate). A split
+    # form issues three products per algorithmic one, so it can reach at most 1/3 of the peak
+    # in these units; frac_issued counts the three.
     ctc_ms, ctc_n = prof.get("chain_tc", (0.0, 0))
     flops = chain_flops(ranks, w.d, w.dtheta, w.n, N)
     tf32_sus = bf16_sus * NOMINAL["tf32"] / NOMINAL["bf16"]
+    nprod = 3.0 if FAST_FORM.endswith("x3") else 1.0
     roof = None
     if ctc_n:
         achieved = flops / (ctc_ms / ctc_n / 1000.0) / 1e12
-        peak = (bf16_sus if FAST_FORM.startswith(("fp16", "bf16")) else tf32_sus) / (3.0 if FAST_FORM.endswith("x3") else 1.0)
+        peak = bf16_sus if FAST_FORM.startswith(("fp16", "bf16")) else tf32_sus
+        tr = NCU_TRAFFIC.get(FAST_FORM, {})
+        traffic = tr.get("bytes") if tr.get("src_sha16") == src_sha16(CHAIN_SRC) else None
         roof = {"kernel": f"chain_tc ({FAST_FORM} factor chain, both sides, N=1M each)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get(FAST_FORM), "traffic_unit": "bytes per launch (ncu dram read+write)",
+                "frac_issued": achieved * nprod / peak,
+                "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
                 "algorithmic_bytes": float(N * 4 * (w.d + ranks[w.d]) + N * 4 * (w.d + ranks[w.d + w.dtheta])),
                 "flops_per_launch": flops, "avg_launch_ms": ctc_ms / ctc_n, "launches": ctc_n,
-                "peak_note": (f"{peak_src} sustained BF16 {bf16_sus} TFLOP/s (FP16 runs at the BF16 rate; TF32 at "
-                              "x 1.1/2.25 nominal), divided by 3 for the split forms (three products per "
-                              "algorithmic product); achieved counts algorithmic flops 2n sum r_{i-1} r_i "
-                              "per point per side")}
+                "peak_note": (f"{peak_src} sustained BF16 {bf16_sus} TFLOP/s (dense FP16 runs at the BF16 rate; "
+                              "the library's tcgen05 FP16 probe is reported in peaks_measured); achieved counts "
+                              "the method's flops 2n sum r_{i-1} r_i per point per side; frac_issued counts the "
+                              f"{int(nprod)} products of the form; traffic is null unless the capture was taken on "
+                              "the current kernel source")}
     gt_ms, gt_n = prof.get("grid_tile", (0.0, 0))
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
     prof_total = sum(v[0] for v in prof.values())
-    # FP64 flops per entry of the FP64 grid kernel (K_nu quadrature + in-tile transform), from
-    # the instruction counts summarised in profiles/grid_tile_fp64_c3n5.md
+    dfma, ffma = pk["dfma"], pk["ffma"]
+    # executed FP64 flops of the FP64 grid kernel: the K_nu quadrature and the in-tile transform
     grid_fp64_flops = GRID_FP64_FLOPS_PER_ENTRY * total * args.steps * world
-    roof_grid_fp64 = {"kernel": "grid_tile_kernel (FP64)", "bound": "alu (FP64)",
-                      "achieved": grid_fp64_flops / (g64_ms / 1000.0) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                      "unit": "TFLOP/s", "frac": grid_fp64_flops / (g64_ms / 1000.0) / 1e12 / FP64_PEAK_TFLOPS,
-                      "peak_note": "nominal FP64 rate of the part (not measured); flops per entry from ncu "
-                                   "instruction counts on the n = 5 grid of the same workload"}
+    ach64 = grid_fp64_flops / (g64_ms / 1000.0) / 1e12
+    roof_grid_fp64 = {"kernel": "grid_tile_kernel (FP64)", "bound": "alu (FP64 FMA pipe)",
+                      "achieved": ach64, "peak": dfma, "unit": "TFLOP/s", "frac": ach64 / dfma,
+                      "peak_note": "measured FP64 FMA rate (pttk_peak_probe DFMA, this run); executed flops per "
+                                   "entry from ncu instruction counts on the n = 5 grid of the same workload"}
     roof_dominant = {"kernel": dom[0], "ms_total": dom[1][0], "launches": dom[1][1],
                      "share_of_timed_kernel_time": dom[1][0] / max(prof_total, 1e-9),
                      "bound": "alu (FP64)" if dom[0] in ("jacobi", "householder", "dgemm", "grid_tile") else "tensor",
                      "note": "the FP64 offline stage (grid, pivoted QR, Jacobi) holds most of the step; see kernel_ms "
                              "and roofline_grid_fp64"}
+    g32_bytes = total * 4.0 * args.steps * world
     roof_grid = {"fp64_entries_per_s": total * args.steps * world / (g64_ms / 1000.0),
                  "fp32_entries_per_s": total * args.steps * world / (g32_ms / 1000.0),
                  "bound": "alu (K_nu by quadrature)",
+                 "fp32_write_gbs": g32_bytes / (g32_ms / 1000.0) / 1e9,
+                 "fp32_write_frac_of_hbm": g32_bytes / (g32_ms / 1000.0) / 1e9 / hbm,
                  "hbm_write_floor_ms": {"fp64": total * 8 / hbm / 1e6, "fp32": total * 4 / hbm / 1e6},
-                 "peak_note": f"HBM {hbm} GB/s ({peak_src}); FP64 {FP64_PEAK_TFLOPS} / FP32 {FP32_PEAK_TFLOPS:.1f} TFLOP/s"}
+                 "peak_note": f"HBM {hbm} GB/s ({peak_src}); measured FP64 FMA {dfma:.2f} / FP32 FMA {ffma:.1f} TFLOP/s"}
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras = run_extras(torch, P, W, w, tt, X32, Y32, wv, thetas, state, flush, ev)
+        extras = run_extras(torch, P, W, w, tt, X32, Y32, wv, thetas, state, flush, ev, pk, hbm, bf16_sus)
         cores = tt.cores()
         cb, ce, tb, tg, ncores = cpu_leg(w, cores, 20000)
         extras["cpu_baseline"] = {
@@ -383,6 +417,8 @@ def main():
                                   ("grid64_ms", "grid32_ms", "ttsvd_ms", "inst_ms", "apply_ms")},
             "roofline": roof, "roofline_dominant": roof_dominant, "roofline_grid": roof_grid,
             "roofline_grid_fp64": roof_grid_fp64,
+            "peaks_measured": {"unit": "TFLOP/s", "how": "pttk_peak_probe loops, median of 3, before the timed region",
+                               **pk},
             "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()},
             "gpu_launches": int(launches),
             "clocks": clock_info,
@@ -424,44 +460,66 @@ def online_only(args):
                       "ms_per_build": a.elapsed_time(b) / args.online_only, "ranks": ranks}), flush=True)
 
 
-def run_extras(torch, P, W, w, tt, X32, Y32, wv, thetas, state, flush, ev):
+def run_extras(torch, P, W, w, tt, X32, Y32, wv, thetas, state, flush, ev, pk, hbm, bf16_sus):
     """Per-form build rates and errors, the batched and adjoint rows, and end to end.
 
     Errors are measured against the library's FP64 form (which the parity tests hold to the
     oracle) and against the dense kernel; the oracle itself runs only in the CPU leg."""
     out = {}
     N = w.n_points
+    ranks = tt.ranks
     rng = np.random.default_rng(W.SEED_SUB)
-    rs = np.sort(rng.choice(N, 300, replace=False))
-    rt_ = np.sort(rng.choice(N, 300, replace=False))
-    Xs, Ys = X32[rs].double().cpu().numpy(), Y32[rt_].double().cpu().numpy()
-    th0 = thetas[0]
-    Kd = dense_kernel(w.kernel, Xs, Ys, th0)
-    Kref = None
+    rs = np.sort(rng.choice(N, N_ERR_SUB, replace=False))
+    rt_ = np.sort(rng.choice(N, N_ERR_SUB, replace=False))
+    rsd, rtd = torch.tensor(rs, device="cuda"), torch.tensor(rt_, device="cuda")
+    Xs, Ys = X32[rsd].double().cpu().numpy(), Y32[rtd].double().cpu().numpy()
+    eth = thetas[:N_ERR_THETA]
+    # dense K at the FP32-rounded points, on the host (scipy's K_nu), one matrix per theta
+    Kd = [torch.tensor(dense_kernel(w.kernel, Xs, Ys, th), device="cuda") for th in eth]
+    Kref = []
     forms = {}
     X64, Y64 = X32.double(), Y32.double()
+    flops = chain_flops(ranks, w.d, w.dtheta, w.n, N)
     for form in FORMS:
         Xf, Yf = (X64, Y64) if form == "fp64" else (X32, Y32)
-        U, M, V = P.instantiate(tt, th0, Xf, Yf, form)   # first call of a form lays out its images
+        U, M, V = P.instantiate(tt, eth[0], Xf, Yf, form)   # first call of a form lays out its images
         times = []
         for _ in range(3):
             flush.zero_()
             a = ev()
-            P.instantiate(tt, th0, Xf, Yf, form, U=U, M=M, V=V)
+            P.instantiate(tt, eth[0], Xf, Yf, form, U=U, M=M, V=V)
             b = ev()
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b))
+        e_ref, e_dense = [], []
+        for i, th in enumerate(eth):
+            P.instantiate(tt, th, Xf, Yf, form, U=U, M=M, V=V)
+            Kg = U[rsd].double() @ M.double() @ V[rtd].double().T
+            if form == "fp64":                     # FORMS starts with the FP64 form
+                Kref.append(Kg)
+            e_ref.append(float(torch.linalg.norm(Kg - Kref[i]) / torch.linalg.norm(Kref[i])))
+            e_dense.append(float(torch.linalg.norm(Kg - Kd[i]) / torch.linalg.norm(Kd[i])))
         tt.check()
-        Kg = U[rs].double().cpu().numpy() @ M.double().cpu().numpy() @ V[rt_].double().cpu().numpy().T
-        if Kref is None:                     # FORMS starts with the FP64 form
-            Kref = Kg
-        forms[form] = {"builds_per_s": 1000.0 / statistics.median(times), "ms": statistics.median(times),
-                       "rel_err_vs_fp64": rel_fro(Kref, Kg), "rel_err_vs_dense": rel_fro(Kd, Kg)}
+        ms = statistics.median(times)
+        rec = {"builds_per_s": 1000.0 / ms, "ms": ms,
+               "rel_err_vs_fp64": {"max": max(e_ref), "mean": float(np.mean(e_ref))},
+               "rel_err_vs_dense": {"max": max(e_dense), "mean": float(np.mean(e_dense))}}
+        if form in ("fp64", "fp32"):
+            # SIMT chains: the method's flops against the measured FMA rate of their precision
+            peak = pk["dfma"] if form == "fp64" else pk["ffma"]
+            ach = flops / (ms / 1000.0) / 1e12
+            rec["roofline"] = {"bound": "alu (FP64 FMA)" if form == "fp64" else "alu (FP32 FMA)",
+                               "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                               "note": "whole build (H(theta) + both chains); peak measured by pttk_peak_probe"}
+        forms[form] = rec
         del U, M, V
+    th0 = eth[0]
     out["forms"] = forms
     out["fp64_plain_builds_per_s"] = forms["fp64"]["builds_per_s"]
-    out["fp64_floor_rel_err_vs_dense"] = rel_fro(Kd, Kref)
-    out["error_sample"] = "300 x 300 seeded subsample (seed 4) at the first theta"
+    out["fp64_floor_rel_err_vs_dense"] = forms["fp64"]["rel_err_vs_dense"]
+    out["error_sample"] = (f"{N_ERR_SUB} x {N_ERR_SUB} seeded subsample (seed 4) of the 1M x 1M matrix, "
+                           f"max and mean over the first {N_ERR_THETA} theta of the workload")
+    del Kd, Kref
 
     # batched: the d = 2 Matern-3/2 TT, 1024 instances with log-uniform 1k-100k points per side
     w2 = W.C2
@@ -494,32 +552,60 @@ def run_extras(torch, P, W, w, tt, X32, Y32, wv, thetas, state, flush, ev):
         times.append(a.elapsed_time(b))
     tt2.check()
     ms_b = statistics.median(times)
-    # per-instance plain FP64 loop for comparison (first 8 instances, extrapolated)
-    X64b, Y64b = Xb.double(), Yb.double()
+    # the same 1024 instances as a loop of single pttk_instantiate calls in the same form
+    Ml = torch.empty_like(M[0])
+    for bi in range(2):
+        P.instantiate(tt2, thb[bi], Xb[xoff[bi]:xoff[bi + 1]], Yb[yoff[bi]:yoff[bi + 1]], FAST_FORM,
+                      U=U[xoff[bi]:xoff[bi + 1]], M=Ml, V=V[yoff[bi]:yoff[bi + 1]])
+    flush.zero_()
     a = ev()
-    for bi in range(8):
-        P.instantiate(tt2, thb[bi], X64b[xoff[bi]:xoff[bi + 1]].contiguous(), Y64b[yoff[bi]:yoff[bi + 1]].contiguous(), "fp64")
+    for bi in range(len(ns)):
+        P.instantiate(tt2, thb[bi], Xb[xoff[bi]:xoff[bi + 1]], Yb[yoff[bi]:yoff[bi + 1]], FAST_FORM,
+                      U=U[xoff[bi]:xoff[bi + 1]], M=Ml, V=V[yoff[bi]:yoff[bi + 1]])
     b = ev()
     torch.cuda.synchronize()
-    fp64_ms_per_point = a.elapsed_time(b) / float(xoff[8] + yoff[8])
+    loop_ms = a.elapsed_time(b)
+    # the plain FP64 form of the same batch: one FP64 plan over all 1024 instances, measured
+    X64b, Y64b = Xb.double(), Yb.double()
+    b64 = P.Batch(tt2, xoff, yoff, "fp64")
+    U64, M64, V64 = b64.instantiate(thd, X64b, Y64b)
+    torch.cuda.synchronize()
+    a = ev()
+    b64.instantiate(thd, X64b, Y64b, U=U64, M=M64, V=V64)
+    b = ev()
+    torch.cuda.synchronize()
+    fp64_batch_ms = a.elapsed_time(b)
+    tt2.check()
     errs = []
     for bi in (0, 511, 1023):
         rx = np.sort(rng.choice(np.arange(xoff[bi], xoff[bi + 1]), 100, replace=False))
         ry = np.sort(rng.choice(np.arange(yoff[bi], yoff[bi + 1]), 100, replace=False))
-        rxt, ryt = torch.tensor(rx, device="cuda"), torch.tensor(ry, device="cuda")
-        Ur, Mr, Vr = P.instantiate(tt2, thb[bi], Xb[rxt].double().contiguous(), Yb[ryt].double().contiguous(), "fp64")
-        Kr = (Ur @ Mr @ Vr.T).cpu().numpy()
+        Kr = U64[rx].cpu().numpy() @ M64[bi].cpu().numpy() @ V64[ry].cpu().numpy().T
         Kg2 = U[rx].double().cpu().numpy() @ M[bi].double().cpu().numpy() @ V[ry].double().cpu().numpy().T
         errs.append(rel_fro(Kr, Kg2))
+    del U64, M64, V64
+    b64.free()
     pts = float(xoff[-1] + yoff[-1])
+    r2 = tt2.ranks
+    src_f = 2.0 * w2.n * sum(r2[i] * r2[i + 1] for i in range(w2.d))
+    D2 = 2 * w2.d + w2.dtheta
+    tgt_f = 2.0 * w2.n * sum(r2[D2 - i] * r2[D2 - i - 1] for i in range(w2.d))
+    bflops = float(xoff[-1]) * src_f + float(yoff[-1]) * tgt_f
+    bbytes = 4.0 * (float(xoff[-1]) * (w2.d + r2[w2.d]) + float(yoff[-1]) * (w2.d + r2[w2.d + w2.dtheta]))
     out["batched"] = {"workload": "d2 matern-3/2 n20 TT; 1024 instances, N_s, N_t log-uniform in [1e3, 1e5]",
                       "form": FAST_FORM, "instances_per_s": 1024 / (ms_b / 1000.0), "ms_per_batch": ms_b,
                       "points_per_s": pts / (ms_b / 1000.0), "launch": "one CUDA graph replay (H kernel + one persistent factor launch)",
                       "autotune_ms_per_config": tune_ms, "config": batch.config[0],
-                      "fp64_plain_ms_per_batch_est": fp64_ms_per_point * pts,
-                      "speedup_vs_fp64_plain": fp64_ms_per_point * pts / ms_b,
-                      "max_rel_err_vs_fp64_sampled": max(errs)}
-    del U, M, V, Xb, Yb, X64b, Y64b
+                      "loop_of_single_calls_ms": loop_ms, "speedup_vs_loop_of_single_calls": loop_ms / ms_b,
+                      "fp64_plain_batched_ms": fp64_batch_ms, "speedup_vs_fp64_plain": fp64_batch_ms / ms_b,
+                      "max_rel_err_vs_fp64_sampled": max(errs),
+                      "roofline": {"bound": "tensor", "achieved": bflops / (ms_b / 1000.0) / 1e12, "peak": bf16_sus,
+                                   "unit": "TFLOP/s", "frac": bflops / (ms_b / 1000.0) / 1e12 / bf16_sus,
+                                   "bytes": bbytes, "achieved_gbs": bbytes / (ms_b / 1000.0) / 1e9,
+                                   "hbm_frac": bbytes / (ms_b / 1000.0) / 1e9 / hbm,
+                                   "note": "the method's flops and bytes (points in, factors out) of the whole "
+                                           "replay (H kernels included) against dense FP16 and HBM"}}
+    del U, M, V, Xb, Yb, X64b, Y64b, Ml
     batch.free()
     tt2.free()
 
@@ -536,10 +622,23 @@ def run_extras(torch, P, W, w, tt, X32, Y32, wv, thetas, state, flush, ev):
         t0 = time.perf_counter()
         L, dth, dX = P.grad(tt, th0, Xa, Ya, wa_d, za_d, FAST_FORM)
         times.append(time.perf_counter() - t0)
+    P.profile_reset()
+    P.profile_enable(True)
+    P.grad(tt, th0, Xa, Ya, wa_d, za_d, FAST_FORM)
+    P.profile_enable(False)
+    adj_ms, _ = P.profile_get("adjoint")
+    src_f = 2.0 * w.n * sum(ranks[i] * ranks[i + 1] for i in range(w.d))
+    adj_flops = 3.0 * src_f * Na
     out["adjoint"] = {"workload": "d3 matern-nu TT, N_s=N_t=500k, w,z~N(0,1), loss w^T K~ z",
                       "form": FAST_FORM, "grads_per_s": 1.0 / statistics.median(times),
                       "ms": 1000.0 * statistics.median(times), "dtheta": list(map(float, dth)),
-                      "note": "wall time of the synchronous pttk_grad call (loss, dL/dtheta, dL/dX)"}
+                      "note": "wall time of the synchronous pttk_grad call (loss, dL/dtheta, dL/dX)",
+                      "reverse_pass_ms": adj_ms,
+                      "roofline": {"bound": "alu (FP32 FMA)", "achieved": adj_flops / (adj_ms / 1000.0) / 1e12,
+                                   "peak": pk["ffma"], "unit": "TFLOP/s",
+                                   "frac": adj_flops / (adj_ms / 1000.0) / 1e12 / pk["ffma"],
+                                   "note": "reverse pass for dL/dX (FP32 SIMT: recomputed chain prefix and two "
+                                           "reverse products per step), counted as 3x the source chain's flops"}}
 
     # TT-Round (Algorithm 1) of the d = 3 TT: to looser tolerances, and of its sum with itself
     # (ranks doubled), back to 1e-10

@@ -252,6 +252,41 @@ pttk_status pttk_global_instantiate(const pttk_global* g, const double* theta, d
 /* Release a handle and its device memory (NULL is a no-op). */
 void pttk_global_free(pttk_global* g);
 
+/* ---- Algorithm 2 for fixed point sets: Phases 3 and 4 -----------------------------------
+ * When X and Y stay fixed and only theta changes, the paper computes the factors once offline
+ * (Algorithm 2, Phase 3: S = U(X), T = V(Y)) and compresses them with the theta cores by
+ * Phase 4: TT-Round (Algorithm 1) of the twisted TT [T^(1)(S), G_{d+1}, .., G_{d+d_theta},
+ * T^(3)(T^T)] of Eq. twist, an order-(d_theta + 2) TT with mode sizes (N_s, n, .., n, N_t).
+ * The online stage (Algorithm 3) then only contracts the rounded theta cores:
+ * K(X, Y; theta) ~= S' H'(theta) T'^T. */
+typedef struct pttk_fixed pttk_fixed;
+
+/* Phases 3 and 4 on the handle's TT. X: dev N_s x d, Y: dev N_t x d, row-major doubles, inside
+ * their boxes (else PTTK_EDOMAIN), N_s, N_t >= 1. S and T are built by the FP64 factor chains;
+ * tol in (0, 1) rounds them as above with delta = tol / sqrt(d_theta + 1) ||X||_F, X the
+ * twisted tensor; tol = 0 skips Phase 4 (the handle then holds S, T and the theta cores as they
+ * are). FP64 throughout; the factorisations are those of the TT-SVD (pivoted Householder QR and
+ * one-sided Jacobi). The handle keeps S' (N_s x r_s'), T' (N_t x r_t') and the rounded theta
+ * cores on the device; `tt` may be freed afterwards. Synchronises `stream`.
+ * Errors: PTTK_EINVAL, PTTK_EDOMAIN, PTTK_ENOMEM, PTTK_ECUDA, PTTK_ETIMEOUT, PTTK_ENOTSUP (ranks
+ * too large for the FP64 chain). */
+pttk_status pttk_fixed_create(const pttk_tt* tt, const double* X, int64_t N_s, const double* Y, int64_t N_t,
+                              double tol, void* stream, pttk_fixed** out);
+/* N_s, N_t, d_theta, and ranks[0 .. d_theta] = (r_s', inner ranks of the rounded theta cores,
+ * r_t'); for d_theta = 0, ranks[0] = r_s' = r_t'. Any output pointer may be NULL. */
+pttk_status pttk_fixed_dims(const pttk_fixed* f, int64_t* N_s, int64_t* N_t, int* d_theta, int* ranks);
+/* Copies S' (N_s x r_s') and T' (N_t x r_t'), row-major doubles, into the caller's device
+ * buffers (either may be NULL), asynchronously on `stream`. */
+pttk_status pttk_fixed_get_factors(const pttk_fixed* f, double* S, double* T, void* stream);
+/* Copies rounded theta core j (0 <= j < d_theta; ranks[j] x n x ranks[j+1], column-major) to
+ * host memory. Synchronous. */
+pttk_status pttk_fixed_get_core(const pttk_fixed* f, int j, double* host_out);
+/* Algorithm 3 on the rounded cores: M = H'(theta) (dev, r_s' x r_t' row-major; double for
+ * PTTK_FP64, float for PTTK_FP32). theta: host [d_theta], inside its box (else PTTK_EDOMAIN). */
+pttk_status pttk_fixed_theta_core(const pttk_fixed* f, const double* theta, pttk_prec prec, void* M, void* stream);
+/* Release a handle and its device memory (NULL is a no-op). */
+void pttk_fixed_free(pttk_fixed* f);
+
 /* ---- random numbers of the TT greedy-cross (Algorithms 5-7) ----------------------------
  * The greedy-cross draws random index vectors, sample sets, a row-or-column bit and check
  * points. They all come from SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) in counter-based
@@ -313,8 +348,12 @@ pttk_status pttk_batch_create(const pttk_tt* tt, int B, const int64_t* xoff, con
                               pttk_prec prec, void* stream, pttk_batch** out);
 void pttk_batch_free(pttk_batch* b);
 
-/* Launch configuration of the plan's tensor-core factor build (chunk width and operand-ring
- * depth): 0 is the default; pttk_batch_get_config reports the current one and how many exist. */
+/* Launch configuration of the plan's tensor-core factor build; pttk_batch_get_config reports
+ * the current one and how many exist. 0 (the default) and 1: the kernel that generates the A
+ * operand in shared memory, with 128- or 64-byte chunks of K per row and its operand-ring depth;
+ * 2, 3, 4: for the FP16/BF16 forms, the kernel that generates A in tensor memory and keeps the
+ * chain's intermediate in registers, run in thread-block clusters of 1, 2 or 4 CTAs that share
+ * each core chunk by a multicast copy (ranks it cannot hold fall back to configuration 0). */
 pttk_status pttk_batch_set_config(pttk_batch* b, int cfg);
 pttk_status pttk_batch_get_config(const pttk_batch* b, int* cfg, int* n_configs);
 

@@ -695,6 +695,511 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
   if (warp == 1) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
 }
 
+// ---------------- A operand in tensor memory ---------------------------------------------
+// The second form of the chain kernel ("TS": A from tensor memory, B from shared memory), for
+// the kind::f16 forms (FP16, BF16 and their split forms). Shared memory then carries only the
+// core chunks: the generated A operand is written by the generator threads straight into
+// TMEM with tcgen05.st, and the step input S_in stays in registers, read back from the
+// previous step's accumulator with tcgen05.ld. In the shared-memory form every A chunk is
+// written once and read by up to three MMAs, and every step reads S_in from shared memory,
+// which together exceed what shared memory delivers per MMA clock.
+//
+// K order of a step: k = a + R_in_pad j (a < R_in_pad, R_in_pad a multiple of 16). Chunk c
+// holds j in [c jpc, (c + 1) jpc), i.e. jpc R_in_pad values of K (about 64). TMEM layout of one
+// A chunk part (kind::f16, M = 128): lane = point row, column = K pair (two 16-bit values per
+// 32-bit column), so one MMA of K = 16 reads 8 columns. The four generator warps of a lane
+// quarter split the a range: part p owns a in [p spt, (p + 1) spt), spt = R_in_pad / 4, and
+// keeps S_in[row, p spt + i] for i < spt in registers.
+__device__ __forceinline__ void umma_f16_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// 16 single columns c0 .. c0 + 15 of this warp's 32 lanes, one load each, and the wait for
+// them, in one block (so that no use of the values can be scheduled before the wait).
+__device__ __forceinline__ void tmem_ld1x16(uint32_t c0, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%16];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%1}, [%17];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%2}, [%18];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%3}, [%19];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%4}, [%20];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%5}, [%21];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%6}, [%22];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%7}, [%23];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%8}, [%24];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%9}, [%25];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%10}, [%26];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%11}, [%27];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%12}, [%28];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%13}, [%29];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%14}, [%30];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%15}, [%31];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(c0), "r"(c0 + 1), "r"(c0 + 2), "r"(c0 + 3), "r"(c0 + 4), "r"(c0 + 5), "r"(c0 + 6), "r"(c0 + 7),
+        "r"(c0 + 8), "r"(c0 + 9), "r"(c0 + 10), "r"(c0 + 11), "r"(c0 + 12), "r"(c0 + 13), "r"(c0 + 14),
+        "r"(c0 + 15)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int TS_SPT = 16;  // largest a range per generator thread (R_in_pad <= 64)
+
+// Per-step constants of the TS kernel, staged once in shared memory.
+struct TsStepS {
+  const uint8_t* hi;
+  const uint8_t* lo;
+  uint32_t bytes;   // bytes of one chunk part (Npad x kcb)
+  uint32_t idesc;
+  uint32_t sbo;     // 8-row group stride of a B chunk (8 kcb)
+  int nchunks, jpc, R_in_pad, spt, R_out, Npad, coord, ksteps;
+  float lo_box, hi_box, a_scale, out_scale;
+};
+struct TsArgs {
+  TsStepS st[2][3];
+  int nsteps, n, d;
+  int s0_coord[2];
+  float s0_lo[2], s0_hi[2];
+  int64_t N[2];
+  int64_t T0p;       // source tiles, padded to a multiple of the cluster size
+  int64_t nitems;    // cluster items: CL consecutive tiles of one side each
+  const float* pts[2];
+  float* out[2];
+  int* status;
+  int ld_seed;       // row stride of the first step's input (odd)
+  int bv_ld;         // row stride of the basis buffers (odd, > every step's nchunks jpc)
+  int acc1_col;      // TMEM column of the first step's own accumulator (two or more steps)
+  int a_col;         // TMEM column of A slot 0
+  int a_part_cols;   // TMEM columns of one A part of a slot
+  int tmem_cols;
+  uint32_t b_slot_bytes;  // bytes reserved per B part per slot
+};
+
+// 16-bit pair of a generated A value pair: FP16 or BF16, and the residual's pair for the split
+template <int FMT, bool SPLIT>
+__device__ __forceinline__ void pack_pair(float v0, float v1, uint32_t& h, uint32_t& l) {
+  if constexpr (FMT == FMT_BF16) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(v0, v1);
+    h = *reinterpret_cast<const uint32_t*>(&hb);
+    if (SPLIT) {
+      const float2 hf = __bfloat1622float2(hb);
+      const __nv_bfloat162 lb = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+      l = *reinterpret_cast<const uint32_t*>(&lb);
+    }
+  } else {
+    const __half2 hh = __floats2half2_rn(v0, v1);
+    h = *reinterpret_cast<const uint32_t*>(&hh);
+    if (SPLIT) {
+      const float2 hf = __half22float2(hh);
+      const __half2 lh = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+      l = *reinterpret_cast<const uint32_t*>(&lh);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// bulk copy of `bytes` from global memory to the same shared-memory offset in every CTA of the
+// cluster named by `mask`, each destination's mbarrier (same offset) receiving the bytes
+__device__ __forceinline__ void tma_load_1d_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+// arrive on the mbarrier at this offset in every CTA of `mask` once this thread's MMAs complete
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "h"(mask)
+               : "memory");
+}
+
+// Warp roles as in chain_tc_kernel: warp 0 (one lane) streams core chunks into the NS-deep
+// shared-memory ring with TMA, warp 1 (one lane) issues the MMAs, warps 2..17 generate A into
+// the NS-deep TMEM ring and run the epilogues.
+//
+// Every 128-point tile streams the whole oriented core through shared memory, so at these
+// ranks the core traffic from L2 rivals the MMA time. The CL CTAs of a thread-block cluster
+// therefore work in lockstep on CL consecutive tiles of one side (a cluster item; each side's
+// tile count is padded to a multiple of CL with empty tiles), and each CTA loads 1/CL of every
+// core chunk with a multicast copy into all CL CTAs: the L2 traffic of the cores falls by CL.
+// Barriers per slot: full_a (16 generator warps arrive after their tcgen05.st completed),
+// full_b (the chunk's bytes from all CL copies), empty_a (the local MMAs of the slot completed:
+// the TMEM slot may be rewritten), empty_b (the MMAs of the slot completed in every CTA of the
+// cluster: the shared-memory slot, written by every CTA's copies, may be reloaded).
+template <int FMT, bool SPLIT, int NS, int CL>
+__global__ void __launch_bounds__(TC_THREADS, 1) chain_ts_kernel(TsArgs a) {
+  constexpr int PARTS = SPLIT ? 2 : 1;
+  constexpr uint16_t MASK = (uint16_t)((1u << CL) - 1u);
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int bv_ld = a.bv_ld;
+  uint8_t* b_base = smem;                                                // NS x PARTS x b_slot_bytes
+  float* Bv = reinterpret_cast<float*>(b_base + (size_t)NS * PARTS * a.b_slot_bytes);  // 2 x 128 x bv_ld
+  float* Sseed = Bv + (size_t)2 * TILE_M * bv_ld;                        // 128 x ld_seed
+  float* stage = Sseed + (size_t)TILE_M * a.ld_seed;                     // NGEN_WARPS x 32 x STAGE_LD
+  TsStepS* steps = reinterpret_cast<TsStepS*>(
+      (reinterpret_cast<uintptr_t>(stage + (size_t)NGEN_WARPS * 32 * STAGE_LD) + 15) & ~uintptr_t(15));  // [2][3]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(steps + 6);
+  uint64_t* full_a = bars;
+  uint64_t* full_b = bars + NS;
+  uint64_t* empty_a = bars + 2 * NS;
+  uint64_t* empty_b = bars + 3 * NS;
+  uint64_t* acc_ready = bars + 4 * NS;  // [0]: accumulator 0, [1]: the first step's own
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4 * NS + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int crank = CL > 1 ? (int)cluster_rank() : 0;
+  const int64_t cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full_a[i], NGEN_WARPS);
+      mbar_init(&full_b[i], 1);
+      mbar_init(&empty_a[i], 1);
+      mbar_init(&empty_b[i], CL);
+    }
+    mbar_init(&acc_ready[0], 1);
+    mbar_init(&acc_ready[1], 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (tid < 2 * a.nsteps) steps[(tid / a.nsteps) * 3 + tid % a.nsteps] = a.st[tid / a.nsteps][tid % a.nsteps];
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (CL > 1) cluster_sync_all();  // every CTA's barriers exist before any copy or commit reaches them
+  const uint32_t tmem = *tmem_slot;
+  const int64_t nitems = a.nitems;
+  const int nsteps = a.nsteps;
+  // side, first row and row count of this CTA's tile in cluster item k
+  auto item_side = [&](int64_t k) -> int { return k * CL < a.T0p ? 0 : 1; };
+  auto item_row0 = [&](int64_t k) -> int64_t {
+    const int sd = item_side(k);
+    return (k * CL + crank - (sd ? a.T0p : 0)) * TILE_M;
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer: this CTA's share of every chunk, to every CTA ----------------
+    if (lane == 0) {
+      uint32_t h = 0;
+      bool ok = true;
+      for (int64_t it = cid; it < nitems && ok; it += ncl) {
+        const int sd = item_side(it);
+        for (int si = 0; si < nsteps && ok; ++si) {
+          const TsStepS& st = steps[sd * 3 + si];
+          const uint32_t bytes = st.bytes;
+          // the chunk's 8-row groups are split over the CL CTAs (the last ones may get none)
+          const uint32_t groups = bytes / st.sbo, gper = (groups + CL - 1) / CL;
+          const uint32_t off = min((uint32_t)crank * gper, groups) * st.sbo;
+          const uint32_t len = min(gper * st.sbo, bytes - off);
+          for (int c = 0; c < st.nchunks; ++c, ++h) {
+            const uint32_t slot = h % NS;
+            if (h >= NS && !mbar_wait(&empty_b[slot], ((h / NS) - 1) & 1, abort_flag)) { ok = false; break; }
+            uint8_t* bh = b_base + (size_t)slot * PARTS * a.b_slot_bytes;
+            mbar_arrive_expect_tx(&full_b[slot], SPLIT ? 2 * bytes : bytes);
+            if (len > 0) {
+              if (CL > 1) {
+                tma_load_1d_mc(bh + off, st.hi + (size_t)c * bytes + off, len, &full_b[slot], MASK);
+                if (SPLIT) tma_load_1d_mc(bh + a.b_slot_bytes + off, st.lo + (size_t)c * bytes + off, len, &full_b[slot], MASK);
+              } else {
+                tma_load_1d(bh, st.hi + (size_t)c * bytes, bytes, &full_b[slot]);
+                if (SPLIT) tma_load_1d(bh + a.b_slot_bytes, st.lo + (size_t)c * bytes, bytes, &full_b[slot]);
+              }
+            }
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(a.status, (int)PTTK_ETIMEOUT);
+      }
+      const int zero = 0;
+      for (uint32_t k = (h > (uint32_t)NS ? h - NS : 0); k < h; ++k) mbar_wait(&full_b[k % NS], (k / NS) & 1, &zero);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t it = cid; it < nitems && ok; it += ncl) {
+        const int sd = item_side(it);
+        for (int si = 0; si < nsteps && ok; ++si) {
+          const TsStepS& st = steps[sd * 3 + si];
+          const uint32_t idesc = st.idesc, sbo = st.sbo;
+          const int ksteps = st.ksteps, nch = st.nchunks;
+          const int ab = (si == 0 && nsteps > 1) ? 1 : 0;
+          const uint32_t dacc = tmem + (ab ? (uint32_t)a.acc1_col : 0u);
+          for (int c = 0; c < nch; ++c, ++g) {
+            const uint32_t slot = g % NS, par = (g / NS) & 1;
+            if (!mbar_wait(&full_a[slot], par, abort_flag) || !mbar_wait(&full_b[slot], par, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t ta = tmem + (uint32_t)(a.a_col + (int)slot * PARTS * a.a_part_cols);
+            const uint32_t sb = smem_u32(b_base + (size_t)slot * PARTS * a.b_slot_bytes);
+            const uint64_t bh0 = smem_desc2(sb, sbo);
+            const uint64_t bl0 = smem_desc2(sb + a.b_slot_bytes, sbo);
+            for (int k = 0; k < ksteps; ++k) {
+              const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+              // +256 bytes of K per MMA: +16 in the descriptor's address field (no carry: the
+              // chunk lies inside the 256 KB the 14-bit field addresses)
+              const uint64_t bh = bh0 + (uint64_t)(16 * k);
+              umma_f16_ts(dacc, ta + 8 * k, bh, idesc, acc);
+              if (SPLIT) {
+                umma_f16_ts(dacc, ta + 8 * k, bl0 + (uint64_t)(16 * k), idesc, 1u);
+                umma_f16_ts(dacc, ta + (uint32_t)a.a_part_cols + 8 * k, bh, idesc, 1u);
+              }
+            }
+            umma_commit(&empty_a[slot]);
+            if (CL > 1) umma_commit_mc(&empty_b[slot], MASK);
+            else umma_commit(&empty_b[slot]);
+            if (c == nch - 1) umma_commit(&acc_ready[ab]);
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(a.status, (int)PTTK_ETIMEOUT);
+      }
+      const int zero = 0;
+      if (g > 0) mbar_wait(&empty_a[(g - 1) % NS], ((g - 1) / NS) & 1, &zero);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- generator warps: A chunks into TMEM, S in registers, epilogues ----------
+    const int gw = warp - 2;                   // 0..NGEN_WARPS-1
+    const int quarter = warp & 3;              // TMEM lane quarter this warp may access
+    const int row = 32 * quarter + lane;
+    const int part = gw >> 2;                  // which quarter of the a range
+    const uint32_t lanes = (uint32_t)(32 * quarter) << 16;
+    uint32_t g = 0;
+    bool dead = false;
+    float S[TS_SPT];                           // S_in[row, part spt + i]
+    auto basis = [&](int sd, int si, int buf, float x) {
+      const TsStepS& st = steps[sd * 3 + si];
+      const float xh = (2.f * x - st.lo_box - st.hi_box) / (st.lo_box - st.hi_box);
+      float* bv = Bv + ((size_t)buf * TILE_M + row) * bv_ld;
+      const float sc = st.a_scale;
+      float t0 = 1.f, t1 = xh;
+      bv[0] = sc;
+      for (int k = 1; k < a.n; ++k) {
+        bv[k] = t1 * sc;
+        const float t2 = 2.f * xh * t1 - t0;
+        t0 = t1;
+        t1 = t2;
+      }
+      for (int k = a.n; k < bv_ld; ++k) bv[k] = 0.f;
+    };
+    auto coord_of = [&](int64_t it, int si) -> float {
+      const int sd = item_side(it);
+      const int64_t gp = item_row0(it) + row;
+      const TsStepS& st = steps[sd * 3 + si];
+      return gp < a.N[sd] ? a.pts[sd][gp * a.d + st.coord] : st.lo_box;
+    };
+    auto seed_coord_of = [&](int64_t it) -> float {
+      const int sd = item_side(it);
+      const int64_t gp = item_row0(it) + row;
+      return (a.s0_coord[sd] >= 0 && gp < a.N[sd]) ? a.pts[sd][gp * a.d + a.s0_coord[sd]] : a.s0_lo[sd];
+    };
+    // input of the first step of item `it` (threads of part 0): T_0..T_{n-1}(xhat) of the seed
+    // coordinate (merged first steps), or S_0 = 1; zero up to the step's R_in_pad
+    auto write_seed = [&](int64_t it, float x) {
+      const int sd = item_side(it);
+      float* w = Sseed + (size_t)row * a.ld_seed;
+      const int pad = steps[sd * 3].R_in_pad;
+      if (a.s0_coord[sd] >= 0) {
+        const float lo = a.s0_lo[sd], hi = a.s0_hi[sd];
+        const float xh = (2.f * x - lo - hi) / (lo - hi);
+        float t0 = 1.f, t1 = xh;
+        w[0] = 1.f;
+        for (int k = 1; k < pad; ++k) {
+          w[k] = k < a.n ? t1 : 0.f;
+          const float t2 = 2.f * xh * t1 - t0;
+          t0 = t1;
+          t1 = t2;
+        }
+      } else {
+        w[0] = 1.f;
+        for (int k = 1; k < pad; ++k) w[k] = 0.f;
+      }
+    };
+    auto load_seed = [&](int sd) {
+      const int spt = steps[sd * 3].spt;
+      const float* w = Sseed + (size_t)row * a.ld_seed + part * spt;
+#pragma unroll
+      for (int i = 0; i < TS_SPT; ++i) S[i] = i < spt ? w[i] : 0.f;
+    };
+    auto write_output = [&](int osd, int64_t orow0, int orows, uint32_t lane_addr) {
+      const TsStepS& st = steps[osd * 3 + nsteps - 1];
+      float* stg = stage + (size_t)gw * 32 * STAGE_LD;
+      const int R = st.R_out;
+      float* outbase = a.out[osd] + (orow0 + 32 * quarter) * R;
+      const int wrows = std::max(0, std::min(32, orows - 32 * quarter));
+      if (wrows == 0) return;
+      const int sub = lane >> 4, lc = lane & 15;
+      for (int cb = STAGE_COLS * part; cb < st.Npad; cb += STAGE_COLS * NPART) {
+        float v[STAGE_COLS];
+        tmem_ld16(lane_addr + (uint32_t)cb, v);
+#pragma unroll
+        for (int i = 0; i < STAGE_COLS; ++i) stg[lane * STAGE_LD + i] = v[i] * st.out_scale;
+        __syncwarp();
+        const int col = cb + lc;
+        if (col < R)
+          for (int rr = sub; rr < wrows; rr += 2) outbase[(int64_t)rr * R + col] = stg[rr * STAGE_LD + lc];
+        __syncwarp();
+      }
+    };
+    uint32_t done_acc[2] = {0u, 0u};
+    auto wait_acc = [&](int ab) {
+      if (!dead && !*abort_flag) dead = !mbar_wait(&acc_ready[ab], done_acc[ab] & 1, abort_flag);
+      ++done_acc[ab];
+      dead = __any_sync(0xffffffffu, dead || *abort_flag);
+      if (dead && lane == 0) *abort_flag = 1;
+      tc_fence_after();
+    };
+    const bool defer = nsteps > 1;
+    float xn[4] = {0.f, 0.f, 0.f, 0.f};
+    if (part == 0 && cid < nitems) {
+      for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(cid, si);
+      xn[3] = seed_coord_of(cid);
+      basis(item_side(cid), 0, 0, xn[0]);
+      write_seed(cid, xn[3]);
+    }
+    gen_barrier();
+    uint32_t bufsel = 0;
+    bool out_pending = false;
+    int out_sd = 0, out_rows = 0;
+    int64_t out_row0 = 0;
+    for (int64_t it = cid; it < nitems; it += ncl) {
+      const int sd = item_side(it);
+      const int64_t row0 = item_row0(it);
+      const int rows = (int)std::max<int64_t>(0, std::min<int64_t>(TILE_M, a.N[sd] - row0));
+      float xcur[3] = {xn[0], xn[1], xn[2]};
+      const int64_t itn = it + ncl;
+      if (part == 0 && itn < nitems) {
+        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
+        xn[3] = seed_coord_of(itn);
+      }
+      load_seed(sd);
+      for (int si = 0; si < nsteps; ++si) {
+        const TsStepS& st = steps[sd * 3 + si];
+        const int nch = st.nchunks, jpc = st.jpc, rpad = st.R_in_pad, spt = st.spt;
+        const float* bvrow = Bv + ((size_t)bufsel * TILE_M + row) * bv_ld;
+        for (int c = 0; c < nch; ++c, ++g) {
+          const uint32_t slot = g % NS, use = g / NS;
+          dead = dead || *abort_flag;
+          if (!dead && g >= (uint32_t)NS) dead = !mbar_wait(&empty_a[slot], (use - 1) & 1, abort_flag);
+          dead = __any_sync(0xffffffffu, dead);
+          if (dead && lane == 0) *abort_flag = 1;
+          if (!dead) {
+            tc_fence_after();
+            const uint32_t cbase = tmem + lanes + (uint32_t)(a.a_col + (int)slot * PARTS * a.a_part_cols);
+            for (int jj = 0; jj < jpc; ++jj) {
+              const float b = bvrow[c * jpc + jj];
+              const uint32_t col = cbase + (uint32_t)((jj * rpad + part * spt) >> 1);
+#pragma unroll
+              for (int i = 0; i < TS_SPT; i += 2) {
+                if (i < spt) {
+                  uint32_t h, l;
+                  pack_pair<FMT, SPLIT>(b * S[i], b * S[i + 1], h, l);
+                  tmem_st1(col + (uint32_t)(i >> 1), h);
+                  if (SPLIT) tmem_st1(col + (uint32_t)a.a_part_cols + (uint32_t)(i >> 1), l);
+                }
+              }
+            }
+            tmem_wait_st();
+            tc_fence_before();
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full_a[slot]);
+        }
+        const bool last = si == nsteps - 1;
+        if (part == 0) {
+          if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
+          else if (itn < nitems) basis(item_side(itn), 0, bufsel ^ 1, xn[0]);
+        }
+        if (si == 0 && out_pending) {
+          wait_acc(0);
+          if (!dead) write_output(out_sd, out_row0, out_rows, tmem + lanes);
+          out_pending = false;
+        }
+        if (last && defer && itn < nitems) {
+          out_pending = true;
+          out_sd = sd;
+          out_row0 = row0;
+          out_rows = rows;
+          // the seed of the next item: this item's seed was read into registers before its
+          // first step, and every thread passed the barrier below since
+          if (part == 0) write_seed(itn, xn[3]);
+          bufsel ^= 1;
+          tc_fence_before();
+          gen_barrier();
+          continue;
+        }
+        const int ab = (si == 0 && defer) ? 1 : 0;
+        wait_acc(ab);
+        const uint32_t lane_addr = tmem + lanes + (ab ? (uint32_t)a.acc1_col : 0u);
+        if (!last) {
+          // S_in of the next step: this thread's spt columns of the accumulator (columns at or
+          // beyond R_out hold zeros: the core images are zero there)
+          const TsStepS& nx = steps[sd * 3 + si + 1];
+          if (!dead) {
+            float v[16];
+            tmem_ld1x16(lane_addr + (uint32_t)(part * nx.spt), v);
+            const float osc = st.out_scale;
+#pragma unroll
+            for (int i = 0; i < TS_SPT; ++i) S[i] = i < nx.spt ? v[i] * osc : 0.f;
+          }
+        } else if (!dead) {
+          write_output(sd, row0, rows, lane_addr);
+        }
+        bufsel ^= 1;
+        tc_fence_before();
+        gen_barrier();
+        if (last && !defer && itn < nitems) {
+          if (part == 0) write_seed(itn, xn[3]);
+          gen_barrier();
+        }
+      }
+    }
+    if (dead && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(a.status, (int)PTTK_ETIMEOUT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  // no CTA leaves while a peer may still copy into its shared memory or commit to its barriers
+  if (CL > 1) cluster_sync_all();
+  if (warp == 1) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+}
+
 // ---------------- core images -------------------------------------------------------------
 // Image of the oriented core (K x R_out, column-major, FP64; K = n R_in) for one chain step in
 // the padded K order k' = a + R_in_pad j (zero rows for a >= R_in): chunk c holds rows o < Npad
@@ -737,6 +1242,7 @@ struct Images {
   uint8_t* buf = nullptr;
   size_t hi_off[2][3] = {}, lo_off[2][3] = {};
   int Npad[2][3] = {}, nchunks[2][3] = {}, R_in_pad[2][3] = {};
+  int jpc[2][3] = {}, kcb[2][3] = {};  // TS images: basis values per chunk, bytes of K per row
   float a_scale[2][3] = {}, out_scale[2][3] = {};
 };
 
@@ -747,6 +1253,7 @@ std::mutex g_img_mu;
 // Per-handle image cache, indexed by form and chunk width (64 or 128 bytes of K per row).
 struct TcImageCache {
   Images img[6][2];
+  Images ts[6];                       // images of the TS kernel (kind::f16 forms)
   double* L[2] = {nullptr, nullptr};  // merged first two cores per side (see tc_chain_steps)
 };
 
@@ -768,6 +1275,8 @@ void tc_cache_free(TcImageCache* c) {
   for (auto& f : c->img)
     for (auto& im : f)
       if (im.buf) cudaFree(im.buf);
+  for (auto& im : c->ts)
+    if (im.buf) cudaFree(im.buf);
   for (double* L : c->L)
     if (L) cudaFree(L);
   delete c;
@@ -930,18 +1439,180 @@ static pttk_status build_images(const pttk_tt* tt, const TcImageCache* cache, pt
   return PTTK_OK;
 }
 
-// Launch configurations per form: {KCB, NSLOT}. Configuration 0 is the default.
+// Launch configurations. 0 and 1: the shared-memory kernel with {KCB, NSLOT} below (0 is the
+// default: the fastest on the d = 3 workload's ranks); 2..4: the TS kernel (A in tensor memory,
+// a ring of 3 slots) in thread-block clusters of 1, 2 or 4 CTAs, for the kind::f16 forms whose
+// ranks fit it (otherwise the shared-memory kernel's default).
 static const int kTcConfigs[2][2] = {{128, 4}, {64, 4}};
 static const int kTcConfigsSplit[2][2] = {{128, 2}, {64, 4}};
+constexpr int kTcSubConfigs = 2, kTsConfigs = 3;
+static const int kTsCluster[kTsConfigs] = {1, 2, 4};
 
-int tc_config_count() { return 2; }
+int tc_config_count() { return kTcSubConfigs + kTsConfigs; }
+static bool ts_form(pttk_prec p) { return p == PTTK_FP16 || p == PTTK_FP16X3 || p == PTTK_BF16 || p == PTTK_BF16X3; }
+static bool ts_config(int cfg) { return cfg >= kTcSubConfigs && cfg < kTcSubConfigs + kTsConfigs; }
+static int tc_sub_config(int cfg) { return cfg >= 0 && cfg < kTcSubConfigs ? cfg : 0; }
 
 static void tc_config(pttk_prec prec, int cfg, int* KCB, int* NS) {
   const bool split = form_split(prec);
   const int (*t)[2] = split ? kTcConfigsSplit : kTcConfigs;
-  cfg = (cfg < 0 || cfg > 1) ? 0 : cfg;
+  cfg = tc_sub_config(cfg);
   *KCB = t[cfg][0];
   *NS = t[cfg][1];
+}
+
+// TS images: per step, R_in padded to 16, jpc basis values per chunk (K of a chunk about 64),
+// each chunk of a part Npad x kcb bytes in the K-major no-swizzle layout.
+static pttk_status build_images_ts(const pttk_tt* tt, const TcImageCache* cache, pttk_prec prec, Images& im,
+                                   cudaStream_t s) {
+  const int fmt = form_fmt(prec);
+  const bool split = form_split(prec);
+  double img_scale[2][3];
+  PTTK_TRY(step_scales(tt, cache, prec, im, img_scale));
+  TcChainStep cs[2][3];
+  int s0[2], nst = 0;
+  for (int side = 0; side < 2; ++side) nst = tc_chain_steps(tt, cache, side, cs[side], &s0[side]);
+  size_t total = 0;
+  for (int side = 0; side < 2; ++side)
+    for (int i = 0; i < nst; ++i) {
+      const int rin = cs[side][i].R_in, rout = cs[side][i].R_out;
+      const int rpad = ((rin + 15) / 16) * 16;
+      const int jpc = std::max(1, std::min(tt->n, 64 / rpad));
+      im.R_in_pad[side][i] = rpad;
+      im.jpc[side][i] = jpc;
+      im.kcb[side][i] = 2 * jpc * rpad;
+      im.Npad[side][i] = ((rout + 15) / 16) * 16;
+      im.nchunks[side][i] = (tt->n + jpc - 1) / jpc;
+      const size_t bytes = (size_t)im.nchunks[side][i] * im.Npad[side][i] * im.kcb[side][i];
+      im.hi_off[side][i] = total;
+      total += bytes;
+      im.lo_off[side][i] = total;
+      if (split) total += bytes;
+    }
+  PTTK_CUDA(cudaMalloc(&im.buf, std::max<size_t>(total, 16)));
+  PTTK_CUDA(cudaMemsetAsync(im.buf, 0, std::max<size_t>(total, 16), s));
+  for (int side = 0; side < 2; ++side)
+    for (int i = 0; i < nst; ++i) {
+      const int KC = im.kcb[side][i] / 2;
+      const int64_t work = (int64_t)im.nchunks[side][i] * im.Npad[side][i] * KC;
+      const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count() * 8);
+      auto* kfn = fmt == FMT_BF16 ? core_image_kernel<FMT_BF16> : core_image_kernel<FMT_FP16>;
+      kfn<<<blocks, 256, 0, s>>>(cs[side][i].G, tt->n, cs[side][i].R_in, im.R_in_pad[side][i], cs[side][i].R_out,
+                                 im.Npad[side][i], im.nchunks[side][i], im.kcb[side][i], split, img_scale[side][i],
+                                 im.buf + im.hi_off[side][i], im.buf + im.lo_off[side][i]); pttk::count_launch();
+    }
+  PTTK_CUDA(cudaGetLastError());
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  return PTTK_OK;
+}
+
+// Launch arguments of the TS kernel for these inputs; false (and no error) when the ranks do
+// not fit it (an a range above 16 per thread, a rank above 256, tensor or shared memory).
+static bool ts_plan(const pttk_tt* tt, const TcImageCache* cache, const Images& im, pttk_prec prec, int NS,
+                    TsArgs& a, size_t* smem_out) {
+  const bool split = form_split(prec);
+  const int parts = split ? 2 : 1;
+  const int fmt = form_fmt(prec);
+  a = TsArgs{};
+  a.n = tt->n;
+  a.d = tt->d;
+  int nst = 0, acc0w = 16, acc1w = 0, a_part = 8, bvl = 1;
+  uint32_t bslot = 0;
+  for (int side = 0; side < 2; ++side) {
+    TcChainStep cs[3];
+    int s0;
+    nst = tc_chain_steps(tt, cache, side, cs, &s0);
+    a.s0_coord[side] = s0;
+    const int b0 = s0 < 0 ? 0 : (side == 0 ? s0 : tt->d + tt->dtheta + s0);
+    a.s0_lo[side] = (float)tt->box[b0][0];
+    a.s0_hi[side] = (float)tt->box[b0][1];
+    for (int i = 0; i < nst; ++i) {
+      TsStepS& st = a.st[side][i];
+      const int rpad = im.R_in_pad[side][i], jpc = im.jpc[side][i], kcb = im.kcb[side][i];
+      if (rpad > 4 * TS_SPT || im.Npad[side][i] > 256) return false;
+      st.hi = im.buf + im.hi_off[side][i];
+      st.lo = split ? im.buf + im.lo_off[side][i] : nullptr;
+      st.Npad = im.Npad[side][i];
+      st.bytes = (uint32_t)st.Npad * kcb;
+      st.idesc = instr_desc(fmt_code(fmt), TILE_M, st.Npad);
+      st.sbo = 8u * (uint32_t)kcb;
+      st.nchunks = im.nchunks[side][i];
+      st.jpc = jpc;
+      st.R_in_pad = rpad;
+      st.spt = rpad / 4;
+      st.R_out = cs[i].R_out;
+      st.coord = cs[i].coord;
+      st.ksteps = jpc * rpad / 16;
+      const int bj = side == 0 ? cs[i].coord : tt->d + tt->dtheta + cs[i].coord;
+      st.lo_box = (float)tt->box[bj][0];
+      st.hi_box = (float)tt->box[bj][1];
+      st.a_scale = im.a_scale[side][i];
+      st.out_scale = im.out_scale[side][i];
+      if (nst > 1 && i == 0) acc1w = std::max(acc1w, st.Npad);
+      else acc0w = std::max(acc0w, st.Npad);
+      a_part = std::max(a_part, jpc * rpad / 2);
+      bslot = std::max(bslot, st.bytes);
+      bvl = std::max(bvl, st.nchunks * jpc);
+    }
+  }
+  a.nsteps = nst;
+  a.bv_ld = (bvl + 1) | 1;
+  const int pad0 = std::max(a.st[0][0].R_in_pad, a.st[1][0].R_in_pad);
+  a.ld_seed = pad0 | 1;
+  auto r32 = [](int x) { return ((x + 31) / 32) * 32; };
+  a.acc1_col = nst > 1 ? r32(acc0w) : 0;
+  a.a_col = nst > 1 ? a.acc1_col + r32(acc1w) : r32(acc0w);
+  a.a_part_cols = a_part;
+  // columns in use; the readback of S may read up to 4 TS_SPT columns past an accumulator's start
+  const int need = std::max(a.a_col + NS * parts * a_part, (nst > 1 ? a.acc1_col : 0) + 4 * TS_SPT);
+  int cols = 32;
+  while (cols < need) cols <<= 1;
+  if (cols > 512) return false;
+  a.tmem_cols = cols;
+  a.b_slot_bytes = bslot;
+  const size_t smem = (size_t)NS * parts * bslot +
+                      sizeof(float) * ((size_t)2 * TILE_M * a.bv_ld + (size_t)TILE_M * a.ld_seed +
+                                       (size_t)NGEN_WARPS * 32 * STAGE_LD) +
+                      16 + sizeof(TsStepS) * 6 + 8 * (4 * NS + 2) + 16;
+  if (smem > 227 * 1024) return false;
+  *smem_out = std::max<size_t>(smem, 116 * 1024);  // one CTA (one TMEM allocation) per SM
+  return true;
+}
+
+// Grid of the TS kernel: one CTA per SM in clusters of CL, as many clusters as can be
+// resident at once (clusters are placed within a GPC, so with CL > 1 a few SMs may stay idle),
+// and no more than there are cluster items.
+template <int FMT, bool SPLIT, int NS, int CL>
+static pttk_status launch_ts(TsArgs a, int64_t T0, int64_t T1, size_t smem, cudaStream_t s) {
+  auto kfn = chain_ts_kernel<FMT, SPLIT, NS, CL>;
+  PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (CL > 1) PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
+  a.T0p = (T0 + CL - 1) / CL * CL;
+  a.nitems = (a.T0p + (T1 + CL - 1) / CL * CL) / CL;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  int64_t nclusters = sm_count() / CL;
+  if (CL > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(nclusters * CL));
+    int active = 0;
+    PTTK_CUDA(cudaOccupancyMaxActiveClusters(&active, kfn, &cfg));
+    if (active < 1) return set_error(PTTK_ENOTSUP, "tensor-core chain: no cluster of this size fits");
+    nclusters = std::min<int64_t>(nclusters, active);
+  }
+  nclusters = std::max<int64_t>(1, std::min<int64_t>(nclusters, a.nitems));
+  cfg.gridDim = dim3((unsigned)(nclusters * CL));
+  PTTK_CUDA(cudaLaunchKernelEx(&cfg, kfn, a));
+  pttk::count_launch();
+  return PTTK_OK;
 }
 
 // Images for (prec, config) exist after this returns (first use lays them out; synchronises).
@@ -953,6 +1624,13 @@ pttk_status tc_prepare(const pttk_tt* tt, TcImageCache* cache, pttk_prec prec, i
   Images& im = cache->img[fi][KCB == 64 ? 0 : 1];
   std::lock_guard<std::mutex> lk(g_img_mu);
   PTTK_TRY(ensure_merged(tt, cache));
+  if (ts_config(cfg) && ts_form(prec)) {
+    Images& ti = cache->ts[fi];
+    if (!ti.buf) PTTK_TRY(build_images_ts(tt, cache, prec, ti, s));
+    TsArgs probe;
+    size_t smem;
+    if (ts_plan(tt, cache, ti, prec, 3, probe, &smem)) return PTTK_OK;
+  }
   if (!im.buf) PTTK_TRY(build_images(tt, cache, prec, KCB, im, s));
   return PTTK_OK;
 }
@@ -974,6 +1652,34 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
   if (N_s == 0 && N_t == 0) return PTTK_OK;
   PTTK_TRY(tc_prepare(tt, cache, prec, cfg, s));
   const int fi = form_index(prec);
+  if (ts_config(cfg) && ts_form(prec)) {
+    const int NS = 3, CL = kTsCluster[cfg - kTcSubConfigs];
+    TsArgs a;
+    size_t smem = 0;
+    if (ts_plan(tt, cache, cache->ts[fi], prec, NS, a, &smem)) {
+      a.N[0] = N_s;
+      a.N[1] = N_t;
+      a.pts[0] = X;
+      a.pts[1] = Y;
+      a.out[0] = U;
+      a.out[1] = V;
+      a.status = d_status;
+      const int64_t T0 = (N_s + TILE_M - 1) / TILE_M, T1 = (N_t + TILE_M - 1) / TILE_M;
+      PTTK_PROF("chain_tc", s);
+      const int fmt = form_fmt(prec);
+      const bool split = form_split(prec);
+#define PTTK_TS_LAUNCH(F, SP)                                                            \
+  return CL == 4 ? launch_ts<F, SP, 3, 4>(a, T0, T1, smem, s)                            \
+                 : CL == 2 ? launch_ts<F, SP, 3, 2>(a, T0, T1, smem, s) : launch_ts<F, SP, 3, 1>(a, T0, T1, smem, s);
+      if (fmt == FMT_BF16) {
+        if (split) { PTTK_TS_LAUNCH(FMT_BF16, true) }
+        PTTK_TS_LAUNCH(FMT_BF16, false)
+      }
+      if (split) { PTTK_TS_LAUNCH(FMT_FP16, true) }
+      PTTK_TS_LAUNCH(FMT_FP16, false)
+#undef PTTK_TS_LAUNCH
+    }
+  }
   int KCB, NS;
   tc_config(prec, cfg, &KCB, &NS);
   const Images& im = cache->img[fi][KCB == 64 ? 0 : 1];

@@ -990,23 +990,19 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
 // TT-Round (Algorithm 1): right-to-left orthogonalisation, then a left-to-right sweep of
 // truncated SVDs with delta = tol / sqrt(D-1) ||X||_F. Each factorisation is svd_basis: with
 // delta = 0 for the orthogonalisation (an orthonormal basis of the whole range, in place of the
-// thin QR; any orthonormal factor serves), with delta for the truncation.
-pttk_status tt_round_run(const pttk_tt* in, double tol, pttk_tt* out, cudaStream_t s) {
-  const int D = in->D, n = in->n;
+// thin QR; any orthonormal factor serves), with delta for the truncation. Works on device cores
+// G[k] (r[k] x nm[k] x r[k+1], column-major) of any mode sizes nm[k]; on return G and r hold the
+// rounded TT.
+pttk_status tt_round_cores(std::vector<Buf>& G, std::vector<int64_t>& r, const std::vector<int64_t>& nm, double tol,
+                           cudaStream_t s) {
+  const int D = (int)G.size();
   StageClock clk(s);
-  std::vector<Buf> G(D), nb(D);
-  std::vector<int64_t> r(D + 1);
-  for (int k = 0; k <= D; ++k) r[k] = in->ranks[k];
-  for (int k = 0; k < D; ++k) {
-    PTTK_TRY(G[k].alloc(in->core_elems(k)));
-    PTTK_CUDA(cudaMemcpyAsync(G[k].p, in->cores64 + in->core_off[k], sizeof(double) * in->core_elems(k),
-                              cudaMemcpyDeviceToDevice, s));
-  }
+  std::vector<Buf> nb(D);
   StepWork wk;
   Buf A, W, T;
   // right to left: (G_i^{1})^T = U W, G_i <- U^T, G_{i-1} <- G_{i-1} x_3 W^T
   for (int i = D - 1; i >= 1; --i) {
-    const int64_t m = n * r[i + 1], c = r[i];
+    const int64_t m = nm[i] * r[i + 1], c = r[i];
     PTTK_TRY(A.alloc(m * c));
     dim3 tg((unsigned)((m + 31) / 32), (unsigned)((c + 31) / 32));
     transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(G[i].p, c, m, nullptr, A.p); pttk::count_launch();
@@ -1017,31 +1013,79 @@ pttk_status tt_round_run(const pttk_tt* in, double tol, pttk_tt* out, cudaStream
     PTTK_TRY(G[i].alloc((int64_t)k * m));
     dim3 tg2((unsigned)((k + 31) / 32), (unsigned)((m + 31) / 32));
     transpose_kernel<<<tg2, dim3(32, 8), 0, s>>>(nb[i].p, m, k, nullptr, G[i].p); pttk::count_launch();
-    const int64_t mp = r[i - 1] * n;                                       // G_{i-1}^{2}: mp x c
+    const int64_t mp = r[i - 1] * nm[i - 1];                               // G_{i-1}^{2}: mp x c
     PTTK_TRY(T.alloc(mp * k));
     dgemm(false, true, mp, k, c, 1.0, G[i - 1].p, mp, W.p, k, 0.0, T.p, mp, s);
     std::swap(G[i - 1].p, T.p);
     r[i] = k;
   }
   double sumsq = 0.0;
-  PTTK_TRY(sumsq_host(G[0].p, r[0] * n * r[1], &sumsq, s));
+  PTTK_TRY(sumsq_host(G[0].p, r[0] * nm[0] * r[1], &sumsq, s));
   const double delta = D > 1 ? tol / sqrt((double)(D - 1)) * sqrt(sumsq) : 0.0;
   // left to right: G_i^{2} = U W (truncated), G_i <- U, G_{i+1} <- W x_1 G_{i+1}
   for (int i = 0; i < D - 1; ++i) {
-    const int64_t m = r[i] * n, c = r[i + 1];
+    const int64_t m = r[i] * nm[i], c = r[i + 1];
     int k = 0;
     PTTK_TRY(svd_basis(G[i].p, m, c, delta, wk, nb[i], &k, clk, i, s));
     PTTK_TRY(W.alloc((int64_t)k * c));
     dgemm(true, false, k, c, m, 1.0, nb[i].p, m, G[i].p, m, 0.0, W.p, k, s);
     std::swap(G[i].p, nb[i].p);
-    const int64_t cn = n * r[i + 2];                                       // G_{i+1}^{1}: c x cn
+    const int64_t cn = nm[i + 1] * r[i + 2];                               // G_{i+1}^{1}: c x cn
     PTTK_TRY(T.alloc((int64_t)k * cn));
     dgemm(false, false, k, cn, c, 1.0, W.p, k, G[i + 1].p, c, 0.0, T.p, k, s);
     std::swap(G[i + 1].p, T.p);
     r[i + 1] = k;
   }
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  return PTTK_OK;
+}
+
+pttk_status tt_round_run(const pttk_tt* in, double tol, pttk_tt* out, cudaStream_t s) {
+  const int D = in->D;
+  std::vector<Buf> G(D);
+  std::vector<int64_t> r(D + 1), nm(D, in->n);
+  for (int k = 0; k <= D; ++k) r[k] = in->ranks[k];
+  for (int k = 0; k < D; ++k) {
+    PTTK_TRY(G[k].alloc(in->core_elems(k)));
+    PTTK_CUDA(cudaMemcpyAsync(G[k].p, in->cores64 + in->core_off[k], sizeof(double) * in->core_elems(k),
+                              cudaMemcpyDeviceToDevice, s));
+  }
+  PTTK_TRY(tt_round_cores(G, r, nm, tol, s));
   for (int k = 0; k <= D; ++k) out->ranks[k] = (int)r[k];
   return pack_cores(out, G, s);
+}
+
+// Phase 4 of Algorithm 2: TT-Round of [T^(1)(S), G_{d+1}, .., G_{d+d_theta}, T^(3)(T^T)]
+// (Eq. twist). Scol: N_s x r_s column-major (the first core 1 x N_s x r_s); theta cores
+// ranks[j] x n x ranks[j+1], j < d_theta (ranks[0] = r_s, ranks[d_theta] = r_t); Tt: r_t x N_t
+// column-major (the last core r_t x N_t x 1, i.e. T row-major). Inputs are not modified. On
+// return out[0] (N_s x r_s' column-major), out[1 .. d_theta] (the rounded theta cores) and
+// out[d_theta + 1] (r_t' x N_t column-major) are cudaMalloc'd arrays the caller frees, and
+// new_ranks[0 .. d_theta] their ranks. Synchronises `s`.
+pttk_status phase4_round(const double* Scol, int64_t Ns, const double* const* theta_cores, const int* ranks, int n,
+                         int dtheta, const double* Tt, int64_t Nt, double tol, double** out, int* new_ranks,
+                         cudaStream_t s) {
+  const int D = dtheta + 2;
+  std::vector<Buf> G(D);
+  std::vector<int64_t> r(D + 1), nm(D, n);
+  r[0] = 1;
+  for (int j = 0; j <= dtheta; ++j) r[j + 1] = ranks[j];
+  r[D] = 1;
+  nm[0] = Ns;
+  nm[D - 1] = Nt;
+  for (int k = 0; k < D; ++k) {
+    const int64_t e = r[k] * nm[k] * r[k + 1];
+    PTTK_TRY(G[k].alloc(e));
+    const double* src = k == 0 ? Scol : k == D - 1 ? Tt : theta_cores[k - 1];
+    PTTK_CUDA(cudaMemcpyAsync(G[k].p, src, sizeof(double) * e, cudaMemcpyDeviceToDevice, s));
+  }
+  PTTK_TRY(tt_round_cores(G, r, nm, tol, s));
+  for (int k = 0; k < D; ++k) {
+    out[k] = G[k].p;
+    G[k].p = nullptr;
+  }
+  for (int j = 0; j <= dtheta; ++j) new_ranks[j] = (int)r[j + 1];
+  return PTTK_OK;
 }
 
 // Orthonormal basis of the range of X (m x c, column-major, not modified): svd_basis with

@@ -79,6 +79,12 @@ SIGNATURES = [
     ("pttk_global_free", None, [_vp]),
     ("pttk_splitmix64", ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
     ("pttk_peak_probe", _int, [_int, _i64, _vp, _c_double_p, _c_double_p]),
+    ("pttk_fixed_create", _int, [_vp, _vp, _i64, _vp, _i64, ctypes.c_double, _vp, ctypes.POINTER(_vp)]),
+    ("pttk_fixed_dims", _int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _c_int_p, _c_int_p]),
+    ("pttk_fixed_get_factors", _int, [_vp, _vp, _vp, _vp]),
+    ("pttk_fixed_get_core", _int, [_vp, _int, _c_double_p]),
+    ("pttk_fixed_theta_core", _int, [_vp, _c_double_p, _int, _vp, _vp]),
+    ("pttk_fixed_free", None, [_vp]),
 ]
 
 _lib = None
@@ -526,6 +532,77 @@ class Global:
     def free(self):
         if self._h:
             load().pttk_global_free(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Fixed:
+    """Algorithm 2 for fixed point sets X, Y: Phase 3 (S = U(X), T = V(Y) in FP64) and Phase 4
+    (TT-Round of the twisted TT at `tol`; 0 skips it). Online: K ~= S' H'(theta) T'^T."""
+
+    def __init__(self, tt: TT, X, Y, tol: float, stream=None):
+        import torch
+        d = tt.dims[0]
+        for P_ in (X, Y):
+            if P_.dtype != torch.float64 or P_.dim() != 2 or P_.shape[1] != d:
+                raise ValueError(f"points must be (N, {d}) float64")
+        h = _vp()
+        _check(load().pttk_fixed_create(tt.handle, _ptr(X), X.shape[0], _ptr(Y), Y.shape[0], float(tol),
+                                        _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self._n = tt.dims[2]
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("fixed-point handle already freed")
+        return self._h
+
+    @property
+    def dims(self):
+        """(N_s, N_t, d_theta, ranks): ranks = [r_s', inner.., r_t']."""
+        Ns, Nt, dth = _i64(), _i64(), _int()
+        r = (_int * 9)()
+        _check(load().pttk_fixed_dims(self.handle, ctypes.byref(Ns), ctypes.byref(Nt), ctypes.byref(dth), r))
+        return Ns.value, Nt.value, dth.value, list(r[:max(dth.value, 0) + 1])
+
+    def factors(self, stream=None):
+        """(S', T') as float64 CUDA tensors."""
+        import torch
+        Ns, Nt, dth, r = self.dims
+        S = torch.empty(Ns, r[0], dtype=torch.float64, device="cuda")
+        T = torch.empty(Nt, r[dth], dtype=torch.float64, device="cuda")
+        _check(load().pttk_fixed_get_factors(self.handle, _ptr(S), _ptr(T), _stream(stream)))
+        return S, T
+
+    def cores(self) -> list:
+        """The rounded theta cores (r_j x n x r_{j+1} numpy arrays)."""
+        Ns, Nt, dth, r = self.dims
+        out = []
+        n = self._n
+        for j in range(dth):
+            buf = np.empty(r[j] * n * r[j + 1], dtype=np.float64)
+            _check(load().pttk_fixed_get_core(self.handle, j, buf.ctypes.data_as(_c_double_p)))
+            out.append(buf.reshape(r[j], n, r[j + 1], order="F"))
+        return out
+
+    def theta_core(self, theta, prec="fp64", M=None, stream=None):
+        import torch
+        prec = _prec(prec)
+        Ns, Nt, dth, r = self.dims
+        if M is None:
+            M = torch.empty(r[0], r[dth], dtype=_dtype(prec), device="cuda")
+        _check(load().pttk_fixed_theta_core(self.handle, _dbl(theta), prec, _ptr(M), _stream(stream)))
+        return M
+
+    def free(self):
+        if self._h:
+            load().pttk_fixed_free(self._h)
             self._h = _vp()
 
     def __del__(self):
