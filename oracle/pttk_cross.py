@@ -25,7 +25,12 @@ Readings of the paper taken here:
       a sweep that adds no pivot ends the iteration.
   X5  Algorithm 7: the random index vectors q1, q2 hold one index per mode 2..N, uniform in
       that mode. Ties in the condition-number minimum go to the first pair in the order
-      (j1, j2) = (0, 0), (0, 1), ...; ties between recorded candidates to the earliest.
+      (j1, j2) = (0, 0), (0, 1), ...; ties between recorded candidates to the earliest. Every
+      argmin and argmax of the method (this minimum, the largest sampled residual and the
+      largest residual of the chosen row or column in Algorithm 5) takes the first index whose
+      value lies within a relative 1e-12 of the extremum: kernels on symmetric boxes produce
+      exactly equal candidates, and an implementation with another rounding order must make
+      the same choice among them.
   X6  Sampling without replacement in Algorithm 5: positions drawn uniformly, repeats
       skipped, until max(rows, cols) distinct ones are drawn (all positions when that is
       every one).
@@ -76,6 +81,21 @@ def _cond2(M: np.ndarray) -> float:
     return float(np.linalg.cond(M, 2))
 
 
+TIE_RTOL = 1e-12
+
+
+def first_argmax(v: np.ndarray) -> int:
+    """The first index i with v[i] >= (1 - TIE_RTOL) max(v) (reading X5)."""
+    v = np.asarray(v, dtype=np.float64)
+    return int(np.flatnonzero(v >= (1.0 - TIE_RTOL) * v.max())[0])
+
+
+def first_argmin(v) -> int:
+    """The first index i with v[i] <= (1 + TIE_RTOL) min(v) (reading X5)."""
+    v = np.asarray(v, dtype=np.float64)
+    return int(np.flatnonzero(v <= (1.0 + TIE_RTOL) * v.min())[0])
+
+
 def greedy_init(phi, dims, rng: CounterRNG, max_it: int = 10):
     """Index sets I<=k, I>k (k = 1..N-1) of cardinality two (Algorithm 7).
 
@@ -98,15 +118,16 @@ def greedy_init(phi, dims, rng: CounterRNG, max_it: int = 10):
         for k in range(1, N):                       # left-to-right: mode k (1-based)
             p, pp = (left[k - 1] * 2)[:2] if k == 1 else left[k - 1]
             a, b = right[k]
-            best, bj = np.inf, None
+            pairs, conds = [], []
             for j1 in range(dims[k - 1]):
                 for j2 in range(dims[k - 1]):
                     if k == 1 and j1 == j2:
                         continue
                     v = entries([p + (j1,) + a, p + (j1,) + b, pp + (j2,) + a, pp + (j2,) + b])
-                    c = _cond2(v.reshape(2, 2))
-                    if c < best:
-                        best, bj = c, (j1, j2)
+                    pairs.append((j1, j2))
+                    conds.append(_cond2(v.reshape(2, 2)))
+            q = first_argmin(conds)
+            bj, best = pairs[q], conds[q]
             left[k] = [p + (bj[0],), pp + (bj[1],)]
             cs.append(best)
         cands.append(([list(x) for x in left], [list(x) for x in right], max(cs)))
@@ -114,19 +135,20 @@ def greedy_init(phi, dims, rng: CounterRNG, max_it: int = 10):
         for k in range(N, 1, -1):                   # right-to-left: mode k (1-based)
             p, pp = left[k - 1]
             a, b = (right[k] * 2)[:2] if k == N else right[k]
-            best, bj = np.inf, None
+            pairs, conds = [], []
             for j1 in range(dims[k - 1]):
                 for j2 in range(dims[k - 1]):
                     if k == N and j1 == j2:
                         continue
                     v = entries([p + (j1,) + a, p + (j2,) + b, pp + (j1,) + a, pp + (j2,) + b])
-                    c = _cond2(v.reshape(2, 2))
-                    if c < best:
-                        best, bj = c, (j1, j2)
+                    pairs.append((j1, j2))
+                    conds.append(_cond2(v.reshape(2, 2)))
+            q = first_argmin(conds)
+            bj, best = pairs[q], conds[q]
             right[k - 1] = [(bj[0],) + a, (bj[1],) + b]
             cs.append(best)
         cands.append(([list(x) for x in left], [list(x) for x in right], max(cs)))
-    i = min(range(len(cands)), key=lambda q: cands[q][2])
+    i = first_argmin([c[2] for c in cands])
     return cands[i][0], cands[i][1]
 
 
@@ -162,15 +184,15 @@ def update_cross(entry, rows: int, cols: int, I: list, J: list, rng: CounterRNG)
         return skel - a, np.abs(a).max() if len(a) else 0.0
 
     R, amax = resid(si, sj)
-    q = int(np.argmax(np.abs(R)))
+    q = first_argmax(np.abs(R))
     l, t = int(si[q]), int(sj[q])
     if rng.bit() == 1:
         Rr, am = resid(np.full(cols, l, dtype=np.int64), np.arange(cols, dtype=np.int64))
-        t = int(np.argmax(np.abs(Rr)))
+        t = first_argmax(np.abs(Rr))
         val = Rr[t]
     else:
         Rc, am = resid(np.arange(rows, dtype=np.int64), np.full(rows, t, dtype=np.int64))
-        l = int(np.argmax(np.abs(Rc)))
+        l = first_argmax(np.abs(Rc))
         val = Rc[l]
     amax = max(amax, am)
     if not abs(val) > 1e-14 * amax or l in I or t in J:
