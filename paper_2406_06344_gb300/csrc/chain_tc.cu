@@ -230,6 +230,7 @@ struct TcArgs {
   int acc1_col;           // TMEM column of the first step's accumulator when it has its own
   int tmem_cols;
   uint32_t b_slot_bytes;  // bytes reserved per B part per slot
+  int region_col;         // chain_tce_kernel: TMEM column of accumulator region 1 (region 0 at 0)
 };
 
 constexpr int NGEN_WARPS = 16;             // A generators: NPART threads per point row
@@ -683,6 +684,376 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
           gen_barrier();
         }
       }
+    }
+    if (dead && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(a.status, (int)PTTK_ETIMEOUT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+}
+
+// ---------------- dedicated epilogue warps, double-buffered accumulators ------------------
+// The same chain with the output written by four epilogue warps of their own (one per TMEM lane
+// quarter) from one of two accumulator regions, while the MMAs of the next tile fill the other:
+// a tile's steps all accumulate into region (tile parity), the first step's result being read
+// back as the second step's input before the second step's first MMA overwrites it. The
+// generators then never wait for a tile's last step and never write output; the output of a
+// tile leaves while the next tile is computed.
+// Barriers: full_a / full_b / empty per ring slot as in chain_tc_kernel; mid[r] (committed after
+// the last chunk of every step but the last into region r; the generators wait for each in
+// turn), last[r] (committed after a tile's last step; the epilogue waits for it), free[r] (the
+// four epilogue warps arrive once they have read region r; the MMA lane waits for it before the
+// first MMA of the next tile in region r). Each barrier has one kind of waiter that can fall at
+// most one phase behind, which is what a parity wait needs.
+constexpr int NEPI_WARPS = 4;
+constexpr int TCE_THREADS = 64 + 32 * NGEN_WARPS + 32 * NEPI_WARPS;
+
+template <int FMT, bool SPLIT, int KCB_, int NS>
+__global__ void __launch_bounds__(TCE_THREADS, 1) chain_tce_kernel(TcArgs a) {
+  using C = Cfg<FMT, SPLIT, KCB_, NS>;
+  constexpr int NSLOT = C::NSLOT;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int bv_ld = (a.n + 1) | 1;
+  uint8_t* a_base = smem;                                            // NSLOT x PARTS x A_PART
+  uint8_t* b_base = a_base + (size_t)NSLOT * C::PARTS * C::A_PART;    // NSLOT x PARTS x b_slot_bytes
+  float* S = reinterpret_cast<float*>(b_base + (size_t)NSLOT * C::PARTS * a.b_slot_bytes);  // 128 x ld_s
+  float* Bv = S + (size_t)TILE_M * a.ld_s;                           // 2 x 128 x bv_ld
+  float* Sseed = Bv + (size_t)2 * TILE_M * bv_ld;                     // 128 x ld_seed
+  float* stage = Sseed + (size_t)TILE_M * a.ld_seed;                  // NEPI_WARPS x 32 x STAGE_LD
+  StepS* steps = reinterpret_cast<StepS*>(
+      (reinterpret_cast<uintptr_t>(stage + (size_t)NEPI_WARPS * 32 * STAGE_LD) + 15) & ~uintptr_t(15));  // [2][3]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(steps + 6);
+  uint64_t* full_a = bars;
+  uint64_t* full_b = bars + NSLOT;
+  uint64_t* empty = bars + 2 * NSLOT;
+  uint64_t* mid = bars + 3 * NSLOT;        // [2]
+  uint64_t* last_done = bars + 3 * NSLOT + 2;  // [2]
+  uint64_t* rfree = bars + 3 * NSLOT + 4;  // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * NSLOT + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < NSLOT; ++i) {
+      mbar_init(&full_a[i], NGEN_WARPS);
+      mbar_init(&full_b[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int r = 0; r < 2; ++r) {
+      mbar_init(&mid[r], 1);
+      mbar_init(&last_done[r], 1);
+      mbar_init(&rfree[r], NEPI_WARPS);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (tid < 2 * a.nsteps) {
+    const int sd = tid / a.nsteps, si = tid % a.nsteps;
+    const TcStep& st = a.st[sd][si];
+    StepS v;
+    v.hi = st.img_hi;
+    v.lo = st.img_lo;
+    v.bytes = (uint32_t)st.Npad * C::KCB;
+    v.idesc = instr_desc(fmt_code(FMT), TILE_M, st.Npad);
+    v.nchunks = st.nchunks;
+    v.R_in_pad = st.R_in_pad;
+    v.R_out = st.R_out;
+    v.Npad = st.Npad;
+    v.coord = st.coord;
+    v.lo_box = st.lo;
+    v.hi_box = st.hi;
+    v.a_scale = st.a_scale;
+    v.out_scale = st.out_scale;
+    steps[sd * 3 + si] = v;
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int64_t ntiles = a.ntiles;
+  const int nsteps = a.nsteps;
+  auto region_addr = [&](uint32_t r) { return tmem + (r ? (uint32_t)a.region_col : 0u); };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t h = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < ntiles && ok; it += gridDim.x) {
+        const int sd = it >= a.T0 ? 1 : 0;
+        for (int si = 0; si < nsteps && ok; ++si) {
+          const StepS& st = steps[sd * 3 + si];
+          for (int c = 0; c < st.nchunks; ++c, ++h) {
+            const uint32_t slot = h % NSLOT;
+            if (h >= NSLOT && !mbar_wait(&empty[slot], ((h / NSLOT) - 1) & 1, abort_flag)) { ok = false; break; }
+            uint8_t* bh = b_base + (size_t)slot * C::PARTS * a.b_slot_bytes;
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&full_b[slot], SPLIT ? 2 * st.bytes : st.bytes);
+            tma_load_1d(bh, st.hi + (size_t)c * st.bytes, st.bytes, &full_b[slot]);
+            if (SPLIT) tma_load_1d(bh + a.b_slot_bytes, st.lo + (size_t)c * st.bytes, st.bytes, &full_b[slot]);
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(a.status, (int)PTTK_ETIMEOUT);
+      }
+      const int zero = 0;
+      for (uint32_t k = (h > (uint32_t)NSLOT ? h - NSLOT : 0); k < h; ++k)
+        mbar_wait(&full_b[k % NSLOT], (k / NSLOT) & 1, &zero);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t g = 0, tile = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < ntiles && ok; it += gridDim.x, ++tile) {
+        const int sd = it >= a.T0 ? 1 : 0;
+        const uint32_t r = tile & 1, use = tile >> 1;
+        // the region's previous tile must have left it
+        if (use >= 1 && !mbar_wait(&rfree[r], (use - 1) & 1, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t dacc = region_addr(r);
+        for (int si = 0; si < nsteps && ok; ++si) {
+          const StepS& st = steps[sd * 3 + si];
+          for (int c = 0; c < st.nchunks; ++c, ++g) {
+            const uint32_t slot = g % NSLOT, par = (g / NSLOT) & 1;
+            if (!mbar_wait(&full_a[slot], par, abort_flag) || !mbar_wait(&full_b[slot], par, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(a_base + (size_t)slot * C::PARTS * C::A_PART);
+            const uint32_t sb = smem_u32(b_base + (size_t)slot * C::PARTS * a.b_slot_bytes);
+            const uint64_t ah0 = smem_desc2(sa, C::SBO), al0 = smem_desc2(sa + C::A_PART, C::SBO);
+            const uint64_t bh0 = smem_desc2(sb, C::SBO), bl0 = smem_desc2(sb + a.b_slot_bytes, C::SBO);
+#pragma unroll
+            for (int k = 0; k < C::KSTEPS; ++k) {
+              const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+              // +256 bytes of K per MMA: +16 in the descriptors' address fields
+              const uint64_t ah = ah0 + (uint64_t)(16 * k), bh = bh0 + (uint64_t)(16 * k);
+              if constexpr (FMT != FMT_TF32) {
+                umma_f16(dacc, ah, bh, st.idesc, acc);
+                if (SPLIT) {
+                  umma_f16(dacc, ah, bl0 + (uint64_t)(16 * k), st.idesc, 1u);
+                  umma_f16(dacc, al0 + (uint64_t)(16 * k), bh, st.idesc, 1u);
+                }
+              } else {
+                umma_tf32(dacc, ah, bh, st.idesc, acc);
+                if (SPLIT) {
+                  umma_tf32(dacc, ah, bl0 + (uint64_t)(16 * k), st.idesc, 1u);
+                  umma_tf32(dacc, al0 + (uint64_t)(16 * k), bh, st.idesc, 1u);
+                }
+              }
+            }
+            umma_commit(&empty[slot]);
+            if (c == st.nchunks - 1) umma_commit(si == nsteps - 1 ? &last_done[r] : &mid[r]);
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(a.status, (int)PTTK_ETIMEOUT);
+      }
+      const int zero = 0;
+      if (g > 0) mbar_wait(&empty[(g - 1) % NSLOT], ((g - 1) / NSLOT) & 1, &zero);
+    }
+    __syncwarp();
+  } else if (warp < 2 + NGEN_WARPS) {
+    // ---------------- generator warps: A chunks ----------------
+    const int gw = warp - 2;
+    const int row = 32 * (warp & 3) + lane;
+    const int part = gw >> 2;
+    uint32_t g = 0, tile = 0;
+    bool dead = false;
+    auto basis = [&](int sd, int si, int buf, float x) {
+      const StepS& st = steps[sd * 3 + si];
+      const float xh = (2.f * x - st.lo_box - st.hi_box) / (st.lo_box - st.hi_box);
+      float* bv = Bv + ((size_t)buf * TILE_M + row) * bv_ld;
+      const float sc = st.a_scale;
+      float t0 = 1.f, t1 = xh;
+      bv[0] = sc;
+      for (int k = 1; k < a.n; ++k) {
+        bv[k] = t1 * sc;
+        const float t2 = 2.f * xh * t1 - t0;
+        t0 = t1;
+        t1 = t2;
+      }
+      for (int k = a.n; k < bv_ld; ++k) bv[k] = 0.f;
+    };
+    auto coord_of = [&](int64_t it, int si) -> float {
+      const int sd = it >= a.T0 ? 1 : 0;
+      const int64_t gp = (sd ? it - a.T0 : it) * TILE_M + row;
+      const StepS& st = steps[sd * 3 + si];
+      return gp < a.N[sd] ? a.pts[sd][gp * a.d + st.coord] : st.lo_box;
+    };
+    auto seed_coord_of = [&](int64_t it) -> float {
+      const int sd = it >= a.T0 ? 1 : 0;
+      const int64_t gp = (sd ? it - a.T0 : it) * TILE_M + row;
+      return (a.s0_coord[sd] >= 0 && gp < a.N[sd]) ? a.pts[sd][gp * a.d + a.s0_coord[sd]] : a.s0_lo[sd];
+    };
+    auto write_seed = [&](int64_t it, float x) {
+      const int sd = it >= a.T0 ? 1 : 0;
+      float* w = Sseed + (size_t)row * a.ld_seed;
+      const int pad = steps[sd * 3].R_in_pad;
+      if (a.s0_coord[sd] >= 0) {
+        const float lo = a.s0_lo[sd], hi = a.s0_hi[sd];
+        const float xh = (2.f * x - lo - hi) / (lo - hi);
+        float t0 = 1.f, t1 = xh;
+        w[0] = 1.f;
+        for (int k = 1; k < pad; ++k) {
+          w[k] = k < a.n ? t1 : 0.f;
+          const float t2 = 2.f * xh * t1 - t0;
+          t0 = t1;
+          t1 = t2;
+        }
+      } else {
+        w[0] = 1.f;
+        for (int k = 1; k < pad; ++k) w[k] = 0.f;
+      }
+    };
+    float xn[4] = {0.f, 0.f, 0.f, 0.f};
+    if (part == 0 && blockIdx.x < ntiles) {
+      for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
+      xn[3] = seed_coord_of(blockIdx.x);
+      basis(blockIdx.x >= a.T0 ? 1 : 0, 0, 0, xn[0]);
+      write_seed(blockIdx.x, xn[3]);
+    }
+    gen_barrier();
+    uint32_t bufsel = 0;
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+    for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x, ++tile) {
+      const int sd = it >= a.T0 ? 1 : 0;
+      const uint32_t r = tile & 1, use = tile >> 1;
+      float xcur[3] = {xn[0], xn[1], xn[2]};
+      const int64_t itn = it + gridDim.x;
+      if (part == 0 && itn < ntiles) {
+        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
+        xn[3] = seed_coord_of(itn);
+      }
+      for (int si = 0; si < nsteps; ++si) {
+        const StepS st = steps[sd * 3 + si];
+        const float* bvrow = Bv + ((size_t)bufsel * TILE_M + row) * bv_ld;
+        const float* srow = si == 0 ? Sseed + (size_t)row * a.ld_seed : S + (size_t)row * a.ld_s;
+        for (int c = 0; c < st.nchunks; ++c, ++g) {
+          const uint32_t slot = g % NSLOT, use_s = g / NSLOT;
+          dead = dead || *abort_flag;
+          if (!dead && g >= (uint32_t)NSLOT) dead = !mbar_wait(&empty[slot], (use_s - 1) & 1, abort_flag);
+          dead = __any_sync(0xffffffffu, dead);
+          if (dead && lane == 0) *abort_flag = 1;
+          if (!dead) {
+            uint8_t* ah = a_base + (size_t)slot * C::PARTS * C::A_PART;
+            const uint32_t row_off = (uint32_t)(row >> 3) * C::SBO + (uint32_t)(row & 7) * 16;
+            constexpr int UH = C::UNITS / NPART;
+            static_assert(C::UNITS % NPART == 0, "units per chunk row must split evenly");
+            const int k = c * C::KC + part * UH * C::E;
+            int j = k / st.R_in_pad;
+            int ai = k - j * st.R_in_pad;
+#pragma unroll
+            for (int u = 0; u < UH; ++u) {
+              const uint32_t off = row_off + (uint32_t)(part * UH + u) * 128;
+              write_unit<FMT, SPLIT>(bvrow[j < a.n ? j : a.n], srow + ai, ah + off, ah + C::A_PART + off);
+              ai += C::E;
+              if (ai == st.R_in_pad) {
+                ai = 0;
+                ++j;
+              }
+            }
+            fence_proxy_async();
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full_a[slot]);
+        }
+        const bool last = si == nsteps - 1;
+        if (part == 0) {
+          if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
+          else if (itn < ntiles) basis(itn >= a.T0 ? 1 : 0, 0, bufsel ^ 1, xn[0]);
+        }
+        if (!last) {
+          // this step's result is the next step's input: wait for it and copy it to S
+          const uint32_t phase = use * (uint32_t)(nsteps - 1) + (uint32_t)si;
+          if (!dead && !*abort_flag) dead = !mbar_wait(&mid[r], phase & 1, abort_flag);
+          dead = __any_sync(0xffffffffu, dead || *abort_flag);
+          if (dead && lane == 0) *abort_flag = 1;
+          tc_fence_after();
+          if (!dead)
+            for (int cb = 32 * part; cb < st.Npad; cb += 32 * NPART) {
+              float v[32];
+              tmem_ld32(region_addr(r) + lanes + (uint32_t)cb, v);
+              float* dst = S + (size_t)row * a.ld_s + cb;
+              const float osc = st.out_scale;
+#pragma unroll
+              for (int i = 0; i < 32; i += 4)
+                if (cb + i < a.ld_s)
+                  *reinterpret_cast<float4*>(dst + i) =
+                      make_float4(v[i] * osc, v[i + 1] * osc, v[i + 2] * osc, v[i + 3] * osc);
+            }
+          tc_fence_before();
+        } else if (itn < ntiles && part == 0 && nsteps > 1) {
+          // the seed of the next tile (this tile's seed was last read by its first step, which
+          // every thread finished before the barrier after that step)
+          write_seed(itn, xn[3]);
+        }
+        bufsel ^= 1;
+        gen_barrier();
+        if (last && nsteps == 1 && itn < ntiles) {
+          // a single step reads its seed until the barrier above
+          if (part == 0) write_seed(itn, xn[3]);
+          gen_barrier();
+        }
+      }
+    }
+    if (dead && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(a.status, (int)PTTK_ETIMEOUT);
+    }
+  } else {
+    // ---------------- epilogue warps: one TMEM lane quarter each ----------------
+    const int ew = warp - 2 - NGEN_WARPS;      // 0..3
+    const int quarter = warp & 3;
+    const uint32_t lanes = (uint32_t)(32 * quarter) << 16;
+    float* stg = stage + (size_t)ew * 32 * STAGE_LD;
+    const int sub = lane >> 4, lc = lane & 15;
+    uint32_t tile = 0;
+    bool dead = false;
+    for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x, ++tile) {
+      const int sd = it >= a.T0 ? 1 : 0;
+      const uint32_t r = tile & 1, use = tile >> 1;
+      const StepS& st = steps[sd * 3 + nsteps - 1];
+      if (!dead && !*abort_flag) dead = !mbar_wait(&last_done[r], use & 1, abort_flag);
+      dead = __any_sync(0xffffffffu, dead || *abort_flag);
+      if (dead && lane == 0) *abort_flag = 1;
+      tc_fence_after();
+      if (!dead) {
+        const int64_t row0 = (sd ? it - a.T0 : it) * TILE_M;
+        const int rows = (int)std::min<int64_t>(TILE_M, a.N[sd] - row0);
+        const int R = st.R_out;
+        float* outbase = a.out[sd] + (row0 + 32 * quarter) * R;
+        const int wrows = std::max(0, std::min(32, rows - 32 * quarter));
+        for (int cb = 0; cb < st.Npad; cb += STAGE_COLS) {
+          float v[STAGE_COLS];
+          tmem_ld16(region_addr(r) + lanes + (uint32_t)cb, v);
+#pragma unroll
+          for (int i = 0; i < STAGE_COLS; ++i) stg[lane * STAGE_LD + i] = v[i] * st.out_scale;
+          __syncwarp();
+          const int col = cb + lc;
+          if (col < R)
+            for (int rr = sub; rr < wrows; rr += 2) outbase[(int64_t)rr * R + col] = stg[rr * STAGE_LD + lc];
+          __syncwarp();
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rfree[r]);
     }
     if (dead && lane == 0) {
       *abort_flag = 1;
@@ -1439,19 +1810,27 @@ static pttk_status build_images(const pttk_tt* tt, const TcImageCache* cache, pt
   return PTTK_OK;
 }
 
-// Launch configurations. 0 and 1: the shared-memory kernel with {KCB, NSLOT} below (0 is the
-// default: the fastest on the d = 3 workload's ranks); 2..4: the TS kernel (A in tensor memory,
-// a ring of 3 slots) in thread-block clusters of 1, 2 or 4 CTAs, for the kind::f16 forms whose
-// ranks fit it (otherwise the shared-memory kernel's default).
+// Launch configurations. 0: the shared-memory kernel with dedicated epilogue warps and
+// double-buffered accumulators (chain_tce_kernel; the default), 128 bytes of K per chunk row;
+// 1 and 2: the shared-memory kernel without them, with {KCB, NSLOT} below; 3..5: the TS kernel
+// (A in tensor memory, a ring of 3 slots) in thread-block clusters of 1, 2 or 4 CTAs, for the
+// kind::f16 forms whose ranks fit it. A configuration whose kernel cannot hold the ranks falls
+// back to configuration 1.
 static const int kTcConfigs[2][2] = {{128, 4}, {64, 4}};
 static const int kTcConfigsSplit[2][2] = {{128, 2}, {64, 4}};
-constexpr int kTcSubConfigs = 2, kTsConfigs = 3;
+constexpr int kTceConfigs = 1, kTcSubConfigs = 2, kTsConfigs = 3;
 static const int kTsCluster[kTsConfigs] = {1, 2, 4};
 
-int tc_config_count() { return kTcSubConfigs + kTsConfigs; }
+int tc_config_count() { return kTceConfigs + kTcSubConfigs + kTsConfigs; }
 static bool ts_form(pttk_prec p) { return p == PTTK_FP16 || p == PTTK_FP16X3 || p == PTTK_BF16 || p == PTTK_BF16X3; }
-static bool ts_config(int cfg) { return cfg >= kTcSubConfigs && cfg < kTcSubConfigs + kTsConfigs; }
-static int tc_sub_config(int cfg) { return cfg >= 0 && cfg < kTcSubConfigs ? cfg : 0; }
+static bool ts_config(int cfg) {
+  return cfg >= kTceConfigs + kTcSubConfigs && cfg < kTceConfigs + kTcSubConfigs + kTsConfigs;
+}
+static int ts_cluster(int cfg) { return kTsCluster[cfg - kTceConfigs - kTcSubConfigs]; }
+static bool tce_config(int cfg) { return cfg >= 0 && cfg < kTceConfigs; }
+static int tc_sub_config(int cfg) {
+  return cfg >= kTceConfigs && cfg < kTceConfigs + kTcSubConfigs ? cfg - kTceConfigs : 0;
+}
 
 static void tc_config(pttk_prec prec, int cfg, int* KCB, int* NS) {
   const bool split = form_split(prec);
@@ -1645,6 +2024,16 @@ static pttk_status launch_tc(const TcArgs& a, size_t smem, cudaStream_t s) {
   return PTTK_OK;
 }
 
+template <int FMT, bool SPLIT, int KCB, int NS>
+static pttk_status launch_tce(const TcArgs& a, size_t smem, cudaStream_t s) {
+  auto kfn = chain_tce_kernel<FMT, SPLIT, KCB, NS>;
+  PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned grid = (unsigned)std::min<int64_t>(a.ntiles, sm_count());
+  kfn<<<grid, TCE_THREADS, smem, s>>>(a); pttk::count_launch();
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
 // Both factors in one persistent launch: U (N_s rows from X) and V (N_t rows from Y).
 pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float* X, int64_t N_s,
                             const float* Y, int64_t N_t, pttk_prec prec, float* U, float* V, int* d_status,
@@ -1653,7 +2042,7 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
   PTTK_TRY(tc_prepare(tt, cache, prec, cfg, s));
   const int fi = form_index(prec);
   if (ts_config(cfg) && ts_form(prec)) {
-    const int NS = 3, CL = kTsCluster[cfg - kTcSubConfigs];
+    const int NS = 3, CL = ts_cluster(cfg);
     TsArgs a;
     size_t smem = 0;
     if (ts_plan(tt, cache, cache->ts[fi], prec, NS, a, &smem)) {
@@ -1744,6 +2133,33 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
     for (int i = 1; i < a.nsteps; ++i) npad_rest = std::max(npad_rest, a.st[side][i].Npad);
   }
   a.ld_seed = ((pad0 + 7) / 8) * 8 + 4;
+  const int bv_ld = (tt->n + 1) | 1;
+  const size_t parts = split ? 2 : 1;
+  if (tce_config(cfg)) {
+    // two accumulator regions of the widest step, an epilogue staging tile per epilogue warp
+    TcArgs b = a;
+    b.ld_s = ((spad_max + 31) / 32) * 32 + 4;
+    b.region_col = ((npad_max + 31) / 32) * 32;
+    int tcols = 32;
+    while (tcols < 2 * b.region_col) tcols <<= 1;
+    b.tmem_cols = tcols;
+    b.b_slot_bytes = (uint32_t)npad_max * KCB;
+    const size_t smem_e = (size_t)NS * parts * TILE_M * KCB + (size_t)NS * parts * b.b_slot_bytes +
+                          sizeof(float) * ((size_t)TILE_M * b.ld_s + (size_t)2 * TILE_M * bv_ld +
+                                           (size_t)TILE_M * b.ld_seed + (size_t)NEPI_WARPS * 32 * STAGE_LD) +
+                          16 + sizeof(StepS) * 6 + 8 * (3 * NS + 6) + 16;
+    if (tcols <= 512 && smem_e <= 227 * 1024) {
+      const size_t req = std::max<size_t>(smem_e, 116 * 1024);
+      PTTK_PROF("chain_tc", s);
+#define PTTK_TCE_LAUNCH(F)                                                                        \
+  if (split) return KCB == 64 ? launch_tce<F, true, 64, 4>(b, req, s) : launch_tce<F, true, 128, 2>(b, req, s); \
+  return KCB == 128 ? launch_tce<F, false, 128, 4>(b, req, s) : launch_tce<F, false, 64, 4>(b, req, s);
+      if (fmt == FMT_BF16) { PTTK_TCE_LAUNCH(FMT_BF16) }
+      if (fmt == FMT_FP16) { PTTK_TCE_LAUNCH(FMT_FP16) }
+      PTTK_TCE_LAUNCH(FMT_TF32)
+#undef PTTK_TCE_LAUNCH
+    }
+  }
   // TMEM: accumulator 0 at column 0; with two or more steps the first step has its own
   // accumulator after it, so that the next item's first step can run while the last step's
   // accumulator is read out
@@ -1754,8 +2170,6 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
   if (cols > 512) return set_error(PTTK_ENOTSUP, "tensor-core chain: accumulators exceed tensor memory");
   a.tmem_cols = cols;
   a.b_slot_bytes = (uint32_t)npad_max * KCB;
-  const int bv_ld = (tt->n + 1) | 1;
-  const size_t parts = split ? 2 : 1;
   const size_t smem = (size_t)NS * parts * TILE_M * KCB + (size_t)NS * parts * a.b_slot_bytes +
                       sizeof(float) * ((size_t)TILE_M * a.ld_s + (size_t)2 * TILE_M * bv_ld +
                                        (size_t)TILE_M * a.ld_seed) + 16 +
