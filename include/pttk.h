@@ -252,6 +252,28 @@ pttk_status pttk_global_instantiate(const pttk_global* g, const double* theta, d
 /* Release a handle and its device memory (NULL is a no-op). */
 void pttk_global_free(pttk_global* g);
 
+/* ---- TT greedy-cross (Algorithms 5, 6, 7; Appendix "TT-cross approximation") ------------
+ * Phase 2 of Algorithm 2 as the paper runs it: a TT of the grid tensor M (Eq. mdc) from sampled
+ * entries, never forming the n^D grid, so that grids beyond device memory (the paper's n = 27,
+ * D = 8 grid holds 2.8e11 entries) can be compressed. The index sets of cardinality two of
+ * Algorithm 7 (init_it passes), then sweeps of Algorithm 5's cross updates on every super-core
+ * unfolding until the largest |x - x^| over n_check random entries, relative to the largest
+ * |x| among them, is <= eps, a sweep adds no pivot, or max_sweeps sweeps have run. The cores
+ * of the interpolation X^ = T_1 P_1^{-1} T_2 .. P_{N-1}^{-1} T_N are then transformed to
+ * Chebyshev coefficients (G_k <- G_k x_2 A), giving a handle like pttk_build_offline's.
+ * Every random number comes from SplitMix64 with the given key (pttk_splitmix64), drawn in the
+ * order the method consumes them: q1 and q2 of Algorithm 7, then per update the sample
+ * positions and the row-or-column bit, per sweep the check entries. Each argmin and argmax
+ * takes the first index within a relative 1e-12 of the extremum. Kernel entries, the cross-
+ * matrix solves, the skeleton residuals and the check are computed on the device; index sets
+ * stay on the host. The problem arguments are those of pttk_grid_coeffs (n <= 32). eps in
+ * (0, 1); n_check >= 1; init_it >= 1; max_sweeps >= 0. *sweeps (may be NULL) = sweeps run,
+ * *evals (may be NULL) = kernel entries evaluated. Synchronises `stream`.
+ * Errors: PTTK_EINVAL, PTTK_ENOMEM, PTTK_ECUDA, PTTK_ENOTSUP (a rank above 1024). */
+pttk_status pttk_cross_build(pttk_kernel kernel, int d, const double* src_box, const double* tgt_box, int d_theta,
+                             const double* theta_box, int n, double eps, uint64_t key, int max_sweeps, int n_check,
+                             int init_it, void* stream, pttk_tt** out, int* sweeps, int64_t* evals);
+
 /* ---- Algorithm 2 for fixed point sets: Phases 3 and 4 -----------------------------------
  * When X and Y stay fixed and only theta changes, the paper computes the factors once offline
  * (Algorithm 2, Phase 3: S = U(X), T = V(Y)) and compresses them with the theta cores by
@@ -286,6 +308,50 @@ pttk_status pttk_fixed_get_core(const pttk_fixed* f, int j, double* host_out);
 pttk_status pttk_fixed_theta_core(const pttk_fixed* f, const double* theta, pttk_prec prec, void* M, void* stream);
 /* Release a handle and its device memory (NULL is a no-op). */
 void pttk_fixed_free(pttk_fixed* f);
+
+/* ---- Gaussian-process workload (Section 1: hyperparameters and CG preconditioning) -------
+ * Section 1 names two uses of the parametric low-rank form in Gaussian-process regression:
+ * choosing the kernel's hyperparameters by maximising the log marginal likelihood, which
+ * needs K(X, X; theta) at many theta, and preconditioning conjugate gradients on the kernel
+ * system. Textbook definitions (Rasmussen and Williams 2006, Eqs. 2.30 and 5.9) with noise
+ * variance s2 > 0. Kernels: PTTK_GAUSS, PTTK_MATERN32, PTTK_EXPONENTIAL, PTTK_MATERN52
+ * (theta = l > 0); X: dev N x d row-major doubles. FP64 throughout. */
+
+/* out = (K(X, X; theta) + s2 I) v with every kernel entry evaluated on the fly (N^2 kernel
+ * evaluations, no N x N storage). v, out: dev [N]. Asynchronous on `stream`.
+ * Errors: PTTK_EINVAL. */
+pttk_status pttk_gp_kv(int kernel, int d, const double* X, int64_t N, const double* theta, double s2, const double* v,
+                       double* out, void* stream);
+
+/* Preconditioned conjugate gradients for (K(X, X; theta) + s2 I) x = b, the matrix applied
+ * exactly by pttk_gp_kv and the preconditioner (Z diag(lambda) Z^T + s2 I)^{-1} in Woodbury form
+ * Z ((Z^T v) ./ (lambda + s2)) + (v - Z Z^T v) / s2, Z (dev N x m, row-major, orthonormal
+ * columns) and lambda (dev [m]) from PTTK-Global (pttk_global_instantiate with compress = 1; eps
+ * = 0 keeps every term); m = 0 runs plain CG. x0 = 0; stops once ||b - A x||_2 <= tol ||b||_2
+ * (the recursively updated residual) or after maxit iterations. b, x: dev [N]. *iters and
+ * *resid (either may be NULL): the iterations taken and the final relative residual.
+ * Allocates scratch; synchronises `stream` every iteration.
+ * Errors: PTTK_EINVAL, PTTK_ENOMEM, PTTK_ECUDA, PTTK_EDOMAIN (p^T A p <= 0: not positive definite). */
+pttk_status pttk_gp_pcg(int kernel, int d, const double* X, int64_t N, const double* theta, double s2, const double* Z,
+                        const double* lam, int m, const double* b, double* x, double tol, int maxit, int* iters,
+                        double* resid, void* stream);
+
+/* Log marginal likelihood of y ~ N(0, K~ + s2 I) and its gradient in theta for the low-rank
+ * kernel of a PTTK-Global handle, K~(theta) = sym(S H(theta) T^T) = Q sym(C1(theta)) Q^T
+ * (Algorithm 4 without the zeroing of negative eigenvalues, so that K~ is differentiable):
+ *   lml = -1/2 y^T (K~ + s2 I)^{-1} y - 1/2 log det(K~ + s2 I) - N/2 log(2 pi),
+ *   d lml / d theta_j = 1/2 (alpha^T dK~_j alpha - tr((K~ + s2 I)^{-1} dK~_j)),
+ *   alpha = (K~ + s2 I)^{-1} y, dK~_j = sym(S dH_j T^T) (dH_j from T_k' in Eq. hmat).
+ * With B = sym(C1) (k x k) and c = Q^T y these reduce exactly to k x k algebra: log det =
+ * sum log(lambda_i(B) + s2) + (N - k) log s2, y^T(..)^{-1}y = c^T (B + s2 I)^{-1} c +
+ * (||y||^2 - ||c||^2) / s2, and the gradient terms through (B + s2 I)^{-1} and dB_j, so the cost
+ * per theta is independent of N beyond one N x k product. Eigenvalues of B within
+ * 64 eps max|lambda| of zero count as zero. theta: host [d_theta] (1 or 2 parameters), inside
+ * its box (else PTTK_EDOMAIN); y: dev [N]; lml: host; grad: host [d_theta] (may be NULL).
+ * Synchronises `stream`. Errors: PTTK_EINVAL, PTTK_EDOMAIN (also: K~ + s2 I not positive
+ * definite), PTTK_ENOTSUP, PTTK_ENOMEM, PTTK_ECUDA. */
+pttk_status pttk_gp_lml(const pttk_global* g, const double* theta, double s2, const double* y, double* lml,
+                        double* grad, void* stream);
 
 /* ---- random numbers of the TT greedy-cross (Algorithms 5-7) ----------------------------
  * The greedy-cross draws random index vectors, sample sets, a row-or-column bit and check
@@ -349,11 +415,14 @@ pttk_status pttk_batch_create(const pttk_tt* tt, int B, const int64_t* xoff, con
 void pttk_batch_free(pttk_batch* b);
 
 /* Launch configuration of the plan's tensor-core factor build; pttk_batch_get_config reports
- * the current one and how many exist. 0 (the default) and 1: the kernel that generates the A
- * operand in shared memory, with 128- or 64-byte chunks of K per row and its operand-ring depth;
- * 2, 3, 4: for the FP16/BF16 forms, the kernel that generates A in tensor memory and keeps the
- * chain's intermediate in registers, run in thread-block clusters of 1, 2 or 4 CTAs that share
- * each core chunk by a multicast copy (ranks it cannot hold fall back to configuration 0). */
+ * the current one and how many exist (6). 0 (the default): the kernel that generates the A
+ * operand in shared memory with four separate epilogue warps, which drain two alternating
+ * tensor-memory accumulators while the next tile's products run (ranks whose two accumulators
+ * or staging tiles do not fit fall back to configuration 1); 1 and 2: the same kernel without
+ * the epilogue warps, with 128- or 64-byte chunks of K per row; 3, 4, 5: for the FP16/BF16
+ * forms, the kernel that generates A in tensor memory and keeps the chain's intermediate in
+ * registers, run in thread-block clusters of 1, 2 or 4 CTAs that share each core chunk by a
+ * multicast copy (ranks it cannot hold fall back to configuration 1). */
 pttk_status pttk_batch_set_config(pttk_batch* b, int cfg);
 pttk_status pttk_batch_get_config(const pttk_batch* b, int* cfg, int* n_configs);
 

@@ -441,7 +441,7 @@ pttk_status pttk_tt_from_cores(pttk_kernel kernel, int d, const double* src_box,
   clear_error();
   if (!out || !ranks || !cores) return set_error(PTTK_EINVAL, "NULL argument");
   *out = nullptr;
-  PTTK_TRY(check_problem(kernel, d, src_box, tgt_box, d_theta, theta_box, n));
+  PTTK_TRY(check_problem(kernel, d, src_box, tgt_box, d_theta, theta_box, n, false));
   const int D = 2 * d + d_theta;
   if (ranks[0] != 1 || ranks[D] != 1) return set_error(PTTK_EINVAL, "ranks[0] and ranks[D] must be 1");
   for (int k = 1; k < D; ++k)

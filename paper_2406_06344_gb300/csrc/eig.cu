@@ -1,0 +1,398 @@
+// Symmetric eigendecomposition of a batch of small dense matrices in FP64, for the online
+// stage of PTTK-Global (Algorithm 4: the eigenpairs of R H^ R^T, one k x k matrix per theta).
+// The paper leaves this step to a library; it is built here from the classical steps:
+//   1. Householder reduction to tridiagonal form T = H^T A H, H = H_0 .. H_{k-3}, with the
+//      reflector of LAPACK's dlarfg (beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta,
+//      v = [1; x_{1:} / (alpha - beta)]) and the two-sided update of dsytd2
+//      (p = tau A22 v, w = p - (tau/2)(p^T v) v, A22 <- A22 - v w^T - w v^T);
+//   2. every eigenvalue of T by bisection on Sturm counts (the number of negative pivots of
+//      T - x I), one thread per eigenvalue;
+//   3. the eigenvectors of T for the selected eigenvalues by inverse iteration (Gaussian
+//      elimination with partial pivoting on T - lambda I), re-orthogonalised by modified
+//      Gram-Schmidt against the earlier vectors of their cluster (eigenvalues closer than
+//      1e-3 ||T||_1, the rule of LAPACK's dstein);
+//   4. the eigenvectors of A = H times those of T (the reflectors applied in reverse order).
+// The matrices of a batch are independent; every launch covers the whole batch (grid z or a
+// block per matrix), so a batch costs the launches of one matrix. No kernel waits on another
+// CTA.
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pttk_internal.cuh"
+
+namespace pttk {
+namespace {
+
+constexpr int EB = 256;        // threads per block
+constexpr int CHUNK = 64;      // columns per partial sum of the symmetric product
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sh[0] = t;
+  }
+  __syncthreads();
+  return sh[0];
+}
+
+// Reflector of step j for matrix blockIdx.x: x = A[j+1:k, j]. Writes v (v_0 = 1) over x,
+// tau[j], the diagonal d[j] = A[j, j] and the off-diagonal e[j] = beta.
+__global__ void __launch_bounds__(EB) reflector_kernel(double* __restrict__ A, int k, int j, double* __restrict__ tau,
+                                                       double* __restrict__ d, double* __restrict__ e) {
+  __shared__ double sh[32];
+  double* a = A + (size_t)blockIdx.x * k * k;
+  double* col = a + (size_t)j * k;
+  const int m = k - j - 1;  // length of x
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += col[j + 1 + i] * col[j + 1 + i];
+  const double xn2 = block_sum(s, sh);
+  const double alpha = col[j + 1];
+  double t = 0.0, beta = alpha, scale = 0.0;
+  if (xn2 > 0.0) {
+    beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+    t = (beta - alpha) / beta;
+    scale = 1.0 / (alpha - beta);
+  }
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) col[j + 1 + i] = xn2 > 0.0 ? col[j + 1 + i] * scale : 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    col[j + 1] = 1.0;
+    tau[(size_t)blockIdx.x * k + j] = t;
+    d[(size_t)blockIdx.x * k + j] = col[j];
+    e[(size_t)blockIdx.x * k + j] = beta;
+  }
+}
+
+// part[(z * nch + c) * k + i] = sum over columns l of chunk c (l > j) of A[i, l] v_l, rows i > j
+__global__ void __launch_bounds__(EB) symv_part_kernel(const double* __restrict__ A, int k, int j, int nch,
+                                                       double* __restrict__ part) {
+  const int z = blockIdx.z, c = blockIdx.y;
+  const double* a = A + (size_t)z * k * k;
+  const double* v = a + (size_t)j * k;  // v_l at v[l], l > j
+  const int i = j + 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int l0 = j + 1 + c * CHUNK, l1 = min(k, l0 + CHUNK);
+  if (i >= k) return;
+  double acc = 0.0;
+  for (int l = l0; l < l1; ++l) acc = fma(a[(size_t)l * k + i], v[l], acc);
+  part[((size_t)z * nch + c) * k + i] = acc;
+}
+
+// w = p - (tau/2)(p^T v) v with p = tau sum_c part, rows i > j (one block per matrix)
+__global__ void __launch_bounds__(EB) make_w_kernel(const double* __restrict__ A, int k, int j, int nch,
+                                                    const double* __restrict__ part, const double* __restrict__ tau,
+                                                    double* __restrict__ w) {
+  __shared__ double sh[32];
+  const int z = blockIdx.x;
+  const double* v = A + (size_t)z * k * k + (size_t)j * k;
+  const double t = tau[(size_t)z * k + j];
+  double* wz = w + (size_t)z * k;
+  double s = 0.0;
+  for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
+    double p = 0.0;
+    for (int c = 0; c < nch; ++c) p += part[((size_t)z * nch + c) * k + i];
+    p *= t;
+    wz[i] = p;
+    s += p * v[i];
+  }
+  const double pv = block_sum(s, sh);
+  for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) wz[i] -= 0.5 * t * pv * v[i];
+}
+
+// A22 <- A22 - v w^T - w v^T (both triangles), A22 = A[j+1:, j+1:]
+__global__ void __launch_bounds__(EB) rank2_kernel(double* __restrict__ A, int k, int j, const double* __restrict__ w) {
+  const int z = blockIdx.z;
+  double* a = A + (size_t)z * k * k;
+  const double* v = a + (size_t)j * k;
+  const double* wz = w + (size_t)z * k;
+  const int m = k - j - 1;
+  const int64_t total = (int64_t)m * m;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = j + 1 + (int)(q % m), l = j + 1 + (int)(q / m);
+    a[(size_t)l * k + i] -= v[i] * wz[l] + wz[i] * v[l];
+  }
+}
+
+// the last 2 x 2 block: d[k-2], d[k-1], e[k-2]
+__global__ void tail_kernel(const double* __restrict__ A, int k, double* __restrict__ d, double* __restrict__ e) {
+  const int z = blockIdx.x;
+  const double* a = A + (size_t)z * k * k;
+  if (threadIdx.x == 0) {
+    if (k >= 2) {
+      d[(size_t)z * k + k - 2] = a[(size_t)(k - 2) * k + k - 2];
+      e[(size_t)z * k + k - 2] = a[(size_t)(k - 2) * k + k - 1];
+    }
+    d[(size_t)z * k + k - 1] = a[(size_t)(k - 1) * k + k - 1];
+  }
+}
+
+// number of eigenvalues of T (d, e) below x: negative pivots of the LDL^T factorisation of
+// T - x I; a zero pivot is replaced by -pivmin (LAPACK's dlaebz convention)
+__device__ int sturm_count(const double* d, const double* e, int k, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < k; ++i) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// lam[z * k + i] = the i-th smallest eigenvalue of T_z, by bisection from Gershgorin bounds
+__global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ d, const double* __restrict__ e, int k,
+                                                     int nb, double* __restrict__ lam) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)k * nb) return;
+  const int z = (int)(q / k), i = (int)(q % k);
+  const double* dz = d + (size_t)z * k;
+  const double* ez = e + (size_t)z * k;
+  double lo = dz[0], hi = dz[0], emax2 = 0.0;
+  for (int r = 0; r < k; ++r) {
+    const double rad = (r > 0 ? fabs(ez[r - 1]) : 0.0) + (r < k - 1 ? fabs(ez[r]) : 0.0);
+    lo = fmin(lo, dz[r] - rad);
+    hi = fmax(hi, dz[r] + rad);
+    if (r < k - 1) emax2 = fmax(emax2, ez[r] * ez[r]);
+  }
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  const double pivmin = fmax(2.2250738585072014e-308 * fmax(emax2, 1.0), 1e-300);
+  lo -= 2.0 * 2.2204460492503131e-16 * tnorm + pivmin;
+  hi += 2.0 * 2.2204460492503131e-16 * tnorm + pivmin;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (hi - lo <= 2.0 * 2.2204460492503131e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    if (sturm_count(dz, ez, k, mid, pivmin) > i) hi = mid;
+    else lo = mid;
+  }
+  lam[q] = 0.5 * (lo + hi);
+}
+
+// Inverse iteration for the selected eigenvalues. One block per cluster: sel[c0 .. c1) of
+// (matrix, eigenvalue) entries listed in `job` (start, count) per cluster; the eigenvalues of a
+// cluster belong to one matrix and are processed in order. Thread 0 solves (T - lambda I) y = x
+// by Gaussian elimination with partial pivoting (a tridiagonal LU, fill-in one super-diagonal);
+// the block normalises and re-orthogonalises y against the cluster's earlier vectors.
+// Vectors go to V[z] columns vcol (k x ncols per matrix, column-major). work: 6 k doubles per
+// block.
+__global__ void __launch_bounds__(EB) inverse_iteration_kernel(const double* __restrict__ d, const double* __restrict__ e,
+                                                               int k, const int* __restrict__ job,
+                                                               const int* __restrict__ sel_z,
+                                                               const double* __restrict__ sel_lam,
+                                                               const int* __restrict__ sel_col, double* V, int ncols,
+                                                               double* work) {
+  __shared__ double sh[32];
+  const int c0 = job[2 * blockIdx.x], cn = job[2 * blockIdx.x + 1];
+  double* wk = work + (size_t)blockIdx.x * 6 * k;
+  double* dl = wk;          // multipliers
+  double* du = wk + k;      // upper factor: diagonal
+  double* du1 = wk + 2 * k; // first super-diagonal
+  double* du2 = wk + 3 * k; // second super-diagonal (fill-in)
+  int* piv = reinterpret_cast<int*>(wk + 4 * k);
+  double* y = wk + 5 * k;
+  const int z = sel_z[c0];
+  const double* dz = d + (size_t)z * k;
+  const double* ez = e + (size_t)z * k;
+  double tn = 0.0;  // ||T||_1
+  for (int r = 0; r < k; ++r) tn = fmax(tn, fabs(dz[r]) + (r > 0 ? fabs(ez[r - 1]) : 0.0) + (r < k - 1 ? fabs(ez[r]) : 0.0));
+  const double eps = 2.2204460492503131e-16;
+  const double tiny = fmax(eps * tn, 1e-300);
+  for (int q = c0; q < c0 + cn; ++q) {
+    const double lambda = sel_lam[q];
+    double* vz = V + (size_t)z * k * ncols;
+    double* vout = vz + (size_t)sel_col[q] * k;
+    // LU of T - lambda I with partial pivoting (thread 0)
+    if (threadIdx.x == 0) {
+      double a = dz[0] - lambda, b = k > 1 ? ez[0] : 0.0;
+      for (int r = 0; r < k - 1; ++r) {
+        const double c = ez[r], dn = dz[r + 1] - lambda, en = r + 1 < k - 1 ? ez[r + 1] : 0.0;
+        if (fabs(a) >= fabs(c)) {
+          if (fabs(a) < tiny) a = tiny;
+          const double m = c / a;
+          dl[r] = m;
+          piv[r] = 0;
+          du[r] = a;
+          du1[r] = b;
+          du2[r] = 0.0;
+          a = dn - m * b;
+          b = en;
+        } else {
+          const double m = a / c;
+          dl[r] = m;
+          piv[r] = 1;
+          du[r] = c;
+          du1[r] = dn;
+          du2[r] = en;
+          a = b - m * dn;
+          b = -m * en;
+        }
+      }
+      if (fabs(a) < tiny) a = tiny;
+      du[k - 1] = a;
+    }
+    // start vector: a fixed, non-degenerate one
+    for (int r = threadIdx.x; r < k; r += blockDim.x) y[r] = 1.0 + 0.3 * sin(1.7 * (r + 1) + 0.37 * (q - c0 + 1));
+    __syncthreads();
+    for (int it = 0; it < 3; ++it) {
+      if (threadIdx.x == 0) {
+        // Both sweeps carry the entries still being updated in registers: every load reads an
+        // entry the sweep has not written yet and every store is final, so no entry is read
+        // back after a store to it.
+        // forward: apply the row interchanges and multipliers; cur is the working row's entry
+        double cur = y[0];
+        for (int r = 0; r < k - 1; ++r) {
+          const double nxt = y[r + 1];
+          if (piv[r]) {
+            y[r] = nxt;
+            cur = cur - dl[r] * nxt;
+          } else {
+            y[r] = cur;
+            cur = nxt - dl[r] * cur;
+          }
+        }
+        y[k - 1] = cur;
+        // back substitution with the upper factor (diagonal, two super-diagonals); x1, x2 are
+        // the solution entries r + 1 and r + 2
+        double x1 = cur / du[k - 1], x2 = 0.0;
+        y[k - 1] = x1;
+        for (int r = k - 2; r >= 0; --r) {
+          const double x0 = (y[r] - du1[r] * x1 - du2[r] * x2) / du[r];
+          y[r] = x0;
+          x2 = x1;
+          x1 = x0;
+        }
+      }
+      __syncthreads();
+      // orthogonalise against the earlier vectors of the cluster, then normalise
+      for (int p = c0; p < q; ++p) {
+        const double* u = vz + (size_t)sel_col[p] * k;
+        double s = 0.0;
+        for (int r = threadIdx.x; r < k; r += blockDim.x) s += u[r] * y[r];
+        const double dot = block_sum(s, sh);
+        for (int r = threadIdx.x; r < k; r += blockDim.x) y[r] -= dot * u[r];
+        __syncthreads();
+      }
+      double s = 0.0;
+      for (int r = threadIdx.x; r < k; r += blockDim.x) s += y[r] * y[r];
+      const double nrm = sqrt(block_sum(s, sh));
+      const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      for (int r = threadIdx.x; r < k; r += blockDim.x) y[r] *= inv;
+      __syncthreads();
+    }
+    for (int r = threadIdx.x; r < k; r += blockDim.x) vout[r] = y[r];
+    __syncthreads();
+  }
+}
+
+// V <- H_0 .. H_{k-3} V for the ncols columns of each matrix (column block per CTA): the
+// reflectors applied from the last to the first, y <- y - tau v (v^T y)
+__global__ void __launch_bounds__(EB) back_transform_kernel(const double* __restrict__ A, const double* __restrict__ tau,
+                                                            int k, double* __restrict__ V, int ncols) {
+  __shared__ double sh[32];
+  const int z = blockIdx.y, col = blockIdx.x;
+  if (col >= ncols) return;
+  const double* a = A + (size_t)z * k * k;
+  double* y = V + ((size_t)z * ncols + col) * k;
+  for (int j = k - 3; j >= 0; --j) {
+    const double t = tau[(size_t)z * k + j];
+    if (t == 0.0) continue;
+    const double* v = a + (size_t)j * k;
+    double s = 0.0;
+    for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) s += v[r] * y[r];
+    const double dot = block_sum(s, sh);
+    for (int r = j + 1 + threadIdx.x; r < k; r += blockDim.x) y[r] -= t * dot * v[r];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// Tridiagonalises nb symmetric k x k matrices (A: nb x k x k, column-major, overwritten by the
+// reflectors) and returns every eigenvalue in ascending order (lam: nb x k), plus the
+// tridiagonal (d, e: nb x k) and tau (nb x k) for sym_eig_vectors. Device buffers throughout.
+pttk_status sym_eig_values(double* A, int k, int nb, double* d, double* e, double* tau, double* lam, cudaStream_t s) {
+  if (k < 1 || nb < 1) return set_error(PTTK_EINVAL, "empty eigenproblem");
+  if (k >= 3) {
+    const int nch_max = (k + CHUNK - 1) / CHUNK;
+    double *part = nullptr, *w = nullptr;
+    PTTK_CUDA(cudaMallocAsync(&part, sizeof(double) * (size_t)nb * nch_max * k, s));
+    PTTK_CUDA(cudaMallocAsync(&w, sizeof(double) * (size_t)nb * k, s));
+    for (int j = 0; j < k - 2; ++j) {
+      const int m = k - j - 1, nch = (m + CHUNK - 1) / CHUNK;
+      reflector_kernel<<<nb, EB, 0, s>>>(A, k, j, tau, d, e); pttk::count_launch();
+      symv_part_kernel<<<dim3((unsigned)((m + EB - 1) / EB), (unsigned)nch, (unsigned)nb), EB, 0, s>>>(A, k, j, nch, part); pttk::count_launch();
+      make_w_kernel<<<nb, EB, 0, s>>>(A, k, j, nch, part, tau, w); pttk::count_launch();
+      const int64_t cells = (int64_t)m * m;
+      const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cells + EB - 1) / EB, (int64_t)sm_count() * 4 / std::max(nb, 1) + 1));
+      rank2_kernel<<<dim3(gx, 1, (unsigned)nb), EB, 0, s>>>(A, k, j, w); pttk::count_launch();
+    }
+    cudaFreeAsync(part, s);
+    cudaFreeAsync(w, s);
+  }
+  tail_kernel<<<nb, 32, 0, s>>>(A, k, d, e); pttk::count_launch();
+  const int64_t nt = (int64_t)k * nb;
+  bisect_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(d, e, k, nb, lam); pttk::count_launch();
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
+// Eigenvectors of the matrices tridiagonalised by sym_eig_values for selected eigenvalues:
+// selection q has matrix sel_z[q], eigenvalue sel_lam[q] and output column sel_col[q] of V
+// (nb x k x ncols, column-major per matrix). Selections of one matrix must be listed in
+// ascending order of eigenvalue. Host arrays; synchronises `s`.
+pttk_status sym_eig_vectors(const double* A, const double* d, const double* e, const double* tau, int k, int nb,
+                            const std::vector<int>& sel_z, const std::vector<double>& sel_lam,
+                            const std::vector<int>& sel_col, double* V, int ncols, cudaStream_t s) {
+  const int nsel = (int)sel_z.size();
+  if (nsel == 0) return PTTK_OK;
+  // clusters: consecutive selections of one matrix whose eigenvalues are closer than
+  // 1e-3 ||T||_1 (estimated here by the largest |eigenvalue| of that matrix's selections)
+  std::vector<double> scale(nb, 0.0);
+  for (int q = 0; q < nsel; ++q) scale[sel_z[q]] = std::max(scale[sel_z[q]], std::fabs(sel_lam[q]));
+  std::vector<int> job;
+  int start = 0;
+  for (int q = 1; q <= nsel; ++q) {
+    const bool brk = q == nsel || sel_z[q] != sel_z[q - 1] ||
+                     std::fabs(sel_lam[q] - sel_lam[q - 1]) > 1e-3 * scale[sel_z[q]];
+    if (brk) {
+      job.push_back(start);
+      job.push_back(q - start);
+      start = q;
+    }
+  }
+  const int nclus = (int)job.size() / 2;
+  int *djob = nullptr, *dz = nullptr, *dcol = nullptr;
+  double *dlam = nullptr, *work = nullptr;
+  PTTK_CUDA(cudaMallocAsync(&djob, sizeof(int) * job.size(), s));
+  PTTK_CUDA(cudaMallocAsync(&dz, sizeof(int) * nsel, s));
+  PTTK_CUDA(cudaMallocAsync(&dcol, sizeof(int) * nsel, s));
+  PTTK_CUDA(cudaMallocAsync(&dlam, sizeof(double) * nsel, s));
+  PTTK_CUDA(cudaMallocAsync(&work, sizeof(double) * 6 * (size_t)k * nclus, s));
+  PTTK_CUDA(cudaMemcpyAsync(djob, job.data(), sizeof(int) * job.size(), cudaMemcpyHostToDevice, s));
+  PTTK_CUDA(cudaMemcpyAsync(dz, sel_z.data(), sizeof(int) * nsel, cudaMemcpyHostToDevice, s));
+  PTTK_CUDA(cudaMemcpyAsync(dcol, sel_col.data(), sizeof(int) * nsel, cudaMemcpyHostToDevice, s));
+  PTTK_CUDA(cudaMemcpyAsync(dlam, sel_lam.data(), sizeof(double) * nsel, cudaMemcpyHostToDevice, s));
+  inverse_iteration_kernel<<<nclus, EB, 0, s>>>(d, e, k, djob, dz, dlam, dcol, V, ncols, work); pttk::count_launch();
+  back_transform_kernel<<<dim3((unsigned)ncols, (unsigned)nb), EB, 0, s>>>(A, tau, k, V, ncols); pttk::count_launch();
+  PTTK_CUDA(cudaGetLastError());
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  cudaFreeAsync(djob, s);
+  cudaFreeAsync(dz, s);
+  cudaFreeAsync(dcol, s);
+  cudaFreeAsync(dlam, s);
+  cudaFreeAsync(work, s);
+  return PTTK_OK;
+}
+
+}  // namespace pttk

@@ -8,10 +8,13 @@
 // Algorithm 4 uses.
 //
 // Online, per theta: H = H(theta) (Algorithm 3); R H^ R^T = sym(C1), C1 = R_s H R_t^T
-// (Eq. pttk1: H^ = [[0, H/2], [H^T/2, 0]], R = [R_s R_t]); its eigendecomposition by one-sided
-// Jacobi on sym(C1) + c I with c = 2 ||C1||_F. That matrix is symmetric positive definite (its
-// eigenvalues lie in [c/2, 3c/2]), so its left singular vectors are the eigenvectors of
-// sym(C1) and its singular values are the eigenvalues plus c.
+// (Eq. pttk1: H^ = [[0, H/2], [H^T/2, 0]], R = [R_s R_t]); its eigendecomposition by Householder
+// tridiagonalisation, bisection and inverse iteration (eig.cu). Eigenvalues within
+// 64 eps max|lambda| of zero are below FP64's resolution for this matrix and give no term.
+//
+// The Gaussian-process use of Section 1 (pttk_gp_lml): the log marginal likelihood of
+// y ~ N(0, K~ + s2 I) and its theta gradient for the low-rank kernel K~ = Q sym(C1) Q^T =
+// sym(S H T^T), reduced to k x k algebra on B = sym(C1) (Woodbury and the eigenbasis of B).
 //
 // Memory: the handle keeps Q (N x k row-major, k <= r_s + r_t), R (k x (r_s + r_t)) and a copy
 // of the FP64 cores (for H(theta)); the offline stage holds about five N x (r_s + r_t) FP64
@@ -139,33 +142,13 @@ __global__ void __launch_bounds__(1024) asym_sumsq_block_kernel(const double* __
   if (threadIdx.x == 0) *out = part[0];
 }
 
-// norms[c] = ||A[:, c]||_2 (rows x ncols, column-major), one warp per column
-__global__ void col_norms_kernel(const double* __restrict__ A, int64_t rows, int ncols,
-                                 double* __restrict__ norms) {
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (gw >= ncols) return;
-  const double* col = A + gw * rows;
-  double acc = 0.0;
-  for (int64_t i = lane; i < rows; i += 32) acc = fma(col[i], col[i], acc);
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) norms[gw] = sqrt(acc);
-}
-
-// out[:, q] = A[:, idx[q]] * (scale[q] / norms[idx[q]]), rows x m column-major; idx, scale
-// packed as sel[0..m) = idx (as doubles), sel[m..2m) = scale
-__global__ void pick_cols_kernel(const double* __restrict__ A, int64_t rows,
-                                 const double* __restrict__ sel, int m,
-                                 const double* __restrict__ norms, double* __restrict__ out) {
+// out[:, q] = A[:, q] * scale[q], rows x m column-major
+__global__ void scale_cols_kernel(const double* __restrict__ A, int64_t rows, const double* __restrict__ scale, int m,
+                                  double* __restrict__ out) {
   const int64_t total = rows * m;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows;
-    const int q = (int)(e / rows);
-    const int src = (int)sel[q];
-    const double nr = norms[src];
-    out[e] = nr > 0.0 ? A[i + (int64_t)src * rows] * (sel[m + q] / nr) : 0.0;
-  }
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = A[e] * scale[e / rows];
 }
 
 // W = diag(lam), m x m
@@ -235,12 +218,11 @@ static pttk_status global_online_run(const pttk_global* g, const double* th, dou
                                      bool definite, double* Z, double* W, int* rank, cudaStream_t s) {
   const int k = g->k, rs = g->rs, rt = g->rt;
   const int64_t N = g->N;
-  DevBuf H, P, C1, B, nrm, t2d;
+  DevBuf H, P, C1, B, t2d;
   PTTK_TRY(H.alloc((size_t)rs * rt));
   PTTK_TRY(P.alloc((size_t)k * rt));
   PTTK_TRY(C1.alloc((size_t)k * k));
   PTTK_TRY(B.alloc((size_t)k * k));
-  PTTK_TRY(nrm.alloc(k));
   PTTK_TRY(t2d.alloc(2));
   PTTK_TRY(theta_core_run(&g->tt, th, true, H.p, s));  // H(theta), rs x rt row-major
   // P = R_s H (k x rt); H row-major is H^T column-major with leading dimension rt
@@ -262,40 +244,47 @@ static pttk_status global_online_run(const pttk_global* g, const double* th, dou
     PTTK_CUDA(cudaStreamSynchronize(s));
     return PTTK_OK;
   }
-  const double shift = 2.0 * sqrt(t2);
-  sym_shift_kernel<<<blocks_for((int64_t)k * k, 256), 256, 0, s>>>(C1.p, k, shift, B.p); pttk::count_launch();
+  // B = sym(C1) = (C1 + C1^T)/2: Q B Q^T = Q R H^ R^T Q^T, the matrix of Algorithm 4
+  sym_shift_kernel<<<blocks_for((int64_t)k * k, 256), 256, 0, s>>>(C1.p, k, 0.0, B.p); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
+  DevBuf dd, ee, dtau, dlam_all;
+  PTTK_TRY(dd.alloc(k));
+  PTTK_TRY(ee.alloc(k));
+  PTTK_TRY(dtau.alloc(k));
+  PTTK_TRY(dlam_all.alloc(k));
   {
     PTTK_PROF("global_eig", s);
-    PTTK_TRY(jacobi_columns(B.p, k, k, s));
+    PTTK_TRY(sym_eig_values(B.p, k, 1, dd.p, ee.p, dtau.p, dlam_all.p, s));
   }
-  col_norms_kernel<<<(unsigned)(((int64_t)k * 32 + 255) / 256), 256, 0, s>>>(B.p, k, k, nrm.p); pttk::count_launch();
-  PTTK_CUDA(cudaGetLastError());
-  std::vector<double> sigma(k);
-  PTTK_CUDA(cudaMemcpyAsync(sigma.data(), nrm.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-  PTTK_CUDA(cudaStreamSynchronize(s));
-  // eigenvalues, in decreasing |lambda|; a definite kernel drops the negative ones
   std::vector<double> lam(k);
-  for (int i = 0; i < k; ++i) lam[i] = sigma[i] - shift;
+  PTTK_CUDA(cudaMemcpyAsync(lam.data(), dlam_all.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  // eigenvalues in decreasing |lambda|; a definite kernel drops the negative ones. Eigenvalues
+  // within 64 eps max|lambda| of zero are below what FP64 resolves (their computed values carry
+  // absolute errors of that order, sign included) and count as zero: no term.
+  double lmax = 0.0;
+  for (int i = 0; i < k; ++i) lmax = std::max(lmax, std::fabs(lam[i]));
+  const double res = 64.0 * 2.2204460492503131e-16 * lmax;
   std::vector<int> order(k);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return std::fabs(lam[a]) > std::fabs(lam[b]); });
   std::vector<int> kept;
+  std::vector<char> is_kept(k, 0);
   for (int i : order)
-    if (!definite || lam[i] > 0.0) kept.push_back(i);
+    if ((!definite || lam[i] > 0.0) && std::fabs(lam[i]) > res) {
+      kept.push_back(i);
+      is_kept[i] = 1;
+    }
   int m = (int)kept.size();
   if (compress) {
     // ||Q U_j Lambda_j U_j^T Q^T - S H T^T||_F^2 = ||C1 - U_j Lambda_j U_j^T||_F^2
     //   = ||(C1 - C1^T)/2||_F^2 + (sum of lambda_i^2 over the eigenpairs not kept),
-    // the symmetric and antisymmetric parts being orthogonal. Summed from the discarded terms
-    // themselves: ||C1||^2 - (sum of the kept lambda^2) would cancel, and the eigenvalues carry
-    // an absolute error of order 1e-14 ||C1||_F (they are singular values of sym(C1) + c I,
-    // minus c), which in the large kept terms alone exceeds eps^2 ||C1||^2 for eps <= 1e-6.
+    // the symmetric and antisymmetric parts being orthogonal, summed from the discarded terms
+    // themselves (||C1||^2 - sum of the kept lambda^2 would cancel).
     const double bound2 = eps * eps * t2;
-    double excl2 = 0.0;  // eigenvalues not eligible: the negative ones of a definite kernel
-    if (definite)
-      for (int i = 0; i < k; ++i)
-        if (!(lam[i] > 0.0)) excl2 += lam[i] * lam[i];
+    double excl2 = 0.0;  // eigenvalues not eligible: negative ones of a definite kernel, unresolved ones
+    for (int i = 0; i < k; ++i)
+      if (!is_kept[i]) excl2 += lam[i] * lam[i];
     std::vector<double> tail(kept.size() + 1, 0.0);  // tail[j] = sum over kept[j..] of lambda^2
     for (int q = (int)kept.size() - 1; q >= 0; --q) tail[q] = tail[q + 1] + lam[kept[q]] * lam[kept[q]];
     int j = 0;
@@ -308,25 +297,32 @@ static pttk_status global_online_run(const pttk_global* g, const double* th, dou
     PTTK_CUDA(cudaStreamSynchronize(s));
     return PTTK_OK;
   }
-  // selection table: column index, then the scale of each picked column
-  std::vector<double> sel(2 * (size_t)m);
-  DevBuf dsel, Un, Ul, dlam;
-  PTTK_TRY(dsel.alloc(2 * (size_t)m));
+  // eigenvectors of the m terms (column q of Un for kept[q]), computed in ascending order of
+  // eigenvalue as the inverse iteration's clustering needs
+  DevBuf Un, Ul, dlam;
   PTTK_TRY(Un.alloc((size_t)k * m));
-  for (int q = 0; q < m; ++q) {
-    sel[q] = kept[q];
-    sel[m + q] = 1.0;
+  {
+    std::vector<int> idx(kept.begin(), kept.begin() + m), pos(m);
+    std::vector<int> asc(m);
+    std::iota(asc.begin(), asc.end(), 0);
+    std::stable_sort(asc.begin(), asc.end(), [&](int a, int b) { return lam[idx[a]] < lam[idx[b]]; });
+    std::vector<int> sz(m, 0), scol(m);
+    std::vector<double> slam(m);
+    for (int q = 0; q < m; ++q) {
+      slam[q] = lam[idx[asc[q]]];
+      scol[q] = asc[q];
+    }
+    PTTK_PROF("global_eig", s);
+    PTTK_TRY(sym_eig_vectors(B.p, dd.p, ee.p, dtau.p, k, 1, sz, slam, scol, Un.p, m, s));
   }
-  PTTK_CUDA(cudaMemcpyAsync(dsel.p, sel.data(), sizeof(double) * 2 * m, cudaMemcpyHostToDevice, s));
-  pick_cols_kernel<<<blocks_for((int64_t)k * m, 256), 256, 0, s>>>(B.p, k, dsel.p, m, nrm.p, Un.p); pttk::count_launch();
-  PTTK_CUDA(cudaGetLastError());
+  std::vector<double> lk(m);
+  for (int q = 0; q < m; ++q) lk[q] = lam[kept[q]];
+  PTTK_TRY(dlam.alloc(m));
+  PTTK_CUDA(cudaMemcpyAsync(dlam.p, lk.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
   if (!compress) {
     // W = U Lambda U^T (k x k)
-    PTTK_CUDA(cudaStreamSynchronize(s));  // sel is rewritten below
-    for (int q = 0; q < m; ++q) sel[m + q] = lam[kept[q]];
     PTTK_TRY(Ul.alloc((size_t)k * m));
-    PTTK_CUDA(cudaMemcpyAsync(dsel.p, sel.data(), sizeof(double) * 2 * m, cudaMemcpyHostToDevice, s));
-    pick_cols_kernel<<<blocks_for((int64_t)k * m, 256), 256, 0, s>>>(B.p, k, dsel.p, m, nrm.p, Ul.p); pttk::count_launch();
+    scale_cols_kernel<<<blocks_for((int64_t)k * m, 256), 256, 0, s>>>(Un.p, k, dlam.p, m, Ul.p); pttk::count_launch();
     PTTK_CUDA(cudaGetLastError());
     dgemm(false, true, k, k, m, 1.0, Ul.p, k, Un.p, k, 0.0, W, k, s);
   } else {
@@ -335,14 +331,132 @@ static pttk_status global_online_run(const pttk_global* g, const double* th, dou
       PTTK_PROF("global_z", s);
       dgemm(true, false, m, N, k, 1.0, Un.p, k, g->Q, k, 0.0, Z, m, s);
     }
-    std::vector<double> lk(m);
-    for (int q = 0; q < m; ++q) lk[q] = lam[kept[q]];
-    PTTK_TRY(dlam.alloc(m));
-    PTTK_CUDA(cudaMemcpyAsync(dlam.p, lk.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
     diag_kernel<<<blocks_for((int64_t)m * m, 256), 256, 0, s>>>(dlam.p, m, W); pttk::count_launch();
     PTTK_CUDA(cudaGetLastError());
   }
   PTTK_CUDA(cudaStreamSynchronize(s));
+  return PTTK_OK;
+}
+
+// ---------------- Gaussian-process likelihood on the low-rank kernel --------------------------
+namespace {
+// out (ra x rb, column-major) = sum_k G[:, k, :] T_k'(th) * scale (derivative of Eq. hmat's
+// contraction; T_0' = 0, T_1' = 1, T_{k+1}' = 2 T_k + 2 th T_k' - T_{k-1}')
+__global__ void contract_theta_deriv_kernel(const double* __restrict__ G, int ra, int n, int rb, double th,
+                                            double scale, double* __restrict__ out) {
+  double T[PTTK_MAX_N], dT[PTTK_MAX_N];
+  T[0] = 1.0;
+  dT[0] = 0.0;
+  if (n > 1) {
+    T[1] = th;
+    dT[1] = 1.0;
+  }
+  for (int k = 2; k < n; ++k) {
+    T[k] = 2.0 * th * T[k - 1] - T[k - 2];
+    dT[k] = 2.0 * T[k - 1] + 2.0 * th * dT[k - 1] - dT[k - 2];
+  }
+  const int64_t total = (int64_t)ra * rb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e % ra, b = e / ra;
+    const double* g = G + a + (int64_t)ra * n * b;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc = fma(g[(int64_t)ra * k], dT[k], acc);
+    out[e] = acc * scale;
+  }
+}
+__global__ void contract_theta_cm_kernel(const double* __restrict__ G, int ra, int n, int rb, double th,
+                                         double* __restrict__ out) {
+  double T[PTTK_MAX_N];
+  T[0] = 1.0;
+  if (n > 1) T[1] = th;
+  for (int k = 2; k < n; ++k) T[k] = 2.0 * th * T[k - 1] - T[k - 2];
+  const int64_t total = (int64_t)ra * rb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e % ra, b = e / ra;
+    const double* g = G + a + (int64_t)ra * n * b;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc = fma(g[(int64_t)ra * k], T[k], acc);
+    out[e] = acc;
+  }
+}
+// sum_i coef[i] (U[:, i] . Y[:, i]) and the trace of A (k x k) into out[0], out[1]; one block
+__global__ void __launch_bounds__(1024) coldot_trace_kernel(const double* __restrict__ U, const double* __restrict__ Y,
+                                                            int k, int m, const double* __restrict__ coef,
+                                                            const double* __restrict__ A, double* __restrict__ out) {
+  __shared__ double sh[2][1024];
+  double acc = 0.0, tr = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)k * m; e += 1024) acc = fma(U[e] * coef[e / k], Y[e], acc);
+  for (int i = threadIdx.x; i < k; i += 1024) tr += A[(int64_t)i * k + i];
+  sh[0][threadIdx.x] = acc;
+  sh[1][threadIdx.x] = tr;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sh[0][0];
+    out[1] = sh[1][0];
+  }
+}
+// a . b (n doubles) into *out, one block in a fixed order
+__global__ void __launch_bounds__(1024) dot_block_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                         int64_t n, double* __restrict__ out) {
+  __shared__ double sh[1024];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 1024) acc = fma(a[i], b[i], acc);
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+// out[i] = a[i] * b[i] (+ c[i] * t when c is given)
+__global__ void mul_add_kernel(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ c,
+                               double t, int n, double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = a[i] * b[i] + (c ? c[i] * t : 0.0);
+}
+__global__ void axpy_kernel(double t, const double* __restrict__ x, int n, double* __restrict__ y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = fma(t, x[i], y[i]);
+}
+}  // namespace
+
+// B (k x k) = sym(R_s M R_t^T) for M (rs x rt, column-major)
+static pttk_status global_sym_form(const pttk_global* g, const double* M, double* P, double* C, double* B, cudaStream_t s) {
+  const int k = g->k, rs = g->rs, rt = g->rt;
+  dgemm(false, false, k, rt, rs, 1.0, g->R, k, M, rs, 0.0, P, k, s);
+  dgemm(false, true, k, k, rt, 1.0, P, k, g->R + (size_t)k * rs, k, 0.0, C, k, s);
+  sym_shift_kernel<<<blocks_for((int64_t)k * k, 256), 256, 0, s>>>(C, k, 0.0, B); pttk::count_launch();
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
+// H(theta) (which < 0) or dH/dtheta_which (column-major rs x rt) of the handle's theta cores
+static pttk_status global_theta_matrix(const pttk_global* g, const double* th, int which, double* out, double* work,
+                                       cudaStream_t s) {
+  const pttk_tt& tt = g->tt;
+  const int d = tt.d, dth = tt.dtheta, n = tt.n;
+  double* Hj[2] = {work, work + (size_t)tt.ranks[d] * tt.ranks[d + 1]};
+  for (int j = 0; j < dth; ++j) {
+    const int ra = tt.ranks[d + j], rb = tt.ranks[d + j + 1];
+    double* dst = dth == 1 ? out : Hj[j];
+    const unsigned blocks = blocks_for((int64_t)ra * rb, 256);
+    if (j == which) {
+      const double lo = tt.box[d + j][0], hi = tt.box[d + j][1];
+      contract_theta_deriv_kernel<<<blocks, 256, 0, s>>>(tt.cores64 + tt.core_off[d + j], ra, n, rb, th[j],
+                                                         2.0 / (lo - hi), dst); pttk::count_launch();
+    } else {
+      contract_theta_cm_kernel<<<blocks, 256, 0, s>>>(tt.cores64 + tt.core_off[d + j], ra, n, rb, th[j], dst); pttk::count_launch();
+    }
+  }
+  if (dth == 2) dgemm(false, false, g->rs, g->rt, tt.ranks[d + 1], 1.0, Hj[0], g->rs, Hj[1], tt.ranks[d + 1], 0.0, out, g->rs, s);
+  PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
 }
 
@@ -419,5 +533,124 @@ pttk_status pttk_global_instantiate(const pttk_global* g, const double* theta, d
 }
 
 void pttk_global_free(pttk_global* g) { global_release(g); }
+
+pttk_status pttk_gp_lml(const pttk_global* g, const double* theta, double s2, const double* y, double* lml,
+                        double* grad, void* stream) {
+  clear_error();
+  if (!g || !y || !lml) return set_error(PTTK_EINVAL, "NULL argument");
+  if (!(s2 > 0.0)) return set_error(PTTK_EINVAL, "the noise variance s2 must be positive");
+  const int dth = g->tt.dtheta;
+  if (dth < 1 || dth > 2) return set_error(PTTK_ENOTSUP, "the likelihood needs a kernel with 1 or 2 parameters");
+  double th[PTTK_MAX_D];
+  PTTK_TRY(theta_hat(&g->tt, theta, th));
+  cudaStream_t s = as_stream(stream);
+  const int k = g->k, rs = g->rs, rt = g->rt;
+  const int64_t N = g->N;
+  const pttk_tt& tt = g->tt;
+  const size_t hwork = (size_t)tt.ranks[tt.d] * tt.ranks[tt.d + 1] + (size_t)tt.ranks[tt.d + 1] * tt.ranks[tt.d + dth];
+  DevBuf c, Mbuf, work, P, C, B, Bw, dB, dd, ee, tau, lamd, sc;
+  PTTK_TRY(c.alloc(k));
+  PTTK_TRY(Mbuf.alloc((size_t)rs * rt));
+  PTTK_TRY(work.alloc(hwork));
+  PTTK_TRY(P.alloc((size_t)k * rt));
+  PTTK_TRY(C.alloc((size_t)k * k));
+  PTTK_TRY(B.alloc((size_t)k * k));
+  PTTK_TRY(Bw.alloc((size_t)k * k));
+  PTTK_TRY(dB.alloc((size_t)dth * k * k));
+  PTTK_TRY(dd.alloc(k));
+  PTTK_TRY(ee.alloc(k));
+  PTTK_TRY(tau.alloc(k));
+  PTTK_TRY(lamd.alloc(k));
+  PTTK_TRY(sc.alloc(8));
+  // c = Q^T y (Q row-major N x k = column-major k x N), ||y||^2, ||c||^2
+  dgemm(false, false, k, 1, N, 1.0, g->Q, k, y, N, 0.0, c.p, k, s);
+  dot_block_kernel<<<1, 1024, 0, s>>>(y, y, N, sc.p); pttk::count_launch();
+  dot_block_kernel<<<1, 1024, 0, s>>>(c.p, c.p, k, sc.p + 1); pttk::count_launch();
+  // B = sym(R_s H R_t^T) and dB_j = sym(R_s dH_j R_t^T)
+  PTTK_TRY(global_theta_matrix(g, th, -1, Mbuf.p, work.p, s));
+  PTTK_TRY(global_sym_form(g, Mbuf.p, P.p, C.p, B.p, s));
+  for (int j = 0; j < dth; ++j) {
+    PTTK_TRY(global_theta_matrix(g, th, j, Mbuf.p, work.p, s));
+    PTTK_TRY(global_sym_form(g, Mbuf.p, P.p, C.p, dB.p + (size_t)j * k * k, s));
+  }
+  PTTK_CUDA(cudaMemcpyAsync(Bw.p, B.p, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, s));
+  {
+    PTTK_PROF("global_eig", s);
+    PTTK_TRY(sym_eig_values(Bw.p, k, 1, dd.p, ee.p, tau.p, lamd.p, s));
+  }
+  std::vector<double> lam(k);
+  double yy_cc[2];
+  PTTK_CUDA(cudaMemcpyAsync(lam.data(), lamd.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaMemcpyAsync(yy_cc, sc.p, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  double lmax = 0.0, logdet = (double)(N - k) * std::log(s2);
+  for (int i = 0; i < k; ++i) {
+    lmax = std::max(lmax, std::fabs(lam[i]));
+    if (!(lam[i] + s2 > 0.0))
+      return set_error(PTTK_EDOMAIN, "the low-rank kernel plus s2 I is not positive definite at this theta");
+    logdet += std::log(lam[i] + s2);
+  }
+  // eigenvectors of the resolved eigenvalues; the others count as zero, their eigenspace
+  // entering only through the 1/s2 terms below
+  const double res = 64.0 * 2.2204460492503131e-16 * lmax;
+  std::vector<int> sz, scol;
+  std::vector<double> slam, coef;
+  for (int i = 0; i < k; ++i)
+    if (std::fabs(lam[i]) > res) {
+      sz.push_back(0);
+      scol.push_back((int)slam.size());
+      slam.push_back(lam[i]);
+      coef.push_back(1.0 / (lam[i] + s2) - 1.0 / s2);
+    }
+  const int m = (int)slam.size();
+  DevBuf U, Y, w, alpha, coefd, v;
+  PTTK_TRY(U.alloc((size_t)k * std::max(m, 1)));
+  PTTK_TRY(Y.alloc((size_t)k * std::max(m, 1)));
+  PTTK_TRY(w.alloc(std::max(m, 1)));
+  PTTK_TRY(alpha.alloc(k));
+  PTTK_TRY(coefd.alloc(std::max(m, 1)));
+  PTTK_TRY(v.alloc(k));
+  if (m > 0) {
+    PTTK_PROF("global_eig", s);
+    PTTK_TRY(sym_eig_vectors(Bw.p, dd.p, ee.p, tau.p, k, 1, sz, slam, scol, U.p, m, s));
+    PTTK_CUDA(cudaMemcpyAsync(coefd.p, coef.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  }
+  // alpha~ = (B + s2 I)^{-1} c = U ((1/(lambda + s2) - 1/s2) .* (U^T c)) + c / s2
+  PTTK_CUDA(cudaMemsetAsync(v.p, 0, sizeof(double) * k, s));
+  if (m > 0) {
+    dgemm(true, false, m, 1, k, 1.0, U.p, k, c.p, k, 0.0, w.p, m, s);
+    mul_add_kernel<<<(m + 255) / 256, 256, 0, s>>>(w.p, coefd.p, nullptr, 0.0, m, w.p); pttk::count_launch();
+    dgemm(false, false, k, 1, m, 1.0, U.p, k, w.p, m, 0.0, v.p, k, s);
+  }
+  // alpha = v + c / s2
+  PTTK_CUDA(cudaMemcpyAsync(alpha.p, v.p, sizeof(double) * k, cudaMemcpyDeviceToDevice, s));
+  axpy_kernel<<<(k + 255) / 256, 256, 0, s>>>(1.0 / s2, c.p, k, alpha.p); pttk::count_launch();
+  dot_block_kernel<<<1, 1024, 0, s>>>(c.p, alpha.p, k, sc.p + 2); pttk::count_launch();
+  // per parameter: alpha~^T dB alpha~ and tr((B + s2 I)^{-1} dB)
+  //   = sum_i (u_i^T dB u_i)(1/(lambda_i + s2) - 1/s2) + tr(dB) / s2
+  std::vector<double> g_quad(dth), g_tr(dth);
+  for (int j = 0; j < dth; ++j) {
+    const double* dBj = dB.p + (size_t)j * k * k;
+    dgemm(false, false, k, 1, k, 1.0, dBj, k, alpha.p, k, 0.0, v.p, k, s);
+    dot_block_kernel<<<1, 1024, 0, s>>>(alpha.p, v.p, k, sc.p + 3); pttk::count_launch();
+    if (m > 0) dgemm(false, false, k, m, k, 1.0, dBj, k, U.p, k, 0.0, Y.p, k, s);
+    coldot_trace_kernel<<<1, 1024, 0, s>>>(U.p, Y.p, k, m, coefd.p, dBj, sc.p + 4); pttk::count_launch();
+    PTTK_CUDA(cudaGetLastError());
+    double h3[3];
+    PTTK_CUDA(cudaMemcpyAsync(h3, sc.p + 3, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    PTTK_CUDA(cudaStreamSynchronize(s));
+    g_quad[j] = h3[0];
+    g_tr[j] = (m > 0 ? h3[1] : 0.0) + h3[2] / s2;
+  }
+  double cq = 0.0;
+  PTTK_CUDA(cudaMemcpyAsync(&cq, sc.p + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  // y^T (K~ + s2 I)^{-1} y = c^T alpha~ + (||y||^2 - ||c||^2) / s2
+  const double quad = cq + (yy_cc[0] - yy_cc[1]) / s2;
+  *lml = -0.5 * quad - 0.5 * logdet - 0.5 * (double)N * std::log(2.0 * 3.141592653589793);
+  if (grad)
+    for (int j = 0; j < dth; ++j) grad[j] = 0.5 * (g_quad[j] - g_tr[j]);
+  return PTTK_OK;
+}
 
 }  // extern "C"

@@ -85,6 +85,13 @@ SIGNATURES = [
     ("pttk_fixed_get_core", _int, [_vp, _int, _c_double_p]),
     ("pttk_fixed_theta_core", _int, [_vp, _c_double_p, _int, _vp, _vp]),
     ("pttk_fixed_free", None, [_vp]),
+    ("pttk_gp_kv", _int, [_int, _int, _vp, _i64, _c_double_p, ctypes.c_double, _vp, _vp, _vp]),
+    ("pttk_gp_pcg", _int, [_int, _int, _vp, _i64, _c_double_p, ctypes.c_double, _vp, _vp, _int, _vp, _vp,
+                           ctypes.c_double, _int, _c_int_p, _c_double_p, _vp]),
+    ("pttk_gp_lml", _int, [_vp, _c_double_p, ctypes.c_double, _vp, _c_double_p, _c_double_p, _vp]),
+    ("pttk_cross_build", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int, ctypes.c_double,
+                                ctypes.c_uint64, _int, _int, _int, _vp, ctypes.POINTER(_vp), _c_int_p,
+                                ctypes.POINTER(_i64)]),
 ]
 
 _lib = None
@@ -218,6 +225,18 @@ class TT:
                                           dtheta, _dbl(_boxflat(theta_box)), n, tol, _ptr(C), prec,
                                           _stream(stream), ctypes.byref(h)))
         return cls(h.value)
+
+    @classmethod
+    def cross(cls, kernel: int, d: int, src_box, tgt_box, dtheta: int, theta_box, n: int, eps: float, key: int,
+              max_sweeps: int = 60, n_check: int = 1000, init_it: int = 10, stream=None):
+        """pttk_cross_build (TT greedy-cross, Algorithms 5-7): (TT, sweeps, kernel evaluations)."""
+        h = _vp()
+        sw, ev = _int(), _i64()
+        _check(load().pttk_cross_build(kernel, d, _dbl(_boxflat(src_box)), _dbl(_boxflat(tgt_box)), dtheta,
+                                       _dbl(_boxflat(theta_box)), n, float(eps), int(key) & ((1 << 64) - 1),
+                                       int(max_sweeps), int(n_check), int(init_it), _stream(stream), ctypes.byref(h),
+                                       ctypes.byref(sw), ctypes.byref(ev)))
+        return cls(h.value), sw.value, ev.value
 
     @classmethod
     def from_cores(cls, kernel: int, d: int, src_box, tgt_box, dtheta: int, theta_box, n: int, cores) -> "TT":
@@ -610,6 +629,59 @@ class Fixed:
             self.free()
         except Exception:
             pass
+
+
+def _f64_points(X):
+    import torch
+    if X.dtype != torch.float64 or X.dim() != 2:
+        raise ValueError("points must be an (N, d) float64 CUDA tensor")
+
+
+def gp_kv(kernel: int, X, theta, s2: float, v, out=None, stream=None):
+    """pttk_gp_kv: (K(X, X; theta) + s2 I) v, kernel entries evaluated on the fly."""
+    import torch
+    _f64_points(X)
+    if v.dtype != torch.float64 or v.numel() != X.shape[0]:
+        raise ValueError("v must hold N float64 values")
+    if out is None:
+        out = torch.empty_like(v)
+    _check(load().pttk_gp_kv(int(kernel), X.shape[1], _ptr(X), X.shape[0], _dbl(theta), float(s2), _ptr(v),
+                             _ptr(out), _stream(stream)))
+    return out
+
+
+def gp_pcg(kernel: int, X, theta, s2: float, b, Z=None, lam=None, tol: float = 1e-10, maxit: int = 1000,
+           stream=None):
+    """pttk_gp_pcg: (x, iterations, relative residual) for (K + s2 I) x = b, preconditioned by
+    (Z diag(lam) Z^T + s2 I)^{-1} when Z and lam are given."""
+    import torch
+    _f64_points(X)
+    N = X.shape[0]
+    if b.dtype != torch.float64 or b.numel() != N:
+        raise ValueError("b must hold N float64 values")
+    m = 0
+    if Z is not None:
+        m = Z.shape[1]
+        if Z.dtype != torch.float64 or Z.shape[0] != N or lam is None or lam.numel() != m:
+            raise ValueError("Z must be (N, m) float64 with m eigenvalues in lam")
+    x = torch.empty_like(b)
+    it, res = _int(), ctypes.c_double()
+    _check(load().pttk_gp_pcg(int(kernel), X.shape[1], _ptr(X), N, _dbl(theta), float(s2), _ptr(Z) if m else None,
+                              _ptr(lam) if m else None, m, _ptr(b), _ptr(x), float(tol), int(maxit),
+                              ctypes.byref(it), ctypes.byref(res), _stream(stream)))
+    return x, it.value, res.value
+
+
+def gp_lml(g: "Global", theta, s2: float, y, stream=None):
+    """pttk_gp_lml: (log marginal likelihood, gradient in theta) for the low-rank kernel of g."""
+    import torch
+    N = g.dims[0]
+    if y.dtype != torch.float64 or y.numel() != N:
+        raise ValueError("y must hold N float64 values")
+    lml = ctypes.c_double()
+    grad = (ctypes.c_double * 2)()
+    _check(load().pttk_gp_lml(g.handle, _dbl(theta), float(s2), _ptr(y), ctypes.byref(lml), grad, _stream(stream)))
+    return lml.value, np.array(grad[:len(theta)])
 
 
 def apply_noalloc(U, M, V, w, out, stream=None):
