@@ -176,7 +176,7 @@ pttk_status pttk_tt_load(const char* path, pttk_tt** out);
 
 /* A handle from given TT cores (the TT format of Section 2.3): for instance cores computed
  * elsewhere, or cores with chosen ranks for timing the online stage. The problem arguments
- * are those of pttk_grid_coeffs; ranks[0..D] with ranks[0] = ranks[D] = 1; `cores` is host
+ * are those of pttk_grid_coeffs, except that n^D may exceed 4e9 (no grid is formed); ranks[0..D] with ranks[0] = ranks[D] = 1; `cores` is host
  * memory holding the D cores one after another, core k as r_{k-1} x n x r_k doubles,
  * column-major (the layout pttk_tt_get_core returns). The cores must be the Chebyshev
  * coefficient form (contracted with T(xhat), not with nodal values). Copied; the caller

@@ -10,7 +10,7 @@
 //   3. the eigenvectors of T for the selected eigenvalues by inverse iteration (Gaussian
 //      elimination with partial pivoting on T - lambda I), re-orthogonalised by modified
 //      Gram-Schmidt against the earlier vectors of their cluster (eigenvalues closer than
-//      1e-3 ||T||_1, the rule of LAPACK's dstein);
+//      1e-3 of the weight the caller gives them, see sym_eig_vectors);
 //   4. the eigenvectors of A = H times those of T (the reflectors applied in reverse order).
 // The matrices of a batch are independent; every launch covers the whole batch (grid z or a
 // block per matrix), so a batch costs the launches of one matrix. No kernel waits on another
@@ -28,6 +28,21 @@ namespace {
 
 constexpr int EB = 256;        // threads per block
 constexpr int CHUNK = 64;      // columns per partial sum of the symmetric product
+constexpr int SB = 64;         // rows per block of the symmetric product
+
+// 1/x by Newton-Raphson from the hardware approximation (rcp.approx.ftz.f64, good to about
+// 20 bits): each step r <- r + r (1 - x r) squares the relative error, so two steps reach
+// the rounding level (within an ulp or two of the IEEE quotient). Arguments below 1e-290 in magnitude (where the approximation
+// flushes) take the IEEE division.
+__device__ __forceinline__ double rcp_nr(double x) {
+  if (fabs(x) < 1e-290) return 1.0 / x;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double h = fma(-x, r, 1.0);
+  r = fma(r, h, r);
+  h = fma(-x, r, 1.0);
+  return fma(r, h, r);
+}
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -45,16 +60,24 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return sh[0];
 }
 
-// Reflector of step j for matrix blockIdx.x: x = A[j+1:k, j]. Writes v (v_0 = 1) over x,
-// tau[j], the diagonal d[j] = A[j, j] and the off-diagonal e[j] = beta.
-__global__ void __launch_bounds__(EB) reflector_kernel(double* __restrict__ A, int k, int j, double* __restrict__ tau,
-                                                       double* __restrict__ d, double* __restrict__ e) {
+// Step j of the tridiagonalisation, first half, for matrix blockIdx.z. Every block forms the
+// reflector of x = A[j+1:k, j] itself (beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta,
+// v = [1; x_{1:} / (alpha - beta)]) and then the partial products
+//   part[(z * nch + c) * k + i] = sum over the columns l of chunk c (l > j) of A[i, l] v_l
+// for its rows i > j. Block (0, 0) also writes v to vbuf, tau[j], the diagonal d[j] = A[j, j]
+// and the off-diagonal e[j] = beta. Column j keeps x until the second half, which runs after
+// every block of this one has read it.
+__global__ void __launch_bounds__(SB) reflect_symv_kernel(const double* __restrict__ A, int k, int j, int nch,
+                                                          double* __restrict__ part, double* __restrict__ vbuf,
+                                                          double* __restrict__ tau, double* __restrict__ d,
+                                                          double* __restrict__ e) {
   __shared__ double sh[32];
-  double* a = A + (size_t)blockIdx.x * k * k;
-  double* col = a + (size_t)j * k;
-  const int m = k - j - 1;  // length of x
+  __shared__ double vs[CHUNK];
+  const int z = blockIdx.z;
+  const double* a = A + (size_t)z * k * k;
+  const double* col = a + (size_t)j * k;
   double s = 0.0;
-  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += col[j + 1 + i] * col[j + 1 + i];
+  for (int i = j + 2 + threadIdx.x; i < k; i += blockDim.x) s += col[i] * col[i];
   const double xn2 = block_sum(s, sh);
   const double alpha = col[j + 1];
   double t = 0.0, beta = alpha, scale = 0.0;
@@ -63,63 +86,63 @@ __global__ void __launch_bounds__(EB) reflector_kernel(double* __restrict__ A, i
     t = (beta - alpha) / beta;
     scale = 1.0 / (alpha - beta);
   }
-  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) col[j + 1 + i] = xn2 > 0.0 ? col[j + 1 + i] * scale : 0.0;
+  const int l0 = j + 1 + blockIdx.y * CHUNK, l1 = min(k, l0 + CHUNK);
+  for (int l = l0 + threadIdx.x; l < l1; l += blockDim.x)
+    vs[l - l0] = l == j + 1 ? 1.0 : (xn2 > 0.0 ? col[l] * scale : 0.0);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    col[j + 1] = 1.0;
-    tau[(size_t)blockIdx.x * k + j] = t;
-    d[(size_t)blockIdx.x * k + j] = col[j];
-    e[(size_t)blockIdx.x * k + j] = beta;
+  const int i = j + 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) {
+    double acc = 0.0;
+    for (int l = l0; l < l1; ++l) acc = fma(a[(size_t)l * k + i], vs[l - l0], acc);
+    part[((size_t)z * nch + blockIdx.y) * k + i] = acc;
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    for (int l = j + 1 + threadIdx.x; l < k; l += blockDim.x)
+      vbuf[(size_t)z * k + l] = l == j + 1 ? 1.0 : (xn2 > 0.0 ? col[l] * scale : 0.0);
+    if (threadIdx.x == 0) {
+      tau[(size_t)z * k + j] = t;
+      d[(size_t)z * k + j] = col[j];
+      e[(size_t)z * k + j] = beta;
+    }
   }
 }
 
-// part[(z * nch + c) * k + i] = sum over columns l of chunk c (l > j) of A[i, l] v_l, rows i > j
-__global__ void __launch_bounds__(EB) symv_part_kernel(const double* __restrict__ A, int k, int j, int nch,
-                                                       double* __restrict__ part) {
-  const int z = blockIdx.z, c = blockIdx.y;
-  const double* a = A + (size_t)z * k * k;
-  const double* v = a + (size_t)j * k;  // v_l at v[l], l > j
-  const int i = j + 1 + blockIdx.x * blockDim.x + threadIdx.x;
-  const int l0 = j + 1 + c * CHUNK, l1 = min(k, l0 + CHUNK);
-  if (i >= k) return;
-  double acc = 0.0;
-  for (int l = l0; l < l1; ++l) acc = fma(a[(size_t)l * k + i], v[l], acc);
-  part[((size_t)z * nch + c) * k + i] = acc;
-}
-
-// w = p - (tau/2)(p^T v) v with p = tau sum_c part, rows i > j (one block per matrix)
-__global__ void __launch_bounds__(EB) make_w_kernel(const double* __restrict__ A, int k, int j, int nch,
-                                                    const double* __restrict__ part, const double* __restrict__ tau,
-                                                    double* __restrict__ w) {
+// Step j, second half (the two-sided update of dsytd2): every block forms p = tau sum_c part
+// for the rows i > j, p^T v and w = p - (tau/2)(p^T v) v in shared memory (the partial sums in
+// the same order in every block), applies A22 <- A22 - v w^T - w v^T to its columns of
+// A22 = A[j+1:, j+1:] (both triangles), and block 0 stores v over x in column j, where the
+// back-transformation reads it. Dynamic shared memory: 2 (k - 1) doubles.
+__global__ void __launch_bounds__(EB) w_rank2_kernel(double* __restrict__ A, int k, int j, int nch,
+                                                     const double* __restrict__ part,
+                                                     const double* __restrict__ vbuf,
+                                                     const double* __restrict__ tau) {
+  extern __shared__ double wv_smem[];
   __shared__ double sh[32];
-  const int z = blockIdx.x;
-  const double* v = A + (size_t)z * k * k + (size_t)j * k;
+  const int z = blockIdx.z, m = k - j - 1;
+  double* ws = wv_smem;
+  double* vs = wv_smem + m;
+  double* a = A + (size_t)z * k * k;
   const double t = tau[(size_t)z * k + j];
-  double* wz = w + (size_t)z * k;
   double s = 0.0;
-  for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
     double p = 0.0;
-    for (int c = 0; c < nch; ++c) p += part[((size_t)z * nch + c) * k + i];
+    for (int c = 0; c < nch; ++c) p += part[((size_t)z * nch + c) * k + j + 1 + i];
     p *= t;
-    wz[i] = p;
-    s += p * v[i];
+    const double v = vbuf[(size_t)z * k + j + 1 + i];
+    ws[i] = p;
+    vs[i] = v;
+    s += p * v;
   }
   const double pv = block_sum(s, sh);
-  for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) wz[i] -= 0.5 * t * pv * v[i];
-}
-
-// A22 <- A22 - v w^T - w v^T (both triangles), A22 = A[j+1:, j+1:]
-__global__ void __launch_bounds__(EB) rank2_kernel(double* __restrict__ A, int k, int j, const double* __restrict__ w) {
-  const int z = blockIdx.z;
-  double* a = A + (size_t)z * k * k;
-  const double* v = a + (size_t)j * k;
-  const double* wz = w + (size_t)z * k;
-  const int m = k - j - 1;
-  const int64_t total = (int64_t)m * m;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int i = j + 1 + (int)(q % m), l = j + 1 + (int)(q / m);
-    a[(size_t)l * k + i] -= v[i] * wz[l] + wz[i] * v[l];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ws[i] -= 0.5 * t * pv * vs[i];
+  __syncthreads();
+  for (int l = blockIdx.x; l < m; l += gridDim.x) {
+    double* cl = a + (size_t)(j + 1 + l) * k + j + 1;
+    const double vl = vs[l], wl = ws[l];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) cl[i] -= vs[i] * wl + ws[i] * vl;
   }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) a[(size_t)j * k + j + 1 + i] = vs[i];
 }
 
 // the last 2 x 2 block: d[k-2], d[k-1], e[k-2]
@@ -143,19 +166,30 @@ __device__ int sturm_count(const double* d, const double* e, int k, double x, do
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < 0.0) ++cnt;
   for (int i = 1; i < k; ++i) {
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    q = (d[i] - x) - e[i - 1] * e[i - 1] * rcp_nr(q);
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0.0) ++cnt;
   }
   return cnt;
 }
 
-// lam[z * k + i] = the i-th smallest eigenvalue of T_z, by bisection from Gershgorin bounds
-__global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ d, const double* __restrict__ e, int k,
-                                                     int nb, double* __restrict__ lam) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)k * nb) return;
-  const int z = (int)(q / k), i = (int)(q % k);
+// lam[z * k + i] = the i-th smallest eigenvalue of T_z, by multisection of the Gershgorin
+// interval: a group of L lanes (L a power of two up to 32, the lanes of one warp) works on one
+// eigenvalue, lane j counting the eigenvalues below the point x_j = lo + (j + 1)(hi - lo)/(L + 1);
+// the first point whose count exceeds i becomes hi and the point before it lo (bisection for
+// L = 1). Every lane of the group computes the same lo and hi. The matrix's own rounding
+// leaves every eigenvalue an absolute uncertainty of order eps ||T||, so the search stops
+// at an interval of 4 eps ||T||.
+__global__ void __launch_bounds__(32) multisect_kernel(const double* __restrict__ d, const double* __restrict__ e,
+                                                       int k, int nb, int L, double* __restrict__ lam) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)k * nb;
+  const int64_t q = gtid / L;
+  const int lane = threadIdx.x & 31, j = lane & (L - 1);
+  // the whole group takes the same q: groups past the end work on the last eigenvalue and
+  // write nothing, so that every lane of a warp takes part in the ballots
+  const int64_t qq = q < total ? q : total - 1;
+  const int z = (int)(qq / k), i = (int)(qq % k);
   const double* dz = d + (size_t)z * k;
   const double* ez = e + (size_t)z * k;
   double lo = dz[0], hi = dz[0], emax2 = 0.0;
@@ -169,38 +203,50 @@ __global__ void __launch_bounds__(128) bisect_kernel(const double* __restrict__ 
   const double pivmin = fmax(2.2250738585072014e-308 * fmax(emax2, 1.0), 1e-300);
   lo -= 2.0 * 2.2204460492503131e-16 * tnorm + pivmin;
   hi += 2.0 * 2.2204460492503131e-16 * tnorm + pivmin;
+  const double tol = 4.0 * 2.2204460492503131e-16 * tnorm + pivmin;
+  const unsigned gmask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (lane & ~(L - 1)));
   for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (hi - lo <= 2.0 * 2.2204460492503131e-16 * fmax(fabs(lo), fabs(hi)) + pivmin) break;
-    if (sturm_count(dz, ez, k, mid, pivmin) > i) hi = mid;
-    else lo = mid;
+    if (hi - lo <= tol) break;
+    const double step = (hi - lo) / (double)(L + 1);
+    const double x0 = lo + step, xl = lo + (double)L * step;
+    if (x0 <= lo || xl >= hi) break;
+    const double x = lo + (double)(j + 1) * step;
+    const bool above = sturm_count(dz, ez, k, x, pivmin) > i;
+    unsigned bits = __ballot_sync(gmask, above) & gmask;
+    bits >>= (lane & ~(L - 1));
+    const int f = bits ? __ffs(bits) - 1 : L;  // first point whose count exceeds i
+    const double nlo = f == 0 ? lo : lo + (double)f * step;
+    const double nhi = f == L ? hi : lo + (double)(f + 1) * step;
+    lo = nlo;
+    hi = nhi;
   }
-  lam[q] = 0.5 * (lo + hi);
+  if (q < total && j == 0) lam[q] = 0.5 * (lo + hi);
 }
 
 // Inverse iteration for the selected eigenvalues. One block per cluster: sel[c0 .. c1) of
 // (matrix, eigenvalue) entries listed in `job` (start, count) per cluster; the eigenvalues of a
 // cluster belong to one matrix and are processed in order. Thread 0 solves (T - lambda I) y = x
-// by Gaussian elimination with partial pivoting (a tridiagonal LU, fill-in one super-diagonal);
-// the block normalises and re-orthogonalises y against the cluster's earlier vectors.
-// Vectors go to V[z] columns vcol (k x ncols per matrix, column-major). work: 6 k doubles per
-// block.
+// by Gaussian elimination with partial pivoting (a tridiagonal LU, fill-in one super-diagonal,
+// the reciprocals of the pivots kept); the block normalises and re-orthogonalises y against the
+// cluster's earlier vectors. Vectors go to V[z] columns vcol (k x ncols per matrix,
+// column-major). The factors and y (5 k doubles and k pivot flags) sit in dynamic shared memory
+// when `in_smem`, else in work (6 k doubles per block).
 __global__ void __launch_bounds__(EB) inverse_iteration_kernel(const double* __restrict__ d, const double* __restrict__ e,
                                                                int k, const int* __restrict__ job,
                                                                const int* __restrict__ sel_z,
                                                                const double* __restrict__ sel_lam,
                                                                const int* __restrict__ sel_col, double* V, int ncols,
-                                                               double* work) {
+                                                               double* work, int in_smem) {
+  extern __shared__ double ii_smem[];
   __shared__ double sh[32];
   const int c0 = job[2 * blockIdx.x], cn = job[2 * blockIdx.x + 1];
-  double* wk = work + (size_t)blockIdx.x * 6 * k;
-  double* dl = wk;          // multipliers
-  double* du = wk + k;      // upper factor: diagonal
-  double* du1 = wk + 2 * k; // first super-diagonal
-  double* du2 = wk + 3 * k; // second super-diagonal (fill-in)
-  int* piv = reinterpret_cast<int*>(wk + 4 * k);
-  double* y = wk + 5 * k;
+  double* wk = in_smem ? ii_smem : work + (size_t)blockIdx.x * 6 * k;
+  double* dl = wk;           // multipliers
+  double* rdu = wk + k;      // reciprocals of the upper factor's diagonal
+  double* du1 = wk + 2 * k;  // first super-diagonal
+  double* du2 = wk + 3 * k;  // second super-diagonal (fill-in)
+  double* y = wk + 4 * k;
+  unsigned char* piv = reinterpret_cast<unsigned char*>(wk + 5 * k);
   const int z = sel_z[c0];
   const double* dz = d + (size_t)z * k;
   const double* ez = e + (size_t)z * k;
@@ -219,19 +265,19 @@ __global__ void __launch_bounds__(EB) inverse_iteration_kernel(const double* __r
         const double c = ez[r], dn = dz[r + 1] - lambda, en = r + 1 < k - 1 ? ez[r + 1] : 0.0;
         if (fabs(a) >= fabs(c)) {
           if (fabs(a) < tiny) a = tiny;
-          const double m = c / a;
+          const double ra = rcp_nr(a), m = c * ra;
           dl[r] = m;
           piv[r] = 0;
-          du[r] = a;
+          rdu[r] = ra;
           du1[r] = b;
           du2[r] = 0.0;
           a = dn - m * b;
           b = en;
         } else {
-          const double m = a / c;
+          const double rc = rcp_nr(c), m = a * rc;
           dl[r] = m;
           piv[r] = 1;
-          du[r] = c;
+          rdu[r] = rc;
           du1[r] = dn;
           du2[r] = en;
           a = b - m * dn;
@@ -239,7 +285,7 @@ __global__ void __launch_bounds__(EB) inverse_iteration_kernel(const double* __r
         }
       }
       if (fabs(a) < tiny) a = tiny;
-      du[k - 1] = a;
+      rdu[k - 1] = rcp_nr(a);
     }
     // start vector: a fixed, non-degenerate one
     for (int r = threadIdx.x; r < k; r += blockDim.x) y[r] = 1.0 + 0.3 * sin(1.7 * (r + 1) + 0.37 * (q - c0 + 1));
@@ -261,13 +307,12 @@ __global__ void __launch_bounds__(EB) inverse_iteration_kernel(const double* __r
             cur = nxt - dl[r] * cur;
           }
         }
-        y[k - 1] = cur;
         // back substitution with the upper factor (diagonal, two super-diagonals); x1, x2 are
         // the solution entries r + 1 and r + 2
-        double x1 = cur / du[k - 1], x2 = 0.0;
+        double x1 = cur * rdu[k - 1], x2 = 0.0;
         y[k - 1] = x1;
         for (int r = k - 2; r >= 0; --r) {
-          const double x0 = (y[r] - du1[r] * x1 - du2[r] * x2) / du[r];
+          const double x0 = (y[r] - du1[r] * x1 - du2[r] * x2) * rdu[r];
           y[r] = x0;
           x2 = x1;
           x1 = x0;
@@ -324,47 +369,69 @@ __global__ void __launch_bounds__(EB) back_transform_kernel(const double* __rest
 pttk_status sym_eig_values(double* A, int k, int nb, double* d, double* e, double* tau, double* lam, cudaStream_t s) {
   if (k < 1 || nb < 1) return set_error(PTTK_EINVAL, "empty eigenproblem");
   if (k >= 3) {
+    const size_t wv_bytes = sizeof(double) * 2 * (size_t)(k - 1);
+    if (wv_bytes > 200 * 1024) return set_error(PTTK_ENOTSUP, "eigenproblem larger than 12800 x 12800");
+    if (wv_bytes > 48 * 1024)
+      PTTK_CUDA(cudaFuncSetAttribute(w_rank2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wv_bytes));
     const int nch_max = (k + CHUNK - 1) / CHUNK;
-    double *part = nullptr, *w = nullptr;
+    double *part = nullptr, *vbuf = nullptr;
     PTTK_CUDA(cudaMallocAsync(&part, sizeof(double) * (size_t)nb * nch_max * k, s));
-    PTTK_CUDA(cudaMallocAsync(&w, sizeof(double) * (size_t)nb * k, s));
+    PTTK_CUDA(cudaMallocAsync(&vbuf, sizeof(double) * (size_t)nb * k, s));
+    PTTK_PROF("eig_tridiag", s);
+    const int gmax = std::max(1, 2 * sm_count() / nb);
     for (int j = 0; j < k - 2; ++j) {
       const int m = k - j - 1, nch = (m + CHUNK - 1) / CHUNK;
-      reflector_kernel<<<nb, EB, 0, s>>>(A, k, j, tau, d, e); pttk::count_launch();
-      symv_part_kernel<<<dim3((unsigned)((m + EB - 1) / EB), (unsigned)nch, (unsigned)nb), EB, 0, s>>>(A, k, j, nch, part); pttk::count_launch();
-      make_w_kernel<<<nb, EB, 0, s>>>(A, k, j, nch, part, tau, w); pttk::count_launch();
-      const int64_t cells = (int64_t)m * m;
-      const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((cells + EB - 1) / EB, (int64_t)sm_count() * 4 / std::max(nb, 1) + 1));
-      rank2_kernel<<<dim3(gx, 1, (unsigned)nb), EB, 0, s>>>(A, k, j, w); pttk::count_launch();
+      reflect_symv_kernel<<<dim3((unsigned)((m + SB - 1) / SB), (unsigned)nch, (unsigned)nb), SB, 0, s>>>(
+          A, k, j, nch, part, vbuf, tau, d, e);
+      pttk::count_launch();
+      w_rank2_kernel<<<dim3((unsigned)std::min(m, gmax), 1, (unsigned)nb), EB, sizeof(double) * 2 * (size_t)m, s>>>(
+          A, k, j, nch, part, vbuf, tau);
+      pttk::count_launch();
     }
     cudaFreeAsync(part, s);
-    cudaFreeAsync(w, s);
+    cudaFreeAsync(vbuf, s);
   }
   tail_kernel<<<nb, 32, 0, s>>>(A, k, d, e); pttk::count_launch();
-  const int64_t nt = (int64_t)k * nb;
-  bisect_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(d, e, k, nb, lam); pttk::count_launch();
+  {
+    // lanes per eigenvalue: the most (up to 32) that keep about one warp per SM, the FP64
+    // pipe being the limit of the Sturm counts
+    const int64_t nt = (int64_t)k * nb;
+    int L = 1;
+    while (L < 32 && (nt * 2 * L + 31) / 32 <= sm_count()) L *= 2;
+    const int64_t threads = nt * L;
+    PTTK_PROF("eig_bisect", s);
+    multisect_kernel<<<(unsigned)((threads + 31) / 32), 32, 0, s>>>(d, e, k, nb, L, lam); pttk::count_launch();
+  }
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
 }
 
 // Eigenvectors of the matrices tridiagonalised by sym_eig_values for selected eigenvalues:
-// selection q has matrix sel_z[q], eigenvalue sel_lam[q] and output column sel_col[q] of V
-// (nb x k x ncols, column-major per matrix). Selections of one matrix must be listed in
-// ascending order of eigenvalue. Host arrays; synchronises `s`.
+// selection q has matrix sel_z[q], eigenvalue sel_lam[q], weight sel_w[q] and output column
+// sel_col[q] of V (nb x k x ncols, column-major per matrix). Selections of one matrix must be
+// listed in ascending order of eigenvalue. Host arrays; synchronises `s`.
+//
+// Clusters. Inverse iteration gives each vector as an eigenvector of its own perturbation
+// T + E_q, ||E_q|| ~ eps ||T||, so two vectors carry components of about eps ||T|| / gap along
+// each other. In a spectral function sum f(lambda_q) u_q u_q^T such a pair is off by about
+// |f| eps ||T|| / gap. Re-orthogonalising the pairs whose gap is below 1e-3 max(|f|) (LAPACK's
+// dstein uses 1e-3 ||T|| for every pair) keeps that below 1e3 eps ||T|| per pair, while
+// eigenvalues that are small against ||T|| (the numerically low-rank tail, dense in absolute
+// terms) stay in clusters of their own and run in parallel.
 pttk_status sym_eig_vectors(const double* A, const double* d, const double* e, const double* tau, int k, int nb,
                             const std::vector<int>& sel_z, const std::vector<double>& sel_lam,
-                            const std::vector<int>& sel_col, double* V, int ncols, cudaStream_t s) {
+                            const std::vector<double>& sel_w, const std::vector<int>& sel_col, double* V,
+                            int ncols, cudaStream_t s) {
   const int nsel = (int)sel_z.size();
   if (nsel == 0) return PTTK_OK;
-  // clusters: consecutive selections of one matrix whose eigenvalues are closer than
-  // 1e-3 ||T||_1 (estimated here by the largest |eigenvalue| of that matrix's selections)
-  std::vector<double> scale(nb, 0.0);
-  for (int q = 0; q < nsel; ++q) scale[sel_z[q]] = std::max(scale[sel_z[q]], std::fabs(sel_lam[q]));
+  if ((int)sel_lam.size() != nsel || (int)sel_w.size() != nsel || (int)sel_col.size() != nsel)
+    return set_error(PTTK_EINVAL, "eigenvector selection arrays of different lengths");
+  // clusters: consecutive selections of one matrix closer than 1e-3 of the larger weight
   std::vector<int> job;
   int start = 0;
   for (int q = 1; q <= nsel; ++q) {
     const bool brk = q == nsel || sel_z[q] != sel_z[q - 1] ||
-                     std::fabs(sel_lam[q] - sel_lam[q - 1]) > 1e-3 * scale[sel_z[q]];
+                     std::fabs(sel_lam[q] - sel_lam[q - 1]) > 1e-3 * std::max(sel_w[q], sel_w[q - 1]);
     if (brk) {
       job.push_back(start);
       job.push_back(q - start);
@@ -378,12 +445,19 @@ pttk_status sym_eig_vectors(const double* A, const double* d, const double* e, c
   PTTK_CUDA(cudaMallocAsync(&dz, sizeof(int) * nsel, s));
   PTTK_CUDA(cudaMallocAsync(&dcol, sizeof(int) * nsel, s));
   PTTK_CUDA(cudaMallocAsync(&dlam, sizeof(double) * nsel, s));
-  PTTK_CUDA(cudaMallocAsync(&work, sizeof(double) * 6 * (size_t)k * nclus, s));
+  // factors in shared memory up to k = 4900 (5 k doubles + k flags); beyond, in global memory
+  const size_t ii_bytes = sizeof(double) * 5 * (size_t)k + (size_t)k;
+  const int in_smem = ii_bytes <= 200 * 1024;
+  if (in_smem && ii_bytes > 48 * 1024)
+    PTTK_CUDA(cudaFuncSetAttribute(inverse_iteration_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ii_bytes));
+  PTTK_CUDA(cudaMallocAsync(&work, in_smem ? sizeof(double) : sizeof(double) * 6 * (size_t)k * nclus, s));
   PTTK_CUDA(cudaMemcpyAsync(djob, job.data(), sizeof(int) * job.size(), cudaMemcpyHostToDevice, s));
   PTTK_CUDA(cudaMemcpyAsync(dz, sel_z.data(), sizeof(int) * nsel, cudaMemcpyHostToDevice, s));
   PTTK_CUDA(cudaMemcpyAsync(dcol, sel_col.data(), sizeof(int) * nsel, cudaMemcpyHostToDevice, s));
   PTTK_CUDA(cudaMemcpyAsync(dlam, sel_lam.data(), sizeof(double) * nsel, cudaMemcpyHostToDevice, s));
-  inverse_iteration_kernel<<<nclus, EB, 0, s>>>(d, e, k, djob, dz, dlam, dcol, V, ncols, work); pttk::count_launch();
+  inverse_iteration_kernel<<<nclus, EB, in_smem ? ii_bytes : 0, s>>>(d, e, k, djob, dz, dlam, dcol, V, ncols, work,
+                                                                     in_smem);
+  pttk::count_launch();
   back_transform_kernel<<<dim3((unsigned)ncols, (unsigned)nb), EB, 0, s>>>(A, tau, k, V, ncols); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
   PTTK_CUDA(cudaStreamSynchronize(s));

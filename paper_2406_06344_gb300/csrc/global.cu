@@ -307,13 +307,17 @@ static pttk_status global_online_run(const pttk_global* g, const double* th, dou
     std::iota(asc.begin(), asc.end(), 0);
     std::stable_sort(asc.begin(), asc.end(), [&](int a, int b) { return lam[idx[a]] < lam[idx[b]]; });
     std::vector<int> sz(m, 0), scol(m);
-    std::vector<double> slam(m);
+    std::vector<double> slam(m), sw(m);
     for (int q = 0; q < m; ++q) {
       slam[q] = lam[idx[asc[q]]];
+      // Global-1 needs W = sum lambda u u^T (weight |lambda|); Global-2 hands out Z = Q U^,
+      // whose columns must be orthonormal to working accuracy (weight max |lambda|, LAPACK's
+      // absolute rule, over its m leading pairs only)
+      sw[q] = compress ? lmax : std::fabs(slam[q]);
       scol[q] = asc[q];
     }
-    PTTK_PROF("global_eig", s);
-    PTTK_TRY(sym_eig_vectors(B.p, dd.p, ee.p, dtau.p, k, 1, sz, slam, scol, Un.p, m, s));
+    PTTK_PROF("global_eigvec", s);
+    PTTK_TRY(sym_eig_vectors(B.p, dd.p, ee.p, dtau.p, k, 1, sz, slam, sw, scol, Un.p, m, s));
   }
   std::vector<double> lk(m);
   for (int q = 0; q < m; ++q) lk[q] = lam[kept[q]];
@@ -594,13 +598,16 @@ pttk_status pttk_gp_lml(const pttk_global* g, const double* theta, double s2, co
   // entering only through the 1/s2 terms below
   const double res = 64.0 * 2.2204460492503131e-16 * lmax;
   std::vector<int> sz, scol;
-  std::vector<double> slam, coef;
+  std::vector<double> slam, coef, sw;
   for (int i = 0; i < k; ++i)
     if (std::fabs(lam[i]) > res) {
       sz.push_back(0);
       scol.push_back((int)slam.size());
       slam.push_back(lam[i]);
       coef.push_back(1.0 / (lam[i] + s2) - 1.0 / s2);
+      // the spectral function here is coef(lambda) = -lambda / (s2 (lambda + s2)); its weight on
+      // the scale of lambda is |coef| s2^2 = |lambda| s2 / (lambda + s2), about min(|lambda|, s2)
+      sw.push_back(std::fabs(lam[i]) * s2 / (lam[i] + s2));
     }
   const int m = (int)slam.size();
   DevBuf U, Y, w, alpha, coefd, v;
@@ -611,8 +618,8 @@ pttk_status pttk_gp_lml(const pttk_global* g, const double* theta, double s2, co
   PTTK_TRY(coefd.alloc(std::max(m, 1)));
   PTTK_TRY(v.alloc(k));
   if (m > 0) {
-    PTTK_PROF("global_eig", s);
-    PTTK_TRY(sym_eig_vectors(Bw.p, dd.p, ee.p, tau.p, k, 1, sz, slam, scol, U.p, m, s));
+    PTTK_PROF("global_eigvec", s);
+    PTTK_TRY(sym_eig_vectors(Bw.p, dd.p, ee.p, tau.p, k, 1, sz, slam, sw, scol, U.p, m, s));
     PTTK_CUDA(cudaMemcpyAsync(coefd.p, coef.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
   }
   // alpha~ = (B + s2 I)^{-1} c = U ((1/(lambda + s2) - 1/s2) .* (U^T c)) + c / s2

@@ -143,11 +143,15 @@ int oriented_core_dims(const pttk_tt* tt, bool source, int step, int* R_in, int*
 // Symmetric eigendecomposition of nb k x k matrices (eig.cu): sym_eig_values tridiagonalises
 // A in place and returns all eigenvalues ascending (lam: nb x k) with d, e, tau for
 // sym_eig_vectors, which computes the eigenvectors of the selected eigenvalues (listed per
-// matrix in ascending order) into columns sel_col of V (nb x k x ncols). Device buffers.
+// matrix in ascending order) into columns sel_col of V (nb x k x ncols). sel_w: the weight
+// |f(lambda)| each eigenpair carries in the caller's spectral function f(A) = sum f u u^T
+// (|lambda| for A itself); vectors are re-orthogonalised where two eigenvalues lie within
+// 1e-3 of the larger weight. Device buffers.
 pttk_status sym_eig_values(double* A, int k, int nb, double* d, double* e, double* tau, double* lam, cudaStream_t s);
 pttk_status sym_eig_vectors(const double* A, const double* d, const double* e, const double* tau, int k, int nb,
                             const std::vector<int>& sel_z, const std::vector<double>& sel_lam,
-                            const std::vector<int>& sel_col, double* V, int ncols, cudaStream_t s);
+                            const std::vector<double>& sel_w, const std::vector<int>& sel_col, double* V,
+                            int ncols, cudaStream_t s);
 // One pass over N points (N x d row-major, double if fp64 else float) of the source (or
 // target) side: records PTTK_EDOMAIN in *status if a coordinate lies outside its box.
 pttk_status point_domain_check(const pttk_tt* tt, bool source, const void* P, int64_t N, bool fp64, int* status,
