@@ -460,6 +460,105 @@ def online_only(args):
                       "ms_per_build": a.elapsed_time(b) / args.online_only, "ranks": ranks}), flush=True)
 
 
+def gp_leg(torch, P, W, g, Xg, ev):
+    """The Gaussian-process workload on the PTTK-Global handle of the SE kernel (N = 1e5, d = 3):
+    log marginal likelihood and its theta gradient per call, ten steps of gradient ascent on the
+    length scale from l = 0.5 (the hyperparameter loop), and CG on (K + s2 I) x = b with exact
+    on-the-fly K v, plain and preconditioned by PTTK-Global-2's Z W Z^T (Woodbury)."""
+    rng = np.random.default_rng(W.SEED_SUB + 11)
+    N = Xg.shape[0]
+    y = torch.tensor(rng.standard_normal(N), device="cuda")
+    s2 = 1.0
+    th = 0.5
+    P.gp_lml(g, (th,), s2, y)
+    hist = []
+    a = ev()
+    for _ in range(10):
+        lml, grad = P.gp_lml(g, (th,), s2, y)
+        hist.append((th, lml))
+        th = float(np.clip(th + 0.05 * np.sign(grad[0]) * min(1.0, abs(grad[0]) / (abs(grad[0]) + 1.0)),
+                           0.2 * math.sqrt(3) + 1e-6, math.sqrt(3) - 1e-6))
+    b = ev()
+    torch.cuda.synchronize()
+    out = {"N": N, "s2": s2, "lml_and_grad_ms": a.elapsed_time(b) / 10, "ascent_steps": 10,
+           "lml_first_last": [hist[0][1], hist[-1][1]], "theta_first_last": [hist[0][0], hist[-1][0]]}
+    # CG with and without the Global-2 preconditioner on a 5,000-point subset (K v exact, O(N^2))
+    n_cg = 5000
+    Xc = Xg[:n_cg].contiguous()
+    tt = None
+    box = ((0.0, 1.0),) * 3
+    Db = math.sqrt(3.0)
+    ttc = P.TT.build_offline(W.GAUSS, 3, box, box, 1, ((0.2 * Db, Db),), 12, 1e-5, "fp64")
+    gc = P.Global(ttc, Xc)
+    ttc.free()
+    Z, Wm = gc.instantiate((0.8,), 1e-6, compress=True)
+    lam = torch.diagonal(Wm).contiguous()
+    bb = torch.tensor(rng.standard_normal(n_cg), device="cuda")
+    for s2c in (1e-2, 1e-3):
+        a = ev()
+        _, it_p, res_p = P.gp_pcg(W.GAUSS, Xc, (0.8,), s2c, bb, Z, lam, tol=1e-8)
+        b = ev()
+        torch.cuda.synchronize()
+        t_p = a.elapsed_time(b)
+        a = ev()
+        _, it_0, res_0 = P.gp_pcg(W.GAUSS, Xc, (0.8,), s2c, bb, tol=1e-8, maxit=5000)
+        b = ev()
+        torch.cuda.synchronize()
+        out[f"cg_s2_{s2c:g}"] = {"N": n_cg, "preconditioned": {"iters": it_p, "ms": t_p, "resid": res_p},
+                                 "plain": {"iters": it_0, "ms": a.elapsed_time(b), "resid": res_0},
+                                 "precond_rank": int(Z.shape[1])}
+    gc.free()
+    return out
+
+
+def fixed_leg(torch, P, W, ev):
+    """Algorithm 2 Phases 3-4 for fixed point sets (the d = 2 Matern-3/2 workload's TT, N_s =
+    N_t = 200k): the FP64 factors S = U(X), T = V(Y), the TT-Round of the twisted TT at 1e-8, and
+    then H'(theta) per parameter value on the rounded cores."""
+    w = W.WORKLOADS["c2"]
+    tt = P.TT.build_offline(w.kernel, w.d, w.src_box, w.tgt_box, w.dtheta, w.theta_box, w.n, w.tol, "fp64")
+    X = torch.tensor(W.sources(w), device="cuda")
+    Y = torch.tensor(W.targets(w), device="cuda")
+    a = ev()
+    f = P.Fixed(tt, X, Y, 1e-8)
+    b = ev()
+    torch.cuda.synchronize()
+    create_ms = a.elapsed_time(b)
+    ths = W.thetas(w, 16)
+    f.theta_core(ths[0])
+    a = ev()
+    for th in ths:
+        f.theta_core(th)
+    b = ev()
+    torch.cuda.synchronize()
+    Ns, Nt, dth, r = f.dims
+    out = {"workload": f"d = 2 Matern-3/2, n = {w.n}, N_s = N_t = {Ns}", "tt_ranks": tt.ranks,
+           "rounded_outer_ranks": [r[0], r[dth]], "create_ms": create_ms,
+           "theta_core_ms": a.elapsed_time(b) / len(ths)}
+    f.free()
+    tt.free()
+    return out
+
+
+def cross_leg(torch, P, W, ev):
+    """TT greedy-cross (Algorithms 5-7) on the GPU: the c1 and c2 workloads and the d = 3
+    general-nu Matern grid at the paper's n = 27 (D = 8: 2.8e11 entries, 2.2 TB in FP64, which
+    no device holds), with the kernel entries it evaluated."""
+    import dataclasses
+    out = {}
+    for name, n, eps in (("c1", 16, 1e-10), ("c2", 20, 1e-8), ("c3", 27, 1e-4)):
+        w = dataclasses.replace(W.WORKLOADS[name], n=n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tt, sweeps, evals = P.TT.cross(w.kernel, w.d, w.src_box, w.tgt_box, w.dtheta, w.theta_box, w.n, eps, 2024,
+                                       max_sweeps=30, n_check=500)
+        torch.cuda.synchronize()
+        out[name] = {"n": n, "eps": eps, "seconds": time.perf_counter() - t0, "sweeps": sweeps, "evals": evals,
+                     "grid_entries": float(n) ** w.D, "ranks": tt.ranks}
+        tt.free()
+    return out
+
+
 def run_extras(torch, P, W, w, tt, X32, Y32, wv, thetas, state, flush, ev, pk, hbm, bf16_sus):
     """Per-form build rates and errors, the batched and adjoint rows, and end to end.
 
@@ -735,9 +834,30 @@ def run_extras(torch, P, W, w, tt, X32, Y32, wv, thetas, state, flush, ev, pk, h
                 Kd = torch.exp(-q) if kid == W.GAUSS else torch.sqrt(1.0 + q)
                 errs.append(float(torch.linalg.norm(Kd - Kt) / torch.linalg.norm(Kd)))
             rec[name] = {"online_ms": float(np.mean(ms)), "rank": float(np.mean(rk)), "error": float(np.mean(errs))}
-        g.free()
+        if kid == W.GAUSS:
+            # Global-1 batched over the same 8 theta: one eigensolver pass for all of them
+            g.instantiate_batched(gthetas[:, None])
+            a = ev()
+            Wb = g.instantiate_batched(gthetas[:, None])
+            b = ev()
+            torch.cuda.synchronize()
+            Qi = g.Q()[Ig]
+            errs = []
+            for j, th in enumerate(gthetas):
+                Kt = Qi @ Wb[j] @ Qi.T
+                Kd = torch.exp(-(Rg / float(th)) ** 2)
+                errs.append(float(torch.linalg.norm(Kd - Kt) / torch.linalg.norm(Kd)))
+            rec["global1_batched"] = {"online_ms_per_theta": a.elapsed_time(b) / len(gthetas),
+                                      "batch": len(gthetas), "error": float(np.mean(errs))}
+            gp_g = g
+        else:
+            g.free()
         glob[W.KERNEL_NAMES[kid]] = rec
     out["global"] = glob
+    out["gp"] = gp_leg(torch, P, W, gp_g, Xg, ev)
+    gp_g.free()
+    out["fixed_phase34"] = fixed_leg(torch, P, W, ev)
+    out["cross"] = cross_leg(torch, P, W, ev)
 
     # end to end through the public API: pinned host inputs copied in, one device->host read
     # of the apply result per build

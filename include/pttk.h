@@ -243,11 +243,23 @@ pttk_status pttk_global_get_r(const pttk_global* g, double* R_host);
  *     ||Z W Z^T - S H T^T||_F <= eps ||S H T^T||_F, or all of them when no prefix meets it.
  *     Z (dev, N x rank, row-major; capacity N x k) = Q U^.
  *     W (dev, rank x rank; capacity k x k) = diag(lambda^). *rank = the terms kept.
+ * Eigenpairs whose eigenvalue lies within 64 eps max|lambda| of zero are below what FP64
+ * resolves and give no term. The eigensolver: Householder tridiagonalisation, every eigenvalue
+ * by multisection on Sturm counts, inverse iteration for the eigenvectors kept, back through
+ * the reflectors (no step waits on another CTA).
  * eps in [0, 1). FP64 throughout. Synchronises `stream`.
- * Errors: PTTK_EINVAL, PTTK_EDOMAIN, PTTK_ENOMEM, PTTK_ECUDA, PTTK_ETIMEOUT (a bounded grid
- * barrier of the Jacobi eigensolver ran out). */
+ * Errors: PTTK_EINVAL, PTTK_EDOMAIN, PTTK_ENOMEM, PTTK_ECUDA, PTTK_ENOTSUP (k > 12800). */
 pttk_status pttk_global_instantiate(const pttk_global* g, const double* theta, double eps, int compress,
                                     int definite, double* Z, double* W, int* rank, void* stream);
+
+/* PTTK-Global-1 (compress = 0 of pttk_global_instantiate) for B parameter values at once:
+ * thetas (host, B x d_theta, row b = theta_b, each inside its box, else PTTK_EDOMAIN); W (dev,
+ * B x k x k doubles, matrix b column-major at offset b k^2) = U_b Lambda_b U_b^T, the same
+ * selection of eigenpairs as the single-theta call. The B eigenproblems share every launch of
+ * the eigensolver, so the launch-bound tridiagonalisation costs about what one theta costs.
+ * B = 0 is a no-op. Synchronises `stream`. Errors: as pttk_global_instantiate. */
+pttk_status pttk_global_instantiate_batched(const pttk_global* g, int B, const double* thetas, int definite,
+                                            double* W, void* stream);
 
 /* Release a handle and its device memory (NULL is a no-op). */
 void pttk_global_free(pttk_global* g);
@@ -415,14 +427,17 @@ pttk_status pttk_batch_create(const pttk_tt* tt, int B, const int64_t* xoff, con
 void pttk_batch_free(pttk_batch* b);
 
 /* Launch configuration of the plan's tensor-core factor build; pttk_batch_get_config reports
- * the current one and how many exist (6). 0 (the default): the kernel that generates the A
+ * the current one and how many exist (7). 0 (the default): the kernel that generates the A
  * operand in shared memory with four separate epilogue warps, which drain two alternating
  * tensor-memory accumulators while the next tile's products run (ranks whose two accumulators
  * or staging tiles do not fit fall back to configuration 1); 1 and 2: the same kernel without
  * the epilogue warps, with 128- or 64-byte chunks of K per row; 3, 4, 5: for the FP16/BF16
  * forms, the kernel that generates A in tensor memory and keeps the chain's intermediate in
  * registers, run in thread-block clusters of 1, 2 or 4 CTAs that share each core chunk by a
- * multicast copy (ranks it cannot hold fall back to configuration 1). */
+ * multicast copy (ranks it cannot hold fall back to configuration 1); 6: for the FP16/BF16
+ * forms, A in tensor memory with the epilogue warps of configuration 0 and a B ring of 3-4
+ * slots in the shared memory A no longer takes (ranks it cannot hold fall back to
+ * configuration 0). */
 pttk_status pttk_batch_set_config(pttk_batch* b, int cfg);
 pttk_status pttk_batch_get_config(const pttk_batch* b, int* cfg, int* n_configs);
 

@@ -83,15 +83,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the phase completes
+// or about `ns` nanoseconds have passed, whichever comes first (the completion wakes it at
+// once, so the hint costs no latency; it only spares the issue slots of repeated polls).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait for the completion of the phase with the given parity: gives up after ~2 s
-// (2^32 SM clocks, or 2^30 polls) or as soon as another thread of the CTA has raised the
-// abort flag. try_wait itself suspends the thread for a while in hardware, so the loop polls
-// without sleeping in software: a software sleep adds its own wake-up delay to every hand-off.
+// (2^32 SM clocks, or 2^24 polls of up to 0.1 ms each) or as soon as another thread of the CTA
+// has raised the abort flag. Each poll suspends the thread in hardware until the phase
+// completes (or the hint runs out), so no software sleep adds a wake-up delay to a hand-off.
 __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
   const long long t0 = clock64();
-  for (uint32_t i = 0; i < (1u << 30); ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 15) == 15 && (*abort_flag || clock64() - t0 > (4ll << 30))) return false;
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
+    if (mbar_try_wait_hint(bar, parity, 100000u)) return true;
+    if (*abort_flag || clock64() - t0 > (4ll << 30)) return false;
   }
   return false;
 }
@@ -1153,6 +1167,7 @@ struct TsArgs {
   int acc1_col;      // TMEM column of the first step's own accumulator (two or more steps)
   int a_col;         // TMEM column of A slot 0
   int a_part_cols;   // TMEM columns of one A part of a slot
+  int region_col;    // columns of one accumulator region (tensor-memory-A kernel with epilogue warps)
   int tmem_cols;
   uint32_t b_slot_bytes;  // bytes reserved per B part per slot
 };
@@ -1571,6 +1586,385 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_ts_kernel(TsArgs a) {
   if (warp == 1) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
 }
 
+// ---------------- A in tensor memory, dedicated epilogue warps -------------------------------
+// The tensor-memory-A chain (A generated into TMEM, S_in in registers, B alone in shared
+// memory) with the output written by four epilogue warps of their own from one of two
+// accumulator regions, as in chain_tce_kernel. With A out of shared memory, shared memory holds
+// a deeper B ring (NSB slots): a B chunk of a split form is 36-48 KB, whose copy from L2 takes
+// about 2,000 SM clocks, so a ring of two slots (what fits beside a shared-memory A ring)
+// leaves every chunk waiting for its copy, while NSB >= 3 keeps the copies ahead of the MMAs.
+// A and B have rings of their own (NSA = 2 TMEM slots, NSB shared-memory slots), each with
+// full and empty barriers.
+// TMEM: region r (r = tile parity) at column r * RC holds a tile's accumulators (the first
+// step's result is read back as the second step's input before the second step's first MMA
+// overwrites it); the NSA A slots follow at column 2 RC.
+// Barriers: full_a[NSA] (the 16 generator warps, after their tcgen05.st completed),
+// empty_a[NSA] (commit of the slot's MMAs), full_b[NSB] (TMA bytes), empty_b[NSB] (commit),
+// mid[r], last_done[r], rfree[r] as in chain_tce_kernel.
+constexpr int NSA_TSE = 2;
+constexpr int EPI_LD = 33;  // epilogue staging: 32 rows x 32 columns, row stride 33 floats
+
+// 32 consecutive TMEM columns of this warp's 32 lanes and the wait for them, in one block (no
+// use of the values can be scheduled before the wait)
+__device__ __forceinline__ void tmem_ld32_wait(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int FMT, bool SPLIT, int NSB>
+__global__ void __launch_bounds__(TCE_THREADS, 1) chain_tse_kernel(TsArgs a) {
+  constexpr int PARTS = SPLIT ? 2 : 1;
+  constexpr int NSA = NSA_TSE;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int bv_ld = a.bv_ld;
+  const int RC = a.region_col;
+  uint8_t* b_base = smem;                                                // NSB x PARTS x b_slot_bytes
+  float* Bv = reinterpret_cast<float*>(b_base + (size_t)NSB * PARTS * a.b_slot_bytes);  // 2 x 128 x bv_ld
+  float* Sseed = Bv + (size_t)2 * TILE_M * bv_ld;                        // 128 x ld_seed
+  float* stage = Sseed + (size_t)TILE_M * a.ld_seed;                     // NEPI_WARPS x 32 x EPI_LD
+  TsStepS* steps = reinterpret_cast<TsStepS*>(
+      (reinterpret_cast<uintptr_t>(stage + (size_t)NEPI_WARPS * 32 * EPI_LD) + 15) & ~uintptr_t(15));  // [2][3]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(steps + 6);
+  uint64_t* full_a = bars;
+  uint64_t* empty_a = bars + NSA;
+  uint64_t* full_b = bars + 2 * NSA;
+  uint64_t* empty_b = bars + 2 * NSA + NSB;
+  uint64_t* mid = bars + 2 * NSA + 2 * NSB;        // [2]
+  uint64_t* last_done = mid + 2;                    // [2]
+  uint64_t* rfree = mid + 4;                        // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mid + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < NSA; ++i) {
+      mbar_init(&full_a[i], NGEN_WARPS);
+      mbar_init(&empty_a[i], 1);
+    }
+    for (int i = 0; i < NSB; ++i) {
+      mbar_init(&full_b[i], 1);
+      mbar_init(&empty_b[i], 1);
+    }
+    for (int r = 0; r < 2; ++r) {
+      mbar_init(&mid[r], 1);
+      mbar_init(&last_done[r], 1);
+      mbar_init(&rfree[r], NEPI_WARPS);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (tid < 2 * a.nsteps) steps[(tid / a.nsteps) * 3 + tid % a.nsteps] = a.st[tid / a.nsteps][tid % a.nsteps];
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int64_t nitems = a.nitems;
+  const int nsteps = a.nsteps;
+  auto item_side = [&](int64_t k) -> int { return k < a.T0p ? 0 : 1; };
+  auto item_row0 = [&](int64_t k) -> int64_t { return (k - (item_side(k) ? a.T0p : 0)) * TILE_M; };
+
+  if (warp == 0) {
+    // ---------------- TMA producer: B chunks into the NSB-deep ring ----------------
+    if (lane == 0) {
+      uint32_t h = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+        const int sd = item_side(it);
+        for (int si = 0; si < nsteps && ok; ++si) {
+          const TsStepS& st = steps[sd * 3 + si];
+          for (int c = 0; c < st.nchunks; ++c, ++h) {
+            const uint32_t slot = h % NSB;
+            if (h >= (uint32_t)NSB && !mbar_wait(&empty_b[slot], ((h / NSB) - 1) & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            uint8_t* bh = b_base + (size_t)slot * PARTS * a.b_slot_bytes;
+            mbar_arrive_expect_tx(&full_b[slot], SPLIT ? 2 * st.bytes : st.bytes);
+            tma_load_1d(bh, st.hi + (size_t)c * st.bytes, st.bytes, &full_b[slot]);
+            if (SPLIT) tma_load_1d(bh + a.b_slot_bytes, st.lo + (size_t)c * st.bytes, st.bytes, &full_b[slot]);
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(a.status, (int)PTTK_ETIMEOUT);
+      }
+      const int zero = 0;
+      for (uint32_t k = (h > (uint32_t)NSB ? h - NSB : 0); k < h; ++k) mbar_wait(&full_b[k % NSB], (k / NSB) & 1, &zero);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t g = 0, tile = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++tile) {
+        const int sd = item_side(it);
+        const uint32_t r = tile & 1, use = tile >> 1;
+        // the region's previous tile must have left it
+        if (use >= 1 && !mbar_wait(&rfree[r], (use - 1) & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dacc = tmem + r * (uint32_t)RC;
+        for (int si = 0; si < nsteps && ok; ++si) {
+          const TsStepS& st = steps[sd * 3 + si];
+          const uint32_t idesc = st.idesc, sbo = st.sbo;
+          const int ksteps = st.ksteps, nch = st.nchunks;
+          for (int c = 0; c < nch; ++c, ++g) {
+            const uint32_t sa = g % NSA, sb = g % NSB;
+            if (!mbar_wait(&full_a[sa], (g / NSA) & 1, abort_flag) ||
+                !mbar_wait(&full_b[sb], (g / NSB) & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t ta = tmem + (uint32_t)(a.a_col + (int)sa * PARTS * a.a_part_cols);
+            const uint32_t bsm = smem_u32(b_base + (size_t)sb * PARTS * a.b_slot_bytes);
+            const uint64_t bh0 = smem_desc2(bsm, sbo);
+            const uint64_t bl0 = smem_desc2(bsm + a.b_slot_bytes, sbo);
+            for (int k = 0; k < ksteps; ++k) {
+              const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+              const uint64_t bh = bh0 + (uint64_t)(16 * k);
+              umma_f16_ts(dacc, ta + 8 * k, bh, idesc, acc);
+              if (SPLIT) {
+                umma_f16_ts(dacc, ta + 8 * k, bl0 + (uint64_t)(16 * k), idesc, 1u);
+                umma_f16_ts(dacc, ta + (uint32_t)a.a_part_cols + 8 * k, bh, idesc, 1u);
+              }
+            }
+            umma_commit(&empty_a[sa]);
+            umma_commit(&empty_b[sb]);
+            if (c == nch - 1) umma_commit(si == nsteps - 1 ? &last_done[r] : &mid[r]);
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(a.status, (int)PTTK_ETIMEOUT);
+      }
+      const int zero = 0;
+      if (g > 0) mbar_wait(&empty_a[(g - 1) % NSA], ((g - 1) / NSA) & 1, &zero);
+    }
+    __syncwarp();
+  } else if (warp < 2 + NGEN_WARPS) {
+    // ---------------- generator warps: A chunks into TMEM, S_in in registers ----------------
+    const int gw = warp - 2;
+    const int quarter = warp & 3;
+    const int row = 32 * quarter + lane;
+    const int part = gw >> 2;
+    const uint32_t lanes = (uint32_t)(32 * quarter) << 16;
+    uint32_t g = 0, tile = 0;
+    bool dead = false;
+    float S[TS_SPT];
+    auto basis = [&](int sd, int si, int buf, float x) {
+      const TsStepS& st = steps[sd * 3 + si];
+      const float xh = (2.f * x - st.lo_box - st.hi_box) / (st.lo_box - st.hi_box);
+      float* bv = Bv + ((size_t)buf * TILE_M + row) * bv_ld;
+      const float sc = st.a_scale;
+      float t0 = 1.f, t1 = xh;
+      bv[0] = sc;
+      for (int k = 1; k < a.n; ++k) {
+        bv[k] = t1 * sc;
+        const float t2 = 2.f * xh * t1 - t0;
+        t0 = t1;
+        t1 = t2;
+      }
+      for (int k = a.n; k < bv_ld; ++k) bv[k] = 0.f;
+    };
+    auto coord_of = [&](int64_t it, int si) -> float {
+      const int sd = item_side(it);
+      const int64_t gp = item_row0(it) + row;
+      const TsStepS& st = steps[sd * 3 + si];
+      return gp < a.N[sd] ? a.pts[sd][gp * a.d + st.coord] : st.lo_box;
+    };
+    auto seed_coord_of = [&](int64_t it) -> float {
+      const int sd = item_side(it);
+      const int64_t gp = item_row0(it) + row;
+      return (a.s0_coord[sd] >= 0 && gp < a.N[sd]) ? a.pts[sd][gp * a.d + a.s0_coord[sd]] : a.s0_lo[sd];
+    };
+    auto write_seed = [&](int64_t it, float x) {
+      const int sd = item_side(it);
+      float* w = Sseed + (size_t)row * a.ld_seed;
+      const int pad = steps[sd * 3].R_in_pad;
+      if (a.s0_coord[sd] >= 0) {
+        const float lo = a.s0_lo[sd], hi = a.s0_hi[sd];
+        const float xh = (2.f * x - lo - hi) / (lo - hi);
+        float t0 = 1.f, t1 = xh;
+        w[0] = 1.f;
+        for (int k = 1; k < pad; ++k) {
+          w[k] = k < a.n ? t1 : 0.f;
+          const float t2 = 2.f * xh * t1 - t0;
+          t0 = t1;
+          t1 = t2;
+        }
+      } else {
+        w[0] = 1.f;
+        for (int k = 1; k < pad; ++k) w[k] = 0.f;
+      }
+    };
+    float xn[4] = {0.f, 0.f, 0.f, 0.f};
+    if (part == 0 && blockIdx.x < nitems) {
+      for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
+      xn[3] = seed_coord_of(blockIdx.x);
+      basis(item_side(blockIdx.x), 0, 0, xn[0]);
+      write_seed(blockIdx.x, xn[3]);
+    }
+    gen_barrier();
+    uint32_t bufsel = 0;
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x, ++tile) {
+      const int sd = item_side(it);
+      const uint32_t r = tile & 1, use = tile >> 1;
+      float xcur[3] = {xn[0], xn[1], xn[2]};
+      const int64_t itn = it + gridDim.x;
+      if (part == 0 && itn < nitems) {
+        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
+        xn[3] = seed_coord_of(itn);
+      }
+      {
+        const int spt = steps[sd * 3].spt;
+        const float* w = Sseed + (size_t)row * a.ld_seed + part * spt;
+#pragma unroll
+        for (int i = 0; i < TS_SPT; ++i) S[i] = i < spt ? w[i] : 0.f;
+      }
+      for (int si = 0; si < nsteps; ++si) {
+        const TsStepS& st = steps[sd * 3 + si];
+        const int nch = st.nchunks, jpc = st.jpc, rpad = st.R_in_pad, spt = st.spt;
+        const float* bvrow = Bv + ((size_t)bufsel * TILE_M + row) * bv_ld;
+        for (int c = 0; c < nch; ++c, ++g) {
+          const uint32_t sa = g % NSA, use_a = g / NSA;
+          dead = dead || *abort_flag;
+          if (!dead && g >= (uint32_t)NSA) dead = !mbar_wait(&empty_a[sa], (use_a - 1) & 1, abort_flag);
+          dead = __any_sync(0xffffffffu, dead);
+          if (dead && lane == 0) *abort_flag = 1;
+          if (!dead) {
+            tc_fence_after();
+            const uint32_t cbase = tmem + lanes + (uint32_t)(a.a_col + (int)sa * PARTS * a.a_part_cols);
+            for (int jj = 0; jj < jpc; ++jj) {
+              const float b = bvrow[c * jpc + jj];
+              const uint32_t col = cbase + (uint32_t)((jj * rpad + part * spt) >> 1);
+#pragma unroll
+              for (int i = 0; i < TS_SPT; i += 2) {
+                if (i < spt) {
+                  uint32_t h, l;
+                  pack_pair<FMT, SPLIT>(b * S[i], b * S[i + 1], h, l);
+                  tmem_st1(col + (uint32_t)(i >> 1), h);
+                  if (SPLIT) tmem_st1(col + (uint32_t)a.a_part_cols + (uint32_t)(i >> 1), l);
+                }
+              }
+            }
+            tmem_wait_st();
+            tc_fence_before();
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full_a[sa]);
+        }
+        const bool last = si == nsteps - 1;
+        if (part == 0) {
+          if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
+          else if (itn < nitems) basis(item_side(itn), 0, bufsel ^ 1, xn[0]);
+        }
+        if (!last) {
+          // this step's result is the next step's input: wait for it and keep this thread's
+          // spt columns of it in registers (columns at or past R_out hold zeros)
+          const uint32_t phase = use * (uint32_t)(nsteps - 1) + (uint32_t)si;
+          if (!dead && !*abort_flag) dead = !mbar_wait(&mid[r], phase & 1, abort_flag);
+          dead = __any_sync(0xffffffffu, dead || *abort_flag);
+          if (dead && lane == 0) *abort_flag = 1;
+          tc_fence_after();
+          const TsStepS& nx = steps[sd * 3 + si + 1];
+          if (!dead) {
+            float v[16];
+            tmem_ld1x16(tmem + lanes + r * (uint32_t)RC + (uint32_t)(part * nx.spt), v);
+            const float osc = st.out_scale;
+#pragma unroll
+            for (int i = 0; i < TS_SPT; ++i) S[i] = i < nx.spt ? v[i] * osc : 0.f;
+          }
+        }
+        bufsel ^= 1;
+        tc_fence_before();
+        gen_barrier();
+        if (last && itn < nitems) {
+          // the next tile's seed: every thread read this tile's seed into registers before
+          // the barrier above
+          if (part == 0) write_seed(itn, xn[3]);
+          gen_barrier();
+        }
+      }
+    }
+    if (dead && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(a.status, (int)PTTK_ETIMEOUT);
+    }
+  } else {
+    // ---------------- epilogue warps: one TMEM lane quarter each ----------------
+    const int ew = warp - 2 - NGEN_WARPS;  // 0..3
+    const int quarter = warp & 3;
+    const uint32_t lanes = (uint32_t)(32 * quarter) << 16;
+    float* stg = stage + (size_t)ew * 32 * EPI_LD;
+    uint32_t tile = 0;
+    bool dead = false;
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x, ++tile) {
+      const int sd = item_side(it);
+      const uint32_t r = tile & 1, use = tile >> 1;
+      const TsStepS& st = steps[sd * 3 + nsteps - 1];
+      if (!dead && !*abort_flag) dead = !mbar_wait(&last_done[r], use & 1, abort_flag);
+      dead = __any_sync(0xffffffffu, dead || *abort_flag);
+      if (dead && lane == 0) *abort_flag = 1;
+      tc_fence_after();
+      if (!dead) {
+        const int64_t row0 = item_row0(it);
+        const int rows = (int)std::max<int64_t>(0, std::min<int64_t>(TILE_M, a.N[sd] - row0));
+        const int R = st.R_out;
+        float* outbase = a.out[sd] + (row0 + 32 * quarter) * R;
+        const int wrows = std::max(0, std::min(32, rows - 32 * quarter));
+        const float osc = st.out_scale;
+        // 32 columns at a time: each row's 32 values through the staging tile, then each store
+        // instruction writes 32 consecutive columns (128 bytes) of one row
+        for (int cb = 0; cb < st.Npad; cb += 32) {
+          float v[32];
+          tmem_ld32_wait(tmem + lanes + r * (uint32_t)RC + (uint32_t)cb, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) stg[lane * EPI_LD + i] = v[i] * osc;
+          __syncwarp();
+          const int col = cb + lane;
+          if (col < R)
+            for (int rr = 0; rr < wrows; ++rr) outbase[(int64_t)rr * R + col] = stg[rr * EPI_LD + lane];
+          __syncwarp();
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rfree[r]);
+    }
+    if (dead && lane == 0) {
+      *abort_flag = 1;
+      atomicExch(a.status, (int)PTTK_ETIMEOUT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+}
+
 // ---------------- core images -------------------------------------------------------------
 // Image of the oriented core (K x R_out, column-major, FP64; K = n R_in) for one chain step in
 // the padded K order k' = a + R_in_pad j (zero rows for a >= R_in): chunk c holds rows o < Npad
@@ -1818,19 +2212,18 @@ static pttk_status build_images(const pttk_tt* tt, const TcImageCache* cache, pt
 // back to configuration 1.
 static const int kTcConfigs[2][2] = {{128, 4}, {64, 4}};
 static const int kTcConfigsSplit[2][2] = {{128, 2}, {64, 4}};
-constexpr int kTceConfigs = 1, kTcSubConfigs = 2, kTsConfigs = 3;
+constexpr int kTceConfigs = 1, kTcSubConfigs = 2, kTsConfigs = 3, kTseConfigs = 1;
+constexpr int kTceFirst = 0, kSubFirst = kTceFirst + kTceConfigs, kTsFirst = kSubFirst + kTcSubConfigs,
+              kTseFirst = kTsFirst + kTsConfigs;
 static const int kTsCluster[kTsConfigs] = {1, 2, 4};
 
-int tc_config_count() { return kTceConfigs + kTcSubConfigs + kTsConfigs; }
+int tc_config_count() { return kTseConfigs + kTceConfigs + kTcSubConfigs + kTsConfigs; }
 static bool ts_form(pttk_prec p) { return p == PTTK_FP16 || p == PTTK_FP16X3 || p == PTTK_BF16 || p == PTTK_BF16X3; }
-static bool ts_config(int cfg) {
-  return cfg >= kTceConfigs + kTcSubConfigs && cfg < kTceConfigs + kTcSubConfigs + kTsConfigs;
-}
-static int ts_cluster(int cfg) { return kTsCluster[cfg - kTceConfigs - kTcSubConfigs]; }
-static bool tce_config(int cfg) { return cfg >= 0 && cfg < kTceConfigs; }
-static int tc_sub_config(int cfg) {
-  return cfg >= kTceConfigs && cfg < kTceConfigs + kTcSubConfigs ? cfg - kTceConfigs : 0;
-}
+static bool ts_config(int cfg) { return cfg >= kTsFirst && cfg < kTsFirst + kTsConfigs; }
+static int ts_cluster(int cfg) { return kTsCluster[cfg - kTsFirst]; }
+static bool tse_config(int cfg) { return cfg >= kTseFirst && cfg < kTseFirst + kTseConfigs; }
+static bool tce_config(int cfg) { return cfg >= kTceFirst && cfg < kTceFirst + kTceConfigs; }
+static int tc_sub_config(int cfg) { return cfg >= kSubFirst && cfg < kSubFirst + kTcSubConfigs ? cfg - kSubFirst : 0; }
 
 static void tc_config(pttk_prec prec, int cfg, int* KCB, int* NS) {
   const bool split = form_split(prec);
@@ -1994,6 +2387,46 @@ static pttk_status launch_ts(TsArgs a, int64_t T0, int64_t T1, size_t smem, cuda
   return PTTK_OK;
 }
 
+// Launch arguments of the tensor-memory-A kernel with epilogue warps; false (and no error) when
+// the ranks do not fit it: two accumulator regions of the widest step and NSA_TSE A slots in
+// 512 TMEM columns, and at least three B slots in shared memory. *nsb_out: the B ring depth
+// (3 or 4).
+static bool tse_plan(const pttk_tt* tt, const TcImageCache* cache, const Images& im, pttk_prec prec, TsArgs& a,
+                     size_t* smem_out, int* nsb_out) {
+  if (!ts_plan(tt, cache, im, prec, 1, a, smem_out)) return false;
+  const int parts = form_split(prec) ? 2 : 1;
+  int npad = 16;
+  for (int side = 0; side < 2; ++side)
+    for (int i = 0; i < a.nsteps; ++i) npad = std::max(npad, a.st[side][i].Npad);
+  a.region_col = ((npad + 31) / 32) * 32;
+  a.a_col = 2 * a.region_col;
+  if (a.a_col + NSA_TSE * parts * a.a_part_cols > 512) return false;
+  a.tmem_cols = 512;
+  const size_t fixed = sizeof(float) * ((size_t)2 * TILE_M * a.bv_ld + (size_t)TILE_M * a.ld_seed +
+                                        (size_t)NEPI_WARPS * 32 * EPI_LD) +
+                       16 + sizeof(TsStepS) * 6 + 8 * (2 * NSA_TSE + 2 * 4 + 6) + 16;
+  int nsb = 0;
+  for (int k = 4; k >= 3 && !nsb; --k)
+    if ((size_t)k * parts * a.b_slot_bytes + fixed <= 227 * 1024) nsb = k;
+  if (!nsb) return false;
+  *nsb_out = nsb;
+  *smem_out = std::max<size_t>((size_t)nsb * parts * a.b_slot_bytes + fixed, 116 * 1024);
+  return true;
+}
+
+template <int FMT, bool SPLIT, int NSB>
+static pttk_status launch_tse(TsArgs a, int64_t T0, int64_t T1, size_t smem, cudaStream_t s) {
+  auto kfn = chain_tse_kernel<FMT, SPLIT, NSB>;
+  PTTK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  a.T0p = T0;
+  a.nitems = T0 + T1;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.nitems, sm_count()));
+  kfn<<<grid, TCE_THREADS, smem, s>>>(a);
+  pttk::count_launch();
+  PTTK_CUDA(cudaGetLastError());
+  return PTTK_OK;
+}
+
 // Images for (prec, config) exist after this returns (first use lays them out; synchronises).
 pttk_status tc_prepare(const pttk_tt* tt, TcImageCache* cache, pttk_prec prec, int cfg, cudaStream_t s) {
   const int fi = form_index(prec);
@@ -2003,12 +2436,14 @@ pttk_status tc_prepare(const pttk_tt* tt, TcImageCache* cache, pttk_prec prec, i
   Images& im = cache->img[fi][KCB == 64 ? 0 : 1];
   std::lock_guard<std::mutex> lk(g_img_mu);
   PTTK_TRY(ensure_merged(tt, cache));
-  if (ts_config(cfg) && ts_form(prec)) {
+  if ((ts_config(cfg) || tse_config(cfg)) && ts_form(prec)) {
     Images& ti = cache->ts[fi];
     if (!ti.buf) PTTK_TRY(build_images_ts(tt, cache, prec, ti, s));
     TsArgs probe;
     size_t smem;
-    if (ts_plan(tt, cache, ti, prec, 3, probe, &smem)) return PTTK_OK;
+    int nsb;
+    if (tse_config(cfg) ? tse_plan(tt, cache, ti, prec, probe, &smem, &nsb) : ts_plan(tt, cache, ti, prec, 3, probe, &smem))
+      return PTTK_OK;
   }
   if (!im.buf) PTTK_TRY(build_images(tt, cache, prec, KCB, im, s));
   return PTTK_OK;
@@ -2041,6 +2476,33 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
   if (N_s == 0 && N_t == 0) return PTTK_OK;
   PTTK_TRY(tc_prepare(tt, cache, prec, cfg, s));
   const int fi = form_index(prec);
+  if (tse_config(cfg) && ts_form(prec)) {
+    TsArgs a;
+    size_t smem = 0;
+    int nsb = 0;
+    if (tse_plan(tt, cache, cache->ts[fi], prec, a, &smem, &nsb)) {
+      a.N[0] = N_s;
+      a.N[1] = N_t;
+      a.pts[0] = X;
+      a.pts[1] = Y;
+      a.out[0] = U;
+      a.out[1] = V;
+      a.status = d_status;
+      const int64_t T0 = (N_s + TILE_M - 1) / TILE_M, T1 = (N_t + TILE_M - 1) / TILE_M;
+      PTTK_PROF("chain_tc", s);
+      const int fmt = form_fmt(prec);
+      const bool split = form_split(prec);
+#define PTTK_TSE_LAUNCH(F, SP) \
+  return nsb == 4 ? launch_tse<F, SP, 4>(a, T0, T1, smem, s) : launch_tse<F, SP, 3>(a, T0, T1, smem, s);
+      if (fmt == FMT_BF16) {
+        if (split) { PTTK_TSE_LAUNCH(FMT_BF16, true) }
+        PTTK_TSE_LAUNCH(FMT_BF16, false)
+      }
+      if (split) { PTTK_TSE_LAUNCH(FMT_FP16, true) }
+      PTTK_TSE_LAUNCH(FMT_FP16, false)
+#undef PTTK_TSE_LAUNCH
+    }
+  }
   if (ts_config(cfg) && ts_form(prec)) {
     const int NS = 3, CL = ts_cluster(cfg);
     TsArgs a;
@@ -2135,7 +2597,7 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
   a.ld_seed = ((pad0 + 7) / 8) * 8 + 4;
   const int bv_ld = (tt->n + 1) | 1;
   const size_t parts = split ? 2 : 1;
-  if (tce_config(cfg)) {
+  if (tce_config(cfg) || tse_config(cfg)) {
     // two accumulator regions of the widest step, an epilogue staging tile per epilogue warp
     TcArgs b = a;
     b.ld_s = ((spad_max + 31) / 32) * 32 + 4;

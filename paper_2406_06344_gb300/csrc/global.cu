@@ -342,6 +342,87 @@ static pttk_status global_online_run(const pttk_global* g, const double* th, dou
   return PTTK_OK;
 }
 
+// Online stage of Algorithm 4, uncompressed (PTTK-Global-1), for B parameter values at once:
+// the B matrices sym(C1(theta_b)) go through one batched eigensolver call (every launch of the
+// tridiagonalisation, the eigenvalues and the eigenvectors covers all of them), then
+// W_b = U_b Lambda_b U_b^T with the same selection as the single-theta call.
+static pttk_status global_online_batched_run(const pttk_global* g, const double* th_all, int nb, bool definite,
+                                             double* W, cudaStream_t s) {
+  const int k = g->k, rs = g->rs, rt = g->rt;
+  const size_t kk = (size_t)k * k;
+  DevBuf H, P, C1, Bb, t2d, dd, ee, dtau, dlam;
+  PTTK_TRY(H.alloc((size_t)rs * rt));
+  PTTK_TRY(P.alloc((size_t)k * rt));
+  PTTK_TRY(C1.alloc(kk));
+  PTTK_TRY(Bb.alloc(kk * nb));
+  PTTK_TRY(t2d.alloc(nb));
+  PTTK_TRY(dd.alloc((size_t)k * nb));
+  PTTK_TRY(ee.alloc((size_t)k * nb));
+  PTTK_TRY(dtau.alloc((size_t)k * nb));
+  PTTK_TRY(dlam.alloc((size_t)k * nb));
+  for (int b = 0; b < nb; ++b) {
+    PTTK_TRY(theta_core_run(&g->tt, th_all + (size_t)b * PTTK_MAX_D, true, H.p, s));
+    dgemm(false, true, k, rt, rs, 1.0, g->R, k, H.p, rt, 0.0, P.p, k, s);
+    dgemm(false, true, k, k, rt, 1.0, P.p, k, g->R + (size_t)k * rs, k, 0.0, C1.p, k, s);
+    sumsq_block_kernel<<<1, 1024, 0, s>>>(C1.p, (int64_t)kk, t2d.p + b); pttk::count_launch();
+    sym_shift_kernel<<<blocks_for((int64_t)kk, 256), 256, 0, s>>>(C1.p, k, 0.0, Bb.p + kk * b); pttk::count_launch();
+  }
+  PTTK_CUDA(cudaGetLastError());
+  {
+    PTTK_PROF("global_eig", s);
+    PTTK_TRY(sym_eig_values(Bb.p, k, nb, dd.p, ee.p, dtau.p, dlam.p, s));
+  }
+  std::vector<double> lam((size_t)k * nb), t2(nb);
+  PTTK_CUDA(cudaMemcpyAsync(lam.data(), dlam.p, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaMemcpyAsync(t2.data(), t2d.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  // per matrix: the resolved eigenvalues (and the positive ones for a definite kernel), listed
+  // in ascending order as the inverse iteration needs; column q of matrix b's block of V
+  std::vector<int> sz, scol, cnt(nb, 0);
+  std::vector<double> slam, sw;
+  for (int b = 0; b < nb; ++b) {
+    const double* lb = lam.data() + (size_t)k * b;
+    if (!(t2[b] > 0.0)) continue;  // S H T^T = 0: W_b = 0
+    double lmax = 0.0;
+    for (int i = 0; i < k; ++i) lmax = std::max(lmax, std::fabs(lb[i]));
+    const double res = 64.0 * 2.2204460492503131e-16 * lmax;
+    for (int i = 0; i < k; ++i)
+      if ((!definite || lb[i] > 0.0) && std::fabs(lb[i]) > res) {
+        sz.push_back(b);
+        scol.push_back(cnt[b]++);
+        slam.push_back(lb[i]);
+        sw.push_back(std::fabs(lb[i]));
+      }
+  }
+  int ncols = 0;
+  for (int b = 0; b < nb; ++b) ncols = std::max(ncols, cnt[b]);
+  PTTK_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * kk * nb, s));
+  if (ncols > 0) {
+    DevBuf U, Ul, dl;
+    PTTK_TRY(U.alloc((size_t)k * ncols * nb));
+    PTTK_TRY(Ul.alloc((size_t)k * ncols));
+    PTTK_TRY(dl.alloc((size_t)ncols * nb));
+    {
+      PTTK_PROF("global_eigvec", s);
+      PTTK_TRY(sym_eig_vectors(Bb.p, dd.p, ee.p, dtau.p, k, nb, sz, slam, sw, scol, U.p, ncols, s));
+    }
+    std::vector<double> lk((size_t)ncols * nb, 0.0);
+    for (size_t q = 0; q < sz.size(); ++q) lk[(size_t)sz[q] * ncols + scol[q]] = slam[q];
+    PTTK_CUDA(cudaMemcpyAsync(dl.p, lk.data(), sizeof(double) * lk.size(), cudaMemcpyHostToDevice, s));
+    for (int b = 0; b < nb; ++b) {
+      const int m = cnt[b];
+      if (m == 0) continue;
+      const double* Ub = U.p + (size_t)k * ncols * b;
+      scale_cols_kernel<<<blocks_for((int64_t)k * m, 256), 256, 0, s>>>(Ub, k, dl.p + (size_t)ncols * b, m, Ul.p);
+      pttk::count_launch();
+      dgemm(false, true, k, k, m, 1.0, Ul.p, k, Ub, k, 0.0, W + kk * b, k, s);
+    }
+    PTTK_CUDA(cudaGetLastError());
+  }
+  PTTK_CUDA(cudaStreamSynchronize(s));
+  return PTTK_OK;
+}
+
 // ---------------- Gaussian-process likelihood on the low-rank kernel --------------------------
 namespace {
 // out (ra x rb, column-major) = sum_k G[:, k, :] T_k'(th) * scale (derivative of Eq. hmat's
@@ -534,6 +615,18 @@ pttk_status pttk_global_instantiate(const pttk_global* g, const double* theta, d
   double th[PTTK_MAX_D];
   PTTK_TRY(theta_hat(&g->tt, theta, th));
   return global_online_run(g, th, eps, compress != 0, definite != 0, Z, W, rank, as_stream(stream));
+}
+
+pttk_status pttk_global_instantiate_batched(const pttk_global* g, int B, const double* thetas, int definite,
+                                            double* W, void* stream) {
+  clear_error();
+  if (!g || (B > 0 && (!thetas || !W))) return set_error(PTTK_EINVAL, "NULL argument");
+  if (B < 0) return set_error(PTTK_EINVAL, "B must be >= 0");
+  if (B == 0) return PTTK_OK;
+  const int dth = g->tt.dtheta;
+  std::vector<double> th((size_t)B * PTTK_MAX_D, 0.0);
+  for (int b = 0; b < B; ++b) PTTK_TRY(theta_hat(&g->tt, thetas + (size_t)b * dth, th.data() + (size_t)b * PTTK_MAX_D));
+  return global_online_batched_run(g, th.data(), B, definite != 0, W, as_stream(stream));
 }
 
 void pttk_global_free(pttk_global* g) { global_release(g); }

@@ -76,6 +76,7 @@ SIGNATURES = [
     ("pttk_global_get_q", _int, [_vp, _vp, _vp]),
     ("pttk_global_get_r", _int, [_vp, _c_double_p]),
     ("pttk_global_instantiate", _int, [_vp, _c_double_p, ctypes.c_double, _int, _int, _vp, _vp, _c_int_p, _vp]),
+    ("pttk_global_instantiate_batched", _int, [_vp, _int, _c_double_p, _int, _vp, _vp]),
     ("pttk_global_free", None, [_vp]),
     ("pttk_splitmix64", ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint64]),
     ("pttk_peak_probe", _int, [_int, _i64, _vp, _c_double_p, _c_double_p]),
@@ -547,6 +548,18 @@ class Global:
         if not compress:
             return self.Q(stream), W.view(k, k)
         return Z[:N * r].view(N, r), W[:r * r].view(r, r)
+
+    def instantiate_batched(self, thetas, definite: bool = True, stream=None):
+        """pttk_global_instantiate_batched: W (B x k x k) of PTTK-Global-1 for every row of
+        thetas (B x d_theta); K(X, X; theta_b) ~= Q W[b] Q^T."""
+        import torch
+        th = np.ascontiguousarray(np.atleast_2d(np.asarray(thetas, dtype=np.float64)))
+        B = th.shape[0]
+        _, k, _, _ = self.dims
+        W = torch.empty(B * k * k, dtype=torch.float64, device="cuda")
+        _check(load().pttk_global_instantiate_batched(self.handle, B, th.ctypes.data_as(_c_double_p),
+                                                      1 if definite else 0, _ptr(W), _stream(stream)))
+        return W.view(B, k, k)
 
     def free(self):
         if self._h:

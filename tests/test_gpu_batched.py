@@ -77,7 +77,10 @@ def test_batched_theta_outside_box_is_reported(env):
     tt.check()  # the status word is cleared once reported
 
 
-def test_batched_under_cuda_graph_and_autotune(env):
+@pytest.mark.parametrize("form", ["tf32x3", "fp16x3"])
+def test_batched_under_cuda_graph_and_autotune(env, form):
+    """tf32x3 runs the shared-memory-A kernels (its tensor-memory configurations fall back);
+    fp16x3 also runs the tensor-memory-A kernel in clusters of 1, 2 and 4."""
     torch, P, w, tt, gc = env
     rng = np.random.default_rng(3)
     sizes_s = list(rng.integers(1, 3000, 40))
@@ -86,7 +89,7 @@ def test_batched_under_cuda_graph_and_autotune(env):
     Xd = torch.tensor(X, device="cuda", dtype=torch.float32)
     Yd = torch.tensor(Y, device="cuda", dtype=torch.float32)
     thd = torch.tensor(th, device="cuda", dtype=torch.float64)
-    batch = P.Batch(tt, xoff, yoff, "tf32x3")
+    batch = P.Batch(tt, xoff, yoff, form)
     U0, M0, V0 = batch.instantiate(thd, Xd, Yd)
     ms = batch.autotune(Xd, Yd, U0, V0)
     assert len(ms) == batch.config[1] and all(m > 0 for m in ms)

@@ -89,6 +89,32 @@ def test_global_2_matches_the_oracle(env, kern, definite, th, eps):
     assert np.linalg.norm(Zh @ Wh @ Zh.T - K1) <= eps * nrm
 
 
+@pytest.mark.parametrize("kern,definite", [(o.GAUSS, True), (o.MULTIQUADRIC, False)])
+def test_global_1_batched_over_theta(env, kern, definite):
+    """pttk_global_instantiate_batched: W_b of five parameter values in one call against the
+    oracle's PTTK-Global-1 at each (1e-10 relative, as the single call), and against the
+    single-theta call on the same handle (1e-11: the batch changes only the multisection
+    lanes, not the method); B = 0 is a no-op and a theta outside its box is EDOMAIN."""
+    torch, P, X, cases = env
+    cores, g = cases[kern]
+    ths = [0.35, 0.7, 0.95, 1.2, 1.39]
+    Wb = g.instantiate_batched(np.array(ths)[:, None], definite=definite)
+    Q = g.Q()
+    Qh = Q.cpu().numpy()
+    for b, th in enumerate(ths):
+        S, H, T = _oracle(cores, X, (th,))
+        Zo, Wo = o.global_factors(S, T, H, definite=definite)
+        Ko = Zo @ Wo @ Zo.T
+        Kb = Qh @ Wb[b].cpu().numpy() @ Qh.T
+        assert o.rel_fro(Ko, Kb) <= 1e-10, (th, o.rel_fro(Ko, Kb))
+        _, W1 = g.instantiate((th,), compress=False, definite=definite)
+        assert torch.linalg.norm(W1 - Wb[b]) <= 1e-11 * torch.linalg.norm(W1)
+    assert g.instantiate_batched(np.zeros((0, 1))).shape[0] == 0
+    with pytest.raises(P.PttkError) as e:
+        g.instantiate_batched(np.array([[0.7], [2.0]]))
+    assert e.value.status == P.EDOMAIN
+
+
 def test_global_apply_and_theta_outside_the_box(env):
     torch, P, X, cases = env
     cores, g = cases[o.GAUSS]
