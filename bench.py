@@ -51,7 +51,7 @@ NOMINAL = {"bf16": 2.25, "tf32": 1.1}
 # DRAM bytes (read + write) of one chain_tc launch of the fast form on this workload, from one
 # ncu capture of the kernel source whose SHA-256 prefix is given: the figure is reported only
 # while the source is unchanged, and null otherwise.
-NCU_TRAFFIC = {"fp16x3": {"src_sha16": None, "bytes": None}}
+NCU_TRAFFIC = {"fp16x3": {"src_sha16": "a6cd5da83c62fdb4", "bytes": 1400251352}}
 CHAIN_SRC = os.path.join(ROOT, "paper_2406_06344_gb300", "csrc", "chain_tc.cu")
 # executed FP64 flops per entry of the FP64 grid kernel (K_nu quadrature + in-tile transform),
 # from ncu instruction counts (DFMA x 2 + DADD + DMUL) on the n = 5 grid of the same workload
@@ -74,6 +74,8 @@ def parse():
                     help="profiling case: BUILDS instantiations at N = 1M on a handle made from seeded cores "
                          "with the d = 3 workload's ranks (no grid, no TT-SVD); not a bench line")
     ap.add_argument("--form", default=FAST_FORM, choices=FORMS)
+    ap.add_argument("--global-only", type=int, default=0, metavar="THETAS",
+                    help="profiling case: PTTK-Global-1 on the d = 3 SE case (N = 1e5), THETAS values batched")
     return ap.parse_args()
 
 
@@ -244,6 +246,8 @@ def main():
         return reference_main(args, rank)
     if args.online_only:
         return online_only(args)
+    if args.global_only:
+        return global_only(args)
 
     import torch
     import torch.distributed as dist
@@ -557,6 +561,34 @@ def cross_leg(torch, P, W, ev):
                      "grid_entries": float(n) ** w.D, "ranks": tt.ranks}
         tt.free()
     return out
+
+
+def global_only(args):
+    """A small case for kernel profiles of the eigensolver: PTTK-Global-1 of the d = 3 SE kernel
+    (N = 1e5 uniform points, TT tol 1e-5, n = 12; k = 828), one theta, then THETAS values in one
+    batched call."""
+    import torch
+    from paper_2406_06344_gb300 import pttk as P
+    from paper_2406_06344_gb300 import workloads as W
+    P.load()
+    Db = math.sqrt(3.0)
+    box, thb = ((0.0, 1.0),) * 3, ((0.2 * Db, Db),)
+    X = torch.tensor(np.random.default_rng(5).uniform(0.0, 1.0, (100000, 3)), device="cuda")
+    tt = P.TT.build_offline(W.GAUSS, 3, box, box, 1, thb, 12, 1e-5, "fp64")
+    g = P.Global(tt, X)
+    ths = np.random.default_rng(7).uniform(0.2 * Db, Db, args.global_only)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.instantiate((float(ths[0]),))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g.instantiate_batched(ths[:, None])
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    print(json.dumps({"case": "PTTK-Global-1 only", "k": g.dims[1], "single_ms": 1000 * (t1 - t0),
+                      "batched_ms_per_theta": 1000 * (t2 - t1) / len(ths)}), flush=True)
+    g.free()
+    tt.free()
 
 
 def run_extras(torch, P, W, w, tt, X32, Y32, wv, thetas, state, flush, ev, pk, hbm, bf16_sus):

@@ -67,12 +67,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // for its rows i > j. Block (0, 0) also writes v to vbuf, tau[j], the diagonal d[j] = A[j, j]
 // and the off-diagonal e[j] = beta. Column j keeps x until the second half, which runs after
 // every block of this one has read it.
-__global__ void __launch_bounds__(SB) reflect_symv_kernel(const double* __restrict__ A, int k, int j, int nch,
-                                                          double* __restrict__ part, double* __restrict__ vbuf,
-                                                          double* __restrict__ tau, double* __restrict__ d,
-                                                          double* __restrict__ e) {
+__global__ void __launch_bounds__(SB * 4) reflect_symv_kernel(const double* __restrict__ A, int k, int j, int nch,
+                                                              double* __restrict__ part, double* __restrict__ vbuf,
+                                                              double* __restrict__ tau, double* __restrict__ d,
+                                                              double* __restrict__ e, unsigned* __restrict__ done,
+                                                              double* __restrict__ w) {
   __shared__ double sh[32];
   __shared__ double vs[CHUNK];
+  __shared__ double red[4][SB];
   const int z = blockIdx.z;
   const double* a = A + (size_t)z * k * k;
   const double* col = a + (size_t)j * k;
@@ -87,15 +89,25 @@ __global__ void __launch_bounds__(SB) reflect_symv_kernel(const double* __restri
     scale = 1.0 / (alpha - beta);
   }
   const int l0 = j + 1 + blockIdx.y * CHUNK, l1 = min(k, l0 + CHUNK);
-  for (int l = l0 + threadIdx.x; l < l1; l += blockDim.x)
-    vs[l - l0] = l == j + 1 ? 1.0 : (xn2 > 0.0 ? col[l] * scale : 0.0);
+  for (int l = l0 + threadIdx.x; l < l0 + CHUNK; l += blockDim.x)
+    vs[l - l0] = l >= l1 ? 0.0 : (l == j + 1 ? 1.0 : (xn2 > 0.0 ? col[l] * scale : 0.0));
   __syncthreads();
-  const int i = j + 1 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < k) {
-    double acc = 0.0;
-    for (int l = l0; l < l1; ++l) acc = fma(a[(size_t)l * k + i], vs[l - l0], acc);
-    part[((size_t)z * nch + blockIdx.y) * k + i] = acc;
+  // four column groups of CHUNK / 4: the 16 loads of a thread are independent, so they are all
+  // in flight together; the groups' sums meet in shared memory
+  const int rr = threadIdx.x % SB, grp = threadIdx.x / SB;
+  const int i = j + 1 + blockIdx.x * SB + rr;
+  const int ir = i < k ? i : k - 1;
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < CHUNK / 4; ++q) {
+    const int l = l0 + grp * (CHUNK / 4) + q;
+    const double x = l < l1 ? a[(size_t)l * k + ir] : 0.0;
+    acc = fma(x, vs[l - l0], acc);
   }
+  red[grp][rr] = acc;
+  __syncthreads();
+  if (grp == 0 && i < k)
+    part[((size_t)z * nch + blockIdx.y) * k + i] = (red[0][rr] + red[1][rr]) + (red[2][rr] + red[3][rr]);
   if (blockIdx.x == 0 && blockIdx.y == 0) {
     for (int l = j + 1 + threadIdx.x; l < k; l += blockDim.x)
       vbuf[(size_t)z * k + l] = l == j + 1 ? 1.0 : (xn2 > 0.0 ? col[l] * scale : 0.0);
@@ -105,36 +117,49 @@ __global__ void __launch_bounds__(SB) reflect_symv_kernel(const double* __restri
       e[(size_t)z * k + j] = beta;
     }
   }
+  // The block that finishes last (a counter per matrix and step, no waiting) forms
+  // w = p - (tau/2)(p^T v) v with p = tau sum_c part once, for the second half to read.
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&done[(size_t)z * k + j], 1u) == gridDim.x * gridDim.y - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int m = k - j - 1;
+  double sp = 0.0;
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    double p = 0.0;
+    for (int c = 0; c < nch; ++c) p += __ldcg(part + ((size_t)z * nch + c) * k + j + 1 + q);
+    p *= t;
+    const double v = q == 0 ? 1.0 : (xn2 > 0.0 ? col[j + 1 + q] * scale : 0.0);
+    w[(size_t)z * k + j + 1 + q] = p;
+    sp += p * v;
+  }
+  const double pv = block_sum(sp, sh);
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    const double v = q == 0 ? 1.0 : (xn2 > 0.0 ? col[j + 1 + q] * scale : 0.0);
+    w[(size_t)z * k + j + 1 + q] -= 0.5 * t * pv * v;
+  }
 }
 
-// Step j, second half (the two-sided update of dsytd2): every block forms p = tau sum_c part
-// for the rows i > j, p^T v and w = p - (tau/2)(p^T v) v in shared memory (the partial sums in
-// the same order in every block), applies A22 <- A22 - v w^T - w v^T to its columns of
-// A22 = A[j+1:, j+1:] (both triangles), and block 0 stores v over x in column j, where the
-// back-transformation reads it. Dynamic shared memory: 2 (k - 1) doubles.
-__global__ void __launch_bounds__(EB) w_rank2_kernel(double* __restrict__ A, int k, int j, int nch,
-                                                     const double* __restrict__ part,
-                                                     const double* __restrict__ vbuf,
-                                                     const double* __restrict__ tau) {
+// Step j, second half (the two-sided update of dsytd2): every block loads w (formed by the
+// first half's last block) and v for the rows i > j into shared memory, applies
+// A22 <- A22 - v w^T - w v^T to its columns of A22 = A[j+1:, j+1:] (both triangles), and block
+// 0 stores v over x in column j, where the back-transformation reads it. Dynamic shared
+// memory: 2 (k - 1) doubles.
+__global__ void __launch_bounds__(EB) w_rank2_kernel(double* __restrict__ A, int k, int j,
+                                                     const double* __restrict__ wbuf,
+                                                     const double* __restrict__ vbuf) {
   extern __shared__ double wv_smem[];
-  __shared__ double sh[32];
   const int z = blockIdx.z, m = k - j - 1;
   double* ws = wv_smem;
   double* vs = wv_smem + m;
   double* a = A + (size_t)z * k * k;
-  const double t = tau[(size_t)z * k + j];
-  double s = 0.0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double p = 0.0;
-    for (int c = 0; c < nch; ++c) p += part[((size_t)z * nch + c) * k + j + 1 + i];
-    p *= t;
-    const double v = vbuf[(size_t)z * k + j + 1 + i];
-    ws[i] = p;
-    vs[i] = v;
-    s += p * v;
+    ws[i] = wbuf[(size_t)z * k + j + 1 + i];
+    vs[i] = vbuf[(size_t)z * k + j + 1 + i];
   }
-  const double pv = block_sum(s, sh);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) ws[i] -= 0.5 * t * pv * vs[i];
   __syncthreads();
   for (int l = blockIdx.x; l < m; l += gridDim.x) {
     double* cl = a + (size_t)(j + 1 + l) * k + j + 1;
@@ -374,22 +399,28 @@ pttk_status sym_eig_values(double* A, int k, int nb, double* d, double* e, doubl
     if (wv_bytes > 48 * 1024)
       PTTK_CUDA(cudaFuncSetAttribute(w_rank2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wv_bytes));
     const int nch_max = (k + CHUNK - 1) / CHUNK;
-    double *part = nullptr, *vbuf = nullptr;
+    double *part = nullptr, *vbuf = nullptr, *wbuf = nullptr;
+    unsigned* done = nullptr;
     PTTK_CUDA(cudaMallocAsync(&part, sizeof(double) * (size_t)nb * nch_max * k, s));
     PTTK_CUDA(cudaMallocAsync(&vbuf, sizeof(double) * (size_t)nb * k, s));
+    PTTK_CUDA(cudaMallocAsync(&wbuf, sizeof(double) * (size_t)nb * k, s));
+    PTTK_CUDA(cudaMallocAsync(&done, sizeof(unsigned) * (size_t)nb * k, s));
+    PTTK_CUDA(cudaMemsetAsync(done, 0, sizeof(unsigned) * (size_t)nb * k, s));
     PTTK_PROF("eig_tridiag", s);
     const int gmax = std::max(1, 2 * sm_count() / nb);
     for (int j = 0; j < k - 2; ++j) {
       const int m = k - j - 1, nch = (m + CHUNK - 1) / CHUNK;
-      reflect_symv_kernel<<<dim3((unsigned)((m + SB - 1) / SB), (unsigned)nch, (unsigned)nb), SB, 0, s>>>(
-          A, k, j, nch, part, vbuf, tau, d, e);
+      reflect_symv_kernel<<<dim3((unsigned)((m + SB - 1) / SB), (unsigned)nch, (unsigned)nb), SB * 4, 0, s>>>(
+          A, k, j, nch, part, vbuf, tau, d, e, done, wbuf);
       pttk::count_launch();
       w_rank2_kernel<<<dim3((unsigned)std::min(m, gmax), 1, (unsigned)nb), EB, sizeof(double) * 2 * (size_t)m, s>>>(
-          A, k, j, nch, part, vbuf, tau);
+          A, k, j, wbuf, vbuf);
       pttk::count_launch();
     }
     cudaFreeAsync(part, s);
     cudaFreeAsync(vbuf, s);
+    cudaFreeAsync(wbuf, s);
+    cudaFreeAsync(done, s);
   }
   tail_kernel<<<nb, 32, 0, s>>>(A, k, d, e); pttk::count_launch();
   {
