@@ -815,9 +815,10 @@ struct StepWork {
 // Orthonormal basis (m x r, unit columns in decreasing singular value, column-major, into
 // `core`) of the top-r left singular subspace of X (m x c, column-major, not modified), r the
 // smallest rank >= 1 whose discarded tail sqrt(sum_{i>r} sigma_i^2) is <= delta; delta = 0
-// keeps every direction X has (an orthonormal basis of its range).
+// keeps every direction X has (an orthonormal basis of its range). stop_frac: the pivoted QR
+// stops once the discarded block has ||R22||_F <= stop_frac delta (see below).
 static pttk_status svd_basis(const double* X, int64_t m, int64_t c, double delta, StepWork& wk, Buf& core,
-                             int* r_out, StageClock& clk, int k, cudaStream_t s) {
+                             int* r_out, StageClock& clk, int k, cudaStream_t s, double stop_frac = 0.03) {
   if (!wk.d_hs) PTTK_CUDA(cudaMalloc(&wk.d_hs, sizeof(HHState)));
   const bool wide = c >= m;
   // QR input: wide -> W = X^T (c x m), tall -> a copy of X (m x c). The pivoted QR makes
@@ -845,13 +846,14 @@ static pttk_status svd_basis(const double* X, int64_t m, int64_t c, double delta
   PTTK_TRY(wk.below.alloc(q));
   PTTK_TRY(wk.R.alloc(q * q));
   clk.mark(k, "layout");
-  // rows of R kept: the QR stops once the discarded block has ||R22||_F <= 0.03 delta. The
-  // tails below count ||R22||^2, so the error bound of the truncation holds as it is; only a
-  // tail within 9e-4 delta^2 of the threshold could give a rank one higher than the exact
-  // singular values would
+  // rows of R kept: the QR stops once the discarded block has ||R22||_F <= stop_frac delta
+  // (0.03 for the TT-SVD). The tails below count ||R22||^2, so the error bound of the
+  // truncation holds as it is; only a tail within stop_frac^2 delta^2 of the threshold could
+  // give a rank one higher than the exact singular values would. The discarded block also
+  // moves the kept subspace by about stop_frac delta against the exact SVD's
   int kq = 0;
   double tail2 = 0.0;
-  const double stop = 0.03 * delta;
+  const double stop = stop_frac * delta;
   PTTK_TRY(householder_qrcp(wk.qrin.p, Mqr, q, stop * stop, wk.R.p, wk.d_perm, wk.part.p, wk.below.p,
                             wk.wpart.p, wk.wv.p, wk.d_hs, &kq, &tail2, s));
   clk.mark(k, "qr");
@@ -861,9 +863,9 @@ static pttk_status svd_basis(const double* X, int64_t m, int64_t c, double delta
   gather_rt_kernel<<<grid1d(q * kq, 256), 256, 0, s>>>(wk.R.p, q, kq, wk.d_perm, wk.A.p); pttk::count_launch();
   // one-sided Jacobi on R1^T: R1^T V = U' Sigma, so R1 = V Sigma U'^T and the right singular
   // vectors of R1 (= of the pivoted QR input, up to the discarded R22) are the normalised
-  // columns of the rotated R1^T; columns below 1e-3 delta / sqrt(kq) together carry
-  // < 1e-6 delta^2, and pairs of them are skipped
-  PTTK_TRY(jacobi(wk.A.p, q, kq, s, 1e-3 * delta / sqrt((double)kq)));
+  // columns of the rotated R1^T; columns below (stop_frac / 30) delta / sqrt(kq) together carry
+  // < (stop_frac / 30)^2 delta^2, and pairs of them are skipped
+  PTTK_TRY(jacobi(wk.A.p, q, kq, s, (stop_frac / 30.0) * delta / sqrt((double)kq)));
   clk.mark(k, "jacobi");
   colnorm_kernel<<<(unsigned)(((int64_t)kq * 32 + 255) / 256), 256, 0, s>>>(wk.A.p, q, kq, wk.norms.p); pttk::count_launch();
   std::vector<double> sigma(kq);
@@ -993,6 +995,11 @@ pttk_status tt_svd_run(pttk_tt* tt, double* X, double tol, cudaStream_t s) {
 // thin QR; any orthonormal factor serves), with delta for the truncation. Works on device cores
 // G[k] (r[k] x nm[k] x r[k+1], column-major) of any mode sizes nm[k]; on return G and r hold the
 // rounded TT.
+// TT-Round's QR stops at 1e-4 delta (the TT-SVD's at 0.03 delta): its unfoldings are small
+// (r_{i-1} n x r_i), so the later stop costs little, and the kept subspaces then agree with
+// an exact SVD's to about 1e-4 delta.
+constexpr double kRoundStopFrac = 1e-4;
+
 pttk_status tt_round_cores(std::vector<Buf>& G, std::vector<int64_t>& r, const std::vector<int64_t>& nm, double tol,
                            cudaStream_t s) {
   const int D = (int)G.size();
@@ -1026,7 +1033,7 @@ pttk_status tt_round_cores(std::vector<Buf>& G, std::vector<int64_t>& r, const s
   for (int i = 0; i < D - 1; ++i) {
     const int64_t m = r[i] * nm[i], c = r[i + 1];
     int k = 0;
-    PTTK_TRY(svd_basis(G[i].p, m, c, delta, wk, nb[i], &k, clk, i, s));
+    PTTK_TRY(svd_basis(G[i].p, m, c, delta, wk, nb[i], &k, clk, i, s, kRoundStopFrac));
     PTTK_TRY(W.alloc((int64_t)k * c));
     dgemm(true, false, k, c, m, 1.0, nb[i].p, m, G[i].p, m, 0.0, W.p, k, s);
     std::swap(G[i].p, nb[i].p);
