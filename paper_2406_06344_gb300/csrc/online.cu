@@ -251,28 +251,86 @@ __global__ void __launch_bounds__((P / 4) * 16) chain_kernel(ChainArgs a, const 
 }
 
 // ---------------- apply: out = U (M (V^T w)) ----------------------------------------
-template <typename T>
+// partial[b, c] = sum over block b's rows r of V[r, c] w[r]. Threads are 4 row lanes x 64
+// column groups, each of VW consecutive columns (VW = 4 when rows are 16-byte aligned: a row
+// of up to 256 columns is then read once, contiguously, by 16-byte loads; else VW = 1 and 64
+// columns a pass). Each thread keeps 4 rows of loads in flight; the row lanes meet in shared
+// memory in a fixed order.
+template <typename T, int VW>
 __global__ void __launch_bounds__(256) vtw_partial_kernel(const T* __restrict__ V, int64_t N,
                                                           int rt, const T* __restrict__ w,
                                                           T* __restrict__ partial) {
+  __shared__ T red[4][64 * VW];
   const int64_t rows_per = (N + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = std::min<int64_t>(N, r0 + rows_per);
-  for (int c = threadIdx.x; c < rt; c += blockDim.x) {
-    T acc = T(0);
-    for (int64_t r = r0; r < r1; ++r) acc = fma(V[r * rt + c], w[r], acc);
-    partial[(int64_t)blockIdx.x * rt + c] = acc;
+  const int cl = threadIdx.x & 63, rl = threadIdx.x >> 6;
+  for (int cb = 0; cb < rt; cb += 64 * VW) {
+    const int c = cb + cl * VW;
+    const bool on = c < rt;  // with VW = 4, rt is a multiple of 4: the whole group is in range
+    T acc[VW];
+#pragma unroll
+    for (int q = 0; q < VW; ++q) acc[q] = T(0);
+    int64_t r = r0 + rl;
+    for (; r + 12 < r1; r += 16) {
+      T v[4][VW];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T* src = V + (r + 4 * u) * rt + c;
+        if constexpr (VW == 4) {
+          if (on) {
+            if constexpr (sizeof(T) == 4) {
+              const float4 x = *reinterpret_cast<const float4*>(src);
+              v[u][0] = x.x; v[u][1] = x.y; v[u][2] = x.z; v[u][3] = x.w;
+            } else {
+              const double2 x0 = *reinterpret_cast<const double2*>(src);
+              const double2 x1 = *reinterpret_cast<const double2*>(src + 2);
+              v[u][0] = x0.x; v[u][1] = x0.y; v[u][2] = x1.x; v[u][3] = x1.y;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < VW; ++q) v[u][q] = T(0);
+          }
+        } else {
+          v[u][0] = on ? *src : T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T wr = w[r + 4 * u];
+#pragma unroll
+        for (int q = 0; q < VW; ++q) acc[q] = fma(v[u][q], wr, acc[q]);
+      }
+    }
+    for (; r < r1; r += 4) {
+      const T wr = w[r];
+#pragma unroll
+      for (int q = 0; q < VW; ++q) acc[q] = fma(on ? V[r * rt + c + q] : T(0), wr, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < VW; ++q) red[rl][cl * VW + q] = acc[q];
+    __syncthreads();
+    for (int q = threadIdx.x; q < 64 * VW; q += blockDim.x)
+      if (cb + q < rt) partial[(int64_t)blockIdx.x * rt + cb + q] = (red[0][q] + red[1][q]) + (red[2][q] + red[3][q]);
+    __syncthreads();
   }
 }
 
-// t = sum over the partial rows, written in place into row 0 of `partial` (one thread per
-// column; the rows it reads belong to no other thread). Grid-stride over the rt columns.
+// t = sum over the partial rows, written into row 0 of `partial`: 32 columns x 8 part lanes
+// per block, each lane summing every eighth part, the lanes then added in a fixed order (the
+// rows a block reads belong to its own columns only).
 template <typename T>
 __global__ void __launch_bounds__(256) reduce_parts_kernel(T* __restrict__ partial, int nparts, int rt) {
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < rt; c += (int64_t)gridDim.x * blockDim.x) {
-    T acc = partial[c];
-    for (int b = 1; b < nparts; ++b) acc += partial[(int64_t)b * rt + c];
-    partial[c] = acc;
-  }
+  __shared__ T red[8][32];
+  const int cl = threadIdx.x & 31, pl = threadIdx.x >> 5;
+  const int64_t c = (int64_t)blockIdx.x * 32 + cl;
+  T acc = T(0);
+  if (c < rt)
+    for (int b = pl; b < nparts; b += 8) acc += partial[(int64_t)b * rt + c];
+  red[pl][cl] = acc;
+  __syncthreads();
+  if (pl == 0 && c < rt)
+    partial[c] = ((red[0][cl] + red[1][cl]) + (red[2][cl] + red[3][cl])) +
+                 ((red[4][cl] + red[5][cl]) + (red[6][cl] + red[7][cl]));
 }
 
 // s = M t, one warp per row of M (rs x rt, row-major); t is read through the L1 cache, so
@@ -291,18 +349,30 @@ __global__ void __launch_bounds__(256) mt_kernel(const T* __restrict__ M, int rs
   }
 }
 
-// out[p] = U[p, :] . s, one warp per row; s is read through the L1 cache
+// out[p] = U[p, :] . s, one warp per row, two rows at a time (the loads of both are in
+// flight before either is reduced); s is read through the L1 cache
 template <typename T>
 __global__ void __launch_bounds__(256) us_kernel(const T* __restrict__ U, int64_t N, int rs,
                                                  const T* __restrict__ s, T* __restrict__ out) {
   const int lane = threadIdx.x & 31;
-  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N;
-       row += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N; row += 2 * nw) {
+    const int64_t row2 = row + nw;
+    const bool two = row2 < N;
     const T* u = U + row * rs;
-    T acc = T(0);
-    for (int c = lane; c < rs; c += 32) acc = fma(u[c], __ldg(s + c), acc);
+    const T* u2 = U + (two ? row2 : row) * rs;
+    T acc = T(0), acc2 = T(0);
+    for (int c = lane; c < rs; c += 32) {
+      const T sc = __ldg(s + c);
+      acc = fma(u[c], sc, acc);
+      acc2 = fma(u2[c], sc, acc2);
+    }
     acc = warp_sum<T>(acc);
-    if (lane == 0) out[row] = acc;
+    acc2 = warp_sum<T>(acc2);
+    if (lane == 0) {
+      out[row] = acc;
+      if (two) out[row2] = acc2;
+    }
   }
 }
 
@@ -313,13 +383,16 @@ pttk_status apply_typed(const T* U, const T* M, const T* V, int64_t N_s, int64_t
   T* sv = scratch + (size_t)nparts * rt;
   PTTK_PROF("apply", s);
   if (N_t > 0) {
-    vtw_partial_kernel<T><<<nparts, 256, 0, s>>>(V, N_t, rt, w, partial); pttk::count_launch();
+    // 16-byte column groups when every row starts on a 16-byte boundary
+    const bool vec = rt % 4 == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0 && (sizeof(T) * rt) % 16 == 0;
+    if (vec) vtw_partial_kernel<T, 4><<<nparts, 256, 0, s>>>(V, N_t, rt, w, partial);
+    else vtw_partial_kernel<T, 1><<<nparts, 256, 0, s>>>(V, N_t, rt, w, partial);
+    pttk::count_launch();
   } else {
     PTTK_CUDA(cudaMemsetAsync(partial, 0, sizeof(T) * (size_t)nparts * rt, s));
   }
   if (nparts > 1) {
-    const int64_t rblocks = std::min<int64_t>((rt + 255) / 256, (int64_t)sm_count() * 4);
-    reduce_parts_kernel<T><<<(unsigned)rblocks, 256, 0, s>>>(partial, nparts, rt); pttk::count_launch();
+    reduce_parts_kernel<T><<<(unsigned)((rt + 31) / 32), 256, 0, s>>>(partial, nparts, rt); pttk::count_launch();
   }
   const int64_t mblocks = std::min<int64_t>(((int64_t)rs * 32 + 255) / 256, (int64_t)sm_count() * 16);
   mt_kernel<T><<<(unsigned)mblocks, 256, 0, s>>>(M, rs, rt, partial, sv); pttk::count_launch();
