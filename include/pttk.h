@@ -330,13 +330,17 @@ void pttk_fixed_free(pttk_fixed* f);
  * (theta = l > 0); X: dev N x d row-major doubles. FP64 throughout. */
 
 /* out = (K(X, X; theta) + s2 I) v with every kernel entry evaluated on the fly (N^2 kernel
- * evaluations, no N x N storage). v, out: dev [N]. Asynchronous on `stream`.
- * Errors: PTTK_EINVAL. */
+ * evaluations, no N x N storage). prec: PTTK_FP64 evaluates in FP64; PTTK_FP32 evaluates each
+ * entry and sums each 128-column tile in FP32, the tile sums in FP64 (relative error of order
+ * 1e-7). Rows and column ranges are split over blocks (four per SM), the ranges' sums added in
+ * a fixed order. v, out: dev [N]. Stream-ordered scratch; asynchronous on `stream`.
+ * Errors: PTTK_EINVAL, PTTK_ECUDA. */
 pttk_status pttk_gp_kv(int kernel, int d, const double* X, int64_t N, const double* theta, double s2, const double* v,
-                       double* out, void* stream);
+                       double* out, pttk_prec prec, void* stream);
 
 /* Preconditioned conjugate gradients for (K(X, X; theta) + s2 I) x = b, the matrix applied
- * exactly by pttk_gp_kv and the preconditioner (Z diag(lambda) Z^T + s2 I)^{-1} in Woodbury form
+ * by pttk_gp_kv in the precision `prec` (with PTTK_FP32 the true residual levels off near the
+ * FP32 evaluation's 1e-7; the CG vectors stay FP64) and the preconditioner (Z diag(lambda) Z^T + s2 I)^{-1} in Woodbury form
  * Z ((Z^T v) ./ (lambda + s2)) + (v - Z Z^T v) / s2, Z (dev N x m, row-major, orthonormal
  * columns) and lambda (dev [m]) from PTTK-Global (pttk_global_instantiate with compress = 1; eps
  * = 0 keeps every term); m = 0 runs plain CG. x0 = 0; stops once ||b - A x||_2 <= tol ||b||_2
@@ -345,8 +349,8 @@ pttk_status pttk_gp_kv(int kernel, int d, const double* X, int64_t N, const doub
  * Allocates scratch; synchronises `stream` every iteration.
  * Errors: PTTK_EINVAL, PTTK_ENOMEM, PTTK_ECUDA, PTTK_EDOMAIN (p^T A p <= 0: not positive definite). */
 pttk_status pttk_gp_pcg(int kernel, int d, const double* X, int64_t N, const double* theta, double s2, const double* Z,
-                        const double* lam, int m, const double* b, double* x, double tol, int maxit, int* iters,
-                        double* resid, void* stream);
+                        const double* lam, int m, const double* b, double* x, double tol, int maxit, pttk_prec prec,
+                        int* iters, double* resid, void* stream);
 
 /* Log marginal likelihood of y ~ N(0, K~ + s2 I) and its gradient in theta for the low-rank
  * kernel of a PTTK-Global handle, K~(theta) = sym(S H(theta) T^T) = Q sym(C1(theta)) Q^T

@@ -2,8 +2,11 @@
 // form: solving (K(X, X; theta) + s2 I) x = b by conjugate gradients preconditioned with the
 // PTTK-Global factorisation (Algorithm 4), with the kernel matrix applied exactly.
 //
-//   pttk_gp_kv   out = (K(X, X; theta) + s2 I) v, every kernel entry evaluated on the fly in
-//                FP64 (tiles of the points in shared memory; N^2 evaluations, no N x N storage).
+//   pttk_gp_kv   out = (K(X, X; theta) + s2 I) v, every kernel entry evaluated on the fly
+//                (tiles of the points in shared memory; N^2 evaluations, no N x N storage), in
+//                FP64, or in FP32 with each tile's 128 terms summed in FP32 and the tile sums
+//                in FP64. Rows and column ranges are split over blocks so that small N fills
+//                the GPU; the column ranges' partial sums are added in a fixed order.
 //   pttk_gp_pcg  preconditioned CG (Hestenes-Stiefel) with M^{-1} = (Z W Z^T + s2 I)^{-1},
 //                Z (N x m) with orthonormal columns and W = diag(lambda) (PTTK-Global-2, or
 //                Global-1 written in its eigenbasis), applied in Woodbury form
@@ -22,33 +25,51 @@ namespace {
 constexpr int GT = 256;       // threads per block
 constexpr int GTILE = 128;    // columns per shared-memory tile of the kernel product
 
-// out[i] = sum_j kappa(||x_i - x_j||^2; l) v[j] + s2 v[i]
+// part[cs * N + i] = sum over the columns j of range cs of kappa(||x_i - x_j||^2; l) v[j]:
+// block (x, y) takes rows [x GT, x GT + GT) and column range y of gridDim.y, ranges of
+// `cols` columns (a multiple of GTILE). T: the precision of the evaluation and of each tile's
+// sum; the tile sums are added in FP64.
+template <typename T>
 __global__ void __launch_bounds__(GT) gp_kv_kernel(int kind, int d, const double* __restrict__ X, int64_t N, double l,
-                                                   double s2, const double* __restrict__ v, double* __restrict__ out) {
-  __shared__ double xs[GTILE * PTTK_MAX_D];
-  __shared__ double vs[GTILE];
-  for (int64_t r0 = (int64_t)blockIdx.x * GT; r0 < N; r0 += (int64_t)gridDim.x * GT) {
-    const int64_t i = r0 + threadIdx.x;
-    double xi[PTTK_MAX_D];
-    for (int c = 0; c < d; ++c) xi[c] = i < N ? X[i * d + c] : 0.0;
-    double acc = 0.0;
-    for (int64_t t0 = 0; t0 < N; t0 += GTILE) {
-      const int nt = (int)std::min<int64_t>(GTILE, N - t0);
-      __syncthreads();
-      for (int q = threadIdx.x; q < nt * d; q += GT) xs[q] = X[t0 * d + q];
-      for (int q = threadIdx.x; q < nt; q += GT) vs[q] = v[t0 + q];
-      __syncthreads();
-      if (i < N)
-        for (int jj = 0; jj < nt; ++jj) {
-          double r2 = 0.0;
-          for (int c = 0; c < d; ++c) {
-            const double df = xi[c] - xs[jj * d + c];
-            r2 = fma(df, df, r2);
-          }
-          acc = fma(kappa_l<double>(kind, r2, l), vs[jj], acc);
+                                                   const double* __restrict__ v, int64_t cols,
+                                                   double* __restrict__ part) {
+  __shared__ T xs[GTILE * PTTK_MAX_D];
+  __shared__ T vs[GTILE];
+  const int64_t i = (int64_t)blockIdx.x * GT + threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.y * cols, c1 = std::min<int64_t>(N, c0 + cols);
+  T xi[PTTK_MAX_D];
+  for (int c = 0; c < d; ++c) xi[c] = i < N ? (T)X[i * d + c] : T(0);
+  const T lt = (T)l;
+  double acc = 0.0;
+  for (int64_t t0 = c0; t0 < c1; t0 += GTILE) {
+    const int nt = (int)std::min<int64_t>(GTILE, c1 - t0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < nt * d; q += GT) xs[q] = (T)X[t0 * d + q];
+    for (int q = threadIdx.x; q < nt; q += GT) vs[q] = (T)v[t0 + q];
+    __syncthreads();
+    if (i < N) {
+      T tacc = T(0);
+      for (int jj = 0; jj < nt; ++jj) {
+        T r2 = T(0);
+        for (int c = 0; c < d; ++c) {
+          const T df = xi[c] - xs[jj * d + c];
+          r2 = fma(df, df, r2);
         }
+        tacc = fma(kappa_l<T>(kind, r2, lt), vs[jj], tacc);
+      }
+      acc += (double)tacc;
     }
-    if (i < N) out[i] = fma(s2, v[i], acc);
+  }
+  if (i < N) part[(int64_t)blockIdx.y * N + i] = acc;
+}
+
+// out[i] = s2 v[i] + sum over the column ranges of part (in order)
+__global__ void gp_kv_reduce(const double* __restrict__ part, int ncs, int64_t N, double s2,
+                             const double* __restrict__ v, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < ncs; ++c) acc += part[(int64_t)c * N + i];
+    out[i] = fma(s2, v[i], acc);
   }
 }
 
@@ -143,11 +164,24 @@ unsigned grid_for(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + GT - 1) / GT, (int64_t)sm_count() * 8));
 }
 
+// column ranges of the kernel product: enough blocks for about four per SM
+int kv_splits(int64_t N) {
+  const int64_t row_tiles = (N + GT - 1) / GT;
+  const int64_t want = std::max<int64_t>(1, (int64_t)sm_count() * 4 / std::max<int64_t>(row_tiles, 1));
+  return (int)std::min<int64_t>({want, 64, (N + GTILE - 1) / GTILE});
+}
+
+// out = (K + s2 I) v; part: scratch of kv_splits(N) * N doubles
 pttk_status kv_launch(int kind, int d, const double* X, int64_t N, double l, double s2, const double* v, double* out,
-                      cudaStream_t s) {
+                      bool fp32, double* part, cudaStream_t s) {
   PTTK_PROF("gp_kv", s);
-  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + GT - 1) / GT, (int64_t)sm_count() * 16));
-  gp_kv_kernel<<<blocks, GT, 0, s>>>(kind, d, X, N, l, s2, v, out); pttk::count_launch();
+  const int ncs = kv_splits(N);
+  const int64_t cols = ((N + ncs - 1) / ncs + GTILE - 1) / GTILE * GTILE;
+  const dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)ncs);
+  if (fp32) gp_kv_kernel<float><<<grid, GT, 0, s>>>(kind, d, X, N, l, v, cols, part);
+  else gp_kv_kernel<double><<<grid, GT, 0, s>>>(kind, d, X, N, l, v, cols, part);
+  pttk::count_launch();
+  gp_kv_reduce<<<grid_for(N), GT, 0, s>>>(part, ncs, N, s2, v, out); pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;
 }
@@ -185,18 +219,25 @@ using namespace pttk;
 extern "C" {
 
 pttk_status pttk_gp_kv(int kernel, int d, const double* X, int64_t N, const double* theta, double s2, const double* v,
-                       double* out, void* stream) {
+                       double* out, pttk_prec prec, void* stream) {
   clear_error();
   PTTK_TRY(check_gp(kernel, d, X, N, theta, s2));
   if (!v || !out) return set_error(PTTK_EINVAL, "NULL argument");
-  return kv_launch(kernel, d, X, N, theta[0], s2, v, out, as_stream(stream));
+  if (prec != PTTK_FP64 && prec != PTTK_FP32) return set_error(PTTK_EINVAL, "K v: prec must be PTTK_FP64 or PTTK_FP32");
+  cudaStream_t s = as_stream(stream);
+  double* part = nullptr;
+  PTTK_CUDA(cudaMallocAsync(&part, sizeof(double) * (size_t)kv_splits(N) * N, s));
+  const pttk_status st = kv_launch(kernel, d, X, N, theta[0], s2, v, out, prec == PTTK_FP32, part, s);
+  cudaFreeAsync(part, s);
+  return st;
 }
 
 pttk_status pttk_gp_pcg(int kernel, int d, const double* X, int64_t N, const double* theta, double s2, const double* Z,
-                        const double* lam, int m, const double* b, double* x, double tol, int maxit, int* iters,
-                        double* resid, void* stream) {
+                        const double* lam, int m, const double* b, double* x, double tol, int maxit, pttk_prec prec,
+                        int* iters, double* resid, void* stream) {
   clear_error();
   PTTK_TRY(check_gp(kernel, d, X, N, theta, s2));
+  if (prec != PTTK_FP64 && prec != PTTK_FP32) return set_error(PTTK_EINVAL, "PCG: prec must be PTTK_FP64 or PTTK_FP32");
   if (!b || !x) return set_error(PTTK_EINVAL, "NULL argument");
   if (m < 0 || (m > 0 && (!Z || !lam))) return set_error(PTTK_EINVAL, "preconditioner: m >= 0 and Z, lambda given");
   if (!(tol > 0.0) || maxit < 0) return set_error(PTTK_EINVAL, "tol > 0 and maxit >= 0 required");
@@ -211,6 +252,8 @@ pttk_status pttk_gp_pcg(int kernel, int d, const double* X, int64_t N, const dou
   PTTK_TRY(sc.get(&p, N));
   PTTK_TRY(sc.get(&Ap, N));
   PTTK_TRY(sc.get(&part, nparts));
+  double* kvpart = nullptr;
+  PTTK_TRY(sc.get(&kvpart, (size_t)kv_splits(N) * N));
   if (m > 0) {
     PTTK_TRY(sc.get(&coef, m));
     PTTK_TRY(sc.get(&gpart, (size_t)gparts * m));
@@ -239,7 +282,7 @@ pttk_status pttk_gp_pcg(int kernel, int d, const double* X, int64_t N, const dou
   double rn = bn;
   int it = 0;
   while (rn > tol * bn && it < maxit) {
-    PTTK_TRY(kv_launch(kernel, d, X, N, l, s2, p, Ap, s));
+    PTTK_TRY(kv_launch(kernel, d, X, N, l, s2, p, Ap, prec == PTTK_FP32, kvpart, s));
     double pAp = 0.0;
     PTTK_TRY(dot_host(p, Ap, N, part, nparts, &pAp, s));
     if (!(pAp > 0.0)) return set_error(PTTK_EDOMAIN, "CG: p^T A p <= 0 (the matrix is not positive definite)");

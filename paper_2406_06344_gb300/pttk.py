@@ -86,9 +86,9 @@ SIGNATURES = [
     ("pttk_fixed_get_core", _int, [_vp, _int, _c_double_p]),
     ("pttk_fixed_theta_core", _int, [_vp, _c_double_p, _int, _vp, _vp]),
     ("pttk_fixed_free", None, [_vp]),
-    ("pttk_gp_kv", _int, [_int, _int, _vp, _i64, _c_double_p, ctypes.c_double, _vp, _vp, _vp]),
+    ("pttk_gp_kv", _int, [_int, _int, _vp, _i64, _c_double_p, ctypes.c_double, _vp, _vp, _int, _vp]),
     ("pttk_gp_pcg", _int, [_int, _int, _vp, _i64, _c_double_p, ctypes.c_double, _vp, _vp, _int, _vp, _vp,
-                           ctypes.c_double, _int, _c_int_p, _c_double_p, _vp]),
+                           ctypes.c_double, _int, _int, _c_int_p, _c_double_p, _vp]),
     ("pttk_gp_lml", _int, [_vp, _c_double_p, ctypes.c_double, _vp, _c_double_p, _c_double_p, _vp]),
     ("pttk_cross_build", _int, [_int, _int, _c_double_p, _c_double_p, _int, _c_double_p, _int, ctypes.c_double,
                                 ctypes.c_uint64, _int, _int, _int, _vp, ctypes.POINTER(_vp), _c_int_p,
@@ -650,8 +650,9 @@ def _f64_points(X):
         raise ValueError("points must be an (N, d) float64 CUDA tensor")
 
 
-def gp_kv(kernel: int, X, theta, s2: float, v, out=None, stream=None):
-    """pttk_gp_kv: (K(X, X; theta) + s2 I) v, kernel entries evaluated on the fly."""
+def gp_kv(kernel: int, X, theta, s2: float, v, out=None, prec="fp64", stream=None):
+    """pttk_gp_kv: (K(X, X; theta) + s2 I) v, kernel entries evaluated on the fly in FP64, or in
+    FP32 with FP64 sums of the tiles (prec="fp32")."""
     import torch
     _f64_points(X)
     if v.dtype != torch.float64 or v.numel() != X.shape[0]:
@@ -659,14 +660,14 @@ def gp_kv(kernel: int, X, theta, s2: float, v, out=None, stream=None):
     if out is None:
         out = torch.empty_like(v)
     _check(load().pttk_gp_kv(int(kernel), X.shape[1], _ptr(X), X.shape[0], _dbl(theta), float(s2), _ptr(v),
-                             _ptr(out), _stream(stream)))
+                             _ptr(out), _prec(prec), _stream(stream)))
     return out
 
 
 def gp_pcg(kernel: int, X, theta, s2: float, b, Z=None, lam=None, tol: float = 1e-10, maxit: int = 1000,
-           stream=None):
+           prec="fp64", stream=None):
     """pttk_gp_pcg: (x, iterations, relative residual) for (K + s2 I) x = b, preconditioned by
-    (Z diag(lam) Z^T + s2 I)^{-1} when Z and lam are given."""
+    (Z diag(lam) Z^T + s2 I)^{-1} when Z and lam are given; K v in the precision `prec`."""
     import torch
     _f64_points(X)
     N = X.shape[0]
@@ -680,7 +681,7 @@ def gp_pcg(kernel: int, X, theta, s2: float, b, Z=None, lam=None, tol: float = 1
     x = torch.empty_like(b)
     it, res = _int(), ctypes.c_double()
     _check(load().pttk_gp_pcg(int(kernel), X.shape[1], _ptr(X), N, _dbl(theta), float(s2), _ptr(Z) if m else None,
-                              _ptr(lam) if m else None, m, _ptr(b), _ptr(x), float(tol), int(maxit),
+                              _ptr(lam) if m else None, m, _ptr(b), _ptr(x), float(tol), int(maxit), _prec(prec),
                               ctypes.byref(it), ctypes.byref(res), _stream(stream)))
     return x, it.value, res.value
 

@@ -2,7 +2,7 @@
 (oracle/pttk_gp.py and the dense kernel):
 
   * pttk_gp_kv: (K + s2 I) v with every entry evaluated on the fly, within 1e-13 of the dense
-    product (FP64, sums of N terms);
+    product (FP64, sums of N terms), and within 1e-6 with the FP32 evaluation;
   * pttk_gp_pcg: CG preconditioned by PTTK-Global's (Z W Z^T + s2 I)^{-1}: the true residual
     ||b - A x|| (dense A, FP64) within 1e-9 ||b|| for a 1e-10 stopping test, and the same
     iteration count as the oracle's PCG with the same preconditioner, within one;
@@ -44,6 +44,45 @@ def test_gp_kv_matches_dense_product(env, kind):
     out = P.gp_kv(kind, torch.tensor(X, device="cuda"), th, s2, torch.tensor(v, device="cuda")).cpu().numpy()
     ref = o.kernel_matrix(kind, X, X, th) @ v + s2 * v
     assert np.linalg.norm(out - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("kind", [o.GAUSS, o.MATERN52])
+def test_gp_kv_fp32_and_small_n_split(env, kind):
+    """FP32 evaluation (each 128-column tile summed in FP32, tiles in FP64): within 1e-6 of the
+    dense FP64 product; N = 300 and N = 5,000 (columns split over many blocks, their partial
+    sums added in order) in FP64 within 1e-13."""
+    torch, P = env
+    for N in (300, 5000):
+        rng = np.random.default_rng(50 + N + kind)
+        X = rng.uniform(0.0, 1.0, (N, 2))
+        v = rng.standard_normal(N)
+        Xd, vd = torch.tensor(X, device="cuda"), torch.tensor(v, device="cuda")
+        ref = o.kernel_matrix(kind, X, X, (0.4,)) @ v + 1e-2 * v
+        out64 = P.gp_kv(kind, Xd, (0.4,), 1e-2, vd).cpu().numpy()
+        assert np.linalg.norm(out64 - ref) <= 1e-13 * np.linalg.norm(ref)
+        out32 = P.gp_kv(kind, Xd, (0.4,), 1e-2, vd, prec="fp32").cpu().numpy()
+        assert np.linalg.norm(out32 - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_gp_pcg_fp32_matvec(env):
+    """PCG with the FP32 K v. An FP32 operator limits what any solver can reach to a normwise
+    backward error of a few u_32 (about 1e-7): here ||b - A x|| / (||A|| ||x|| + ||b||) <= 1e-6
+    (dense FP64 A; with s2 = 1e-3 the system is ill-conditioned, ||x|| ~ 1e3 ||b||, so the
+    relative residual itself is larger), in as many iterations as the FP64 run within two."""
+    torch, P = env
+    tt, g, X, box = _global_case(P, torch)
+    th, s2 = (0.7,), 1e-3
+    Z, Wm = g.instantiate(th, 1e-6, compress=True, definite=True)
+    lam = torch.diagonal(Wm).contiguous()
+    b = np.random.default_rng(46).standard_normal(len(X))
+    Xd, bd = torch.tensor(X, device="cuda"), torch.tensor(b, device="cuda")
+    x32, it32, _ = P.gp_pcg(o.GAUSS, Xd, th, s2, bd, Z, lam, tol=1e-6, prec="fp32")
+    _, it64, _ = P.gp_pcg(o.GAUSS, Xd, th, s2, bd, Z, lam, tol=1e-6)
+    A = o.kernel_matrix(o.GAUSS, X, X, th) + s2 * np.eye(len(X))
+    xh = x32.cpu().numpy()
+    eta = np.linalg.norm(b - A @ xh) / (np.linalg.norm(A, 2) * np.linalg.norm(xh) + np.linalg.norm(b))
+    assert eta <= 1e-6, eta
+    assert abs(it32 - it64) <= 2, (it32, it64)
 
 
 def _global_case(P, torch, d=3, n=12, N=600, kind=o.GAUSS, theta_box=((0.2 * math.sqrt(3), math.sqrt(3)),),
