@@ -31,19 +31,21 @@ struct KvEps<float> {
 // The integrand is even, analytic and decays doubly exponentially, so the trapezoidal sum
 // h [1/2 + sum_{k>=1} g(k h)] converges exponentially in 1/h (Trefethen & Weideman,
 // SIAM Review 56 (2014), "The exponentially convergent trapezoidal rule"). The step is
-// halved until h <= pi^2 / (x + 38): the discretisation error behaves like
-// exp(x (1 - cos a) - 2 pi a / h) for a strip half-width a < pi/2, about e^-38 at a = pi/2.
-// Against 30-digit values the scaled result is within 1.2e-15 (relative) for
-// 0.5 <= x <= 20, nu in [0.5, 2.5], and within 2.3e-15 for 0.05 <= x <= 700, nu <= 5: the
-// rounding level of the sum. (A margin of 45 in place of 38 gives the same accuracy with
-// about 25 % more nodes for x in [1, 20].) All terms are positive, so the sum has no
+// halved until h <= pi^2 / (x + 33 + 3 nu): the discretisation error behaves like
+// exp(x cosh(t*) (1 - cos a) - 2 pi a / h) for a strip half-width a < pi/2, where t* is
+// where the integrand peaks (sinh t* ~ nu / x), so the margin grows with nu. Against
+// 30-digit values the scaled result is within 1.8e-15 (relative) for 0.5 <= x <= 20,
+// nu in [0.5, 2.5], within 1.2e-15 for 8 <= x <= 20, nu in [3, 5], and within 2.9e-15 for
+// 0.05 <= x <= 700, nu <= 5: the rounding level of the sum (a fixed margin of 60 is no
+// better). A fixed margin of 38 loses accuracy for nu > 2.5 (1.2e-14 at x = 16, nu = 5).
+// All terms are positive, so the sum has no
 // cancellation. Summation stops once a term is below KvEps::stop of the running sum on
 // the decreasing side of the integrand (x sinh t > nu), with a hard cap on nodes.
 template <typename T>
 __device__ __forceinline__ T kv_scaled(T nu, T x, const T* __restrict__ stab) {
   int q = 0;
   T h = T(KV_H0);
-  const T hmax = T(9.869604401089358) / (x + T(38));
+  const T hmax = T(9.869604401089358) / (x + T(33) + T(3) * nu);
   while (q < 4 && h > hmax) {
     h *= T(0.5);
     ++q;
