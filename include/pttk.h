@@ -16,9 +16,9 @@
  *
  * Conventions shared by every entry point
  *   - Variable order is xi = (x, theta, y); D = 2 d + d_theta (Eq. fkappa).
- *   - Boxes are arrays of (lo, hi) pairs: box[2 j] = alpha_j, box[2 j + 1] = beta_j, and
- *     lo < hi is required. The interval map is the one printed in Section 2.4,
- *     phi_[a,b](t) = ((a-b)/2) t + (a+b)/2; Chebyshev nodes are the roots of T_n.
+ *   - Boxes are arrays of (lo, hi) pairs: box[2 j] = alpha_j, box[2 j + 1] = beta_j, with
+ *     finite ends and lo < hi (else PTTK_EINVAL). The interval map is the one printed in
+ *     Section 2.4, phi_[a,b](t) = ((a-b)/2) t + (a+b)/2; Chebyshev nodes are the roots of T_n.
  *   - The coefficient tensor C (n^D entries) is stored column-major: i_1 varies fastest
  *     (the little-endian flattening of Section 2.2).
  *   - A TT core G_k has shape r_{k-1} x n x r_k, stored column-major (index
@@ -431,7 +431,7 @@ pttk_status pttk_batch_create(const pttk_tt* tt, int B, const int64_t* xoff, con
 void pttk_batch_free(pttk_batch* b);
 
 /* Launch configuration of the plan's tensor-core factor build; pttk_batch_get_config reports
- * the current one and how many exist (7). 0 (the default): the kernel that generates the A
+ * the current one and how many exist (8). 0 (the default): the kernel that generates the A
  * operand in shared memory with four separate epilogue warps, which drain two alternating
  * tensor-memory accumulators while the next tile's products run (ranks whose two accumulators
  * or staging tiles do not fit fall back to configuration 1); 1 and 2: the same kernel without
@@ -441,7 +441,7 @@ void pttk_batch_free(pttk_batch* b);
  * multicast copy (ranks it cannot hold fall back to configuration 1); 6: for the FP16/BF16
  * forms, A in tensor memory with the epilogue warps of configuration 0 and a B ring of 3-4
  * slots in the shared memory A no longer takes (ranks it cannot hold fall back to
- * configuration 0). */
+ * configuration 0); 7: configuration 0 with 64-byte chunks of K per row in a ring of 4 slots. */
 pttk_status pttk_batch_set_config(pttk_batch* b, int cfg);
 pttk_status pttk_batch_get_config(const pttk_batch* b, int* cfg, int* n_configs);
 

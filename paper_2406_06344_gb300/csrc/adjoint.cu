@@ -285,8 +285,7 @@ pttk_status grad_typed(const pttk_tt* tt, const double* theta, const T* X, int64
     th[j] = (2.0 * theta[j] - lo - hi) / (lo - hi);
   }
   PTTK_TRY(theta_core_run(tt, th, true, M, s));
-  PTTK_TRY(point_domain_check(tt, true, X, N_s, fp64, tt_status_word(tt), s));
-  PTTK_TRY(point_domain_check(tt, false, Y, N_t, fp64, tt_status_word(tt), s));
+  PTTK_TRY(point_domain_check(tt, X, N_s, Y, N_t, fp64, tt_status_word(tt), s));
   if (prec == PTTK_FP64 || prec == PTTK_FP32) {
     PTTK_TRY(factor_build_run(tt, true, X, N_s, prec, U, s));
     PTTK_TRY(factor_build_run(tt, false, Y, N_t, prec, V, s));

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -117,13 +118,19 @@ static pttk_status check_problem(int kernel, int d, const double* src_box, const
   for (int j = 0; j < d; ++j) {
     if (!(src_box[2 * j] < src_box[2 * j + 1]) || !(tgt_box[2 * j] < tgt_box[2 * j + 1]))
       return set_error(PTTK_EINVAL, "box with lo >= hi");
+    if (!std::isfinite(src_box[2 * j]) || !std::isfinite(src_box[2 * j + 1]) || !std::isfinite(tgt_box[2 * j]) ||
+        !std::isfinite(tgt_box[2 * j + 1]))
+      return set_error(PTTK_EINVAL, "box ends must be finite");
     const double g = std::max({0.0, tgt_box[2 * j] - src_box[2 * j + 1], src_box[2 * j] - tgt_box[2 * j + 1]});
     gap2 += g * g;
   }
   if (d_theta == 0 && !(gap2 > 0.0))
     return set_error(PTTK_EINVAL, "this kernel is singular at r = 0: the boxes must be apart (dist > 0)");
-  for (int j = 0; j < d_theta; ++j)
+  for (int j = 0; j < d_theta; ++j) {
     if (!(theta_box[2 * j] < theta_box[2 * j + 1])) return set_error(PTTK_EINVAL, "theta box with lo >= hi");
+    if (!std::isfinite(theta_box[2 * j]) || !std::isfinite(theta_box[2 * j + 1]))
+      return set_error(PTTK_EINVAL, "box ends must be finite");
+  }
   if (d_theta > 0 && !(theta_box[0] > 0.0)) return set_error(PTTK_EINVAL, "length scale box must be positive");
   if (kernel == PTTK_MATERN_NU && !(theta_box[2] > 0.0))
     return set_error(PTTK_EINVAL, "nu box must be positive");
@@ -507,8 +514,7 @@ pttk_status pttk_instantiate(const pttk_tt* tt, const double* theta, const void*
   PTTK_TRY(theta_hat(tt, theta, th));
   cudaStream_t s = as_stream(stream);
   PTTK_TRY(theta_core_run(tt, th, prec == PTTK_FP64, M, s));
-  PTTK_TRY(point_domain_check(tt, true, X, N_s, prec == PTTK_FP64, tt_status_word(tt), s));
-  PTTK_TRY(point_domain_check(tt, false, Y, N_t, prec == PTTK_FP64, tt_status_word(tt), s));
+  PTTK_TRY(point_domain_check(tt, X, N_s, Y, N_t, prec == PTTK_FP64, tt_status_word(tt), s));
   if (prec == PTTK_FP64 || prec == PTTK_FP32) {
     PTTK_TRY(factor_build_run(tt, true, X, N_s, prec, U, s));
     PTTK_TRY(factor_build_run(tt, false, Y, N_t, prec, V, s));

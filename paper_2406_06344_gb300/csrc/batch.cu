@@ -262,8 +262,7 @@ pttk_status pttk_instantiate_batched(const pttk_batch* b, const double* thetas, 
   else
     { store_batched_rowmajor<float><<<blocks_for((int64_t)B * rs * rt), 256, 0, s>>>(H, rs, rt, B, static_cast<float*>(M)); pttk::count_launch(); }
   PTTK_CUDA(cudaGetLastError());
-  PTTK_TRY(point_domain_check(tt, true, X, b->Ns, b->prec == PTTK_FP64, status, s));
-  PTTK_TRY(point_domain_check(tt, false, Y, b->Nt, b->prec == PTTK_FP64, status, s));
+  PTTK_TRY(point_domain_check(tt, X, b->Ns, Y, b->Nt, b->prec == PTTK_FP64, status, s));
   if (tc_form(b->prec))
     return factor_build_tc(tt, tt_tc_cache(tt), static_cast<const float*>(X), b->Ns, static_cast<const float*>(Y),
                            b->Nt, b->prec, static_cast<float*>(U), static_cast<float*>(V), status, b->cfg, s);

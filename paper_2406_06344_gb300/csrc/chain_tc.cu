@@ -584,7 +584,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
     // coordinates of this row for the next tile to build; xn[3]: the seed coordinate
     float xn[4] = {0.f, 0.f, 0.f, 0.f};
     if (part == 0 && blockIdx.x < ntiles) {
-      for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
+      #pragma unroll
+      for (int si = 0; si < 3; ++si)
+        if (si < nsteps) xn[si] = coord_of(blockIdx.x, si);
       xn[3] = seed_coord_of(blockIdx.x);
       basis(blockIdx.x >= a.T0 ? 1 : 0, 0, 0, xn[0]);
       write_seed(blockIdx.x, xn[3]);
@@ -598,10 +600,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
       const int sd = it >= a.T0 ? 1 : 0;
       const int64_t row0 = (sd ? it - a.T0 : it) * TILE_M;
       const int rows = (int)std::min<int64_t>(TILE_M, a.N[sd] - row0);
-      float xcur[3] = {xn[0], xn[1], xn[2]};
+      const float xcur1 = xn[1], xcur2 = xn[2];
       const int64_t itn = it + gridDim.x;  // next item: prefetch its coordinates
       if (part == 0 && itn < ntiles) {
-        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
+        #pragma unroll
+        for (int si = 0; si < 3; ++si)
+          if (si < nsteps) xn[si] = coord_of(itn, si);
         xn[3] = seed_coord_of(itn);
       }
       for (int si = 0; si < nsteps; ++si) {
@@ -641,7 +645,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_tc_kernel(TcArgs a) {
         // while this step's MMAs drain
         const bool last = si == nsteps - 1;
         if (part == 0) {
-          if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
+          if (!last) basis(sd, si + 1, bufsel ^ 1, si == 0 ? xcur1 : xcur2);
           else if (itn < ntiles) basis(itn >= a.T0 ? 1 : 0, 0, bufsel ^ 1, xn[0]);
         }
         if (si == 0 && out_pending) {
@@ -935,9 +939,14 @@ __global__ void __launch_bounds__(TCE_THREADS, 1) chain_tce_kernel(TcArgs a) {
         for (int k = 1; k < pad; ++k) w[k] = 0.f;
       }
     };
+    // the coordinates of the next tile are loaded one tile ahead into registers (constant
+    // indices only: a runtime-indexed array would sit in local memory, and the store into it
+    // would wait for the global load at once)
     float xn[4] = {0.f, 0.f, 0.f, 0.f};
     if (part == 0 && blockIdx.x < ntiles) {
-      for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
+#pragma unroll
+      for (int si = 0; si < 3; ++si)
+        if (si < nsteps) xn[si] = coord_of(blockIdx.x, si);
       xn[3] = seed_coord_of(blockIdx.x);
       basis(blockIdx.x >= a.T0 ? 1 : 0, 0, 0, xn[0]);
       write_seed(blockIdx.x, xn[3]);
@@ -948,10 +957,12 @@ __global__ void __launch_bounds__(TCE_THREADS, 1) chain_tce_kernel(TcArgs a) {
     for (int64_t it = blockIdx.x; it < ntiles; it += gridDim.x, ++tile) {
       const int sd = it >= a.T0 ? 1 : 0;
       const uint32_t r = tile & 1, use = tile >> 1;
-      float xcur[3] = {xn[0], xn[1], xn[2]};
+      const float xcur1 = xn[1], xcur2 = xn[2];
       const int64_t itn = it + gridDim.x;
       if (part == 0 && itn < ntiles) {
-        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
+#pragma unroll
+        for (int si = 0; si < 3; ++si)
+          if (si < nsteps) xn[si] = coord_of(itn, si);
         xn[3] = seed_coord_of(itn);
       }
       for (int si = 0; si < nsteps; ++si) {
@@ -989,7 +1000,7 @@ __global__ void __launch_bounds__(TCE_THREADS, 1) chain_tce_kernel(TcArgs a) {
         }
         const bool last = si == nsteps - 1;
         if (part == 0) {
-          if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
+          if (!last) basis(sd, si + 1, bufsel ^ 1, si == 0 ? xcur1 : xcur2);
           else if (itn < ntiles) basis(itn >= a.T0 ? 1 : 0, 0, bufsel ^ 1, xn[0]);
         }
         if (!last) {
@@ -1471,7 +1482,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_ts_kernel(TsArgs a) {
     const bool defer = nsteps > 1;
     float xn[4] = {0.f, 0.f, 0.f, 0.f};
     if (part == 0 && cid < nitems) {
-      for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(cid, si);
+      #pragma unroll
+      for (int si = 0; si < 3; ++si)
+        if (si < nsteps) xn[si] = coord_of(cid, si);
       xn[3] = seed_coord_of(cid);
       basis(item_side(cid), 0, 0, xn[0]);
       write_seed(cid, xn[3]);
@@ -1485,10 +1498,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_ts_kernel(TsArgs a) {
       const int sd = item_side(it);
       const int64_t row0 = item_row0(it);
       const int rows = (int)std::max<int64_t>(0, std::min<int64_t>(TILE_M, a.N[sd] - row0));
-      float xcur[3] = {xn[0], xn[1], xn[2]};
+      const float xcur1 = xn[1], xcur2 = xn[2];
       const int64_t itn = it + ncl;
       if (part == 0 && itn < nitems) {
-        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
+        #pragma unroll
+        for (int si = 0; si < 3; ++si)
+          if (si < nsteps) xn[si] = coord_of(itn, si);
         xn[3] = seed_coord_of(itn);
       }
       load_seed(sd);
@@ -1526,7 +1541,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) chain_ts_kernel(TsArgs a) {
         }
         const bool last = si == nsteps - 1;
         if (part == 0) {
-          if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
+          if (!last) basis(sd, si + 1, bufsel ^ 1, si == 0 ? xcur1 : xcur2);
           else if (itn < nitems) basis(item_side(itn), 0, bufsel ^ 1, xn[0]);
         }
         if (si == 0 && out_pending) {
@@ -1822,7 +1837,9 @@ __global__ void __launch_bounds__(TCE_THREADS, 1) chain_tse_kernel(TsArgs a) {
     };
     float xn[4] = {0.f, 0.f, 0.f, 0.f};
     if (part == 0 && blockIdx.x < nitems) {
-      for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(blockIdx.x, si);
+      #pragma unroll
+      for (int si = 0; si < 3; ++si)
+        if (si < nsteps) xn[si] = coord_of(blockIdx.x, si);
       xn[3] = seed_coord_of(blockIdx.x);
       basis(item_side(blockIdx.x), 0, 0, xn[0]);
       write_seed(blockIdx.x, xn[3]);
@@ -1832,10 +1849,12 @@ __global__ void __launch_bounds__(TCE_THREADS, 1) chain_tse_kernel(TsArgs a) {
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x, ++tile) {
       const int sd = item_side(it);
       const uint32_t r = tile & 1, use = tile >> 1;
-      float xcur[3] = {xn[0], xn[1], xn[2]};
+      const float xcur1 = xn[1], xcur2 = xn[2];
       const int64_t itn = it + gridDim.x;
       if (part == 0 && itn < nitems) {
-        for (int si = 0; si < nsteps; ++si) xn[si] = coord_of(itn, si);
+        #pragma unroll
+        for (int si = 0; si < 3; ++si)
+          if (si < nsteps) xn[si] = coord_of(itn, si);
         xn[3] = seed_coord_of(itn);
       }
       {
@@ -1878,7 +1897,7 @@ __global__ void __launch_bounds__(TCE_THREADS, 1) chain_tse_kernel(TsArgs a) {
         }
         const bool last = si == nsteps - 1;
         if (part == 0) {
-          if (!last) basis(sd, si + 1, bufsel ^ 1, xcur[si + 1]);
+          if (!last) basis(sd, si + 1, bufsel ^ 1, si == 0 ? xcur1 : xcur2);
           else if (itn < nitems) basis(item_side(itn), 0, bufsel ^ 1, xn[0]);
         }
         if (!last) {
@@ -2209,21 +2228,29 @@ static pttk_status build_images(const pttk_tt* tt, const TcImageCache* cache, pt
 // 1 and 2: the shared-memory kernel without them, with {KCB, NSLOT} below; 3..5: the TS kernel
 // (A in tensor memory, a ring of 3 slots) in thread-block clusters of 1, 2 or 4 CTAs, for the
 // kind::f16 forms whose ranks fit it. A configuration whose kernel cannot hold the ranks falls
-// back to configuration 1.
+// back to configuration 1. 6: A in tensor memory with the epilogue warps (falls back to 0).
+// 7: configuration 0 with 64 bytes of K per chunk row and a ring of 4 slots: the same shared
+// memory as 0's 128-byte ring of 2 at large ranks, so each core chunk's copy has three chunks
+// of products to land behind.
 static const int kTcConfigs[2][2] = {{128, 4}, {64, 4}};
 static const int kTcConfigsSplit[2][2] = {{128, 2}, {64, 4}};
-constexpr int kTceConfigs = 1, kTcSubConfigs = 2, kTsConfigs = 3, kTseConfigs = 1;
+constexpr int kTceConfigs = 1, kTcSubConfigs = 2, kTsConfigs = 3, kTseConfigs = 1, kTce64Configs = 1;
 constexpr int kTceFirst = 0, kSubFirst = kTceFirst + kTceConfigs, kTsFirst = kSubFirst + kTcSubConfigs,
-              kTseFirst = kTsFirst + kTsConfigs;
+              kTseFirst = kTsFirst + kTsConfigs, kTce64First = kTseFirst + kTseConfigs;
 static const int kTsCluster[kTsConfigs] = {1, 2, 4};
 
-int tc_config_count() { return kTseConfigs + kTceConfigs + kTcSubConfigs + kTsConfigs; }
+int tc_config_count() { return kTseConfigs + kTceConfigs + kTcSubConfigs + kTsConfigs + kTce64Configs; }
 static bool ts_form(pttk_prec p) { return p == PTTK_FP16 || p == PTTK_FP16X3 || p == PTTK_BF16 || p == PTTK_BF16X3; }
 static bool ts_config(int cfg) { return cfg >= kTsFirst && cfg < kTsFirst + kTsConfigs; }
 static int ts_cluster(int cfg) { return kTsCluster[cfg - kTsFirst]; }
 static bool tse_config(int cfg) { return cfg >= kTseFirst && cfg < kTseFirst + kTseConfigs; }
-static bool tce_config(int cfg) { return cfg >= kTceFirst && cfg < kTceFirst + kTceConfigs; }
-static int tc_sub_config(int cfg) { return cfg >= kSubFirst && cfg < kSubFirst + kTcSubConfigs ? cfg - kSubFirst : 0; }
+static bool tce_config(int cfg) {
+  return (cfg >= kTceFirst && cfg < kTceFirst + kTceConfigs) || (cfg >= kTce64First && cfg < kTce64First + kTce64Configs);
+}
+static int tc_sub_config(int cfg) {
+  if (cfg >= kTce64First && cfg < kTce64First + kTce64Configs) return 1;  // {64, 4}
+  return cfg >= kSubFirst && cfg < kSubFirst + kTcSubConfigs ? cfg - kSubFirst : 0;
+}
 
 static void tc_config(pttk_prec prec, int cfg, int* KCB, int* NS) {
   const bool split = form_split(prec);
@@ -2606,15 +2633,23 @@ pttk_status factor_build_tc(const pttk_tt* tt, TcImageCache* cache, const float*
     while (tcols < 2 * b.region_col) tcols <<= 1;
     b.tmem_cols = tcols;
     b.b_slot_bytes = (uint32_t)npad_max * KCB;
-    const size_t smem_e = (size_t)NS * parts * TILE_M * KCB + (size_t)NS * parts * b.b_slot_bytes +
-                          sizeof(float) * ((size_t)TILE_M * b.ld_s + (size_t)2 * TILE_M * bv_ld +
-                                           (size_t)TILE_M * b.ld_seed + (size_t)NEPI_WARPS * 32 * STAGE_LD) +
-                          16 + sizeof(StepS) * 6 + 8 * (3 * NS + 6) + 16;
+    auto smem_tce = [&](int ns) {
+      return (size_t)ns * parts * TILE_M * KCB + (size_t)ns * parts * b.b_slot_bytes +
+             sizeof(float) * ((size_t)TILE_M * b.ld_s + (size_t)2 * TILE_M * bv_ld + (size_t)TILE_M * b.ld_seed +
+                              (size_t)NEPI_WARPS * 32 * STAGE_LD) +
+             16 + sizeof(StepS) * 6 + 8 * (3 * ns + 6) + 16;
+    };
+    // the split forms' {128, 2} ring takes a third slot where shared memory has room for it
+    // (ranks up to ~100): each core chunk's TMA then has two chunks of MMAs to land behind
+    const bool ring3 = split && KCB == 128 && NS == 2 && smem_tce(3) <= 227 * 1024;
+    const size_t smem_e = smem_tce(ring3 ? 3 : NS);
     if (tcols <= 512 && smem_e <= 227 * 1024) {
       const size_t req = std::max<size_t>(smem_e, 116 * 1024);
       PTTK_PROF("chain_tc", s);
-#define PTTK_TCE_LAUNCH(F)                                                                        \
-  if (split) return KCB == 64 ? launch_tce<F, true, 64, 4>(b, req, s) : launch_tce<F, true, 128, 2>(b, req, s); \
+#define PTTK_TCE_LAUNCH(F)                                                                                     \
+  if (split)                                                                                                   \
+    return KCB == 64 ? launch_tce<F, true, 64, 4>(b, req, s)                                                   \
+                     : ring3 ? launch_tce<F, true, 128, 3>(b, req, s) : launch_tce<F, true, 128, 2>(b, req, s); \
   return KCB == 128 ? launch_tce<F, false, 128, 4>(b, req, s) : launch_tce<F, false, 64, 4>(b, req, s);
       if (fmt == FMT_BF16) { PTTK_TCE_LAUNCH(FMT_BF16) }
       if (fmt == FMT_FP16) { PTTK_TCE_LAUNCH(FMT_FP16) }

@@ -77,8 +77,7 @@ pttk_status pttk_fixed_create(const pttk_tt* tt, const double* X, int64_t N_s, c
   cudaStream_t s = as_stream(stream);
   const int d = tt->d, dth = tt->dtheta, n = tt->n;
   const int rs = tt->ranks[d], rt = tt->ranks[d + dth];
-  PTTK_TRY(point_domain_check(tt, true, X, N_s, true, tt_status_word(tt), s));
-  PTTK_TRY(point_domain_check(tt, false, Y, N_t, true, tt_status_word(tt), s));
+  PTTK_TRY(point_domain_check(tt, X, N_s, Y, N_t, true, tt_status_word(tt), s));
   // Phase 3: S (N_s x r_s) and T (N_t x r_t), row-major FP64
   double *U = nullptr, *V = nullptr, *Scol = nullptr;
   struct Frees {

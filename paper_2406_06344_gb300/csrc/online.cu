@@ -15,7 +15,11 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
 #include <mutex>
+#include <type_traits>
 
 #include "pttk_internal.cuh"
 
@@ -415,36 +419,144 @@ int apply_parts(int64_t N_t) {
 // records PTTK_EDOMAIN in the handle's status word if any coordinate lies outside its
 // interval by more than a relative slack of 1e-12. FP32 points are compared with the
 // FP32-rounded interval ends: rounding is monotone, so a point inside the box stays inside
-// the rounded box when it is cast.
-struct PointBox {
-  double lo[PTTK_MAX_D], hi[PTTK_MAX_D];
+// the rounded box when it is cast. Both sides are checked in one launch (blockIdx.y picks
+// the side). The pass is a plain read of the point sets (12 B per point for d = 3 in FP32),
+// so nothing in it may use the FP64 pipe, which runs at about 2 operations per clock per SM:
+//  - FP32 points are compared in FP32 with bounds rounded inwards on the host (the smallest
+//    float >= lo - slack, the largest float <= hi + slack), which accepts exactly the floats
+//    the FP64 comparison accepts;
+//  - FP64 points are compared as order-preserving 64-bit integer keys of their bit patterns.
+// A NaN coordinate fails both forms of the comparison. A side whose base is 16-byte aligned
+// and whose N d elements fill whole 16-byte units is read with 16-byte loads, else element by
+// element. The coordinate index is carried from step to step instead of taken modulo d, and
+// the bounds sit in shared memory.
+struct PointCheck {
+  const void* P[2];
+  int64_t total[2];                        // N * d elements per side
+  int vec[2];                              // 16-byte loads: base 16-byte aligned, total a multiple of 16 B
+  long long klo[2][PTTK_MAX_D], khi[2][PTTK_MAX_D];  // FP64 points: integer keys of the bounds
+  float flo[2][PTTK_MAX_D], fhi[2][PTTK_MAX_D];      // FP32 points: the bounds as floats
 };
+
+// Key of a double: a signed 64-bit integer ordered as the doubles are, with -0 and +0 equal
+// (the magnitude bits, negated for a set sign bit). A NaN's key lies beyond the keys of the
+// infinities on its sign's side, so it fails any comparison with finite bounds.
+__host__ __device__ __forceinline__ long long order_key(long long bits) {
+  return bits < 0 ? -(bits & 0x7FFFFFFFFFFFFFFFLL) : bits;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) point_domain_kernel(const T* __restrict__ P, int64_t total, int d,
-                                                           PointBox box, int* __restrict__ status) {
+__global__ void __launch_bounds__(256) point_domain_kernel(PointCheck a, int d, int* __restrict__ status) {
+  constexpr bool F64 = std::is_same_v<T, double>;
+  using B = std::conditional_t<F64, long long, float>;
+  constexpr int W = 16 / (int)sizeof(T);  // elements per 16-byte load
+  __shared__ B lo[PTTK_MAX_D], hi[PTTK_MAX_D];
+  const int side = blockIdx.y;
+  if (threadIdx.x < d) {
+    if constexpr (F64) {
+      lo[threadIdx.x] = a.klo[side][threadIdx.x];
+      hi[threadIdx.x] = a.khi[side][threadIdx.x];
+    } else {
+      lo[threadIdx.x] = a.flo[side][threadIdx.x];
+      hi[threadIdx.x] = a.fhi[side][threadIdx.x];
+    }
+  }
+  __syncthreads();
   bool bad = false;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e % d);
-    const double x = (double)P[e];
-    bad |= !(x >= box.lo[c] && x <= box.hi[c]);  // also catches NaN
+  auto check = [&](B x, int c) {
+    if constexpr (F64) bad |= order_key(x) < lo[c] || order_key(x) > hi[c];
+    else bad |= !(x >= lo[c] && x <= hi[c]);  // also catches NaN
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a.vec[side]) {
+    // e counts 16-byte units; the coordinate of the unit's first element is carried
+    const int64_t units = a.total[side] / W;
+    int c = (int)((e * W) % d);
+    const int cstep = (int)((stride * W) % d);
+    using V = std::conditional_t<F64, longlong2, float4>;
+    const V* __restrict__ P = static_cast<const V*>(a.P[side]);
+#pragma unroll 2
+    for (; e < units; e += stride) {
+      const V v = __ldg(P + e);
+      int cc = c;
+      if constexpr (F64) {
+        check(v.x, cc);
+        cc = cc + 1 == d ? 0 : cc + 1;
+        check(v.y, cc);
+      } else {
+        check(v.x, cc);
+        cc = cc + 1 == d ? 0 : cc + 1;
+        check(v.y, cc);
+        cc = cc + 1 == d ? 0 : cc + 1;
+        check(v.z, cc);
+        cc = cc + 1 == d ? 0 : cc + 1;
+        check(v.w, cc);
+      }
+      c += cstep;
+      if (c >= d) c -= d;
+    }
+  } else {
+    const int64_t total = a.total[side];
+    int c = (int)(e % d);
+    const int cstep = (int)(stride % d);
+    const B* __restrict__ P = static_cast<const B*>(a.P[side]);
+#pragma unroll 4
+    for (; e < total; e += stride) {
+      check(__ldg(P + e), c);
+      c += cstep;
+      if (c >= d) c -= d;
+    }
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(status, 0, (int)PTTK_EDOMAIN);
 }
 
-pttk_status point_domain_check(const pttk_tt* tt, bool source, const void* P, int64_t N, bool fp64, int* status,
-                               cudaStream_t s) {
-  if (N <= 0) return PTTK_OK;
-  PointBox b{};
-  for (int c = 0; c < tt->d; ++c) {
-    const int bj = source ? c : tt->d + tt->dtheta + c;
-    const double lo = tt->box[bj][0], hi = tt->box[bj][1], slack = 1e-12 * (hi - lo);
-    b.lo[c] = (fp64 ? lo : (double)(float)lo) - slack;
-    b.hi[c] = (fp64 ? hi : (double)(float)hi) + slack;
+// The smallest float >= v and the largest float <= v.
+static float float_at_or_above(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+  return f;
+}
+static float float_at_or_below(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = std::nextafter(f, -std::numeric_limits<float>::infinity());
+  return f;
+}
+static long long key_of(double v) {
+  long long bits;
+  std::memcpy(&bits, &v, sizeof bits);
+  return order_key(bits);
+}
+
+pttk_status point_domain_check(const pttk_tt* tt, const void* X, int64_t N_s, const void* Y, int64_t N_t, bool fp64,
+                               int* status, cudaStream_t s) {
+  N_s = X ? std::max<int64_t>(N_s, 0) : 0;
+  N_t = Y ? std::max<int64_t>(N_t, 0) : 0;
+  if (N_s == 0 && N_t == 0) return PTTK_OK;
+  PTTK_PROF("domain", s);
+  PointCheck a{};
+  a.P[0] = X;
+  a.P[1] = Y;
+  a.total[0] = N_s * tt->d;
+  a.total[1] = N_t * tt->d;
+  for (int side = 0; side < 2; ++side)
+    for (int c = 0; c < tt->d; ++c) {
+      const int bj = side == 0 ? c : tt->d + tt->dtheta + c;
+      const double lo = tt->box[bj][0], hi = tt->box[bj][1], slack = 1e-12 * (hi - lo);
+      a.klo[side][c] = key_of(lo - slack);
+      a.khi[side][c] = key_of(hi + slack);
+      a.flo[side][c] = float_at_or_above((double)(float)lo - slack);
+      a.fhi[side][c] = float_at_or_below((double)(float)hi + slack);
+    }
+  const int W = fp64 ? 2 : 4;
+  int64_t work = 0;
+  for (int side = 0; side < 2; ++side) {
+    a.vec[side] = (reinterpret_cast<uintptr_t>(a.P[side]) & 15) == 0 && a.total[side] % W == 0;
+    work = std::max(work, a.vec[side] ? a.total[side] / W : a.total[side]);
   }
-  const int64_t total = N * tt->d;
-  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 4);
-  if (fp64) point_domain_kernel<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(P), total, tt->d, b, status);
-  else point_domain_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(P), total, tt->d, b, status);
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)sm_count() * 4)), 2);
+  if (fp64) point_domain_kernel<double><<<grid, 256, 0, s>>>(a, tt->d, status);
+  else point_domain_kernel<float><<<grid, 256, 0, s>>>(a, tt->d, status);
   pttk::count_launch();
   PTTK_CUDA(cudaGetLastError());
   return PTTK_OK;

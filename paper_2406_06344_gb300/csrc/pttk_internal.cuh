@@ -152,10 +152,11 @@ pttk_status sym_eig_vectors(const double* A, const double* d, const double* e, c
                             const std::vector<int>& sel_z, const std::vector<double>& sel_lam,
                             const std::vector<double>& sel_w, const std::vector<int>& sel_col, double* V,
                             int ncols, cudaStream_t s);
-// One pass over N points (N x d row-major, double if fp64 else float) of the source (or
-// target) side: records PTTK_EDOMAIN in *status if a coordinate lies outside its box.
-pttk_status point_domain_check(const pttk_tt* tt, bool source, const void* P, int64_t N, bool fp64, int* status,
-                               cudaStream_t s);
+// One pass over the source points X (N_s x d) and the target points Y (N_t x d), row-major,
+// double if fp64 else float: records PTTK_EDOMAIN in *status if a coordinate lies outside
+// its box. A NULL side or a count <= 0 is skipped.
+pttk_status point_domain_check(const pttk_tt* tt, const void* X, int64_t N_s, const void* Y, int64_t N_t, bool fp64,
+                               int* status, cudaStream_t s);
 const void* oriented_core_ptr(const pttk_tt* tt, bool source, int k, bool fp64);
 int* tt_status_word(const pttk_tt* tt);
 struct TcImageCache;

@@ -1,6 +1,7 @@
 """The C-ABI library: loads, exports every declared entry point, and rejects bad
 arguments on the host (no GPU work is issued by these calls)."""
 import ctypes
+import math
 import os
 import re
 
@@ -82,6 +83,11 @@ def test_bad_box_and_tol_are_rejected(so):
     st = so.pttk_build_offline(0, 1, pttk._dbl([1, 0]), pttk._dbl([2, 3]), 1, pttk._dbl([0.5, 2]), 8,
                                1e-10, 0, None, ctypes.byref(h))
     assert st == pttk.EINVAL and "lo >= hi" in so.pttk_last_error().decode()
+    for sb, tb, pb in (([-math.inf, 1], [2, 3], [0.5, 2]), ([0, 1], [2, math.inf], [0.5, 2]),
+                       ([0, 1], [2, 3], [0.5, math.inf])):
+        st = so.pttk_build_offline(0, 1, pttk._dbl(sb), pttk._dbl(tb), 1, pttk._dbl(pb), 8, 1e-10, 0, None,
+                                   ctypes.byref(h))
+        assert st == pttk.EINVAL and "finite" in so.pttk_last_error().decode()
     s, t, p = _boxes()
     st = so.pttk_build_offline(0, 1, s, t, 1, p, 8, 0.0, 0, None, ctypes.byref(h))
     assert st == pttk.EINVAL and "tol" in so.pttk_last_error().decode()

@@ -8,6 +8,7 @@ Tolerances:
     FP32 coefficients within 2e-6 of max|C| (a few FP32 roundings of exp/K_nu values whose
     arguments reach ~20, times the O(n) transform sums).
 """
+import dataclasses
 import json
 import math
 import os
@@ -260,6 +261,38 @@ def test_points_outside_box_record_a_domain_error(P, torch_cuda, prec):
     # the status word is cleared by the check: a valid call afterwards reports OK
     P.instantiate(tt, th, torch.tensor(Xin, device="cuda", dtype=dt), torch.tensor(Yin, device="cuda", dtype=dt),
                   prec)
+    assert P.load().pttk_tt_check(tt.handle, None) == P.OK
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_domain_check_on_large_point_sets(P, torch_cuda, prec):
+    """The check strides over N x d coordinates with the coordinate index carried from step to
+    step: d = 3 boxes whose first interval ([3, 4] on the target side) differs from the others,
+    N = 400,001 points (several grid strides), one bad coordinate at a time near the start,
+    the middle and the ragged end. A bad value is chosen inside another coordinate's
+    interval, so a wrong coordinate index would miss it; NaN of either sign and -inf fail,
+    and -0.0 on a face at 0 passes."""
+    torch = torch_cuda
+    w = dataclasses.replace(W.C3, n=6)
+    tt = _gpu_tt(P, w, tol=1e-4)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    th = W.thetas(w, 1)[0]
+    N = 400_001
+    X0, Y0 = W.sources(w, N), W.targets(w, N)
+    Xd, Yd = torch.tensor(X0, device="cuda", dtype=dt), torch.tensor(Y0, device="cuda", dtype=dt)
+    P.instantiate(tt, th, Xd, Yd, prec)
+    assert P.load().pttk_tt_check(tt.handle, None) == P.OK
+    for side, i, j, v in ((1, N - 1, 1, 3.5), (1, N - 1, 2, 3.5), (1, 200_000, 0, 0.5), (1, 7, 2, 3.0),
+                          (0, N - 1, 2, 1.5), (0, 155_649, 1, -0.25), (0, 0, 0, 2.0),
+                          (0, 12_345, 1, math.nan), (1, N - 2, 0, -math.inf), (1, 3, 2, -math.nan)):
+        Xb, Yb = Xd.clone(), Yd.clone()
+        (Xb if side == 0 else Yb)[i, j] = v
+        P.instantiate(tt, th, Xb, Yb, prec)
+        assert P.load().pttk_tt_check(tt.handle, None) == P.EDOMAIN, (side, i, j, v)
+    Xz = Xd.clone()
+    Xz[N - 1, 0] = -0.0
+    Xz[0, 2] = 0.0
+    P.instantiate(tt, th, Xz, Yd, prec)
     assert P.load().pttk_tt_check(tt.handle, None) == P.OK
 
 
