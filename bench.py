@@ -51,11 +51,13 @@ NOMINAL = {"bf16": 2.25, "tf32": 1.1}
 # DRAM bytes (read + write) of one chain_tc launch of the fast form on this workload, from one
 # ncu capture of the kernel source whose SHA-256 prefix is given: the figure is reported only
 # while the source is unchanged, and null otherwise.
-NCU_TRAFFIC = {"fp16x3": {"src_sha16": "a6cd5da83c62fdb4", "bytes": 1400251352}}
+NCU_TRAFFIC = {"fp16x3": {"src_sha16": "90d8050ec85c5546", "bytes": 1398013160}}
 CHAIN_SRC = os.path.join(ROOT, "paper_2406_06344_gb300", "csrc", "chain_tc.cu")
 # executed FP64 flops per entry of the FP64 grid kernel (K_nu quadrature + in-tile transform),
-# from ncu instruction counts (DFMA x 2 + DADD + DMUL) on the n = 5 grid of the same workload
-GRID_FP64_FLOPS_PER_ENTRY = 944.0
+# from ncu instruction counts (DFMA x 2 + DADD + DMUL) on the n = 5 grid of the same workload,
+# tied like NCU_TRAFFIC to the SHA-256 prefix of the kernel sources it was counted on
+GRID_FP64_FLOPS = {"src_sha16": "e76f7e9d2b1a908d", "flops_per_entry": 903.8}
+GRID_SRC = [os.path.join(ROOT, "paper_2406_06344_gb300", "csrc", f) for f in ("kernels.cuh", "grid.cu")]
 # peak probes (pttk_peak_probe): loop trips per run, sized for tens of milliseconds
 PROBES = (("dfma", 20000), ("ffma", 200000), ("dmma", 20000), ("tf32", 200000), ("f16", 200000))
 N_ERR_THETA = 8
@@ -133,9 +135,13 @@ class Clocks:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
-def src_sha16(path: str):
+def src_sha16(path):
+    """SHA-256 prefix of a source file, or of several files concatenated in order."""
     import hashlib
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for q in ([path] if isinstance(path, str) else path):
+        h.update(open(q, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measure_peaks(P):
@@ -376,12 +382,14 @@ def main():
     prof_total = sum(v[0] for v in prof.values())
     dfma, ffma = pk["dfma"], pk["ffma"]
     # executed FP64 flops of the FP64 grid kernel: the K_nu quadrature and the in-tile transform
-    grid_fp64_flops = GRID_FP64_FLOPS_PER_ENTRY * total * args.steps * world
-    ach64 = grid_fp64_flops / (g64_ms / 1000.0) / 1e12
+    fpe = GRID_FP64_FLOPS["flops_per_entry"] if GRID_FP64_FLOPS["src_sha16"] == src_sha16(GRID_SRC) else None
+    ach64 = fpe * total * args.steps * world / (g64_ms / 1000.0) / 1e12 if fpe else None
     roof_grid_fp64 = {"kernel": "grid_tile_kernel (FP64)", "bound": "alu (FP64 FMA pipe)",
-                      "achieved": ach64, "peak": dfma, "unit": "TFLOP/s", "frac": ach64 / dfma,
+                      "achieved": ach64, "peak": dfma, "unit": "TFLOP/s", "frac": ach64 / dfma if fpe else None,
+                      "flops_per_entry": fpe,
                       "peak_note": "measured FP64 FMA rate (pttk_peak_probe DFMA, this run); executed flops per "
-                                   "entry from ncu instruction counts on the n = 5 grid of the same workload"}
+                                   "entry from ncu instruction counts on the n = 5 grid of the same workload "
+                                   "(null once the kernel sources differ from the counted ones)"}
     roof_dominant = {"kernel": dom[0], "ms_total": dom[1][0], "launches": dom[1][1],
                      "share_of_timed_kernel_time": dom[1][0] / max(prof_total, 1e-9),
                      "bound": "alu (FP64)" if dom[0] in ("jacobi", "householder", "dgemm", "grid_tile") else "tensor",

@@ -543,7 +543,10 @@ pttk_status pttk_profile_names(char* buf, int64_t len);
  *   PTTK_PROBE_DMMA  FP64 mma.sync m8n8k4, 4 independent accumulators per warp per trip;
  *   PTTK_PROBE_TF32  tcgen05.mma kind::tf32 M = 128, N = 256, K = 8, one CTA per SM, one MMA
  *                    per trip;
- *   PTTK_PROBE_F16   tcgen05.mma kind::f16 (FP16 operands) M = 128, N = 256, K = 16.
+ *   PTTK_PROBE_F16   tcgen05.mma kind::f16 (FP16 operands) M = 128, N = 256, K = 16;
+ *   PTTK_PROBE_F16S64, _F16S128, _F16S256: the same with N = 64, 128, 256 and operands that
+ *                    walk through four A and four B slots of shared memory (every MMA reads
+ *                    new operand bytes), one CTA per SM.
  * Operands are seeded nonzero values. iters in [1, 2^32]. Synchronises `stream`.
  * Errors: PTTK_EINVAL, PTTK_ECUDA, PTTK_ETIMEOUT (an MMA loop's bounded final wait ran out). */
 typedef enum pttk_probe {
@@ -551,7 +554,10 @@ typedef enum pttk_probe {
   PTTK_PROBE_FFMA = 1,
   PTTK_PROBE_DMMA = 2,
   PTTK_PROBE_TF32 = 3,
-  PTTK_PROBE_F16 = 4
+  PTTK_PROBE_F16 = 4,
+  PTTK_PROBE_F16S64 = 5,
+  PTTK_PROBE_F16S128 = 6,
+  PTTK_PROBE_F16S256 = 7
 } pttk_probe;
 pttk_status pttk_peak_probe(int kind, int64_t iters, void* stream, double* tflops, double* ms);
 

@@ -7,7 +7,9 @@
 //   FFMA   FP32 fused multiply-add, the same;
 //   DMMA   FP64 warp-level MMA (mma.sync m8n8k4), four independent accumulators per warp;
 //   TF32   tcgen05.mma kind::tf32, M = 128, N = 256, K = 8 per instruction, one CTA per SM;
-//   F16    tcgen05.mma kind::f16 (FP16 operands), M = 128, N = 256, K = 16 per instruction.
+//   F16    tcgen05.mma kind::f16 (FP16 operands), M = 128, N = 256, K = 16 per instruction;
+//   F16S*  the same with N = 64, 128 or 256 and operands that walk through four A and four B
+//          slots of shared memory (every MMA reads new operand bytes, as in a pipelined GEMM).
 // Operand values are seeded, nonzero and bounded, so the pipes switch real bits (power, and
 // hence clocks, depend on the data). Each loop runs for tens of milliseconds.
 #include <cuda_fp16.h>
@@ -145,6 +147,78 @@ __global__ void __launch_bounds__(128, 1) umma_loop_kernel(int64_t iters, int* _
 
 constexpr int kUmmaPadSmem = 120 * 1024;
 
+// Streaming-operand MMA loop: M = 128, K = 16 FP16 MMAs of width N whose operands walk through
+// 4 A slots (128 rows x 128 B) and 4 B slots (256 rows x 128 B) in the K-major no-swizzle layout
+// (core matrices 128 B apart along K, 8-row groups 1024 B apart); MMA it reads slot it % 4 at K
+// step (it / 4) % 4. One CTA per SM, one thread issues; bounded final wait as in umma_loop_kernel.
+constexpr int kStreamASlot = 128 * 128, kStreamBSlot = 256 * 128;
+constexpr int kStreamOps = 4 * (kStreamASlot + kStreamBSlot);  // 196,608 bytes
+constexpr int kStreamSmem = kStreamOps + 16;                    // + mbarrier and TMEM address
+
+__device__ __forceinline__ uint64_t stream_desc(uint32_t saddr) {
+  return umma_desc(saddr, 1024);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128, 1) umma_stream_kernel(int64_t iters, int* __restrict__ status) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStreamOps);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kStreamOps + 8);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kStreamOps / 4; i += blockDim.x) {
+    const float v = 0.25f + 0.5f * (float)((i * 2654435761u) >> 24) / 256.f;
+    reinterpret_cast<__half2*>(smem)[i] = __floats2half2_rn(v, 1.f - v);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(smem), b0 = a0 + 4 * kStreamASlot;
+    const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    for (int64_t it = 0; it < iters; ++it) {
+      const uint32_t slot = (uint32_t)(it & 3), koff = (uint32_t)((it >> 2) & 3) * 256u;  // 2 core matrices
+      const uint64_t a = stream_desc(a0 + slot * kStreamASlot + koff), b = stream_desc(b0 + slot * kStreamBSlot + koff);
+      const uint32_t acc = it > 0 ? 1u : 0u;
+      asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                   "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                   "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+    const long long t0 = clock64();
+    bool done = false;
+    while (!done) {
+      uint32_t ok;
+      asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                   "selp.u32 %0, 1, 0, p;\n\t}\n"
+                   : "=r"(ok)
+                   : "r"(smem_u32(bar))
+                   : "memory");
+      done = ok != 0;
+      if (!done && clock64() - t0 > (4ll << 30)) {
+        atomicExch(status, (int)PTTK_ETIMEOUT);
+        break;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
 }  // namespace
 }  // namespace pttk
 
@@ -152,7 +226,7 @@ extern "C" pttk_status pttk_peak_probe(int kind, int64_t iters, void* stream, do
   using namespace pttk;
   clear_error();
   if (!tflops || iters < 1 || iters > (int64_t)1 << 32) return set_error(PTTK_EINVAL, "bad probe argument");
-  if (kind < PTTK_PROBE_DFMA || kind > PTTK_PROBE_F16) return set_error(PTTK_EINVAL, "unknown probe");
+  if (kind < PTTK_PROBE_DFMA || kind > PTTK_PROBE_F16S256) return set_error(PTTK_EINVAL, "unknown probe");
   cudaStream_t s = as_stream(stream);
   const int sms = sm_count();
   int* d_status = nullptr;
@@ -165,6 +239,9 @@ extern "C" pttk_status pttk_peak_probe(int kind, int64_t iters, void* stream, do
   // their CTAs share an SM
   PTTK_CUDA(cudaFuncSetAttribute(umma_loop_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaPadSmem));
   PTTK_CUDA(cudaFuncSetAttribute(umma_loop_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaPadSmem));
+  PTTK_CUDA(cudaFuncSetAttribute(umma_stream_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem));
+  PTTK_CUDA(cudaFuncSetAttribute(umma_stream_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem));
+  PTTK_CUDA(cudaFuncSetAttribute(umma_stream_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem));
   double flops = 0.0;
   PTTK_CUDA(cudaEventRecord(e0, s));
   switch (kind) {
@@ -189,6 +266,18 @@ extern "C" pttk_status pttk_peak_probe(int kind, int64_t iters, void* stream, do
     case PTTK_PROBE_TF32:
       umma_loop_kernel<true><<<(unsigned)sms, 128, kUmmaPadSmem, s>>>(iters, d_status);
       flops = 2.0 * 128 * 256 * 8 * (double)sms * (double)iters;
+      break;
+    case PTTK_PROBE_F16S64:
+      umma_stream_kernel<64><<<(unsigned)sms, 128, kStreamSmem, s>>>(iters, d_status);
+      flops = 2.0 * 128 * 64 * 16 * (double)sms * (double)iters;
+      break;
+    case PTTK_PROBE_F16S128:
+      umma_stream_kernel<128><<<(unsigned)sms, 128, kStreamSmem, s>>>(iters, d_status);
+      flops = 2.0 * 128 * 128 * 16 * (double)sms * (double)iters;
+      break;
+    case PTTK_PROBE_F16S256:
+      umma_stream_kernel<256><<<(unsigned)sms, 128, kStreamSmem, s>>>(iters, d_status);
+      flops = 2.0 * 128 * 256 * 16 * (double)sms * (double)iters;
       break;
     default:
       umma_loop_kernel<false><<<(unsigned)sms, 128, kUmmaPadSmem, s>>>(iters, d_status);

@@ -708,8 +708,9 @@ def apply_noalloc(U, M, V, w, out, stream=None):
     return out
 
 
-PROBE_DFMA, PROBE_FFMA, PROBE_DMMA, PROBE_TF32, PROBE_F16 = range(5)
-PROBE_NAMES = {"dfma": PROBE_DFMA, "ffma": PROBE_FFMA, "dmma": PROBE_DMMA, "tf32": PROBE_TF32, "f16": PROBE_F16}
+PROBE_DFMA, PROBE_FFMA, PROBE_DMMA, PROBE_TF32, PROBE_F16, PROBE_F16S64, PROBE_F16S128, PROBE_F16S256 = range(8)
+PROBE_NAMES = {"dfma": PROBE_DFMA, "ffma": PROBE_FFMA, "dmma": PROBE_DMMA, "tf32": PROBE_TF32, "f16": PROBE_F16,
+               "f16s64": PROBE_F16S64, "f16s128": PROBE_F16S128, "f16s256": PROBE_F16S256}
 
 
 def peak_probe(kind, iters: int, stream=None):
