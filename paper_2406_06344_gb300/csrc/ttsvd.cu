@@ -333,6 +333,26 @@ __global__ void gather_rt_kernel(const double* __restrict__ Rp, int64_t N, int k
   }
 }
 
+// Rd[i + k * l] = R[i, l] = Rp[i + N * perm[l]] for i < k, l < N: the kept rows of R, dense,
+// in pivoted column order
+__global__ void gather_r_kernel(const double* __restrict__ Rp, int64_t N, int k, const int* __restrict__ perm,
+                                double* __restrict__ Rd) {
+  const int64_t total = N * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % k, l = e / k;
+    Rd[e] = Rp[i + N * (int64_t)perm[l]];
+  }
+}
+
+// V = I (n x n, column-major)
+__global__ void eye_kernel(double* __restrict__ V, int64_t n) {
+  const int64_t total = n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    V[e] = (e % n == e / n) ? 1.0 : 0.0;
+}
+
 __global__ void iota_kernel(int* __restrict__ p, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -355,7 +375,10 @@ __global__ void iota_kernel(int* __restrict__ p, int64_t n) {
 // < 1e-4 delta^2 in total, so they change neither the kept subspace nor, except within that
 // margin of the threshold, the truncation rank.
 // Columns and norms written by other blocks in earlier rounds are read through L2 (ld.cg),
-// never from a possibly stale L1 line.
+// never from a possibly stale L1 line. A pair's alpha and beta are read from colsq[] (the
+// squared norms its last rotation, or the initial pass, summed from the stored columns), so the
+// first pass over the pair only forms gamma = a.b. When V is given (vrows x ncols), every
+// rotation is applied to V's columns as well, accumulating the right rotation.
 constexpr int JB = 256;            // threads per block
 constexpr int JU = 8;              // rows per lane per load batch
 constexpr int JMAX_SWEEPS = 60;
@@ -408,7 +431,8 @@ __device__ bool grid_barrier(JacobiSync* js, unsigned nblocks) {
 __global__ void __launch_bounds__(JB) jacobi_kernel(double* __restrict__ A, int64_t rows, int ncols,
                                                     int p, double tol, double small2, double count2,
                                                     double* __restrict__ colsq,
-                                                    JacobiSync* __restrict__ js) {
+                                                    JacobiSync* __restrict__ js, double* __restrict__ V,
+                                                    int64_t vrows) {
   const unsigned nb = gridDim.x;
   const int npairs = p / 2;
   const int lane = threadIdx.x & 31;
@@ -433,12 +457,13 @@ __global__ void __launch_bounds__(JB) jacobi_kernel(double* __restrict__ A, int6
           b = t;
         }
         if (b >= ncols) continue;  // dummy player when ncols is odd
-        if (__ldcg(colsq + a) < small2 && __ldcg(colsq + b) < small2) continue;
+        const double al = __ldcg(colsq + a), be = __ldcg(colsq + b);
+        if (al < small2 && be < small2) continue;
         double* ca = A + (int64_t)a * rows;
         double* cb = A + (int64_t)b * rows;
         // JU rows per lane per iteration, all loads issued before the arithmetic, so that the
         // L2 latency is paid once per JU rows
-        double al = 0.0, be = 0.0, ga = 0.0;
+        double ga = 0.0;
         for (int64_t i0 = lane; i0 < rows; i0 += 32 * JU) {
           double x[JU], y[JU];
 #pragma unroll
@@ -448,14 +473,8 @@ __global__ void __launch_bounds__(JB) jacobi_kernel(double* __restrict__ A, int6
             y[u] = i < rows ? __ldcg(cb + i) : 0.0;
           }
 #pragma unroll
-          for (int u = 0; u < JU; ++u) {
-            al = fma(x[u], x[u], al);
-            be = fma(y[u], y[u], be);
-            ga = fma(x[u], y[u], ga);
-          }
+          for (int u = 0; u < JU; ++u) ga = fma(x[u], y[u], ga);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
         ga = warp_sum(ga);
         if (!(al > 0.0) || !(be > 0.0) || !(fabs(ga) > tol * sqrt(al) * sqrt(be))) continue;
         const double zeta = (be - al) / (2.0 * ga);
@@ -480,6 +499,27 @@ __global__ void __launch_bounds__(JB) jacobi_kernel(double* __restrict__ A, int6
             }
             na = fma(xa, xa, na);
             nbb = fma(yb, yb, nbb);
+          }
+        }
+        if (V) {
+          double* va = V + (int64_t)a * vrows;
+          double* vb = V + (int64_t)b * vrows;
+          for (int64_t i0 = lane; i0 < vrows; i0 += 32 * JU) {
+            double x[JU], y[JU];
+#pragma unroll
+            for (int u = 0; u < JU; ++u) {
+              const int64_t i = i0 + 32 * u;
+              x[u] = i < vrows ? __ldcg(va + i) : 0.0;
+              y[u] = i < vrows ? __ldcg(vb + i) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < JU; ++u) {
+              const int64_t i = i0 + 32 * u;
+              if (i < vrows) {
+                va[i] = cs * x[u] - sn * y[u];
+                vb[i] = sn * x[u] + cs * y[u];
+              }
+            }
           }
         }
         na = warp_sum(na);
@@ -699,7 +739,8 @@ pttk_status householder_qrcp(double* A, int64_t M, int64_t N, double stop2, doub
 }
 
 static pttk_status launch_jacobi(double* A, int64_t rows, int ncols, int p, double tol, double small2,
-                                 double count2, double* colsq, JacobiSync* js, cudaStream_t s) {
+                                 double count2, double* colsq, JacobiSync* js, double* V, int64_t vrows,
+                                 cudaStream_t s) {
   int per_sm = 0;
   PTTK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JB, 0));
   if (per_sm < 1) return set_error(PTTK_ECUDA, "Jacobi kernel cannot be resident");
@@ -707,15 +748,17 @@ static pttk_status launch_jacobi(double* A, int64_t rows, int ncols, int p, doub
   // round at a time, pairs dealt round-robin over the blocks
   const int want = p / 2;
   const unsigned grid = (unsigned)std::max(1, std::min(want, sm_count()));
-  void* args[] = {&A, &rows, &ncols, &p, &tol, &small2, &count2, &colsq, &js};
+  void* args[] = {&A, &rows, &ncols, &p, &tol, &small2, &count2, &colsq, &js, &V, &vrows};
   PTTK_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(JB), args, 0, s));
   pttk::count_launch();
   return PTTK_OK;
 }
 
 // One-sided Jacobi on the columns of A (rows x ncols), all sweeps in one cooperative launch;
-// synchronises `s` once to read the outcome.
-pttk_status jacobi(double* A, int64_t rows, int ncols, cudaStream_t s, double small = 0.0) {
+// synchronises `s` once to read the outcome. With V (vrows x ncols), every rotation is also
+// applied to V's columns.
+pttk_status jacobi(double* A, int64_t rows, int ncols, cudaStream_t s, double small = 0.0, double* V = nullptr,
+                   int64_t vrows = 0) {
   if (ncols < 2) return PTTK_OK;
   Buf colsq, state;
   PTTK_TRY(colsq.alloc(ncols));
@@ -733,7 +776,7 @@ pttk_status jacobi(double* A, int64_t rows, int ncols, cudaStream_t s, double sm
   const double tol = sqrt((double)std::max<int64_t>(rows, 16)) * 2.220446049250313e-16;
   {
     PTTK_PROF("jacobi", s);
-    PTTK_TRY(launch_jacobi(A, rows, ncols, p, tol, small2, count2, colsq.p, js, s));
+    PTTK_TRY(launch_jacobi(A, rows, ncols, p, tol, small2, count2, colsq.p, js, V, vrows, s));
   }
   JacobiSync h{};
   PTTK_CUDA(cudaMemcpyAsync(&h, js, sizeof(JacobiSync), cudaMemcpyDeviceToHost, s));
@@ -803,11 +846,13 @@ struct StageClock {
 
 // Working buffers of svd_basis, reused (reallocated) from call to call.
 struct StepWork {
-  Buf qrin, A, U, Y, Yt, norms, part, wpart, wv, below, R;
+  Buf qrin, A, U, Y, Yt, norms, part, wpart, wv, below, R, A0, Rd, V, PV;
   int* d_perm = nullptr;
+  int* d_perm2 = nullptr;
   HHState* d_hs = nullptr;
   ~StepWork() {
     if (d_perm) cudaFree(d_perm);
+    if (d_perm2) cudaFree(d_perm2);
     if (d_hs) cudaFree(d_hs);
   }
 };
@@ -865,7 +910,39 @@ static pttk_status svd_basis(const double* X, int64_t m, int64_t c, double delta
   // vectors of R1 (= of the pivoted QR input, up to the discarded R22) are the normalised
   // columns of the rotated R1^T; columns below (stop_frac / 30) delta / sqrt(kq) together carry
   // < (stop_frac / 30)^2 delta^2, and pairs of them are skipped
-  PTTK_TRY(jacobi(wk.A.p, q, kq, s, (stop_frac / 30.0) * delta / sqrt((double)kq)));
+  const double jsmall = (stop_frac / 30.0) * delta / sqrt((double)kq);
+  if (2 * q >= 5 * (int64_t)kq && kq >= 2) {
+    // R1^T has at least 2.5 times as many rows as columns: a second pivoted QR,
+    // R1^T P2 = Q2 R2, and the Jacobi on R2 (kq x kq), whose columns have the Gram matrix of
+    // R1^T P2's and so take the same rotations, accumulated in V; the rotated R1^T is then
+    // R1^T (P2 V), one DGEMM. Each rotation touches 2 kq rows (R2 and V) instead of q. The
+    // second QR and the fixed cost of a Jacobi round (L2 round trips, grid barrier) eat the
+    // gain below that ratio (c3: 2124 x 751 254 -> 201 ms, 1728 x 256 46 -> 37 ms, but
+    // 528 x 236 21 -> 27 ms).
+    PTTK_TRY(wk.A0.alloc(q * kq));
+    PTTK_CUDA(cudaMemcpyAsync(wk.A0.p, wk.A.p, sizeof(double) * q * kq, cudaMemcpyDeviceToDevice, s));
+    if (wk.d_perm2) cudaFree(wk.d_perm2);
+    wk.d_perm2 = nullptr;
+    PTTK_CUDA(cudaMalloc(&wk.d_perm2, sizeof(int) * kq));
+    int k2 = 0;
+    double t2 = 0.0;
+    // the first QR's work buffers are large enough (its rows >= q, its columns q >= kq), and
+    // its R has been consumed into wk.A; stop2 < 0: every column is factored
+    PTTK_TRY(householder_qrcp(wk.A.p, q, kq, -1.0, wk.R.p, wk.d_perm2, wk.part.p, wk.below.p, wk.wpart.p, wk.wv.p,
+                              wk.d_hs, &k2, &t2, s));
+    PTTK_TRY(wk.Rd.alloc((int64_t)k2 * kq));
+    gather_r_kernel<<<grid1d((int64_t)k2 * kq, 256), 256, 0, s>>>(wk.R.p, kq, k2, wk.d_perm2, wk.Rd.p); pttk::count_launch();
+    PTTK_TRY(wk.V.alloc((int64_t)kq * kq));
+    PTTK_TRY(wk.PV.alloc((int64_t)kq * kq));
+    eye_kernel<<<grid1d((int64_t)kq * kq, 256), 256, 0, s>>>(wk.V.p, kq); pttk::count_launch();
+    PTTK_TRY(jacobi(wk.Rd.p, k2, kq, s, jsmall, wk.V.p, kq));
+    // P2 V: row perm2[l] of the result is row l of V
+    scatter_rows_kernel<<<grid1d((int64_t)kq * kq, 256), 256, 0, s>>>(wk.V.p, kq, kq, wk.d_perm2, wk.PV.p); pttk::count_launch();
+    dgemm(false, false, q, kq, kq, 1.0, wk.A0.p, q, wk.PV.p, kq, 0.0, wk.A.p, q, s);
+    PTTK_CUDA(cudaGetLastError());
+  } else {
+    PTTK_TRY(jacobi(wk.A.p, q, kq, s, jsmall));
+  }
   clk.mark(k, "jacobi");
   colnorm_kernel<<<(unsigned)(((int64_t)kq * 32 + 255) / 256), 256, 0, s>>>(wk.A.p, q, kq, wk.norms.p); pttk::count_launch();
   std::vector<double> sigma(kq);
