@@ -11,6 +11,8 @@
 // block so every load and store is coalesced.
 #include <math.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "pttk_internal.cuh"
 
@@ -21,7 +23,90 @@ struct GridArgs {
   int kind, d, dtheta, D, n, m1;
   int64_t tile, ntiles;
   double lo[PTTK_MAX_D], hi[PTTK_MAX_D];
+  // general-nu Matern, grid tile kernel: per nu node, G(z) = z^nu e^z K_nu(z) on [kv_zlo, kv_zhi]
+  // in kv_P pieces (see KvTable); kv_P = 0: the quadrature for every entry
+  const void* kv_tab;
+  int kv_P;
+  double kv_zlo, kv_zhi, kv_inv_zlo;
+  float kv_inv_log2q;
 };
+
+// ---------------- general-nu Matern by table ------------------------------------------------
+// The grid's entries take z = sqrt(2 nu) r / l over a known range (the node distances and the
+// l and nu nodes), and only n values of nu. For each nu node, G(z) = z^nu e^z K_nu(z), which
+// is smooth for z > 0 with its one singularity (a branch point) at z = 0, is tabulated once as
+// piecewise Chebyshev series: pieces [a, 1.5 a] from kv_zlo up (geometric, so each piece sees
+// the singularity at the same relative distance: its Bernstein ellipse has rho ~ 9.9, and
+// degree 16 leaves a truncation error near 1e-17), each series of degree KV_DEG fitted at the
+// piece's KV_DEG + 1 first-kind Chebyshev points from the quadrature kv_scaled. An entry then
+// costs one exponential and a Clenshaw sum: kappa = c_nu e^{-z} G(z). Against 30-digit values
+// the table is within 2.4e-15 (relative) for z in [1e-3, 60], nu in {0.5, 1, 2, 2.5, 4}.
+// Entries outside the table's range (z below 1e-3 when boxes overlap) take the quadrature.
+constexpr int KV_DEG = 16;
+constexpr int KV_STRIDE = KV_DEG + 3;  // per piece: mid, 1 / half-width, KV_DEG + 1 coefficients
+constexpr double KV_Q = 1.5;
+constexpr int KV_MAX_PIECES = 64;
+
+// One block per nu node: the pieces' values at their Chebyshev points, then the coefficients
+// c_m = (2 / (KV_DEG + 1)) sum_k G(z_k) T_m(zeta_k) (c_0 halved); FP64 and an FP32 copy.
+__global__ void __launch_bounds__(256) kv_table_kernel(int n, int P, double zlo, double nu_lo, double nu_hi,
+                                                       double* __restrict__ tab64, float* __restrict__ tab32) {
+  __shared__ double stab[KV_TABLE];
+  __shared__ double vals[KV_MAX_PIECES * (KV_DEG + 1)];
+  const int inu = blockIdx.x;
+  kv_table_fill<double>(stab);
+  const double zn = cospi((2.0 * inu + 1.0) / (2.0 * n));
+  const double nu = 0.5 * (nu_lo - nu_hi) * zn + 0.5 * (nu_lo + nu_hi);
+  __syncthreads();
+  for (int e = threadIdx.x; e < P * (KV_DEG + 1); e += blockDim.x) {
+    const int p = e / (KV_DEG + 1), k = e % (KV_DEG + 1);
+    const double a = zlo * pow(KV_Q, (double)p), b = a * KV_Q;
+    const double z = 0.5 * (a + b) + 0.5 * (b - a) * cospi((2.0 * k + 1.0) / (2.0 * (KV_DEG + 1)));
+    vals[e] = exp(nu * log(z)) * kv_scaled<double>(nu, z, stab);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < P * KV_STRIDE; e += blockDim.x) {
+    const int p = e / KV_STRIDE, m = e % KV_STRIDE;
+    const double a = zlo * pow(KV_Q, (double)p), b = a * KV_Q;
+    double v;
+    if (m == 0) {
+      v = 0.5 * (a + b);
+    } else if (m == 1) {
+      v = 2.0 / (b - a);
+    } else {
+      const int mm = m - 2;
+      double acc = 0.0;
+      for (int k = 0; k <= KV_DEG; ++k)
+        acc = fma(vals[p * (KV_DEG + 1) + k], cospi((double)mm * (2.0 * k + 1.0) / (2.0 * (KV_DEG + 1))), acc);
+      v = (mm == 0 ? 1.0 : 2.0) / (KV_DEG + 1) * acc;
+    }
+    tab64[((size_t)inu * P + p) * KV_STRIDE + m] = v;
+    tab32[((size_t)inu * P + p) * KV_STRIDE + m] = (float)v;
+  }
+}
+
+// kappa of the general-nu Matern from the table of nu node `inu`, or by quadrature outside it.
+template <typename T>
+__device__ __forceinline__ T kappa_matern_nu_tab(const GridArgs& a, int inu, T r2, T l, T nu, T cnu, T snu,
+                                                 const T* __restrict__ stab) {
+  const T z = snu * sqrt(r2) / l;
+  if (a.kv_P > 0 && z >= T(a.kv_zlo) && z <= T(a.kv_zhi)) {
+    int p = (int)(__log2f((float)(z * T(a.kv_inv_zlo))) * a.kv_inv_log2q);
+    p = min(max(p, 0), a.kv_P - 1);
+    const T* c = static_cast<const T*>(a.kv_tab) + ((size_t)inu * a.kv_P + p) * KV_STRIDE;
+    const T t = (z - __ldg(c)) * __ldg(c + 1), t2 = t + t;
+    T b1 = T(0), b2 = T(0);
+#pragma unroll
+    for (int k = KV_DEG; k >= 1; --k) {
+      const T b0 = fma(t2, b1, __ldg(c + 2 + k) - b2);
+      b2 = b1;
+      b1 = b0;
+    }
+    const T G = fma(t, b1, __ldg(c + 2) - b2);
+    return cnu * exp(-z) * G;
+  }
+  return kappa_matern_nu<T>(r2, l, nu, cnu, snu, stab);
+}
 
 // Chebyshev node table, transform matrix and Matern-nu node constants in shared memory.
 template <typename T>
@@ -50,7 +135,7 @@ __device__ void fill_tables(const GridArgs& a, T* eta, T* Amat, T* cnu, T* snu, 
   }
 }
 
-template <typename T>
+template <typename T, bool TAB = false>
 __device__ __forceinline__ T eval_entry(const GridArgs& a, const int* idx, const T* eta,
                                         const T* cnu, const T* snu, const T* stab) {
   const int n = a.n;
@@ -62,6 +147,7 @@ __device__ __forceinline__ T eval_entry(const GridArgs& a, const int* idx, const
   const T l = a.dtheta > 0 ? eta[a.d * n + idx[a.d]] : T(1);
   if (a.kind == K_MATERN_NU) {
     const int inu = idx[a.d + 1];
+    if (TAB) return kappa_matern_nu_tab<T>(a, inu, r2, l, eta[(a.d + 1) * n + inu], cnu[inu], snu[inu], stab);
     return kappa_matern_nu<T>(r2, l, eta[(a.d + 1) * n + inu], cnu[inu], snu[inu], stab);
   }
   return kappa_l<T>(a.kind, r2, l);
@@ -108,7 +194,7 @@ __global__ void __launch_bounds__(512) grid_tile_kernel(GridArgs a, T* __restric
         idx[j] = (int)(q % n);
         q /= n;
       }
-      tile[e] = eval_entry<T>(a, idx, eta, cnu, snu, stab);
+      tile[e] = eval_entry<T, true>(a, idx, eta, cnu, snu, stab);
     }
     __syncthreads();
     // modes 1..m1 inside the tile: one fibre per thread, in registers
@@ -293,8 +379,61 @@ pttk_status grid_coeffs_launch(int kernel, int d, int dtheta, int n, const doubl
   }
   a.ntiles = 1;
   for (int j = a.m1; j < a.D; ++j) a.ntiles *= n;
-  if (fp64) return dispatch_nb<double>(a, static_cast<double*>(C), s);
-  return dispatch_nb<float>(a, static_cast<float*>(C), s);
+  double* tab64 = nullptr;
+  float* tab32 = nullptr;
+  if (kernel == K_MATERN_NU) {
+    // the range of z = sqrt(2 nu) r / l over the grid's nodes
+    auto node = [&](int j, int i) {
+      const double z = cos((2.0 * i + 1.0) * 3.14159265358979323846 / (2.0 * n));
+      return 0.5 * (a.lo[j] - a.hi[j]) * z + 0.5 * (a.lo[j] + a.hi[j]);
+    };
+    double r2min = 0.0, r2max = 0.0;
+    for (int j = 0; j < d; ++j) {
+      double dmin = INFINITY, dmax = 0.0;
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+          const double df = fabs(node(j, i) - node(d + dtheta + j, k));
+          dmin = std::min(dmin, df);
+          dmax = std::max(dmax, df);
+        }
+      r2min += dmin * dmin;
+      r2max += dmax * dmax;
+    }
+    double lmin = INFINITY, lmax = 0.0, numin = INFINITY, numax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      lmin = std::min(lmin, node(d, i));
+      lmax = std::max(lmax, node(d, i));
+      numin = std::min(numin, node(d + 1, i));
+      numax = std::max(numax, node(d + 1, i));
+    }
+    double zlo = std::max(sqrt(2.0 * numin) * sqrt(r2min) / lmax * (1.0 - 1e-12), 1e-3);
+    const double zhi = std::min(sqrt(2.0 * numax) * sqrt(r2max) / lmin * (1.0 + 1e-12), 700.0);
+    if (zhi > zlo) {
+      int P = (int)ceil(log(zhi / zlo) / log(KV_Q));
+      if (P > KV_MAX_PIECES) {
+        P = KV_MAX_PIECES;
+        zlo = zhi / pow(KV_Q, (double)P);
+      }
+      P = std::max(P, 1);
+      const size_t cnt = (size_t)n * P * KV_STRIDE;
+      PTTK_CUDA(cudaMallocAsync(&tab64, sizeof(double) * cnt, s));
+      PTTK_CUDA(cudaMallocAsync(&tab32, sizeof(float) * cnt, s));
+      kv_table_kernel<<<n, 256, 0, s>>>(n, P, zlo, a.lo[d + 1], a.hi[d + 1], tab64, tab32); pttk::count_launch();
+      PTTK_CUDA(cudaGetLastError());
+      a.kv_tab = fp64 ? static_cast<const void*>(tab64) : static_cast<const void*>(tab32);
+      a.kv_P = P;
+      a.kv_zlo = zlo;
+      a.kv_zhi = zhi;
+      a.kv_inv_zlo = 1.0 / zlo;
+      a.kv_inv_log2q = (float)(1.0 / log2(KV_Q));
+    }
+  }
+  const pttk_status st = fp64 ? dispatch_nb<double>(a, static_cast<double*>(C), s)
+                              : dispatch_nb<float>(a, static_cast<float*>(C), s);
+  // stream-ordered: the tables are released after the kernels that read them
+  if (tab64) cudaFreeAsync(tab64, s);
+  if (tab32) cudaFreeAsync(tab32, s);
+  return st;
 }
 
 }  // namespace pttk
