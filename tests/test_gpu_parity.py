@@ -87,15 +87,29 @@ def test_coefficients_fp32(P, name, n):
 
 
 def test_matern_nu_kernel_values_over_wide_range(P):
-    # K_nu over z ~ 0.03 .. 60 and nu in [0.5, 2.5]: a 1-D source box close to a long
-    # target box; n = 16 puts nodes densely through the range
-    import dataclasses
+    # K_nu over z ~ 0.03 .. 130 and nu in [0.5, 2.5]: a 1-D source box close to a long
+    # target box; n = 9 puts nodes through the range (the grid's per-nu table spans ~21 pieces)
     w = dataclasses.replace(W.C3, d=1, src_box=((0.0, 0.05),), tgt_box=((0.1, 30.0),), n=9,
                             theta_box=((0.5, 2.0), (0.5, 2.5)))
     M = o.grid_tensor(o.kernel_f(w.kernel), w.d, w.dtheta, w.mode_boxes(), w.n)
     C = o.coefficient_tensor(M, w.n).ravel(order="F")
     Cg = gpu_coeffs(P, w, "fp64")
     assert np.abs(Cg - C).max() <= 1e-13 * np.abs(C).max()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_matern_nu_on_nearly_one_box(P, prec, tol):
+    """Target box = source box shifted by 0.001 in x_1: node distances reach 0.001, so z
+    runs from about 5e-4 (below the per-nu table's floor of 1e-3: those entries take the
+    quadrature) to about 4 (the table). The oracle's z^nu K_nu(z) form has no value at
+    z = 0 itself, so the boxes are not made identical."""
+    w = dataclasses.replace(W.C3, d=2, src_box=((0.0, 1.0), (0.0, 1.0)), tgt_box=((0.001, 1.001), (0.0, 1.0)),
+                            n=6, theta_box=((0.5, 2.0), (0.5, 2.5)))
+    M = o.grid_tensor(o.kernel_f(w.kernel), w.d, w.dtheta, w.mode_boxes(), w.n)
+    C = o.coefficient_tensor(M, w.n).ravel(order="F")
+    assert np.all(np.isfinite(C))
+    Cg = gpu_coeffs(P, w, prec).astype(np.float64)
+    assert np.abs(Cg - C).max() <= tol * np.abs(C).max()
 
 
 # --- TT-SVD ---------------------------------------------------------------------------
