@@ -56,7 +56,7 @@ CHAIN_SRC = os.path.join(ROOT, "paper_2406_06344_gb300", "csrc", "chain_tc.cu")
 # executed FP64 flops per entry of the FP64 grid kernel (K_nu quadrature + in-tile transform),
 # from ncu instruction counts (DFMA x 2 + DADD + DMUL) on the n = 5 grid of the same workload,
 # tied like NCU_TRAFFIC to the SHA-256 prefix of the kernel sources it was counted on
-GRID_FP64_FLOPS = {"src_sha16": "e75a015bed45e41c", "flops_per_entry": 187.9}
+GRID_FP64_FLOPS = {"src_sha16": "575d6e63341b7f92", "flops_per_entry": 187.9}
 GRID_SRC = [os.path.join(ROOT, "paper_2406_06344_gb300", "csrc", f) for f in ("kernels.cuh", "grid.cu")]
 # peak probes (pttk_peak_probe): loop trips per run, sized for tens of milliseconds
 PROBES = (("dfma", 20000), ("ffma", 200000), ("dmma", 20000), ("tf32", 200000), ("f16", 200000))

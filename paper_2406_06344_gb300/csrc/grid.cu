@@ -379,8 +379,19 @@ pttk_status grid_coeffs_launch(int kernel, int d, int dtheta, int n, const doubl
   }
   a.ntiles = 1;
   for (int j = a.m1; j < a.D; ++j) a.ntiles *= n;
-  double* tab64 = nullptr;
-  float* tab32 = nullptr;
+  // the per-nu tables live until the kernels that read them have run: released stream-ordered
+  // on every return path
+  struct Tables {
+    double* t64 = nullptr;
+    float* t32 = nullptr;
+    cudaStream_t s;
+    ~Tables() {
+      if (t64) cudaFreeAsync(t64, s);
+      if (t32) cudaFreeAsync(t32, s);
+    }
+  } tabs{nullptr, nullptr, s};
+  double*& tab64 = tabs.t64;
+  float*& tab32 = tabs.t32;
   if (kernel == K_MATERN_NU) {
     // the range of z = sqrt(2 nu) r / l over the grid's nodes
     auto node = [&](int j, int i) {
@@ -428,12 +439,7 @@ pttk_status grid_coeffs_launch(int kernel, int d, int dtheta, int n, const doubl
       a.kv_inv_log2q = (float)(1.0 / log2(KV_Q));
     }
   }
-  const pttk_status st = fp64 ? dispatch_nb<double>(a, static_cast<double*>(C), s)
-                              : dispatch_nb<float>(a, static_cast<float*>(C), s);
-  // stream-ordered: the tables are released after the kernels that read them
-  if (tab64) cudaFreeAsync(tab64, s);
-  if (tab32) cudaFreeAsync(tab32, s);
-  return st;
+  return fp64 ? dispatch_nb<double>(a, static_cast<double*>(C), s) : dispatch_nb<float>(a, static_cast<float*>(C), s);
 }
 
 }  // namespace pttk
