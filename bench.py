@@ -163,6 +163,62 @@ def chain_flops(ranks, d, dtheta, n, N):
     return 2.0 * n * N * (src + tgt)
 
 
+def kernel_rooflines(prof, steps, ranks, d, dtheta, n, N, hbm, dfma):
+    """A fraction of a measured peak for each kernel group of kernel_ms, from the workload's
+    sizes (prof: name -> (total ms, launches) over `steps` bench steps; hbm in GB/s, dfma in
+    TFLOP/s):
+    - apply, domain, mode_transform: HBM bytes (FP32 factors; FP32 points; one FP64 and one
+      FP32 grid, each with its D - m1 = 4 strided passes that read and write every entry);
+    - dgemm: FP64 flops of the TT-SVD's projections X <- G_k^T X alone, so its fraction is a
+      lower bound (the tall steps' X V products and the preconditioned Jacobi's R1^T (P2 V)
+      are not counted);
+    - householder, jacobi, theta_core: null, with the reason (their work depends on the QR's
+      stopping step, the Jacobi's sweeps, or is latency-bound)."""
+    D = 2 * d + dtheta
+    total = float(n) ** D
+    rs, rt = ranks[d], ranks[d + dtheta]
+
+    def ms_of(name):
+        ms, cnt = prof.get(name, (0.0, 0))
+        return ms, cnt
+
+    out = {}
+
+    def hbm_entry(name, bytes_total, note):
+        ms, cnt = ms_of(name)
+        if not cnt or ms <= 0:
+            return
+        gbs = bytes_total / (ms / 1000.0) / 1e9
+        out[name] = {"bound": "hbm", "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                     "bytes": bytes_total, "launches": cnt, "note": note}
+
+    a_ms, a_cnt = ms_of("apply")
+    hbm_entry("apply", a_cnt * 4.0 * (N * rs + N * rt + 2 * N),
+              "reads U (N x r_s) and V (N x r_t), w; writes out; FP32")
+    m_ms, m_cnt = ms_of("domain")
+    hbm_entry("domain", m_cnt * 4.0 * 2 * N * d, "reads X and Y once (N x d each, FP32)")
+    t_ms, t_cnt = ms_of("mode_transform")
+    hbm_entry("mode_transform", steps * 4 * (16.0 + 8.0) * total,
+              "per step 4 passes over the FP64 grid (16 B per entry) and 4 over the FP32 grid (8 B)")
+    g_ms, g_cnt = ms_of("dgemm")
+    if g_cnt and g_ms > 0:
+        proj = 0.0
+        for k in range(1, D):
+            m = ranks[k - 1] * n
+            c = float(n) ** (D - k)
+            proj += 2.0 * ranks[k] * c * m
+        ach = steps * proj / (g_ms / 1000.0) / 1e12
+        out["dgemm"] = {"bound": "alu (FP64 FMA)", "achieved": ach, "peak": dfma, "unit": "TFLOP/s",
+                        "frac_lower_bound": ach / dfma, "launches": g_cnt,
+                        "note": "the TT-SVD projections' flops only: a lower bound of the DGEMM work"}
+    for name, why in (("householder", "work depends on the step at which each pivoted QR stops"),
+                      ("jacobi", "work depends on the number of sweeps"),
+                      ("theta_core", "latency-bound: a few small contractions per theta")):
+        if name in prof:
+            out[name] = {"frac": None, "note": why}
+    return out
+
+
 def rel_fro(A, B) -> float:
     """||A - B||_F / ||A||_F."""
     return float(np.linalg.norm(A - B) / np.linalg.norm(A))
@@ -390,6 +446,10 @@ def main():
                       "peak_note": "measured FP64 FMA rate (pttk_peak_probe DFMA, this run); executed flops per "
                                    "entry from ncu instruction counts on the n = 5 grid of the same workload "
                                    "(null once the kernel sources differ from the counted ones)"}
+    try:
+        roof_kernels = kernel_rooflines(prof, args.steps, ranks, w.d, w.dtheta, w.n, N, hbm, dfma)
+    except Exception as exc:  # a reporting helper must not cost the bench line
+        roof_kernels = {"error": repr(exc)}
     roof_dominant = {"kernel": dom[0], "ms_total": dom[1][0], "launches": dom[1][1],
                      "share_of_timed_kernel_time": dom[1][0] / max(prof_total, 1e-9),
                      "bound": "alu (FP64)" if dom[0] in ("jacobi", "householder", "dgemm", "grid_tile") else "tensor",
@@ -428,7 +488,7 @@ def main():
             "stage_ms_per_step": {k: tot(k) / args.steps for k in
                                   ("grid64_ms", "grid32_ms", "ttsvd_ms", "inst_ms", "apply_ms")},
             "roofline": roof, "roofline_dominant": roof_dominant, "roofline_grid": roof_grid,
-            "roofline_grid_fp64": roof_grid_fp64,
+            "roofline_grid_fp64": roof_grid_fp64, "roofline_kernels": roof_kernels,
             "peaks_measured": {"unit": "TFLOP/s", "how": "pttk_peak_probe loops, median of 3, before the timed region",
                                **pk},
             "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()},
