@@ -401,8 +401,10 @@ pttk_status pttk_tt_check(const pttk_tt* tt, void* stream);
  * Khatri-Rao chain; B_i[p, k] = T_k(phi^{-1}(x_{p,i})). K(X, Y; theta) ~= U M V^T.
  *   X: dev N_s x d, Y: dev N_t x d (double for PTTK_FP64, float otherwise); points must lie
  *   in their boxes (Section 1: X in B_s, Y in B_t), a point on a face is valid. One pass over
- *   X and Y checks it on the device; a point outside records PTTK_EDOMAIN in the handle's
- *   status word (reported by pttk_tt_check) and its factor row is an extrapolation.
+ *   X and Y checks it on the device; a coordinate outside its interval by more than 1e-12 of
+ *   the interval's width (FP32 points: of the FP32-rounded interval), or NaN, records
+ *   PTTK_EDOMAIN in the handle's status word (reported by pttk_tt_check), and that point's
+ *   factor row is an extrapolation.
  *   N_s, N_t >= 0 (0 is allowed and writes nothing for that side).
  *   U, M, V: dev outputs (double for PTTK_FP64, float otherwise).
  *   prec: PTTK_FP64 / PTTK_FP32 run the SIMT chain; PTTK_TF32, PTTK_TF32X3, PTTK_BF16,
